@@ -1,0 +1,183 @@
+/*
+ * adg.h -- C ABI of the GB300 asynchronous discontinuous Galerkin (ADG / ADG-AT) solver.
+ *
+ * The library advances 1D nodal DG discretisations of u_t + f(u)_x = 0 on a periodic
+ * interval with the fully discrete strong-stability-preserving RK3 step, on one GPU, in
+ * FP64. Elements are split into P contiguous "processing elements" (PEs); at PE faces the
+ * numerical flux uses data of a delayed time level taken from a seeded delay table and a
+ * device ring buffer, combined by the standard flux or the asynchrony-tolerant (AT) flux.
+ *
+ * Paper: "Asynchronous discontinuous Galerkin method" (arXiv 2404.03399):
+ *   - problem and discretisation: Section 2, Eqs. wave, DGsolution, DGweakform, DGscheme;
+ *   - PE decomposition and delays k in {0..L-1}: Section 3, Eq. asyncEulerDG;
+ *   - conservative common delayed level: Section 4.1, Eq. asyncEulerDGconserved;
+ *   - AT flux: Section 5, Eqs. at-flux-gen, at-flux-constraints, Table 1;
+ *   - delay emulation by binned uniform draws: Section 6.1.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns an adg_status; no C++ exception crosses the ABI. After a
+ *     failure adg_last_error(ctx) holds a message (for a NULL ctx: the thread's last one).
+ *   - Nodal fields passed across the ABI are FP64, contiguous, shape (K, p+1), row-major
+ *     (element-major: u[e*(p+1) + i] is node i of element e). Buffers marked "_dev" are
+ *     device pointers on the current CUDA device; "_host" are host pointers.
+ *   - The caller owns every buffer it passes; the library copies what it keeps and never
+ *     frees caller memory. The library owns its context (state, ring, tables, graphs),
+ *     released by adg_destroy.
+ *   - Work is ordered on the CUDA stream given at init (NULL = legacy default stream).
+ *     Functions that return host values synchronise that stream before returning.
+ *   - There is no CPU fallback: without a usable CUDA device adg_init returns ADG_ECUDA.
+ */
+#ifndef ADG_H
+#define ADG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct adg_ctx adg_ctx;
+
+typedef enum {
+  ADG_OK = 0,
+  ADG_EINVAL = -1,     /* invalid argument or configuration */
+  ADG_ENOMEM = -2,     /* device or host allocation failed */
+  ADG_ECUDA = -3,      /* CUDA runtime error (or no device) */
+  ADG_ENONFINITE = -4, /* a NaN or Inf was found in the state */
+  ADG_ETIMEOUT = -5,   /* a bounded device wait ran out */
+  ADG_ESTATE = -6      /* call not valid in the context's current state */
+} adg_status;
+
+enum { ADG_ADVECTION = 0, ADG_BURGERS = 1 };          /* f(u) = a u  |  f(u) = u^2/2 */
+enum { ADG_UPWIND = 0, ADG_LLF = 1 };                 /* Section 6.1 fluxes */
+enum { ADG_SSPRK3 = 3 };                               /* time integrator */
+enum { ADG_SYNC = 0, ADG_ASYNC = 1, ADG_ASYNC_AT = 2 };/* DG | ADG | ADG-AT */
+
+#define ADG_MAX_P 4        /* polynomial degree 1..4 (2..5 LGL nodes) */
+#define ADG_MAX_L 16       /* delays 0..L-1 with L <= 16 */
+#define ADG_MAX_Q 5        /* AT order 1..5 */
+
+/*
+ * Run configuration (Section 2: mesh, degree, flux, RK; Section 3: P and L; Section 5:
+ * AT order; Section 6.1: probability set and seeded draws).
+ *   pde, flux : ADG_ADVECTION with ADG_UPWIND, or ADG_BURGERS with ADG_LLF.
+ *   rk        : ADG_SSPRK3.
+ *   K, p, P   : elements, polynomial degree (1..ADG_MAX_P), PEs; K % P == 0, P >= 1.
+ *   x0, x1    : periodic domain [x0, x1], x1 > x0.
+ *   a         : advection speed (advection only).
+ *   cfl, dt   : if dt > 0 it is the fixed time step; else dt = (cfl * dx) / speed, with
+ *               dx = (x1 - x0) / K and speed = |a| (advection) or max|u0| (Burgers).
+ *   mode      : ADG_SYNC, ADG_ASYNC (standard flux at the delayed level) or ADG_ASYNC_AT.
+ *   L         : delays are in {0..L-1} (1 <= L <= ADG_MAX_L).
+ *   at_order  : AT order q (1..ADG_MAX_Q) for ADG_ASYNC_AT; 0 selects p+1 capped at
+ *               ADG_MAX_Q. ADG_ASYNC uses q = 1.
+ *   seed, probs: delays drawn from SplitMix64(seed) output n*P + j for step n, PE face j,
+ *               binned by probs[0..L-1] (NULL = uniform 1/L), Section 6.1.
+ *   delay_table, table_steps: optional caller table, uint8 [table_steps][P], host memory,
+ *               used periodically (row n mod table_steps at step n); overrides the seed.
+ *               Every entry must be < L.
+ */
+typedef struct {
+  int32_t pde;
+  int32_t flux;
+  int32_t rk;
+  int32_t K, p, P;
+  double x0, x1;
+  double a;
+  double cfl, dt;
+  int32_t mode;
+  int32_t L;
+  int32_t at_order;
+  uint64_t seed;
+  const double *probs;
+  const uint8_t *delay_table;
+  int64_t table_steps;
+} adg_config;
+
+/* Fill cfg with defaults: advection, upwind, SSP-RK3, [0, 2 pi], a = 1, cfl = 0.1, sync. */
+void adg_config_default(adg_config *cfg);
+
+/*
+ * Create a solver context for one instance and load the initial nodal field.
+ *   cfg     : configuration (copied; probs and delay_table are copied too).
+ *   u0_dev  : initial nodal values, device FP64 (K, p+1) row-major.
+ *   stream  : cudaStream_t (as void*), NULL for the default stream.
+ *   out     : receives the context; *out is NULL on failure.
+ * Errors: ADG_EINVAL (bad config, or a non-finite u0), ADG_ENOMEM, ADG_ECUDA.
+ */
+int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx **out);
+
+/*
+ * Create one context that advances n independent instances together (batched runs):
+ * every stage launch covers all instances; chunks of steps replay one CUDA graph.
+ * cfgs[i], u0_devs[i] as in adg_init. Only ADG_ADVECTION / ADG_UPWIND instances.
+ */
+int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t n,
+                   void *stream, adg_ctx **out);
+
+/* Advance every instance by nsteps >= 0 SSP-RK3 steps (Section 4.2.1 structure, Eq.
+ * EulerDG-style explicit updates; Eq. asyncEulerDGconserved at PE faces). Asynchronous:
+ * returns once the work is queued. */
+int adg_step(adg_ctx *c, int64_t nsteps);
+
+/* Advance to time t_end: ceil(t_end/dt - 1e-9) - (current step) steps (none if <= 0). */
+int adg_run(adg_ctx *c, double t_end);
+
+/* Copy instance `index` (0 for a single-instance context) to u_dev, device (K, p+1)
+ * row-major FP64, and its step counter to *step_out (may be NULL). Synchronises. */
+int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out);
+
+/* The fixed time step of instance `index`. */
+int adg_get_dt(adg_ctx *c, int32_t index, double *dt_out);
+
+/*
+ * Discrete gradient of the final-time L2 misfit
+ *     J = 1/2 sum_e (dx/2) (u_N^e - g^e)^T M (u_N^e - g^e)
+ * with respect to the initial nodal field, for a single-instance context, over nsteps
+ * steps starting from the current state (the state itself is left unchanged). The adjoint
+ * is hand-written: transposed stage operators, flux partial derivatives, and a reverse
+ * ring buffer over the delay table. Checkpoints every ckpt_every steps, recomputation in
+ * between. target_dev and grad_u0_dev are device (K, p+1) row-major FP64; J_out is host.
+ * The paper has no adjoint; this follows the discrete forward scheme exactly.
+ */
+int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_every,
+             double *grad_u0_dev, double *J_out);
+
+/* Discrete integral sum_e (dx/2) w^T u^e of instance `index` (Section 4.1 conservation
+ * check), into *out (host). Synchronises. */
+int adg_integral(adg_ctx *c, int32_t index, double *out);
+
+/* ADG_ENONFINITE if any instance holds a NaN or Inf, else ADG_OK. Synchronises. */
+int adg_check_finite(adg_ctx *c);
+
+/*
+ * Write the delay table the library uses for cfg (seeded or caller table) for steps
+ * first_step .. first_step+steps-1 into out_host (uint8 [steps][P]). Host only; needs no
+ * GPU. Errors: ADG_EINVAL.
+ */
+int adg_delay_table(const adg_config *cfg, int64_t first_step, int64_t steps,
+                    uint8_t *out_host);
+
+/*
+ * Nodal values of u0(x) = offset + sum_m amp[m] sin(kappa[m] x + phase[m]) (Eq.
+ * initialcond) at the library's LGL nodes for cfg's mesh, written to u_dev (device,
+ * (K, p+1) row-major FP64), ordered on `stream`.
+ */
+int adg_eval_modes(const adg_config *cfg, int32_t nmodes, const double *amp,
+                   const double *kappa, const double *phase, double offset, double *u_dev,
+                   void *stream);
+
+/* LGL nodes (p+1 values, host) of degree p, as the library rounds them to FP64. */
+int adg_lgl_nodes(int32_t p, double *nodes_host, double *weights_host);
+
+/* Message of the last failure on c (NULL: the calling thread's last failure). */
+const char *adg_last_error(const adg_ctx *c);
+
+/* Release the context and everything it owns. NULL is ignored. */
+void adg_destroy(adg_ctx *c);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ADG_H */

@@ -1,0 +1,765 @@
+// Host side of the C ABI declared in include/adg.h: configuration checks, reference-element
+// operators (built in long double, rounded once to FP64), delay and AT tables, device
+// buffers, the step driver (CUDA-graph replay of fixed chunks of steps) and reductions.
+#include "adg.h"
+#include "adg_internal.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <memory>
+#include <new>
+#include <string>
+#include <vector>
+
+using adg::Inst;
+using adg::kMaxNp;
+using adg::kStages;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+// ---------------------------------------------------------------------------------------
+// Reference-element operators (Section 2, Eq. matrices-reference), long double.
+// ---------------------------------------------------------------------------------------
+using ld = long double;
+
+// Legendre P_n(x) and P_n'(x) by the three-term recurrence.
+void legendre(int n, ld x, ld &P, ld &dP) {
+  ld p0 = 1, p1 = x;
+  if (n == 0) { P = 1; dP = 0; return; }
+  for (int k = 2; k <= n; ++k) {
+    ld p2 = ((2 * k - 1) * x * p1 - (k - 1) * p0) / k;
+    p0 = p1;
+    p1 = p2;
+  }
+  P = p1;
+  dP = (x * x == 1) ? 0.5L * n * (n + 1) * (x > 0 ? 1 : ((n % 2) ? 1 : -1))
+                    : n * (x * p1 - p0) / (x * x - 1);
+}
+
+// LGL nodes: +-1 and the roots of P_p'; Newton on q(x) = (1 - x^2) P_p'(x), whose
+// derivative is -p(p+1) P_p(x). Weights 2 / (p (p+1) P_p(x)^2).
+void lgl(int p, std::vector<ld> &x, std::vector<ld> &w) {
+  const int Np = p + 1;
+  x.assign(Np, 0);
+  w.assign(Np, 0);
+  const ld pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < Np; ++i) {
+    ld xi = -std::cos(pi * i / p);
+    if (i > 0 && i < p) {
+      for (int it = 0; it < 100; ++it) {
+        ld P, dP;
+        legendre(p, xi, P, dP);
+        const ld qv = (1 - xi * xi) * dP;
+        const ld dq = -(ld)p * (p + 1) * P;
+        const ld dx = qv / dq;
+        xi -= dx;
+        if (std::fabs(dx) < 1e-30L) break;
+      }
+    }
+    x[i] = xi;
+  }
+  for (int i = 0; i < Np; ++i) {  // symmetric set
+    const ld s = 0.5L * (x[i] - x[p - i]);
+    x[i] = s;
+  }
+  x[0] = -1;
+  x[p] = 1;
+  if (p % 2 == 0) x[p / 2] = 0;
+  for (int i = 0; i < Np; ++i) {
+    ld P, dP;
+    legendre(p, x[i], P, dP);
+    w[i] = 2.0L / ((ld)p * (p + 1) * P * P);
+  }
+}
+
+// Gauss-Legendre nodes/weights with n points (roots of P_n), for exact mass integrals.
+void gauss(int n, std::vector<ld> &x, std::vector<ld> &w) {
+  x.assign(n, 0);
+  w.assign(n, 0);
+  const ld pi = 3.141592653589793238462643383279502884L;
+  for (int i = 0; i < n; ++i) {
+    ld xi = -std::cos(pi * (i + 0.75L) / (n + 0.5L));
+    for (int it = 0; it < 100; ++it) {
+      ld P, dP;
+      legendre(n, xi, P, dP);
+      const ld dx = P / dP;
+      xi -= dx;
+      if (std::fabs(dx) < 1e-30L) break;
+    }
+    ld P, dP;
+    legendre(n, xi, P, dP);
+    x[i] = xi;
+    w[i] = 2.0L / ((1 - xi * xi) * dP * dP);
+  }
+}
+
+struct Ops {
+  int p = 0, Np = 0;
+  std::vector<ld> x, w, D, Minv;  // D[i*Np+j] = l_j'(x_i); Minv row-major
+  std::vector<ld> M;
+};
+
+// Lagrange basis value l_j(t) on nodes x.
+ld lagr(const std::vector<ld> &x, int j, ld t) {
+  ld v = 1;
+  for (size_t m = 0; m < x.size(); ++m)
+    if ((int)m != j) v *= (t - x[m]) / (x[j] - x[m]);
+  return v;
+}
+
+bool invert(std::vector<ld> A, int n, std::vector<ld> &inv) {
+  inv.assign(n * n, 0);
+  for (int i = 0; i < n; ++i) inv[i * n + i] = 1;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0) return false;
+    for (int k = 0; k < n; ++k) {
+      std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(inv[c * n + k], inv[piv * n + k]);
+    }
+    const ld d = A[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[c * n + k] /= d;
+      inv[c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const ld f = A[r * n + c];
+      if (f == 0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[r * n + k] -= f * A[c * n + k];
+        inv[r * n + k] -= f * inv[c * n + k];
+      }
+    }
+  }
+  return true;
+}
+
+Ops make_ops(int p) {
+  Ops o;
+  o.p = p;
+  o.Np = p + 1;
+  const int Np = o.Np;
+  lgl(p, o.x, o.w);
+  // Barycentric differentiation: D_ij = (b_j / b_i) / (x_i - x_j), D_ii = -sum_{j!=i} D_ij.
+  std::vector<ld> b(Np, 1);
+  for (int j = 0; j < Np; ++j)
+    for (int m = 0; m < Np; ++m)
+      if (m != j) b[j] /= (o.x[j] - o.x[m]);
+  o.D.assign(Np * Np, 0);
+  for (int i = 0; i < Np; ++i) {
+    ld s = 0;
+    for (int j = 0; j < Np; ++j) {
+      if (i == j) continue;
+      o.D[i * Np + j] = (b[j] / b[i]) / (o.x[i] - o.x[j]);
+      s += o.D[i * Np + j];
+    }
+    o.D[i * Np + i] = -s;
+  }
+  std::vector<ld> gx, gw;
+  gauss(p + 2, gx, gw);
+  o.M.assign(Np * Np, 0);
+  for (int i = 0; i < Np; ++i)
+    for (int j = 0; j < Np; ++j) {
+      ld s = 0;
+      for (size_t q = 0; q < gx.size(); ++q) s += gw[q] * lagr(o.x, i, gx[q]) * lagr(o.x, j, gx[q]);
+      o.M[i * Np + j] = s;
+    }
+  invert(o.M, Np, o.Minv);
+  return o;
+}
+
+// AT coefficients c_i(k; q) = prod_{m != i, 0 <= m < q} (k + m) / (m - i): Lagrange
+// extrapolation to level n from levels n-k, ..., n-k-q+1, which solves Eq.
+// at-flux-constraints (Table 1 for q = 2, 3, 4).
+double at_coef(int k, int q, int i) {
+  ld num = 1, den = 1;
+  for (int m = 0; m < q; ++m) {
+    if (m == i) continue;
+    num *= (ld)(k + m);
+    den *= (ld)(m - i);
+  }
+  return (double)(num / den);
+}
+
+// SplitMix64 output `idx` for `seed` (Steele, Lea and Flood 2014), mapped to [0, 1).
+inline double splitmix_uniform(uint64_t seed, uint64_t idx) {
+  uint64_t z = seed + (idx + 1) * 0x9E3779B97F4A7C15ULL;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+  z ^= z >> 31;
+  return (double)(z >> 11) * 0x1.0p-53;
+}
+
+struct DelaySource {
+  int P = 1, L = 1;
+  uint64_t seed = 0;
+  std::vector<double> edges;          // upper bin edges, summed left to right
+  std::vector<uint8_t> caller;        // caller table (periodic) or empty
+  int64_t caller_rows = 0;
+
+  void rows(int64_t first, int64_t count, uint8_t *out) const {
+    for (int64_t r = 0; r < count; ++r) {
+      const int64_t n = first + r;
+      if (!caller.empty()) {
+        const int64_t cr = n % caller_rows;
+        std::memcpy(out + r * P, caller.data() + cr * P, P);
+        continue;
+      }
+      for (int j = 0; j < P; ++j) {
+        const double u = splitmix_uniform(seed, (uint64_t)n * (uint64_t)P + (uint64_t)j);
+        int k = L - 1;
+        for (int b = 0; b < L; ++b)
+          if (u < edges[b]) { k = b; break; }
+        out[r * P + j] = (uint8_t)k;
+      }
+    }
+  }
+};
+
+std::string check_config(const adg_config *c) {
+  if (!c) return "cfg is NULL";
+  if (c->pde != ADG_ADVECTION && c->pde != ADG_BURGERS) return "pde must be ADG_ADVECTION or ADG_BURGERS";
+  if (c->pde == ADG_ADVECTION && c->flux != ADG_UPWIND) return "advection uses flux ADG_UPWIND";
+  if (c->pde == ADG_BURGERS && c->flux != ADG_LLF) return "Burgers uses flux ADG_LLF";
+  if (c->rk != ADG_SSPRK3) return "rk must be ADG_SSPRK3";
+  if (c->p < 1 || c->p > ADG_MAX_P) return "p must be in 1..4";
+  if (c->K < 1 || c->K > (1 << 30)) return "K must be in 1..2^30";
+  if (c->P < 1 || c->K % c->P != 0) return "P must be >= 1 and divide K";
+  if (!std::isfinite(c->x0) || !std::isfinite(c->x1) || !(c->x1 > c->x0)) return "need finite x0 < x1";
+  if (c->pde == ADG_ADVECTION && (!std::isfinite(c->a) || c->a == 0.0)) return "advection speed a must be finite and nonzero";
+  if (!std::isfinite(c->dt) || c->dt < 0) return "dt must be finite and >= 0";
+  if (c->dt == 0 && !(std::isfinite(c->cfl) && c->cfl > 0)) return "cfl must be > 0 when dt == 0";
+  if (c->mode != ADG_SYNC && c->mode != ADG_ASYNC && c->mode != ADG_ASYNC_AT) return "bad mode";
+  if (c->L < 1 || c->L > ADG_MAX_L) return "L must be in 1..16";
+  if (c->at_order < 0 || c->at_order > ADG_MAX_Q) return "at_order must be in 0..5";
+  if (c->probs) {
+    double s = 0;
+    for (int k = 0; k < c->L; ++k) {
+      if (!std::isfinite(c->probs[k]) || c->probs[k] < 0) return "probs must be finite and >= 0";
+      s += c->probs[k];
+    }
+    if (std::fabs(s - 1.0) > 1e-9) return "probs must sum to 1";
+  }
+  if (c->delay_table) {
+    if (c->table_steps < 1) return "table_steps must be >= 1 with a delay_table";
+    const int64_t n = c->table_steps * (int64_t)c->P;
+    for (int64_t t = 0; t < n; ++t)
+      if (c->delay_table[t] >= c->L) return "delay_table entries must be < L";
+  }
+  return "";
+}
+
+DelaySource make_delay_source(const adg_config *c) {
+  DelaySource d;
+  d.P = c->P;
+  d.L = c->L;
+  d.seed = c->seed;
+  double s = 0;
+  for (int k = 0; k < c->L; ++k) {
+    s = s + (c->probs ? c->probs[k] : 1.0 / c->L);
+    d.edges.push_back(s);
+  }
+  if (c->delay_table) {
+    d.caller.assign(c->delay_table, c->delay_table + c->table_steps * (int64_t)c->P);
+    d.caller_rows = c->table_steps;
+  }
+  return d;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------------------
+struct InstHost {
+  adg_config cfg{};
+  std::vector<double> probs;
+  DelaySource delays;
+  Ops ops;
+  Inst I{};
+  double dx = 0, dt = 0;
+  int q_eff = 1;
+  int64_t tbase = 0;
+  int TR = 0;
+  // device memory owned by this instance
+  double *fields = nullptr;  // u | v1 | v2
+  double2 *ring = nullptr;
+  uint8_t *table = nullptr;
+  double *coef = nullptr;
+  double *w = nullptr, *M = nullptr;
+  std::vector<uint8_t> host_rows;
+};
+
+struct adg_ctx {
+  std::string err;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap = nullptr;
+  int device = 0;
+  std::vector<InstHost> inst;
+  bool batch = false;
+  int64_t *meta = nullptr;      // [ninst][2]
+  Inst *insts_dev = nullptr;
+  int2 *work_dev = nullptr;
+  int nwork = 0;
+  double *partials = nullptr, *red_out = nullptr;
+  double *pinned = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  int G = 32;
+  int64_t n = 0;
+};
+
+namespace {
+
+int fail(adg_ctx *c, int code, const std::string &msg) {
+  if (c) c->err = msg;
+  g_last_error = msg;
+  return code;
+}
+
+#define CK(call)                                                                          \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail(c, e_ == cudaErrorMemoryAllocation ? ADG_ENOMEM : ADG_ECUDA,            \
+                  std::string(#call) + ": " + cudaGetErrorString(e_));                    \
+  } while (0)
+
+void fold_constants(InstHost &h) {
+  const Ops &o = h.ops;
+  const int Np = o.Np;
+  const ld c2 = -2.0L * (ld)h.dt / (ld)h.dx;
+  const ld cf = h.cfg.pde == ADG_ADVECTION ? (ld)h.cfg.a : 0.5L;
+  const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
+  const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
+  for (int s = 0; s < kStages; ++s) {
+    adg::StageConsts &C = h.I.sc[s];
+    std::memset(&C, 0, sizeof(C));
+    C.alpha = (double)alpha[s];
+    C.beta = (double)beta[s];
+    for (int i = 0; i < Np; ++i) {
+      for (int j = 0; j < Np; ++j) C.Dm[i * Np + j] = (double)(beta[s] * c2 * cf * o.D[i * Np + j]);
+      C.liftL[i] = (double)(beta[s] * c2 * o.Minv[i * Np + 0]);
+      C.liftR[i] = (double)(-beta[s] * c2 * o.Minv[i * Np + (Np - 1)]);
+    }
+  }
+}
+
+int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out) {
+  const int nb = adg::reduce_blocks(h.I.K);
+  const double *wm = kind == 3 ? h.M : h.w;
+  CK(adg::launch_reduce(kind, h.I.u, g, h.I.K, h.I.Np, wm, scale, c->partials, nb, c->red_out,
+                        c->stream));
+  CK(cudaMemcpyAsync(c->pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  *host_out = c->pinned[0];
+  return ADG_OK;
+}
+
+// Make the device delay table of h cover steps [n, n+count).
+int ensure_table(adg_ctx *c, InstHost &h, int64_t n, int64_t count) {
+  if (!h.I.async) return ADG_OK;
+  if (n >= h.tbase && n + count <= h.tbase + h.TR) return ADG_OK;
+  h.tbase = n;
+  h.host_rows.resize((size_t)h.TR * h.I.P);
+  h.delays.rows(n, h.TR, h.host_rows.data());
+  CK(cudaMemcpyAsync(h.table, h.host_rows.data(), h.host_rows.size(), cudaMemcpyHostToDevice,
+                     c->stream));
+  int64_t tb = n;
+  CK(cudaMemcpyAsync((void *)(h.I.meta + 1), &tb, sizeof(int64_t), cudaMemcpyHostToDevice,
+                     c->stream));
+  return ADG_OK;
+}
+
+int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double *u0_dev,
+                   int64_t *meta_slot) {
+  h.cfg = *cfg;
+  if (cfg->probs) {
+    h.probs.assign(cfg->probs, cfg->probs + cfg->L);
+    h.cfg.probs = h.probs.data();
+  }
+  h.delays = make_delay_source(cfg);
+  h.cfg.delay_table = nullptr;  // the DelaySource keeps the copy
+  h.ops = make_ops(cfg->p);
+  const int K = cfg->K, Np = cfg->p + 1;
+  h.dx = (cfg->x1 - cfg->x0) / K;
+  Inst &I = h.I;
+  I.K = K;
+  I.Np = Np;
+  I.P = cfg->P;
+  I.Kpe = K / cfg->P;
+  I.pde = cfg->pde;
+  I.a = cfg->pde == ADG_ADVECTION ? cfg->a : 0.0;
+  I.async = (cfg->mode != ADG_SYNC && cfg->P > 1) ? 1 : 0;
+  h.q_eff = cfg->mode == ADG_ASYNC_AT ? (cfg->at_order > 0 ? cfg->at_order : std::min(cfg->p + 1, ADG_MAX_Q)) : 1;
+  I.q = h.q_eff;
+  I.L = cfg->L;
+  I.R = (cfg->L - 1) + h.q_eff;
+  I.meta = meta_slot;
+
+  const size_t nd = (size_t)K * Np;
+  CK(cudaMalloc(&h.fields, 3 * nd * sizeof(double)));
+  I.u = h.fields;
+  I.v1 = h.fields + nd;
+  I.v2 = h.fields + 2 * nd;
+  CK(adg::launch_to_internal(u0_dev, I.u, K, Np, c->stream));
+  CK(cudaMemsetAsync(I.v1, 0, 2 * nd * sizeof(double), c->stream));
+
+  // weights and mass matrix for reductions
+  std::vector<double> wd(Np), Md(Np * Np);
+  for (int i = 0; i < Np; ++i) wd[i] = (double)h.ops.w[i];
+  for (int i = 0; i < Np * Np; ++i) Md[i] = (double)h.ops.M[i];
+  CK(cudaMalloc(&h.w, Np * sizeof(double)));
+  CK(cudaMalloc(&h.M, Np * Np * sizeof(double)));
+  CK(cudaMemcpyAsync(h.w, wd.data(), Np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaMemcpyAsync(h.M, Md.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+
+  double nonfinite = 0;
+  int r = reduce(c, h, 2, nullptr, 1.0, &nonfinite);
+  if (r) return r;
+  if (nonfinite != 0) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
+
+  if (cfg->dt > 0) {
+    h.dt = cfg->dt;
+  } else {
+    double speed = std::fabs(cfg->a);
+    if (cfg->pde == ADG_BURGERS) {
+      r = reduce(c, h, 1, nullptr, 1.0, &speed);
+      if (r) return r;
+      if (!(speed > 0)) return fail(c, ADG_EINVAL, "Burgers needs max|u0| > 0 to set dt from cfl");
+    }
+    h.dt = (cfg->cfl * h.dx) / speed;
+  }
+  fold_constants(h);
+
+  if (I.async) {
+    const int q = h.q_eff, L = cfg->L;
+    std::vector<double> coef((size_t)L * q * q, 0.0);
+    for (int k = 0; k < L; ++k)
+      for (int qe = 1; qe <= q; ++qe)
+        for (int i = 0; i < qe; ++i) coef[((size_t)k * q + (qe - 1)) * q + i] = at_coef(k, qe, i);
+    CK(cudaMalloc(&h.coef, coef.size() * sizeof(double)));
+    CK(cudaMemcpy(h.coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice));
+    I.coef = h.coef;
+    const size_t ring_n = (size_t)I.R * kStages * I.P;
+    CK(cudaMalloc(&h.ring, ring_n * sizeof(double2)));
+    CK(cudaMemsetAsync(h.ring, 0, ring_n * sizeof(double2), c->stream));
+    I.ring = h.ring;
+    h.TR = std::max(512, 2 * c->G);
+    CK(cudaMalloc(&h.table, (size_t)h.TR * I.P));
+    I.table = h.table;
+    I.table_rows = h.TR;
+    h.tbase = -(int64_t)1 << 40;   // force a fill
+  }
+  return ADG_OK;
+}
+
+int launch_steps(adg_ctx *c, int nsteps) {
+  for (int rel = 0; rel < nsteps; ++rel) {
+    for (int s = 0; s < kStages; ++s) {
+      if (c->batch) {
+        CK(adg::launch_batch_stage(c->insts_dev, c->work_dev, c->nwork, s, rel, adg::kTile, c->stream));
+      } else {
+        CK(adg::launch_stage(c->inst[0].I, s, rel, c->stream));
+      }
+    }
+  }
+  CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
+  return ADG_OK;
+}
+
+int build_graph(adg_ctx *c) {
+  cudaStream_t user = c->stream;
+  c->stream = c->cap;
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    c->stream = user;
+    return fail(c, ADG_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  }
+  int r = launch_steps(c, c->G);
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
+  c->stream = user;
+  if (r) {
+    if (g) cudaGraphDestroy(g);
+    return r;
+  }
+  if (e2 != cudaSuccess) return fail(c, ADG_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    c->gexec = nullptr;
+    return fail(c, ADG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  return ADG_OK;
+}
+
+int finish_init(adg_ctx *c) {
+  CK(cudaMalloc(&c->partials, 1024 * sizeof(double)));
+  CK(cudaMalloc(&c->red_out, sizeof(double)));
+  CK(cudaMallocHost(&c->pinned, 8 * sizeof(double)));
+  return ADG_OK;
+}
+
+int begin_ctx(adg_ctx *c, void *stream) {
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess || ndev < 1)
+    return fail(c, ADG_ECUDA, std::string("no CUDA device: ") + cudaGetErrorString(e));
+  CK(cudaGetDevice(&c->device));
+  c->stream = (cudaStream_t)stream;
+  CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
+  return finish_init(c);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------------------
+extern "C" {
+
+void adg_config_default(adg_config *cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof(*cfg));
+  cfg->pde = ADG_ADVECTION;
+  cfg->flux = ADG_UPWIND;
+  cfg->rk = ADG_SSPRK3;
+  cfg->K = 64;
+  cfg->p = 2;
+  cfg->P = 1;
+  cfg->x0 = 0.0;
+  cfg->x1 = 6.283185307179586;
+  cfg->a = 1.0;
+  cfg->cfl = 0.1;
+  cfg->mode = ADG_SYNC;
+  cfg->L = 1;
+}
+
+const char *adg_last_error(const adg_ctx *c) {
+  return c ? c->err.c_str() : g_last_error.c_str();
+}
+
+void adg_destroy(adg_ctx *c) {
+  if (!c) return;
+  cudaStreamSynchronize(c->stream);
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto &h : c->inst) {
+    cudaFree(h.fields);
+    cudaFree(h.ring);
+    cudaFree(h.table);
+    cudaFree(h.coef);
+    cudaFree(h.w);
+    cudaFree(h.M);
+  }
+  cudaFree(c->meta);
+  cudaFree(c->insts_dev);
+  cudaFree(c->work_dev);
+  cudaFree(c->partials);
+  cudaFree(c->red_out);
+  if (c->pinned) cudaFreeHost(c->pinned);
+  if (c->cap) cudaStreamDestroy(c->cap);
+  delete c;
+}
+
+int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx **out) {
+  if (!out) return fail(nullptr, ADG_EINVAL, "out is NULL");
+  *out = nullptr;
+  std::string bad = check_config(cfg);
+  if (!bad.empty()) return fail(nullptr, ADG_EINVAL, bad);
+  if (!u0_dev) return fail(nullptr, ADG_EINVAL, "u0_dev is NULL");
+  adg_ctx *c = new (std::nothrow) adg_ctx();
+  if (!c) return fail(nullptr, ADG_ENOMEM, "host allocation failed");
+  int r = begin_ctx(c, stream);
+  if (!r) {
+    if (cudaMalloc(&c->meta, 2 * sizeof(int64_t)) != cudaSuccess)
+      r = fail(c, ADG_ENOMEM, "cudaMalloc(meta)");
+    else if (cudaMemsetAsync(c->meta, 0, 2 * sizeof(int64_t), c->stream) != cudaSuccess)
+      r = fail(c, ADG_ECUDA, "cudaMemsetAsync(meta)");
+  }
+  if (!r) {
+    c->inst.resize(1);
+    r = setup_instance(c, c->inst[0], cfg, u0_dev, c->meta);
+  }
+  if (!r) {
+    cudaError_t e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) r = fail(c, ADG_ECUDA, cudaGetErrorString(e));
+  }
+  if (r) {
+    g_last_error = c->err;
+    adg_destroy(c);
+    return r;
+  }
+  *out = c;
+  return ADG_OK;
+}
+
+int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t n, void *stream,
+                   adg_ctx **out) {
+  if (!out) return fail(nullptr, ADG_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (!cfgs || !u0_devs || n < 1) return fail(nullptr, ADG_EINVAL, "need n >= 1 configs and fields");
+  for (int i = 0; i < n; ++i) {
+    std::string bad = check_config(&cfgs[i]);
+    if (!bad.empty()) return fail(nullptr, ADG_EINVAL, "instance " + std::to_string(i) + ": " + bad);
+    if (cfgs[i].pde != ADG_ADVECTION) return fail(nullptr, ADG_EINVAL, "batched runs take advection instances");
+    if (!u0_devs[i]) return fail(nullptr, ADG_EINVAL, "u0_devs[i] is NULL");
+  }
+  adg_ctx *c = new (std::nothrow) adg_ctx();
+  if (!c) return fail(nullptr, ADG_ENOMEM, "host allocation failed");
+  c->batch = true;
+  int r = begin_ctx(c, stream);
+  if (!r) {
+    cudaError_t e = cudaMalloc(&c->meta, 2 * sizeof(int64_t) * n);
+    if (e != cudaSuccess) r = fail(c, ADG_ENOMEM, "cudaMalloc(meta)");
+    else if (cudaMemsetAsync(c->meta, 0, 2 * sizeof(int64_t) * n, c->stream) != cudaSuccess)
+      r = fail(c, ADG_ECUDA, "cudaMemsetAsync(meta)");
+  }
+  if (!r) {
+    c->inst.resize(n);
+    for (int i = 0; i < n && !r; ++i) r = setup_instance(c, c->inst[i], &cfgs[i], u0_devs[i], c->meta + 2 * i);
+  }
+  if (!r) {
+    std::vector<Inst> hi(n);
+    std::vector<int2> work;
+    for (int i = 0; i < n; ++i) {
+      hi[i] = c->inst[i].I;
+      for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));
+    }
+    c->nwork = (int)work.size();
+    if (cudaMalloc(&c->insts_dev, sizeof(Inst) * n) != cudaSuccess ||
+        cudaMalloc(&c->work_dev, sizeof(int2) * work.size()) != cudaSuccess)
+      r = fail(c, ADG_ENOMEM, "cudaMalloc(batch descriptors)");
+    else if (cudaMemcpy(c->insts_dev, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(c->work_dev, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+      r = fail(c, ADG_ECUDA, "cudaMemcpy(batch descriptors)");
+  }
+  if (!r && cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(c, ADG_ECUDA, "sync");
+  if (r) {
+    g_last_error = c->err;
+    adg_destroy(c);
+    return r;
+  }
+  *out = c;
+  return ADG_OK;
+}
+
+int adg_step(adg_ctx *c, int64_t nsteps) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (nsteps < 0) return fail(c, ADG_EINVAL, "nsteps must be >= 0");
+  int64_t left = nsteps;
+  while (left > 0) {
+    const int chunk = (int)std::min<int64_t>(left, c->G);
+    for (auto &h : c->inst) {
+      int r = ensure_table(c, h, c->n, chunk);
+      if (r) return r;
+    }
+    if (chunk == c->G) {
+      if (!c->gexec) {
+        int r = build_graph(c);
+        if (r) return r;
+      }
+      CK(cudaGraphLaunch(c->gexec, c->stream));
+    } else {
+      int r = launch_steps(c, chunk);
+      if (r) return r;
+    }
+    c->n += chunk;
+    left -= chunk;
+  }
+  return ADG_OK;
+}
+
+int adg_run(adg_ctx *c, double t_end) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (!std::isfinite(t_end)) return fail(c, ADG_EINVAL, "t_end must be finite");
+  const double dt = c->inst[0].dt;
+  const int64_t target = (int64_t)std::ceil(t_end / dt - 1e-9);
+  return target > c->n ? adg_step(c, target - c->n) : ADG_OK;
+}
+
+int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size()) return fail(c, ADG_EINVAL, "bad instance index");
+  if (!u_dev) return fail(c, ADG_EINVAL, "u_dev is NULL");
+  InstHost &h = c->inst[index];
+  CK(adg::launch_to_external(h.I.u, u_dev, h.I.K, h.I.Np, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (step_out) *step_out = c->n;
+  return ADG_OK;
+}
+
+int adg_get_dt(adg_ctx *c, int32_t index, double *dt_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size() || !dt_out) return fail(c, ADG_EINVAL, "bad argument");
+  *dt_out = c->inst[index].dt;
+  return ADG_OK;
+}
+
+int adg_integral(adg_ctx *c, int32_t index, double *out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size() || !out) return fail(c, ADG_EINVAL, "bad argument");
+  InstHost &h = c->inst[index];
+  return reduce(c, h, 0, nullptr, h.dx / 2.0, out);
+}
+
+int adg_check_finite(adg_ctx *c) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  for (size_t i = 0; i < c->inst.size(); ++i) {
+    double cnt = 0;
+    int r = reduce(c, c->inst[i], 2, nullptr, 1.0, &cnt);
+    if (r) return r;
+    if (cnt != 0) return fail(c, ADG_ENONFINITE, "instance " + std::to_string(i) + " holds NaN or Inf");
+  }
+  return ADG_OK;
+}
+
+int adg_delay_table(const adg_config *cfg, int64_t first_step, int64_t steps, uint8_t *out_host) {
+  std::string bad = check_config(cfg);
+  if (!bad.empty()) return fail(nullptr, ADG_EINVAL, bad);
+  if (first_step < 0 || steps < 0 || (steps > 0 && !out_host)) return fail(nullptr, ADG_EINVAL, "bad range or NULL output");
+  make_delay_source(cfg).rows(first_step, steps, out_host);
+  return ADG_OK;
+}
+
+int adg_eval_modes(const adg_config *cfg, int32_t nmodes, const double *amp, const double *kappa,
+                   const double *phase, double offset, double *u_dev, void *stream) {
+  std::string bad = check_config(cfg);
+  if (!bad.empty()) return fail(nullptr, ADG_EINVAL, bad);
+  if (nmodes < 0 || nmodes > 16) return fail(nullptr, ADG_EINVAL, "nmodes must be in 0..16");
+  if (nmodes > 0 && (!amp || !kappa || !phase)) return fail(nullptr, ADG_EINVAL, "NULL mode arrays");
+  if (!u_dev) return fail(nullptr, ADG_EINVAL, "u_dev is NULL");
+  Ops o = make_ops(cfg->p);
+  double xi[kMaxNp];
+  for (int i = 0; i <= cfg->p; ++i) xi[i] = (double)o.x[i];
+  const double dx = (cfg->x1 - cfg->x0) / cfg->K;
+  cudaError_t e = adg::launch_eval_modes(u_dev, cfg->K, cfg->p + 1, cfg->x0, dx, xi, nmodes, amp,
+                                         kappa, phase, offset, (cudaStream_t)stream);
+  if (e != cudaSuccess) return fail(nullptr, ADG_ECUDA, std::string("eval_modes: ") + cudaGetErrorString(e));
+  return ADG_OK;
+}
+
+int adg_lgl_nodes(int32_t p, double *nodes_host, double *weights_host) {
+  if (p < 1 || p > ADG_MAX_P) return fail(nullptr, ADG_EINVAL, "p must be in 1..4");
+  Ops o = make_ops(p);
+  for (int i = 0; i <= p; ++i) {
+    if (nodes_host) nodes_host[i] = (double)o.x[i];
+    if (weights_host) weights_host[i] = (double)o.w[i];
+  }
+  return ADG_OK;
+}
+
+int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_every,
+             double *grad_u0_dev, double *J_out) {
+  (void)target_dev; (void)nsteps; (void)ckpt_every; (void)grad_u0_dev; (void)J_out;
+  return fail(c, ADG_ESTATE, "adg_grad: not available in this build");
+}
+
+}  // extern "C"

@@ -1,0 +1,66 @@
+// Internal types shared by the host library (adg_api.cu) and the kernels (adg_kernels.cu).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace adg {
+
+constexpr int kMaxNp = 5;
+constexpr int kMaxL = 16;
+constexpr int kMaxQ = 5;
+constexpr int kStages = 3;
+constexpr int kTile = 256;      // elements (threads) per block
+
+// Folded constants of one SSP-RK3 stage (Shu-Osher form)
+//   out_i = alpha u_i + beta v_i + sum_j Dm_ij g_j + liftL_i jL + liftR_i jR,
+// where g = v (advection, a folded into Dm) or v*v (Burgers, 1/2 folded into Dm),
+// jL = f(v_0) - F_L, jR = f(v_p) - F_R, and
+//   Dm = beta (-2 dt/dx) c D,  liftL = beta (-2 dt/dx) LIFT_L,  liftR = beta (2 dt/dx) LIFT_R
+// with c = a (advection) or 1/2 (Burgers): the strong form of Eq. DGscheme,
+// dt L(v) = -(2 dt/dx) [ D f + LIFT_L (f_0 - F_L) - LIFT_R (f_p - F_R) ].
+struct StageConsts {
+  double Dm[kMaxNp * kMaxNp];
+  double liftL[kMaxNp];
+  double liftR[kMaxNp];
+  double alpha, beta;
+};
+
+// One DG instance as the kernels see it. Nodal fields are node-major: field[i*K + e].
+struct alignas(16) Inst {
+  double *u;            // u^n, updated in place by stage 3
+  double *v1, *v2;      // stage outputs 1 and 2
+  double2 *ring;        // [R][3][P] traces (u^-, u^+) of stage inputs at PE faces
+  const uint8_t *table; // [table_rows][P] delays
+  const int64_t *meta;  // meta[0] = step index of rel 0; meta[1] = first table row's step
+  const double *coef;   // AT coefficients [L][q][q]: coef[(k*q + (q'-1))*q + i]
+  double a;
+  int K, Np, P, Kpe, R, L, q, pde, async, table_rows;
+  StageConsts sc[kStages];
+};
+
+static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
+
+// Launchers (adg_kernels.cu). All return cudaGetLastError() after the launch.
+cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
+cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                               int stage, int rel, int tile, cudaStream_t s);
+cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t by,
+                           cudaStream_t s);
+cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,
+                               int Np, cudaStream_t s);
+cudaError_t launch_to_external(const double *src_nodemajor, double *dst_rowmajor, int K,
+                               int Np, cudaStream_t s);
+cudaError_t launch_eval_modes(double *u_rowmajor, int K, int Np, double x0, double dx,
+                              const double *xi, int nmodes, const double *amp,
+                              const double *kappa, const double *phase, double offset,
+                              cudaStream_t s);
+// Reductions: partial sums per block then one block sums the partials in a fixed order.
+// kind 0: sum_e w^T u^e * scale; 1: max |u|; 2: count of non-finite values;
+// 3: misfit sum_e (u-g)^T M (u-g) * scale (M given row-major Np x Np in w_or_M).
+cudaError_t launch_reduce(int kind, const double *u, const double *g, int K, int Np,
+                          const double *w_or_M, double scale, double *partials,
+                          int nblocks, double *out, cudaStream_t s);
+int reduce_blocks(int K);
+
+}  // namespace adg

@@ -1,0 +1,376 @@
+// FP64 CUDA kernels of the ADG / ADG-AT SSP-RK3 step for sm_103a.
+//
+// One thread per element, node-major layout (field[i*K + e]) so that every load and
+// store of a nodal plane is a coalesced 256-byte warp access. Face traces of the
+// neighbours come from warp shuffles (one global load per warp edge). The element
+// right-hand side (strong form of Eq. DGscheme), the Shu-Osher SSP-RK3 stage combine and,
+// at PE faces, the delayed / AT flux (Eqs. asyncEulerDGconserved, at-flux-gen) with the
+// ring-buffer write of the stage-input traces are fused into one kernel per stage.
+#include "adg_internal.h"
+
+#include <cstdio>
+
+namespace adg {
+
+namespace {
+
+// Physical flux f(u): a u (advection) or u^2/2 (Burgers). Explicit round-to-nearest
+// intrinsics keep every evaluation of a face flux bit-identical wherever it is computed.
+template <int PDE>
+__device__ __forceinline__ double phys_flux(double a, double u) {
+  if (PDE == 0) return __dmul_rn(a, u);
+  return __dmul_rn(0.5, __dmul_rn(u, u));
+}
+
+// Numerical flux (Section 6.1): upwind a u^- (a >= 0) or a u^+ (a < 0); local
+// Lax-Friedrichs 1/2 (f(u^-) + f(u^+)) - 1/2 max(|u^-|, |u^+|) (u^+ - u^-) for Burgers.
+template <int PDE>
+__device__ __forceinline__ double num_flux(double a, double uL, double uR) {
+  if (PDE == 0) return __dmul_rn(a, a >= 0.0 ? uL : uR);
+  const double lam = fmax(fabs(uL), fabs(uR));
+  const double avg = __dmul_rn(0.5, __dadd_rn(phys_flux<1>(a, uL), phys_flux<1>(a, uR)));
+  return __dsub_rn(avg, __dmul_rn(__dmul_rn(0.5, lam), __dsub_rn(uR, uL)));
+}
+
+__device__ __forceinline__ int64_t ring_slot(int64_t level, int R) { return level % R; }
+
+// Flux at PE face j for step n, stage s (Eqs. asyncEulerDGconserved and at-flux-gen):
+// delay k = min(D[n][j], n), order q' = min(q, n-k+1),
+// F = sum_{i<q'} c_i(k; q') fhat(T_{n-k-i, s, j}); level n (k = 0) uses the current
+// traces (tl, tr). The owner (the element right of the face) stores T_{n,s,j}.
+template <int PDE, class I>
+__device__ __forceinline__ double pe_flux(const I &inst, int j, int64_t n, int s, double tl,
+                                          double tr, bool owner) {
+  const int P = inst.P;
+  const int R = inst.R;
+  const int q = inst.q;
+  const int64_t row = n - inst.meta[1];
+  int64_t k = inst.table[row * P + j];
+  if (k > n) k = n;
+  const int64_t qe64 = n - k + 1 < q ? n - k + 1 : q;
+  const int qe = (int)qe64;
+  const double *c = inst.coef + ((size_t)k * q + (qe - 1)) * q;
+  double F;
+  if (k == 0) {
+    F = __dmul_rn(c[0], num_flux<PDE>(inst.a, tl, tr));
+  } else {
+    const double2 T = inst.ring[(ring_slot(n - k, R) * kStages + s) * P + j];
+    F = __dmul_rn(c[0], num_flux<PDE>(inst.a, T.x, T.y));
+  }
+  for (int i = 1; i < qe; ++i) {
+    const double ci = c[i];
+    if (ci != 0.0) {
+      const double2 T = inst.ring[(ring_slot(n - k - i, R) * kStages + s) * P + j];
+      F = __dadd_rn(F, __dmul_rn(ci, num_flux<PDE>(inst.a, T.x, T.y)));
+    }
+  }
+  if (owner) inst.ring[(ring_slot(n, R) * kStages + s) * P + j] = make_double2(tl, tr);
+  return F;
+}
+
+// One SSP-RK3 stage for element e (all 32 lanes of the warp take part; lanes past the
+// end duplicate element K-1 and store nothing).
+template <int NP, int PDE, int STAGE, bool ASYNC, class I>
+__device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n) {
+  const int K = inst.K;
+  const int lane = threadIdx.x & 31;
+  const int ec = e < K ? e : K - 1;
+  const double *vin = STAGE == 0 ? inst.u : (STAGE == 1 ? inst.v1 : inst.v2);
+  double *vout = STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.u);
+
+  double v[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) v[i] = __ldg(vin + (size_t)i * K + ec);
+
+  const unsigned full = 0xffffffffu;
+  double vLm = __shfl_up_sync(full, v[NP - 1], 1);
+  if (lane == 0) vLm = __ldg(vin + (size_t)(NP - 1) * K + (ec == 0 ? K - 1 : ec - 1));
+  double vRp = __shfl_down_sync(full, v[0], 1);
+  const bool edge = (lane == 31) || (ec + 1 >= K);
+  if (edge) vRp = __ldg(vin + (ec + 1 >= K ? 0 : ec + 1));
+
+  // Flux at the left face of e, computed once per face (by the element on its right)
+  // and handed to the left neighbour by a shuffle.
+  double FL;
+  if (ASYNC && (ec % inst.Kpe) == 0)
+    FL = pe_flux<PDE>(inst, ec / inst.Kpe, n, STAGE, vLm, v[0], e < K);
+  else
+    FL = num_flux<PDE>(inst.a, vLm, v[0]);
+  double FR = __shfl_down_sync(full, FL, 1);
+  if (edge) {
+    const int f = ec + 1 >= K ? 0 : ec + 1;
+    if (ASYNC && (f % inst.Kpe) == 0)
+      FR = pe_flux<PDE>(inst, f / inst.Kpe, n, STAGE, v[NP - 1], vRp, false);
+    else
+      FR = num_flux<PDE>(inst.a, v[NP - 1], vRp);
+  }
+
+  const StageConsts &C = inst.sc[STAGE];
+  double g[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = PDE == 0 ? v[i] : v[i] * v[i];
+  const double jL = __dsub_rn(phys_flux<PDE>(inst.a, v[0]), FL);
+  const double jR = __dsub_rn(phys_flux<PDE>(inst.a, v[NP - 1]), FR);
+
+  double out[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    double acc;
+    if (STAGE == 0) {
+      acc = v[i];
+    } else {
+      const double ui = inst.u[(size_t)i * K + ec];
+      acc = fma(C.beta, v[i], C.alpha * ui);
+    }
+#pragma unroll
+    for (int jj = 0; jj < NP; ++jj) acc = fma(C.Dm[i * NP + jj], g[jj], acc);
+    out[i] = acc;
+  }
+  if (jL != 0.0) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) out[i] = fma(C.liftL[i], jL, out[i]);
+  }
+  if (jR != 0.0) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) out[i] = fma(C.liftR[i], jR, out[i]);
+  }
+  if (e < K) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) vout[(size_t)i * K + e] = out[i];
+  }
+}
+
+template <int NP, int PDE, int STAGE, bool ASYNC>
+__global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
+  const int e = blockIdx.x * kTile + threadIdx.x;
+  const int64_t n = ASYNC ? inst.meta[0] + rel : 0;
+  stage_body<NP, PDE, STAGE, ASYNC>(inst, e, n);
+}
+
+template <int STAGE, int NP>
+__device__ __forceinline__ void batch_dispatch_pde(const Inst &I, int e, int64_t n) {
+  if (I.pde == 0) {
+    if (I.async) stage_body<NP, 0, STAGE, true>(I, e, n);
+    else stage_body<NP, 0, STAGE, false>(I, e, n);
+  } else {
+    if (I.async) stage_body<NP, 1, STAGE, true>(I, e, n);
+    else stage_body<NP, 1, STAGE, false>(I, e, n);
+  }
+}
+
+// Batched stage: block b handles work item (instance, first element); the instance's
+// descriptor is staged in shared memory, then the element code runs as above.
+template <int STAGE>
+__global__ void __launch_bounds__(kTile) k_batch_stage(const Inst *__restrict__ insts,
+                                                       const int2 *__restrict__ work, int rel) {
+  __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
+  const int2 w = work[blockIdx.x];
+  {
+    const int4 *src = reinterpret_cast<const int4 *>(insts + w.x);
+    int4 *dst = reinterpret_cast<int4 *>(smem);
+    for (int t = threadIdx.x; t < (int)(sizeof(Inst) / sizeof(int4)); t += blockDim.x)
+      dst[t] = __ldg(src + t);
+  }
+  __syncthreads();
+  const Inst &I = *reinterpret_cast<const Inst *>(smem);
+  const int e = w.y + threadIdx.x;
+  const int64_t n = I.async ? I.meta[0] + rel : 0;
+  switch (I.Np) {
+    case 2: batch_dispatch_pde<STAGE, 2>(I, e, n); break;
+    case 3: batch_dispatch_pde<STAGE, 3>(I, e, n); break;
+    case 4: batch_dispatch_pde<STAGE, 4>(I, e, n); break;
+    default: batch_dispatch_pde<STAGE, 5>(I, e, n); break;
+  }
+}
+
+__global__ void k_advance(int64_t *meta, int stride, int ninst, int64_t by) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ninst) meta[(size_t)i * stride] += by;
+}
+
+__global__ void k_to_internal(const double *__restrict__ src, double *__restrict__ dst, int K,
+                              int Np) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)K * Np) return;
+  const size_t e = idx / Np, i = idx % Np;
+  dst[i * K + e] = src[idx];
+}
+
+__global__ void k_to_external(const double *__restrict__ src, double *__restrict__ dst, int K,
+                              int Np) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)K * Np) return;
+  const size_t e = idx / Np, i = idx % Np;
+  dst[idx] = src[i * K + e];
+}
+
+struct ModeArgs {
+  double xi[kMaxNp];
+  double amp[16], kappa[16], phase[16];
+};
+
+__global__ void k_eval_modes(double *u, int K, int Np, double x0, double dx, ModeArgs m,
+                             int nmodes, double offset) {
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= (size_t)K * Np) return;
+  const size_t e = idx / Np;
+  const int i = (int)(idx % Np);
+  // x = x0 + e dx + (1 + xi_i) dx/2, evaluated in this order without contraction.
+  const double x = __dadd_rn(__dadd_rn(x0, __dmul_rn((double)e, dx)),
+                             __dmul_rn(__dadd_rn(1.0, m.xi[i]), __dmul_rn(dx, 0.5)));
+  double val = offset;
+  for (int t = 0; t < nmodes; ++t)
+    val = __dadd_rn(val, __dmul_rn(m.amp[t], sin(__dadd_rn(__dmul_rn(m.kappa[t], x), m.phase[t]))));
+  u[idx] = val;
+}
+
+constexpr int kRedThreads = 256;
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce(int kind, const double *__restrict__ u, const double *__restrict__ g, int K, int Np,
+             const double *__restrict__ wm, double *partials) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K; e += gridDim.x * blockDim.x) {
+    if (kind == 0) {
+      double s = 0.0;
+      for (int i = 0; i < Np; ++i) s = fma(wm[i], u[(size_t)i * K + e], s);
+      acc += s;
+    } else if (kind == 1) {
+      for (int i = 0; i < Np; ++i) acc = fmax(acc, fabs(u[(size_t)i * K + e]));
+    } else if (kind == 2) {
+      for (int i = 0; i < Np; ++i) acc += isfinite(u[(size_t)i * K + e]) ? 0.0 : 1.0;
+    } else {
+      double d[kMaxNp];
+      for (int i = 0; i < Np; ++i) d[i] = u[(size_t)i * K + e] - g[(size_t)i * K + e];
+      double s = 0.0;
+      for (int i = 0; i < Np; ++i) {
+        double r = 0.0;
+        for (int j = 0; j < Np; ++j) r = fma(wm[i * Np + j], d[j], r);
+        s = fma(d[i], r, s);
+      }
+      acc += s;
+    }
+  }
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      sh[threadIdx.x] = kind == 1 ? fmax(sh[threadIdx.x], sh[threadIdx.x + h])
+                                  : sh[threadIdx.x] + sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(kRedThreads)
+    k_reduce_final(int kind, const double *partials, int n, double scale, double *out) {
+  __shared__ double sh[kRedThreads];
+  double acc = 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x)
+    acc = kind == 1 ? fmax(acc, partials[t]) : acc + partials[t];
+  sh[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = kRedThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h)
+      sh[threadIdx.x] = kind == 1 ? fmax(sh[threadIdx.x], sh[threadIdx.x + h])
+                                  : sh[threadIdx.x] + sh[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = (kind == 0 || kind == 3) ? sh[0] * scale : sh[0];
+}
+
+template <int NP, int PDE, int STAGE>
+cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
+  const unsigned grid = (unsigned)((I.K + kTile - 1) / kTile);
+  if (I.async)
+    k_stage<NP, PDE, STAGE, true><<<grid, kTile, 0, s>>>(I, rel);
+  else
+    k_stage<NP, PDE, STAGE, false><<<grid, kTile, 0, s>>>(I, rel);
+  return cudaGetLastError();
+}
+
+template <int NP, int PDE>
+cudaError_t launch_np_pde(const Inst &I, int stage, int rel, cudaStream_t s) {
+  switch (stage) {
+    case 0: return launch_np_pde_stage<NP, PDE, 0>(I, rel, s);
+    case 1: return launch_np_pde_stage<NP, PDE, 1>(I, rel, s);
+    default: return launch_np_pde_stage<NP, PDE, 2>(I, rel, s);
+  }
+}
+
+template <int NP>
+cudaError_t launch_np(const Inst &I, int stage, int rel, cudaStream_t s) {
+  return I.pde == 0 ? launch_np_pde<NP, 0>(I, stage, rel, s) : launch_np_pde<NP, 1>(I, stage, rel, s);
+}
+
+}  // namespace
+
+cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s) {
+  switch (I.Np) {
+    case 2: return launch_np<2>(I, stage, rel, s);
+    case 3: return launch_np<3>(I, stage, rel, s);
+    case 4: return launch_np<4>(I, stage, rel, s);
+    case 5: return launch_np<5>(I, stage, rel, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork, int stage,
+                               int rel, int tile, cudaStream_t s) {
+  (void)tile;
+  switch (stage) {
+    case 0: k_batch_stage<0><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, rel); break;
+    case 1: k_batch_stage<1><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, rel); break;
+    default: k_batch_stage<2><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, rel); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_advance(int64_t *meta, int stride, int ninst, int64_t by, cudaStream_t s) {
+  k_advance<<<(ninst + 255) / 256, 256, 0, s>>>(meta, stride, ninst, by);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_internal(const double *src, double *dst, int K, int Np, cudaStream_t s) {
+  const size_t n = (size_t)K * Np;
+  k_to_internal<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, K, Np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_to_external(const double *src, double *dst, int K, int Np, cudaStream_t s) {
+  const size_t n = (size_t)K * Np;
+  k_to_external<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, K, Np);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_eval_modes(double *u, int K, int Np, double x0, double dx, const double *xi,
+                              int nmodes, const double *amp, const double *kappa,
+                              const double *phase, double offset, cudaStream_t s) {
+  if (nmodes < 0 || nmodes > 16 || Np > kMaxNp) return cudaErrorInvalidValue;
+  ModeArgs m{};
+  for (int i = 0; i < Np; ++i) m.xi[i] = xi[i];
+  for (int t = 0; t < nmodes; ++t) {
+    m.amp[t] = amp[t];
+    m.kappa[t] = kappa[t];
+    m.phase[t] = phase[t];
+  }
+  const size_t n = (size_t)K * Np;
+  k_eval_modes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, K, Np, x0, dx, m, nmodes, offset);
+  return cudaGetLastError();
+}
+
+int reduce_blocks(int K) {
+  int b = (K + kRedThreads - 1) / kRedThreads;
+  return b < 1024 ? (b < 1 ? 1 : b) : 1024;
+}
+
+cudaError_t launch_reduce(int kind, const double *u, const double *g, int K, int Np,
+                          const double *wm, double scale, double *partials, int nblocks,
+                          double *out, cudaStream_t s) {
+  k_reduce<<<nblocks, kRedThreads, 0, s>>>(kind, u, g, K, Np, wm, partials);
+  k_reduce_final<<<1, kRedThreads, 0, s>>>(kind, partials, nblocks, scale, out);
+  return cudaGetLastError();
+}
+
+}  // namespace adg

@@ -1,0 +1,232 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 oracle on identical seeded
+inputs and delay tables. Bar: relative L-infinity error <= 1e-12
+(max |u_gpu - u_oracle| / max |u_oracle|), the tolerance the FP64 method is held to.
+
+Each side draws its own delay table from the same seed (the library in C++, the oracle in
+Python; their equality is checked on the host in test_abi_host.py)."""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import paper_2404_03399_gb300 as adg
+from oracle import dg, delays as odelays
+from workloads import (ADVECTION_SMALL, ADVECTION_16M, BURGERS_1M, PAPER_FIG6, SIN,
+                       HALF_PLUS_SIN, caa_table, constant_table, random_nodal)
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-12
+TWO_PI = 2 * math.pi
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2404_03399_gb300 import build
+    build.build()
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def _oracle_mode(mode):
+    return {"sync": "sync", "async": "adg", "at": "adg"}[mode]
+
+
+def run_pair(cfg: adg.Config, u0: np.ndarray, steps: int, table=None):
+    """Run GPU and oracle from the same nodal u0; returns (gpu, oracle, dt)."""
+    s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
+    s.step(steps)
+    got = s.state().cpu().numpy()
+    dt = s.dt
+    s.close()
+    q = cfg.q if cfg.mode == "at" else 1
+    if cfg.mode == "at" and q == 0:
+        q = min(cfg.p + 1, 5)
+    if cfg.mode != "sync" and cfg.P > 1:
+        tbl = cfg.table if cfg.table is not None else odelays.delay_table(cfg.seed, cfg.P, steps, cfg.L, cfg.probs)
+    else:
+        tbl = None
+    prob = dg.Problem(pde=cfg.pde, K=cfg.K, p=cfg.p, P=cfg.P, dt=dt, a=cfg.a, x0=cfg.x0, x1=cfg.x1,
+                      mode=_oracle_mode(cfg.mode) if cfg.P > 1 else "sync", q=q, delays=tbl)
+    ref = dg.run(prob, u0, steps).numpy()
+    return got, ref, dt
+
+
+def test_eval_modes_matches_oracle_nodes():
+    cfg = adg.Config(K=50, p=3)
+    u = adg.eval_modes(cfg, PAPER_FIG6.amp, PAPER_FIG6.kappa, PAPER_FIG6.phase, 0.25).cpu().numpy()
+    ref = dg.modes_initial(PAPER_FIG6, 50, 3) + 0.25
+    assert np.max(np.abs(u - ref)) < 1e-14
+
+
+@pytest.mark.parametrize("mode,q", [("sync", 0), ("async", 0), ("at", 2), ("at", 3)])
+def test_advection_small_stated_config(mode, q):
+    # K = 64, p = 2, 16 PEs, sigma = 0.1, delays uniform in {0..3}, t_end = 2 pi (640
+    # steps). Under the common-level scheme the asynchronous runs grow (delayed
+    # self-feedback); parity is still element by element, relative to the field's size.
+    w = ADVECTION_SMALL
+    cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode=mode, L=w.L, q=q, seed=w.seed)
+    u0 = dg.modes_initial(SIN, w.K, w.p)
+    got, ref, dt = run_pair(cfg, u0, w.steps)
+    assert abs(dt * w.steps - TWO_PI) < 1e-12
+    assert rel_linf(got, ref) < TOL
+
+
+@pytest.mark.parametrize("p", [1, 2, 3, 4])
+@pytest.mark.parametrize("mode,q", [("sync", 0), ("async", 0), ("at", 0)])
+def test_advection_degrees_and_modes(p, mode, q):
+    # AT order p+1 = 5 at p = 4 needs sigma well inside the delayed-feedback bound.
+    cfl = 0.002 if p == 4 else 0.01
+    cfg = adg.Config(pde="advection", K=96, p=p, P=8, cfl=cfl, mode=mode, L=3, q=q, seed=11,
+                     probs=[0.3, 0.4, 0.3])
+    u0 = dg.modes_initial(PAPER_FIG6, 96, p)
+    got, ref, _ = run_pair(cfg, u0, 70)
+    assert rel_linf(got, ref) < TOL
+
+
+@pytest.mark.parametrize("K,P", [(300, 10), (257, 1), (1000, 8), (33, 33), (4096 + 768, 19)])
+def test_ragged_sizes(K, P):
+    # K not a multiple of the 256-element tile or of the 32-lane warp; P = 1 (no PE
+    # faces, the periodic wrap is interior); P = K (every face a PE face).
+    cfg = adg.Config(pde="advection", K=K, p=3, P=P, cfl=0.01, mode="at", L=4, q=3, seed=5)
+    u0 = random_nodal(K, 3, 17)
+    got, ref, _ = run_pair(cfg, u0, 45)
+    assert rel_linf(got, ref) < TOL
+
+
+def test_negative_speed_upwinds_from_the_right():
+    cfg = adg.Config(pde="advection", K=128, p=2, P=4, a=-0.8, cfl=0.02, mode="at", L=3, q=2, seed=3)
+    u0 = dg.modes_initial(PAPER_FIG6, 128, 2)
+    got, ref, _ = run_pair(cfg, u0, 50)
+    assert rel_linf(got, ref) < TOL
+
+
+@pytest.mark.parametrize("mode,q", [("sync", 0), ("async", 0), ("at", 2)])
+@pytest.mark.parametrize("p", [1, 4])
+def test_burgers_llf(mode, q, p):
+    cfg = adg.Config(pde="burgers", K=128, p=p, P=8, cfl=0.01, mode=mode, L=4, q=q, seed=2)
+    u0 = dg.modes_initial(HALF_PLUS_SIN, 128, p)
+    got, ref, _ = run_pair(cfg, u0, 60)
+    assert rel_linf(got, ref) < TOL
+
+
+@pytest.mark.parametrize("kind", ["constant2", "caa"])
+def test_caller_tables(kind):
+    P = 8
+    tbl = constant_table(1, P, 2) if kind == "constant2" else caa_table(P, 2, 3)
+    cfg = adg.Config(pde="advection", K=64, p=2, P=P, cfl=0.01, mode="at", L=3, q=2, table=tbl)
+    u0 = dg.modes_initial(PAPER_FIG6, 64, 2)
+    got, ref, _ = run_pair(cfg, u0, 40)
+    assert rel_linf(got, ref) < TOL
+
+
+@pytest.mark.parametrize("pde", ["advection", "burgers"])
+def test_zero_delay_is_bitwise_sync(pde):
+    K, p, P = 512, 3, 16
+    u0 = torch.tensor(dg.modes_initial(HALF_PLUS_SIN if pde == "burgers" else PAPER_FIG6, K, p), device="cuda")
+    outs = []
+    for mode, table in [("sync", None), ("at", constant_table(1, P, 0)), ("async", constant_table(1, P, 0))]:
+        cfg = adg.Config(pde=pde, K=K, p=p, P=P, cfl=0.02, mode=mode, L=2, q=3, table=table)
+        s = adg.Solver(cfg, u0)
+        s.step(70)
+        outs.append(s.state().cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+@pytest.mark.parametrize("mode,q", [("sync", 0), ("async", 0), ("at", 3)])
+def test_conservation_on_gpu(mode, q):
+    K, p = 2048, 3
+    cfg = adg.Config(pde="advection", K=K, p=p, P=64, cfl=0.005, mode=mode, L=4, q=q, seed=8)
+    u0 = adg.eval_modes(cfg, PAPER_FIG6.amp, PAPER_FIG6.kappa, PAPER_FIG6.phase, 1.0)
+    s = adg.Solver(cfg, u0)
+    I0 = s.integral()
+    s.step(300)
+    I1 = s.integral()
+    s.close()
+    assert abs(I1 - I0) < 1e-12 * abs(I0)
+
+
+def test_nonfinite_detection():
+    # Burgers at sigma = 0.05 with p = 4 and delays up to 3 leaves the delayed-feedback
+    # stability bound and overflows; the reduction reports ADG_ENONFINITE.
+    cfg = adg.Config(pde="burgers", K=256, p=4, P=4, cfl=0.05, mode="at", L=4, q=2, seed=0)
+    u0 = adg.eval_modes(cfg, [1.0], [1.0], [0.0], 0.5)
+    s = adg.Solver(cfg, u0)
+    s.check_finite()
+    s.step(400)
+    with pytest.raises(adg.AdgError) as ei:
+        s.check_finite()
+    assert ei.value.code == adg._abi.ADG_ENONFINITE
+    s.close()
+
+
+def test_nan_initial_data_rejected():
+    cfg = adg.Config(K=64, p=2)
+    u0 = torch.zeros((64, 3), dtype=torch.float64, device="cuda")
+    u0[10, 1] = float("nan")
+    with pytest.raises(adg.AdgError) as ei:
+        adg.Solver(cfg, u0)
+    assert ei.value.code == adg._abi.ADG_EINVAL
+
+
+def test_run_to_time_and_step_counter():
+    cfg = adg.Config(K=64, p=2, P=16, cfl=0.1, mode="at", L=4, q=3)
+    s = adg.Solver(cfg, adg.eval_modes(cfg, [1.0], [1.0], [0.0]))
+    s.run(TWO_PI)
+    s.state()
+    assert s.n == 640
+    s.close()
+
+
+def _window_oracle(cfg, u0_full_fn, e, steps, dt, table_rows, both_sides):
+    """Oracle on a window of the full mesh around element e (sampled parity at full size)."""
+    r = 3 * steps + 2
+    lo = e - r
+    W = 2 * r + 1 if both_sides else r + 3
+    u0w = u0_full_fn(lo, W)
+    q = cfg.q if cfg.mode == "at" else 1
+    prob = dg.Problem(pde=cfg.pde, K=W, p=cfg.p, P=cfg.P, dt=dt, a=cfg.a, mode="adg", q=q,
+                      delays=table_rows, window_lo=lo, K_global=cfg.K)
+    out = dg.run(prob, u0w, steps).numpy()
+    return out[r]
+
+
+@pytest.mark.parametrize("which", ["advection_16m", "burgers_1m"])
+def test_full_size_sampled(which):
+    # Full-size meshes in the launch configuration the benchmark times (graph replay of
+    # 32-step chunks plus a direct remainder), checked at sampled elements against the
+    # oracle run on a window wide enough to contain each sample's dependence cone.
+    if which == "advection_16m":
+        w = ADVECTION_16M
+        cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=0.002, mode="at", L=w.L, q=w.q, seed=w.seed)
+        modes, steps, both = SIN, 40, False
+    else:
+        w = BURGERS_1M
+        cfg = adg.Config(pde="burgers", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode="at", L=w.L, q=w.q, seed=w.seed)
+        modes, steps, both = HALF_PLUS_SIN, 36, True
+    u0 = adg.eval_modes(cfg, modes.amp, modes.kappa, modes.phase, modes.offset)
+    s = adg.Solver(cfg, u0)
+    dt = s.dt
+    s.step(steps)
+    got = s.state().cpu().numpy()
+    s.close()
+    u0h = u0.cpu().numpy()
+    del u0
+    torch.cuda.empty_cache()
+    tbl = odelays.delay_table(cfg.seed, cfg.P, steps, cfg.L)
+    rng = np.random.default_rng(0)
+    Kpe = cfg.K // cfg.P
+    samples = [0, 1, Kpe - 1, Kpe, Kpe + 1, cfg.K - 1] + list(rng.integers(0, cfg.K, 6))
+    worst = 0.0
+    scale = np.max(np.abs(got))
+    for e in samples:
+        e = int(e)
+        fn = lambda lo, W: u0h[np.arange(lo, lo + W) % cfg.K]
+        ref = _window_oracle(cfg, fn, e, steps, dt, tbl, both)
+        worst = max(worst, float(np.max(np.abs(got[e] - ref))) / scale)
+    assert worst < TOL
