@@ -1,0 +1,351 @@
+"""Benchmark of the ADG-AT SSP-RK3 step on GB300.
+
+One "step" is one full SSP-RK3 step of ADG-AT over the whole mesh of the large advection
+workload (K = 2^24 elements, p = 3, 2^26 DOF in FP64, 16384 PEs, delays uniform in
+{0..7}, AT order 3, ring of L+q-1 = 10 levels). The metric is DOF-stage updates per second
+(K (p+1) x 3 stages per step). The same line carries the synchronous-DG throughput on the
+same mesh, the roofline of the stage kernel, the oracle timed on the host cores, clocks
+sampled during the timed region and an end-to-end figure through the C ABI from host
+buffers.
+
+Multi-GPU (torchrun, one rank per GPU): the mesh does not shard without a face exchange,
+so each rank advances its own replica of the workload (weak scaling, no collective on the
+data path); value = all ranks' DOF-stage updates / max over ranks of the timed region.
+
+    python bench.py [--steps 500] [--warmup 5] [--gpus N] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "ADG-AT DOF-stage updates/s and % HBM roofline vs sync DG; adjoint/forward cost"
+UNIT = "DOF-stage updates/s"
+STAGES = 3
+# The large advection workload; its Courant number is not fixed by the workload statement
+# and is set inside the stability bound of the delayed self-feedback (sigma (p+1)^2 k < 1
+# for k <= 7 with the AT extrapolation); the work per step does not depend on it.
+WORKLOAD = dict(name="advection_16m", pde="advection", K=1 << 24, p=3, P=16384, L=8, q=3,
+                cfl=0.002, seed=0, modes=([1.0], [1.0], [0.0], 0.0))
+# Algorithmic FP64 work per DOF-stage of upwind advection: (Np + 2) multiply-adds
+# (volume D u, the left lift, the stage combine) = 2 (Np + 2) flops.
+FLOP_PER_DOF_STAGE = 2 * (WORKLOAD["p"] + 1 + 2)
+# Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
+BYTES_PER_DOF_STEP = 16
+GRAPH_STEPS = 32
+
+
+def peaks():
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (else the recipe's fallback);
+    FP64 ALU peak from unit counts and the maximum SM clock: 152 SMs x 2 DFMA/clk x 2 flop
+    x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 of GB300)."""
+    hbm, src = 6800.0, "fallback"
+    sm_mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mp = json.load(f)
+        hbm, src = float(mp["hbm_gbs"]), "measured"
+        sm_mhz = float(mp.get("sm_max_mhz", sm_mhz))
+    except Exception:
+        pass
+    fp64_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
+    return hbm, src, fp64_tflops
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.dev}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.fh, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in open(self.path):
+            parts = [t.strip() for t in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                rows.append((float(parts[1]), float(parts[2]), float(parts[3]), parts[5:9]))
+            except ValueError:
+                continue
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i, v in enumerate(r[3]) if v == "Active"})
+        loaded = [r[0] for r in rows if r[2] > 200.0] or [r[0] for r in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(r[1] for r in rows),
+                "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
+
+
+def make_cfg(mode: str):
+    import paper_2404_03399_gb300 as adg
+    w = WORKLOAD
+    return adg.Config(pde=w["pde"], K=w["K"], p=w["p"], P=w["P"], cfl=w["cfl"], mode=mode,
+                      L=w["L"], q=w["q"] if mode == "at" else 0, seed=w["seed"])
+
+
+def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks: bool, dev: int):
+    import torch
+    import paper_2404_03399_gb300 as adg
+    cfg = make_cfg(mode)
+    amp, kap, ph, off = WORKLOAD["modes"]
+    u0 = adg.eval_modes(cfg, amp, kap, ph, off)
+    s = adg.Solver(cfg, u0)
+    del u0
+    stream = torch.cuda.current_stream()
+    s.step(warmup)
+    torch.cuda.synchronize()
+    dist_barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = ClockSampler(dev) if sample_clocks else None
+    if clocks:
+        clocks.__enter__()
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    torch.cuda.synchronize()
+    dist_barrier()
+    if clocks:
+        clocks.__exit__(None, None, None)
+    ms = ev0.elapsed_time(ev1)
+    s.check_finite_ok = True
+    try:
+        s.check_finite()
+    except adg.AdgError:
+        s.check_finite_ok = False
+    finite = s.check_finite_ok
+    s.close()
+    return ms, (clocks.summary() if clocks else None), finite
+
+
+def e2e_timed(steps: int):
+    """Public-API run from host buffers: pinned u0 -> device, adg_init, `steps` steps,
+    state -> pinned host; all inside one timed region (wall clock around synchronised
+    work, bracketed by CUDA events on the same stream)."""
+    import torch
+    import paper_2404_03399_gb300 as adg
+    cfg = make_cfg("at")
+    amp, kap, ph, off = WORKLOAD["modes"]
+    host_u0 = adg.eval_modes(cfg, amp, kap, ph, off).cpu().pin_memory()
+    host_out = torch.empty_like(host_u0).pin_memory()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
+    ev0.record(stream)
+    dev_u0 = host_u0.to("cuda", non_blocking=True)
+    s = adg.Solver(cfg, dev_u0)
+    s.step(steps)
+    out = s.state()
+    host_out.copy_(out, non_blocking=True)
+    ev1.record(stream)
+    ev1.synchronize()
+    wall = time.perf_counter() - t0
+    s.close()
+    nbytes = host_u0.numel() * 8
+    return max(wall * 1e3, ev0.elapsed_time(ev1)), nbytes
+
+
+def cpu_oracle_rate(window: int, steps: int):
+    """The FP64 oracle as it stands, on the host cores: `steps` SSP-RK3 steps of ADG-AT on
+    a contiguous window of `window` elements of the large mesh (its PE faces and delays
+    included). Returns (DOF-stage updates/s, threads, sample description)."""
+    import numpy as np
+    import torch
+    from oracle import dg, delays
+    w = WORKLOAD
+    K, p = w["K"], w["p"]
+    dx = 2 * math.pi / K
+    dt = (w["cfl"] * dx) / 1.0
+    tbl = delays.delay_table(w["seed"], w["P"], steps + 2, w["L"])
+    x = dg.node_coordinates(window, p, 0.0, 2 * math.pi, 0, K)
+    u0 = np.sin(x)
+    prob = dg.Problem(pde="advection", K=window, p=p, P=w["P"], dt=dt, mode="adg", q=w["q"],
+                      delays=tbl, window_lo=0, K_global=K)
+    s = dg.Solver(prob, u0)
+    s.step()                                 # untimed first step (setup of the caches)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        s.step()
+    el = time.perf_counter() - t0
+    rate = window * (p + 1) * STAGES * steps / el
+    sample = (f"{steps} SSP-RK3 steps of the oracle on a {window}-element window "
+              f"({window // (K // w['P'])} PE faces) of the K=2^24 mesh")
+    return rate, torch.get_num_threads(), sample
+
+
+def dist_setup():
+    import torch
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+        return rank, ws, local, dist
+    return 0, 1, 0, None
+
+
+def aggregate(dist, ms: float, units: float):
+    """Max of the timed region over ranks and the sum of units (weak scaling)."""
+    if dist is None:
+        return ms, units
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    u = torch.tensor([units], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
+def reference_arm(args, rank, ws):
+    """The oracle (the reference for this method) on the host cores, on the same metric:
+    each step is a bounded sample (a window of the mesh)."""
+    if rank != 0:
+        return
+    import torch
+    window = args.ref_window
+    rate, cores, sample = cpu_oracle_rate(window, max(1, min(args.steps, 3)))
+    K = WORKLOAD["K"]
+    ms_per_step = (K * (WORKLOAD["p"] + 1) * STAGES) / rate * 1e3
+    line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "K": K,
+                                            "p": WORKLOAD["p"], "P": WORKLOAD["P"]},
+            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=500)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--sync-steps", type=int, default=200)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip sync-DG and e2e runs")
+    ap.add_argument("--ref-window", type=int, default=1 << 22)
+    args = ap.parse_args()
+
+    rank, ws, local, dist = dist_setup()
+    if args.impl == "reference":
+        reference_arm(args, rank, ws)
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    import torch
+    import paper_2404_03399_gb300 as adg
+    torch.cuda.set_device(local)
+    adg.load()
+    barrier = (lambda: dist.barrier()) if dist is not None else (lambda: None)
+
+    K, p = WORKLOAD["K"], WORKLOAD["p"]
+    ndof = K * (p + 1)
+    ms, clocks, finite = device_timed("at", args.steps, args.warmup, barrier, rank == 0, local)
+    units = ndof * STAGES * args.steps
+    ms_max, units_all = aggregate(dist, ms, units)
+    value = units_all / (ms_max * 1e-3)
+
+    hbm_gbs, hbm_src, fp64_tflops = peaks()
+    ms_step = ms / args.steps
+    launch_ms = ms_step / STAGES
+    flop_per_launch = ndof * FLOP_PER_DOF_STAGE
+    achieved_tflops = flop_per_launch / (launch_ms * 1e-3) / 1e12
+    traffic = None
+    try:
+        with open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")) as f:
+            traffic = json.load(f).get("bytes_per_launch")
+    except Exception:
+        pass
+    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
+                "frac": achieved_tflops / fp64_tflops, "traffic": traffic,
+                "kernel": "k_stage (fused RHS + SSP-RK3 combine + PE-face AT flux + ring write), FP64",
+                "peak_source": "FP64 from unit counts x max SM clock (152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
+    hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / (ms_step * 1e-3) / 1e9
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD["name"], "K": K, "p": p, "P": WORKLOAD["P"],
+                       "L": WORKLOAD["L"], "at_order": WORKLOAD["q"], "cfl": WORKLOAD["cfl"],
+                       "dof": ndof, "parallelism": f"replicas x{ws}",
+                       "l2": "inputs larger than L2 (537 MB per nodal field)",
+                       "graph_steps": GRAPH_STEPS},
+            "roofline": roofline,
+            "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
+                    "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
+            "gpu_launches": STAGES * args.steps + math.ceil(args.steps / GRAPH_STEPS),
+            "finite": finite, "clocks": clocks}
+
+    if not args.no_extras:
+        sms, _, _ = device_timed("sync", args.sync_steps, args.warmup, barrier, False, local)
+        line["sync_dg"] = {"value": ndof * STAGES * args.sync_steps / (sms * 1e-3), "unit": UNIT,
+                           "ms_per_step": sms / args.sync_steps}
+        line["at_over_sync"] = value / ws / line["sync_dg"]["value"]
+        ems, nbytes = e2e_timed(args.steps)
+        line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+                       "what": "pinned host u0 -> device, adg_init, all steps, state -> pinned host"}
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(1 << 22, 3)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
