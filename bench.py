@@ -311,7 +311,8 @@ def main():
         pass
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_tflops, "traffic": traffic,
-                "kernel": "k_stage (fused RHS + SSP-RK3 combine + PE-face AT flux + ring write), FP64",
+                "kernel": "k_stage (fused RHS + SSP-RK3 stage combine, FP64); achieved uses step time / 3, "
+                          "so the PE-face passes (about 1%) are charged to it",
                 "peak_source": "FP64 from unit counts x max SM clock (152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
     hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / (ms_step * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -325,7 +326,8 @@ def main():
             "roofline": roofline,
             "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
                     "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
-            "gpu_launches": STAGES * args.steps + math.ceil(args.steps / GRAPH_STEPS),
+            # per step: 3 stage kernels + 3 PE-face passes; one step-counter kernel per chunk
+            "gpu_launches": 2 * STAGES * args.steps + math.ceil(args.steps / GRAPH_STEPS),
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:

@@ -308,6 +308,8 @@ struct adg_ctx {
   Inst *insts_dev = nullptr;
   int2 *work_dev = nullptr;
   int nwork = 0;
+  int2 *fwork_dev = nullptr;   // (instance, first PE face) items of the batched face pass
+  int nfwork = 0;
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -335,7 +337,8 @@ void fold_constants(InstHost &h) {
   const Ops &o = h.ops;
   const int Np = o.Np;
   const ld c2 = -2.0L * (ld)h.dt / (ld)h.dx;
-  const ld cf = h.cfg.pde == ADG_ADVECTION ? (ld)h.cfg.a : 0.5L;
+  const bool adv = h.cfg.pde == ADG_ADVECTION;
+  const ld a = (ld)h.cfg.a;
   const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
   const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
   for (int s = 0; s < kStages; ++s) {
@@ -343,10 +346,16 @@ void fold_constants(InstHost &h) {
     std::memset(&C, 0, sizeof(C));
     C.alpha = (double)alpha[s];
     C.beta = (double)beta[s];
+    const ld b = beta[s];
     for (int i = 0; i < Np; ++i) {
-      for (int j = 0; j < Np; ++j) C.Dm[i * Np + j] = (double)(beta[s] * c2 * cf * o.D[i * Np + j]);
-      C.liftL[i] = (double)(beta[s] * c2 * o.Minv[i * Np + 0]);
-      C.liftR[i] = (double)(-beta[s] * c2 * o.Minv[i * Np + (Np - 1)]);
+      for (int j = 0; j < Np; ++j) {
+        const ld d = o.D[i * Np + j];
+        C.A[i * Np + j] = adv ? (double)(b * ((i == j ? 1.0L : 0.0L) + c2 * a * d))
+                              : (double)(b * c2 * 0.5L * d);
+      }
+      const ld sc = adv ? b * c2 * a : b * c2;
+      C.lL[i] = (double)(sc * o.Minv[i * Np + 0]);
+      C.lR[i] = (double)(-sc * o.Minv[i * Np + (Np - 1)]);
     }
   }
 }
@@ -466,8 +475,11 @@ int launch_steps(adg_ctx *c, int nsteps) {
     for (int s = 0; s < kStages; ++s) {
       if (c->batch) {
         CK(adg::launch_batch_stage(c->insts_dev, c->work_dev, c->nwork, s, rel, adg::kTile, c->stream));
+        if (c->nfwork > 0)
+          CK(adg::launch_batch_faces(c->insts_dev, c->fwork_dev, c->nfwork, s, rel, c->stream));
       } else {
         CK(adg::launch_stage(c->inst[0].I, s, rel, c->stream));
+        if (c->inst[0].I.async) CK(adg::launch_faces(c->inst[0].I, s, rel, c->stream));
       }
     }
   }
@@ -562,6 +574,7 @@ void adg_destroy(adg_ctx *c) {
   cudaFree(c->meta);
   cudaFree(c->insts_dev);
   cudaFree(c->work_dev);
+  cudaFree(c->fwork_dev);
   cudaFree(c->partials);
   cudaFree(c->red_out);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -628,17 +641,22 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
   }
   if (!r) {
     std::vector<Inst> hi(n);
-    std::vector<int2> work;
+    std::vector<int2> work, fwork;
     for (int i = 0; i < n; ++i) {
       hi[i] = c->inst[i].I;
       for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));
+      if (hi[i].async)
+        for (int j0 = 0; j0 < hi[i].P; j0 += 256) fwork.push_back(make_int2(i, j0));
     }
     c->nwork = (int)work.size();
+    c->nfwork = (int)fwork.size();
     if (cudaMalloc(&c->insts_dev, sizeof(Inst) * n) != cudaSuccess ||
-        cudaMalloc(&c->work_dev, sizeof(int2) * work.size()) != cudaSuccess)
+        cudaMalloc(&c->work_dev, sizeof(int2) * work.size()) != cudaSuccess ||
+        cudaMalloc(&c->fwork_dev, sizeof(int2) * std::max<size_t>(1, fwork.size())) != cudaSuccess)
       r = fail(c, ADG_ENOMEM, "cudaMalloc(batch descriptors)");
     else if (cudaMemcpy(c->insts_dev, hi.data(), sizeof(Inst) * n, cudaMemcpyHostToDevice) != cudaSuccess ||
-             cudaMemcpy(c->work_dev, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+             cudaMemcpy(c->work_dev, work.data(), sizeof(int2) * work.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+             (!fwork.empty() && cudaMemcpy(c->fwork_dev, fwork.data(), sizeof(int2) * fwork.size(), cudaMemcpyHostToDevice) != cudaSuccess))
       r = fail(c, ADG_ECUDA, "cudaMemcpy(batch descriptors)");
   }
   if (!r && cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(c, ADG_ECUDA, "sync");

@@ -12,17 +12,20 @@ constexpr int kMaxQ = 5;
 constexpr int kStages = 3;
 constexpr int kTile = 256;      // elements (threads) per block
 
-// Folded constants of one SSP-RK3 stage (Shu-Osher form)
-//   out_i = alpha u_i + beta v_i + sum_j Dm_ij g_j + liftL_i jL + liftR_i jR,
-// where g = v (advection, a folded into Dm) or v*v (Burgers, 1/2 folded into Dm),
-// jL = f(v_0) - F_L, jR = f(v_p) - F_R, and
-//   Dm = beta (-2 dt/dx) c D,  liftL = beta (-2 dt/dx) LIFT_L,  liftR = beta (2 dt/dx) LIFT_R
-// with c = a (advection) or 1/2 (Burgers): the strong form of Eq. DGscheme,
-// dt L(v) = -(2 dt/dx) [ D f + LIFT_L (f_0 - F_L) - LIFT_R (f_p - F_R) ].
+// Folded constants of one SSP-RK3 stage in Shu-Osher form, v_out = alpha u + beta (v + dt L(v)),
+// with the strong form of Eq. DGscheme
+//   dt L(v) = c2 [ D f(v) + LIFT_L (f(v_0) - F_L) - LIFT_R (f(v_p) - F_R) ],  c2 = -2 dt/dx.
+// Advection (f = a v; every face flux is a G with G the upwind trace, or at a PE face the
+// AT combination of delayed upwind traces):
+//   out_i = alpha u_i + sum_j A_ij v_j + lL_i (v_0 - G_L) + lR_i (v_p - G_R),
+//   A = beta (I + c2 a D),  lL = beta c2 a LIFT_L,  lR = -beta c2 a LIFT_R.
+// Burgers (f = v^2/2, local Lax-Friedrichs face fluxes F):
+//   out_i = alpha u_i + beta v_i + sum_j A_ij v_j^2 + lL_i (f(v_0) - F_L) + lR_i (f(v_p) - F_R),
+//   A = beta c2 D / 2,  lL = beta c2 LIFT_L,  lR = -beta c2 LIFT_R.
 struct StageConsts {
-  double Dm[kMaxNp * kMaxNp];
-  double liftL[kMaxNp];
-  double liftR[kMaxNp];
+  double A[kMaxNp * kMaxNp];
+  double lL[kMaxNp];
+  double lR[kMaxNp];
   double alpha, beta;
 };
 
@@ -45,6 +48,11 @@ static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4")
 cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
 cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                int stage, int rel, int tile, cudaStream_t s);
+// PE-face pass after each stage: ring write of the stage-input traces and replacement of
+// the synchronous flux by the delayed / AT flux in the elements next to each PE face.
+cudaError_t launch_faces(const Inst &I, int stage, int rel, cudaStream_t s);
+cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int nwork, int stage,
+                               int rel, cudaStream_t s);
 cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t by,
                            cudaStream_t s);
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,

@@ -34,13 +34,26 @@ __device__ __forceinline__ double num_flux(double a, double uL, double uR) {
 
 __device__ __forceinline__ int64_t ring_slot(int64_t level, int R) { return level % R; }
 
-// Flux at PE face j for step n, stage s (Eqs. asyncEulerDGconserved and at-flux-gen):
+__device__ __forceinline__ bool nonzero(double x) {
+  return (__double_as_longlong(x) << 1) != 0;   // integer test: not +0 or -0
+}
+
+// Value at PE face j for step n, stage s (Eqs. asyncEulerDGconserved and at-flux-gen):
 // delay k = min(D[n][j], n), order q' = min(q, n-k+1),
-// F = sum_{i<q'} c_i(k; q') fhat(T_{n-k-i, s, j}); level n (k = 0) uses the current
-// traces (tl, tr). The owner (the element right of the face) stores T_{n,s,j}.
-template <int PDE, class I>
-__device__ __forceinline__ double pe_flux(const I &inst, int j, int64_t n, int s, double tl,
-                                          double tr, bool owner) {
+//   V = sum_{i<q'} c_i(k; q') v(T_{n-k-i, s, j}),
+// where T are the traces (u^-, u^+) of the stage-s input of step n-k-i and v is the
+// numerical flux (Burgers) or, for linear advection, the upwind trace (the flux is a V,
+// the same AT flux with the factor a taken out of the sum). Level n (k = 0) uses the
+// current traces (tl, tr); the owner (the element right of the face) stores T_{n,s,j}.
+template <int PDE, int DIR, class I>
+__device__ __forceinline__ double face_value(const I &inst, double uL, double uR) {
+  if (PDE == 0) return DIR > 0 ? uL : uR;
+  return num_flux<1>(0.0, uL, uR);
+}
+
+template <int PDE, int DIR, class I>
+__device__ __forceinline__ double pe_value(const I &inst, int j, int64_t n, int s, double tl,
+                                        double tr, bool owner) {
   const int P = inst.P;
   const int R = inst.R;
   const int q = inst.q;
@@ -50,89 +63,97 @@ __device__ __forceinline__ double pe_flux(const I &inst, int j, int64_t n, int s
   const int64_t qe64 = n - k + 1 < q ? n - k + 1 : q;
   const int qe = (int)qe64;
   const double *c = inst.coef + ((size_t)k * q + (qe - 1)) * q;
-  double F;
+  double V;
   if (k == 0) {
-    F = __dmul_rn(c[0], num_flux<PDE>(inst.a, tl, tr));
+    V = __dmul_rn(c[0], face_value<PDE, DIR>(inst, tl, tr));
   } else {
     const double2 T = inst.ring[(ring_slot(n - k, R) * kStages + s) * P + j];
-    F = __dmul_rn(c[0], num_flux<PDE>(inst.a, T.x, T.y));
+    V = __dmul_rn(c[0], face_value<PDE, DIR>(inst, T.x, T.y));
   }
   for (int i = 1; i < qe; ++i) {
     const double ci = c[i];
     if (ci != 0.0) {
       const double2 T = inst.ring[(ring_slot(n - k - i, R) * kStages + s) * P + j];
-      F = __dadd_rn(F, __dmul_rn(ci, num_flux<PDE>(inst.a, T.x, T.y)));
+      V = __dadd_rn(V, __dmul_rn(ci, face_value<PDE, DIR>(inst, T.x, T.y)));
     }
   }
   if (owner) inst.ring[(ring_slot(n, R) * kStages + s) * P + j] = make_double2(tl, tr);
-  return F;
+  return V;
 }
 
 // One SSP-RK3 stage for element e (all 32 lanes of the warp take part; lanes past the
-// end duplicate element K-1 and store nothing).
-template <int NP, int PDE, int STAGE, bool ASYNC, class I>
-__device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n) {
+// end duplicate element K-1 and store nothing). DIR is the upwind side for advection
+// (+1: a > 0, -1: a < 0) and 0 for Burgers.
+template <int NP, int PDE, int STAGE, int DIR, class I>
+__device__ __forceinline__ void stage_body(const I &inst, int e) {
   const int K = inst.K;
   const int lane = threadIdx.x & 31;
   const int ec = e < K ? e : K - 1;
   const double *vin = STAGE == 0 ? inst.u : (STAGE == 1 ? inst.v1 : inst.v2);
   double *vout = STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.u);
+  const StageConsts &C = inst.sc[STAGE];
 
   double v[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) v[i] = __ldg(vin + (size_t)i * K + ec);
-
-  const unsigned full = 0xffffffffu;
-  double vLm = __shfl_up_sync(full, v[NP - 1], 1);
-  if (lane == 0) vLm = __ldg(vin + (size_t)(NP - 1) * K + (ec == 0 ? K - 1 : ec - 1));
-  double vRp = __shfl_down_sync(full, v[0], 1);
-  const bool edge = (lane == 31) || (ec + 1 >= K);
-  if (edge) vRp = __ldg(vin + (ec + 1 >= K ? 0 : ec + 1));
-
-  // Flux at the left face of e, computed once per face (by the element on its right)
-  // and handed to the left neighbour by a shuffle.
-  double FL;
-  if (ASYNC && (ec % inst.Kpe) == 0)
-    FL = pe_flux<PDE>(inst, ec / inst.Kpe, n, STAGE, vLm, v[0], e < K);
-  else
-    FL = num_flux<PDE>(inst.a, vLm, v[0]);
-  double FR = __shfl_down_sync(full, FL, 1);
-  if (edge) {
-    const int f = ec + 1 >= K ? 0 : ec + 1;
-    if (ASYNC && (f % inst.Kpe) == 0)
-      FR = pe_flux<PDE>(inst, f / inst.Kpe, n, STAGE, v[NP - 1], vRp, false);
-    else
-      FR = num_flux<PDE>(inst.a, v[NP - 1], vRp);
+  double u[NP];
+  if (STAGE > 0) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) u[i] = inst.u[(size_t)i * K + ec];
   }
 
-  const StageConsts &C = inst.sc[STAGE];
+  const unsigned full = 0xffffffffu;
+  const bool edge = (lane == 31) || (ec + 1 >= K);
+  const int fR = ec + 1 >= K ? 0 : ec + 1;
+  double vLm = 0.0, vRp = 0.0;
+  if (PDE == 1 || DIR > 0) {
+    vLm = __shfl_up_sync(full, v[NP - 1], 1);
+    if (lane == 0) vLm = __ldg(vin + (size_t)(NP - 1) * K + (ec == 0 ? K - 1 : ec - 1));
+  }
+  if (PDE == 1 || DIR < 0) {
+    vRp = __shfl_down_sync(full, v[0], 1);
+    if (edge) vRp = __ldg(vin + fR);
+  }
+  // Every face takes its synchronous flux here; at PE faces the face pass that follows
+  // the stage replaces it by the delayed / AT flux (a correction of the two elements).
+  double jL = 0.0, jR = 0.0;
+  if (PDE == 0) {
+    // Face values in trace units (the flux is a times the value).
+    if (DIR > 0) jL = __dsub_rn(v[0], vLm);
+    else jR = __dsub_rn(v[NP - 1], vRp);
+  } else {
+    const double FL = num_flux<1>(0.0, vLm, v[0]);
+    double FR = __shfl_down_sync(full, FL, 1);
+    if (edge) FR = num_flux<1>(0.0, v[NP - 1], vRp);
+    jL = __dsub_rn(phys_flux<1>(0.0, v[0]), FL);
+    jR = __dsub_rn(phys_flux<1>(0.0, v[NP - 1]), FR);
+  }
+
   double g[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) g[i] = PDE == 0 ? v[i] : v[i] * v[i];
-  const double jL = __dsub_rn(phys_flux<PDE>(inst.a, v[0]), FL);
-  const double jR = __dsub_rn(phys_flux<PDE>(inst.a, v[NP - 1]), FR);
 
   double out[NP];
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
     double acc;
-    if (STAGE == 0) {
-      acc = v[i];
+    if (PDE == 0) {
+      acc = STAGE == 0 ? C.A[i * NP] * g[0] : fma(C.A[i * NP], g[0], C.alpha * u[i]);
     } else {
-      const double ui = inst.u[(size_t)i * K + ec];
-      acc = fma(C.beta, v[i], C.alpha * ui);
+      acc = STAGE == 0 ? v[i] : fma(C.beta, v[i], C.alpha * u[i]);
+      acc = fma(C.A[i * NP], g[0], acc);
     }
 #pragma unroll
-    for (int jj = 0; jj < NP; ++jj) acc = fma(C.Dm[i * NP + jj], g[jj], acc);
+    for (int jj = 1; jj < NP; ++jj) acc = fma(C.A[i * NP + jj], g[jj], acc);
     out[i] = acc;
   }
-  if (jL != 0.0) {
+  if (PDE == 1 || DIR > 0) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) out[i] = fma(C.liftL[i], jL, out[i]);
+    for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], jL, out[i]);
   }
-  if (jR != 0.0) {
+  if (PDE == 1 || DIR < 0) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) out[i] = fma(C.liftR[i], jR, out[i]);
+    for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], jR, out[i]);
   }
   if (e < K) {
 #pragma unroll
@@ -140,21 +161,93 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n) {
   }
 }
 
-template <int NP, int PDE, int STAGE, bool ASYNC>
-__global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
-  const int e = blockIdx.x * kTile + threadIdx.x;
-  const int64_t n = ASYNC ? inst.meta[0] + rel : 0;
-  stage_body<NP, PDE, STAGE, ASYNC>(inst, e, n);
+template <int NP, int PDE, int STAGE, int DIR>
+__global__ void __launch_bounds__(kTile) k_stage(const Inst inst) {
+  stage_body<NP, PDE, STAGE, DIR>(inst, blockIdx.x * kTile + threadIdx.x);
+}
+
+// Face pass of one stage, run after the stage kernel. For PE face j (between elements
+// e-1 = j Kpe - 1 and e = j Kpe) it reads the stage-input traces, forms the synchronous
+// face value Vs and the delayed / AT value V from the ring, writes the traces into the ring
+// slot of step n, and replaces the synchronous flux by the delayed one in both elements:
+// out^e += lL (Vs - V), out^{e-1} += lR (Vs - V) (the flux enters the stage linearly through
+// the lift terms). With Kpe == 1 an element borders two PE faces; then thread j owns
+// element j and applies the corrections of both its faces.
+template <int PDE, int DIR, class I>
+__device__ __forceinline__ double face_delta(const I &inst, const double *vin, int j, int64_t n,
+                                             int stage, bool owner) {
+  const int K = inst.K;
+  const int e = j * inst.Kpe;
+  const double tl = vin[(size_t)(inst.Np - 1) * K + (e == 0 ? K - 1 : e - 1)];
+  const double tr = vin[e];
+  const double Vs = face_value<PDE, DIR>(inst, tl, tr);
+  const double V = pe_value<PDE, DIR>(inst, j, n, stage, tl, tr, owner);
+  return __dsub_rn(Vs, V);
+}
+
+template <class I>
+__device__ __forceinline__ void apply_delta(const I &inst, double *out, int e, const double *lift,
+                                            double d) {
+  if (!nonzero(d)) return;
+  const int K = inst.K;
+  for (int i = 0; i < inst.Np; ++i) out[(size_t)i * K + e] = fma(lift[i], d, out[(size_t)i * K + e]);
+}
+
+template <int PDE, int DIR, class I>
+__device__ __forceinline__ void face_body(const I &inst, int stage, int j, int64_t n) {
+  const double *vin = stage == 0 ? inst.u : (stage == 1 ? inst.v1 : inst.v2);
+  double *out = stage == 0 ? inst.v1 : (stage == 1 ? inst.v2 : inst.u);
+  const StageConsts &C = inst.sc[stage];
+  const int K = inst.K;
+  if (inst.Kpe > 1) {
+    const double d = face_delta<PDE, DIR>(inst, vin, j, n, stage, true);
+    const int e = j * inst.Kpe;
+    apply_delta(inst, out, e, C.lL, d);
+    apply_delta(inst, out, e == 0 ? K - 1 : e - 1, C.lR, d);
+  } else {
+    // element j borders faces j (left) and j+1 (right); the right face's value is formed
+    // again here with the same arithmetic as by its owner, so both agree bit for bit.
+    const double dL = face_delta<PDE, DIR>(inst, vin, j, n, stage, true);
+    const double dR = face_delta<PDE, DIR>(inst, vin, j + 1 == inst.P ? 0 : j + 1, n, stage, false);
+    double *o = out;
+    if (nonzero(dL) || nonzero(dR)) {
+      for (int i = 0; i < inst.Np; ++i) {
+        double x = o[(size_t)i * K + j];
+        if (nonzero(dL)) x = fma(C.lL[i], dL, x);
+        if (nonzero(dR)) x = fma(C.lR[i], dR, x);
+        o[(size_t)i * K + j] = x;
+      }
+    }
+  }
+}
+
+template <int PDE, int DIR>
+__global__ void __launch_bounds__(256) k_faces(const Inst inst, int stage, int rel) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= inst.P) return;
+  face_body<PDE, DIR>(inst, stage, j, inst.meta[0] + rel);
+}
+
+__global__ void __launch_bounds__(256) k_batch_faces(const Inst *__restrict__ insts,
+                                                     const int2 *__restrict__ work, int stage,
+                                                     int rel) {
+  const int2 w = work[blockIdx.x];
+  const Inst &I = insts[w.x];
+  const int j = w.y + threadIdx.x;
+  if (j >= I.P) return;
+  const int64_t n = I.meta[0] + rel;
+  if (I.pde == 1) face_body<1, 0>(I, stage, j, n);
+  else if (I.a >= 0.0) face_body<0, 1>(I, stage, j, n);
+  else face_body<0, -1>(I, stage, j, n);
 }
 
 template <int STAGE, int NP>
-__device__ __forceinline__ void batch_dispatch_pde(const Inst &I, int e, int64_t n) {
+__device__ __forceinline__ void batch_dispatch_pde(const Inst &I, int e) {
   if (I.pde == 0) {
-    if (I.async) stage_body<NP, 0, STAGE, true>(I, e, n);
-    else stage_body<NP, 0, STAGE, false>(I, e, n);
+    if (I.a >= 0.0) stage_body<NP, 0, STAGE, 1>(I, e);
+    else stage_body<NP, 0, STAGE, -1>(I, e);
   } else {
-    if (I.async) stage_body<NP, 1, STAGE, true>(I, e, n);
-    else stage_body<NP, 1, STAGE, false>(I, e, n);
+    stage_body<NP, 1, STAGE, 0>(I, e);
   }
 }
 
@@ -162,7 +255,7 @@ __device__ __forceinline__ void batch_dispatch_pde(const Inst &I, int e, int64_t
 // descriptor is staged in shared memory, then the element code runs as above.
 template <int STAGE>
 __global__ void __launch_bounds__(kTile) k_batch_stage(const Inst *__restrict__ insts,
-                                                       const int2 *__restrict__ work, int rel) {
+                                                       const int2 *__restrict__ work) {
   __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
   const int2 w = work[blockIdx.x];
   {
@@ -174,12 +267,11 @@ __global__ void __launch_bounds__(kTile) k_batch_stage(const Inst *__restrict__ 
   __syncthreads();
   const Inst &I = *reinterpret_cast<const Inst *>(smem);
   const int e = w.y + threadIdx.x;
-  const int64_t n = I.async ? I.meta[0] + rel : 0;
   switch (I.Np) {
-    case 2: batch_dispatch_pde<STAGE, 2>(I, e, n); break;
-    case 3: batch_dispatch_pde<STAGE, 3>(I, e, n); break;
-    case 4: batch_dispatch_pde<STAGE, 4>(I, e, n); break;
-    default: batch_dispatch_pde<STAGE, 5>(I, e, n); break;
+    case 2: batch_dispatch_pde<STAGE, 2>(I, e); break;
+    case 3: batch_dispatch_pde<STAGE, 3>(I, e); break;
+    case 4: batch_dispatch_pde<STAGE, 4>(I, e); break;
+    default: batch_dispatch_pde<STAGE, 5>(I, e); break;
   }
 }
 
@@ -280,28 +372,27 @@ __global__ void __launch_bounds__(kRedThreads)
   if (threadIdx.x == 0) out[0] = (kind == 0 || kind == 3) ? sh[0] * scale : sh[0];
 }
 
-template <int NP, int PDE, int STAGE>
+template <int NP, int PDE, int STAGE, int DIR>
 cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
+  (void)rel;
   const unsigned grid = (unsigned)((I.K + kTile - 1) / kTile);
-  if (I.async)
-    k_stage<NP, PDE, STAGE, true><<<grid, kTile, 0, s>>>(I, rel);
-  else
-    k_stage<NP, PDE, STAGE, false><<<grid, kTile, 0, s>>>(I, rel);
+  k_stage<NP, PDE, STAGE, DIR><<<grid, kTile, 0, s>>>(I);
   return cudaGetLastError();
 }
 
-template <int NP, int PDE>
+template <int NP, int PDE, int DIR>
 cudaError_t launch_np_pde(const Inst &I, int stage, int rel, cudaStream_t s) {
   switch (stage) {
-    case 0: return launch_np_pde_stage<NP, PDE, 0>(I, rel, s);
-    case 1: return launch_np_pde_stage<NP, PDE, 1>(I, rel, s);
-    default: return launch_np_pde_stage<NP, PDE, 2>(I, rel, s);
+    case 0: return launch_np_pde_stage<NP, PDE, 0, DIR>(I, rel, s);
+    case 1: return launch_np_pde_stage<NP, PDE, 1, DIR>(I, rel, s);
+    default: return launch_np_pde_stage<NP, PDE, 2, DIR>(I, rel, s);
   }
 }
 
 template <int NP>
 cudaError_t launch_np(const Inst &I, int stage, int rel, cudaStream_t s) {
-  return I.pde == 0 ? launch_np_pde<NP, 0>(I, stage, rel, s) : launch_np_pde<NP, 1>(I, stage, rel, s);
+  if (I.pde == 1) return launch_np_pde<NP, 1, 0>(I, stage, rel, s);
+  return I.a >= 0.0 ? launch_np_pde<NP, 0, 1>(I, stage, rel, s) : launch_np_pde<NP, 0, -1>(I, stage, rel, s);
 }
 
 }  // namespace
@@ -320,10 +411,24 @@ cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int 
                                int rel, int tile, cudaStream_t s) {
   (void)tile;
   switch (stage) {
-    case 0: k_batch_stage<0><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, rel); break;
-    case 1: k_batch_stage<1><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, rel); break;
-    default: k_batch_stage<2><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, rel); break;
+    case 0: k_batch_stage<0><<<nwork, kTile, 0, s>>>(insts_dev, work_dev); break;
+    case 1: k_batch_stage<1><<<nwork, kTile, 0, s>>>(insts_dev, work_dev); break;
+    default: k_batch_stage<2><<<nwork, kTile, 0, s>>>(insts_dev, work_dev); break;
   }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_faces(const Inst &I, int stage, int rel, cudaStream_t s) {
+  const unsigned grid = (unsigned)((I.P + 255) / 256);
+  if (I.pde == 1) k_faces<1, 0><<<grid, 256, 0, s>>>(I, stage, rel);
+  else if (I.a >= 0.0) k_faces<0, 1><<<grid, 256, 0, s>>>(I, stage, rel);
+  else k_faces<0, -1><<<grid, 256, 0, s>>>(I, stage, rel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int nwork, int stage,
+                               int rel, cudaStream_t s) {
+  if (nwork > 0) k_batch_faces<<<nwork, 256, 0, s>>>(insts_dev, work_dev, stage, rel);
   return cudaGetLastError();
 }
 
