@@ -151,6 +151,31 @@ int adg_integral(adg_ctx *c, int32_t index, double *out);
 int adg_check_finite(adg_ctx *c);
 
 /*
+ * Same value as adg_integral, sum_e (dx/2) w^T u^e, but for a caller's own field and
+ * without allocating anything. The paper has no counterpart; this entry point exists for
+ * callers that must not allocate device memory where they call it: code inside a framework
+ * that hands out all device memory from its own pool, processes running under a fixed
+ * device-memory cap, and latency-critical loops that cannot afford cudaMalloc, which may
+ * synchronise the device.
+ *   p, K    : degree (1..ADG_MAX_P) and element count (1..2^30).
+ *   dx      : element width (> 0).
+ *   u_dev   : device (K, p+1) row-major FP64 field (read only, caller-owned).
+ *   out_dev : device pointer to one double that receives the integral (caller-owned).
+ *   stream  : cudaStream_t (as void*), NULL for the default stream; the call is queued on
+ *             it and returns without synchronising.
+ * Scratch: a fixed 8 KiB array of 1024 partial sums compiled into the library; each GPU
+ * that loads the library holds it until the process exits. Its device address is looked
+ * up on the first call made on each device, so make that first call outside any stream
+ * capture. Every call shares the array and it keeps the last call's contents (each call
+ * overwrites every partial it reads), so calls whose work overlaps on the GPU (other
+ * streams, other host threads) race; order them on one stream. Nothing is allocated or
+ * freed. Errors: ADG_EINVAL for sizes outside the limits above or NULL pointers,
+ * ADG_ECUDA for CUDA failures (message in adg_last_error(NULL)).
+ */
+int adg_integral_noalloc(int32_t p, int32_t K, double dx, const double *u_dev, double *out_dev,
+                         void *stream);
+
+/*
  * Write the delay table the library uses for cfg (seeded or caller table) for steps
  * first_step .. first_step+steps-1 into out_host (uint8 [steps][P]). Host only; needs no
  * GPU. Errors: ADG_EINVAL.

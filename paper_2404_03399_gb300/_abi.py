@@ -21,6 +21,7 @@ EXPORTS = [
     "adg_config_default", "adg_init", "adg_batch_init", "adg_step", "adg_run",
     "adg_get_state", "adg_get_dt", "adg_grad", "adg_integral", "adg_check_finite",
     "adg_delay_table", "adg_eval_modes", "adg_lgl_nodes", "adg_last_error", "adg_destroy",
+    "adg_integral_noalloc",
 ]
 
 
@@ -76,6 +77,7 @@ def load(require: bool = True):
         "adg_lgl_nodes": (C.c_int, [i32, dp, dp]),
         "adg_last_error": (C.c_char_p, [vp]),
         "adg_destroy": (None, [vp]),
+        "adg_integral_noalloc": (C.c_int, [i32, i32, C.c_double, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -533,6 +533,14 @@ int begin_ctx(adg_ctx *c, void *stream) {
 
 }  // namespace
 
+namespace adg {
+void set_last_error(const char *msg) { g_last_error = msg ? msg : ""; }
+void lgl_weights(int p, double *w) {
+  Ops o = make_ops(p);
+  for (int i = 0; i <= p; ++i) w[i] = (double)o.w[i];
+}
+}  // namespace adg
+
 // ---------------------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------------------

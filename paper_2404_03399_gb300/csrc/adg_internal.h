@@ -71,4 +71,9 @@ cudaError_t launch_reduce(int kind, const double *u, const double *g, int K, int
                           int nblocks, double *out, cudaStream_t s);
 int reduce_blocks(int K);
 
+// Host helpers shared by the library's translation units (adg_api.cu).
+void set_last_error(const char *msg);
+// LGL quadrature weights of degree p (p+1 values), rounded to FP64.
+void lgl_weights(int p, double *w);
+
 }  // namespace adg
