@@ -36,8 +36,12 @@ STAGES = 3
 # The large advection workload; its Courant number is not fixed by the workload statement
 # and is set inside the stability bound of the delayed self-feedback (sigma (p+1)^2 k < 1
 # for k <= 7 with the AT extrapolation); the work per step does not depend on it.
-WORKLOAD = dict(name="advection_16m", pde="advection", K=1 << 24, p=3, P=16384, L=8, q=3,
-                cfl=0.002, seed=0, modes=([1.0], [1.0], [0.0], 0.0))
+from workloads import ADVECTION_16M as _W16M, batched_instances  # noqa: E402
+
+WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P, L=_W16M.L,
+                q=_W16M.q, cfl=_W16M.cfl, seed=_W16M.seed,
+                modes=(list(_W16M.modes.amp), list(_W16M.modes.kappa), list(_W16M.modes.phase),
+                       _W16M.modes.offset))
 # Algorithmic FP64 work per DOF-stage of upwind advection: (Np + 2) multiply-adds
 # (volume D u, the left lift, the stage combine) = 2 (Np + 2) flops.
 FLOP_PER_DOF_STAGE = 2 * (WORKLOAD["p"] + 1 + 2)
@@ -191,6 +195,32 @@ def e2e_timed(steps: int):
     return max(wall * 1e3, ev0.elapsed_time(ev1)), nbytes
 
 
+def batched_timed(steps: int, warmup: int):
+    """The 512-instance batched workload (uneven K, p, a, L, seeds) advanced by one work
+    list per stage; returns (DOF-stage updates/s, ms per step, total DOF, instances)."""
+    import torch
+    import paper_2404_03399_gb300 as adg
+    ws = batched_instances()
+    cfgs = [adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, a=w.a, cfl=w.cfl, mode=w.mode,
+                       L=w.L, q=w.q, seed=w.seed) for w in ws]
+    u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
+    b = adg.BatchSolver(cfgs, u0s)
+    del u0s
+    ndof = sum(w.K * (w.p + 1) for w in ws)
+    stream = torch.cuda.current_stream()
+    b.step(warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    b.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    b.check_finite()
+    b.close()
+    return ndof * STAGES * steps / (ms * 1e-3), ms / steps, ndof, len(ws)
+
+
 def cpu_oracle_rate(window: int, steps: int):
     """The FP64 oracle as it stands, on the host cores: `steps` SSP-RK3 steps of ADG-AT on
     a contiguous window of `window` elements of the large mesh (its PE faces and delays
@@ -335,6 +365,11 @@ def main():
         line["sync_dg"] = {"value": ndof * STAGES * args.sync_steps / (sms * 1e-3), "unit": UNIT,
                            "ms_per_step": sms / args.sync_steps}
         line["at_over_sync"] = value / ws / line["sync_dg"]["value"]
+        brate, bms, bdof, bn = batched_timed(100, 3)
+        line["batched"] = {"value": brate, "unit": UNIT, "ms_per_step": bms, "instances": bn,
+                           "dof": bdof, "steps": 100,
+                           "workload": "512 advection instances, K log-uniform in [1024, 262144], "
+                                       "p in 1..4, L in 2..8, AT order min(p+1, 3)"}
         ems, nbytes = e2e_timed(args.steps)
         line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
