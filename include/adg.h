@@ -147,6 +147,10 @@ int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_
  * check), into *out (host). Synchronises. */
 int adg_integral(adg_ctx *c, int32_t index, double *out);
 
+/* Misfit J = 1/2 sum_e (dx/2) (u^e - g^e)^T M (u^e - g^e) of instance `index` against a
+ * target g (device (K, p+1) row-major FP64), into *J_out (host). Synchronises. */
+int adg_misfit(adg_ctx *c, int32_t index, const double *target_dev, double *J_out);
+
 /* ADG_ENONFINITE if any instance holds a NaN or Inf, else ADG_OK. Synchronises. */
 int adg_check_finite(adg_ctx *c);
 

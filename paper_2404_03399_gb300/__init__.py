@@ -165,6 +165,13 @@ class Solver:
     def check_finite(self) -> None:
         check(load().adg_check_finite(self.ctx), self.ctx)
 
+    def misfit(self, target: torch.Tensor) -> float:
+        """J = 1/2 ||u - g||_M^2 of the current state against target g."""
+        g = _as_field(target, self.cfg.K, self.Np)
+        J = C.c_double()
+        check(load().adg_misfit(self.ctx, 0, g.data_ptr(), C.byref(J)), self.ctx)
+        return J.value
+
     def grad(self, target: torch.Tensor, nsteps: int, ckpt_every: int = 50):
         """(J, dJ/du0) of J = 1/2 ||u_N - g||_M^2 over nsteps from the current state."""
         g = _as_field(target, self.cfg.K, self.Np)

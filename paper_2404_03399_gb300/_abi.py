@@ -21,7 +21,7 @@ EXPORTS = [
     "adg_config_default", "adg_init", "adg_batch_init", "adg_step", "adg_run",
     "adg_get_state", "adg_get_dt", "adg_grad", "adg_integral", "adg_check_finite",
     "adg_delay_table", "adg_eval_modes", "adg_lgl_nodes", "adg_last_error", "adg_destroy",
-    "adg_integral_noalloc",
+    "adg_integral_noalloc", "adg_misfit",
 ]
 
 
@@ -78,6 +78,7 @@ def load(require: bool = True):
         "adg_last_error": (C.c_char_p, [vp]),
         "adg_destroy": (None, [vp]),
         "adg_integral_noalloc": (C.c_int, [i32, i32, C.c_double, vp, vp, vp]),
+        "adg_misfit": (C.c_int, [vp, i32, vp, dp]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

@@ -38,7 +38,8 @@ def _stale(obj: str, deps) -> bool:
 
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
-    headers = [os.path.join(CSRC, "adg_internal.h"), os.path.join(INCLUDE, "adg.h")]
+    headers = [os.path.join(CSRC, "adg_internal.h"), os.path.join(CSRC, "adg_device.cuh"),
+               os.path.join(INCLUDE, "adg.h")]
     objs, procs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)

@@ -371,19 +371,31 @@ int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, dou
   return ADG_OK;
 }
 
-// Make the device delay table of h cover steps [n, n+count).
-int ensure_table(adg_ctx *c, InstHost &h, int64_t n, int64_t count) {
-  if (!h.I.async) return ADG_OK;
-  if (n >= h.tbase && n + count <= h.tbase + h.TR) return ADG_OK;
-  h.tbase = n;
+// Refill the device delay table of h with the rows of steps [first, first+TR).
+int fill_table(adg_ctx *c, InstHost &h, int64_t first) {
+  h.tbase = first;
   h.host_rows.resize((size_t)h.TR * h.I.P);
-  h.delays.rows(n, h.TR, h.host_rows.data());
+  h.delays.rows(first, h.TR, h.host_rows.data());
   CK(cudaMemcpyAsync(h.table, h.host_rows.data(), h.host_rows.size(), cudaMemcpyHostToDevice,
                      c->stream));
-  int64_t tb = n;
+  int64_t tb = first;
   CK(cudaMemcpyAsync((void *)(h.I.meta + 1), &tb, sizeof(int64_t), cudaMemcpyHostToDevice,
                      c->stream));
   return ADG_OK;
+}
+
+// Make the device delay table of h cover steps [n, n+count) (forward runs).
+int ensure_table(adg_ctx *c, InstHost &h, int64_t n, int64_t count) {
+  if (!h.I.async) return ADG_OK;
+  if (n >= h.tbase && n + count <= h.tbase + h.TR) return ADG_OK;
+  return fill_table(c, h, n);
+}
+
+// Make it cover step n for a sweep that runs backwards (the window ends at n).
+int ensure_table_back(adg_ctx *c, InstHost &h, int64_t n) {
+  if (!h.I.async) return ADG_OK;
+  if (n >= h.tbase && n < h.tbase + h.TR) return ADG_OK;
+  return fill_table(c, h, std::max<int64_t>(0, n - h.TR + 1));
 }
 
 int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double *u0_dev,
@@ -529,6 +541,168 @@ int begin_ctx(adg_ctx *c, void *stream) {
   c->stream = (cudaStream_t)stream;
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
   return finish_init(c);
+}
+
+// Device memory owned for the duration of one adg_grad call.
+struct DevBuf {
+  void *p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  double *d() const { return static_cast<double *>(p); }
+};
+
+int dev_alloc(adg_ctx *c, DevBuf &b, size_t bytes) {
+  if (bytes == 0) return ADG_OK;
+  cudaError_t e = cudaMalloc(&b.p, bytes);
+  if (e != cudaSuccess) {
+    b.p = nullptr;
+    return fail(c, ADG_ENOMEM, std::string("adg_grad: cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  return ADG_OK;
+}
+
+int set_step(adg_ctx *c, InstHost &h, int64_t n) {
+  int64_t v = n;
+  CK(cudaMemcpyAsync((void *)h.I.meta, &v, sizeof(int64_t), cudaMemcpyHostToDevice, c->stream));
+  c->n = n;
+  return ADG_OK;
+}
+
+// One forward step whose stage inputs are recorded: u_work is advanced in place, v1 and v2
+// receive the stage-1 and stage-2 inputs.
+int forward_step_recorded(adg_ctx *c, InstHost &h, double *u_work, double *v1, double *v2) {
+  int r = ensure_table(c, h, c->n, 1);
+  if (r) return r;
+  Inst I = h.I;
+  I.u = u_work;
+  I.v1 = v1;
+  I.v2 = v2;
+  for (int s = 0; s < kStages; ++s) {
+    CK(adg::launch_stage(I, s, 0, c->stream));
+    if (I.async) CK(adg::launch_faces(I, s, 0, c->stream));
+  }
+  CK(adg::launch_advance(c->meta, 2, 1, 1, c->stream));
+  c->n += 1;
+  return ADG_OK;
+}
+
+// adg_grad: forward with checkpoints every C steps, misfit, then segments in reverse: restore
+// the checkpoint, recompute the segment recording the stage inputs (Burgers; the linear
+// advection adjoint needs no forward state), and run the adjoint stages from the last step
+// of the segment to its first. The state of the context is restored at the end.
+int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, double *grad_dev,
+                 double *J_out) {
+  InstHost &h = c->inst[0];
+  Inst &I = h.I;
+  const int K = I.K, Np = I.Np;
+  const size_t nd = (size_t)K * Np;
+  const int64_t n0 = c->n;
+  const int64_t nseg = nsteps == 0 ? 0 : (nsteps + C - 1) / C;
+  const bool states = I.pde == ADG_BURGERS;
+  const int64_t nck = states ? nseg : std::min<int64_t>(nseg, 1);
+  const size_t ring_n = I.async ? (size_t)I.R * kStages * I.P : 0;
+  const int dir = I.a >= 0.0 ? 1 : -1;
+
+  DevBuf g, ck_u, ck_ring, seg, lam, lring;
+  int r = dev_alloc(c, g, nd * sizeof(double));
+  if (!r) r = dev_alloc(c, ck_u, (size_t)nck * nd * sizeof(double));
+  if (!r) r = dev_alloc(c, ck_ring, (size_t)nck * ring_n * sizeof(double2));
+  if (!r && states) r = dev_alloc(c, seg, (size_t)C * kStages * nd * sizeof(double));
+  if (!r) r = dev_alloc(c, lam, 4 * nd * sizeof(double));
+  if (!r) r = dev_alloc(c, lring, ring_n * sizeof(double));
+  if (r) return r;
+  CK(adg::launch_to_internal(target_dev, g.d(), K, Np, c->stream));
+
+  // Forward pass with checkpoints (u^n and the forward ring at each segment start).
+  for (int64_t sidx = 0; sidx < nseg; ++sidx) {
+    if (sidx < nck) {
+      CK(cudaMemcpyAsync(ck_u.d() + sidx * nd, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      if (ring_n)
+        CK(cudaMemcpyAsync(static_cast<double2 *>(ck_ring.p) + sidx * ring_n, I.ring,
+                           ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    }
+    r = adg_step(c, std::min<int64_t>(C, nsteps - sidx * C));
+    if (r) return r;
+  }
+  double J = 0.0;
+  r = reduce(c, h, 3, g.d(), 0.5 * (h.dx / 2.0), &J);
+  if (r) return r;
+
+  double *Lu = lam.d(), *Lacc = lam.d() + nd, *Lv = lam.d() + 2 * nd, *Lv2 = lam.d() + 3 * nd;
+  CK(adg::launch_adj_init(I.u, g.d(), K, Np, h.M, h.dx / 2.0, Lu, c->stream));
+  if (ring_n) CK(cudaMemsetAsync(lring.p, 0, ring_n * sizeof(double), c->stream));
+
+  for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
+    const int64_t start = n0 + sidx * C;
+    const int64_t len = std::min<int64_t>(C, nsteps - sidx * C);
+    if (states) {
+      CK(cudaMemcpyAsync(I.u, ck_u.d() + sidx * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      if (ring_n)
+        CK(cudaMemcpyAsync(I.ring, static_cast<double2 *>(ck_ring.p) + sidx * ring_n,
+                           ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+      r = set_step(c, h, start);
+      if (r) return r;
+      for (int64_t t = 0; t < len; ++t) {
+        double *slot = seg.d() + (size_t)t * kStages * nd;
+        CK(cudaMemcpyAsync(slot, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        r = forward_step_recorded(c, h, I.u, slot + nd, slot + 2 * nd);
+        if (r) return r;
+      }
+    }
+    for (int64_t t = len - 1; t >= 0; --t) {
+      const int64_t n = start + t;
+      r = ensure_table_back(c, h, n);
+      if (r) return r;
+      const double *slot = states ? seg.d() + (size_t)t * kStages * nd : nullptr;
+      for (int s = kStages - 1; s >= 0; --s) {
+        adg::AdjStage A;
+        A.w = s == 2 ? Lu : (s == 1 ? Lv : Lv2);
+        A.v = slot ? slot + (size_t)s * nd : nullptr;
+        A.lv = s == 2 ? Lv : (s == 1 ? Lv2 : nullptr);
+        A.lacc = Lacc;
+        A.K = K;
+        A.Np = Np;
+        A.C = I.sc[s];
+        CK(adg::launch_adj_stage(A, I.pde, s, dir, c->stream));
+        if (I.async) {
+          adg::AdjFace F;
+          F.w = A.w;
+          F.v = A.v;
+          F.target = s == 0 ? Lacc : A.lv;
+          F.lring = lring.d();
+          F.table = I.table;
+          F.meta = I.meta;
+          F.coef = I.coef;
+          F.n = n;
+          F.K = K;
+          F.Np = Np;
+          F.P = I.P;
+          F.Kpe = I.Kpe;
+          F.R = I.R;
+          F.q = I.q;
+          F.stage = s;
+          for (int i = 0; i < adg::kMaxNp; ++i) {
+            F.lL[i] = I.sc[s].lL[i];
+            F.lR[i] = I.sc[s].lR[i];
+          }
+          CK(adg::launch_adj_faces(F, I.pde, dir, c->stream));
+        }
+      }
+      std::swap(Lu, Lacc);
+    }
+  }
+  CK(adg::launch_to_external(Lu, grad_dev, K, Np, c->stream));
+  if (nseg > 0) {
+    CK(cudaMemcpyAsync(I.u, ck_u.d(), nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (ring_n)
+      CK(cudaMemcpyAsync(I.ring, ck_ring.p, ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+    r = set_step(c, h, n0);
+    if (r) return r;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  *J_out = J;
+  return ADG_OK;
 }
 
 }  // namespace
@@ -736,6 +910,19 @@ int adg_integral(adg_ctx *c, int32_t index, double *out) {
   return reduce(c, h, 0, nullptr, h.dx / 2.0, out);
 }
 
+int adg_misfit(adg_ctx *c, int32_t index, const double *target_dev, double *J_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size() || !target_dev || !J_out)
+    return fail(c, ADG_EINVAL, "bad argument");
+  InstHost &h = c->inst[index];
+  const size_t nd = (size_t)h.I.K * h.I.Np;
+  DevBuf g;
+  int r = dev_alloc(c, g, nd * sizeof(double));
+  if (r) return r;
+  CK(adg::launch_to_internal(target_dev, g.d(), h.I.K, h.I.Np, c->stream));
+  return reduce(c, h, 3, g.d(), 0.5 * (h.dx / 2.0), J_out);
+}
+
 int adg_check_finite(adg_ctx *c) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   for (size_t i = 0; i < c->inst.size(); ++i) {
@@ -784,8 +971,11 @@ int adg_lgl_nodes(int32_t p, double *nodes_host, double *weights_host) {
 
 int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_every,
              double *grad_u0_dev, double *J_out) {
-  (void)target_dev; (void)nsteps; (void)ckpt_every; (void)grad_u0_dev; (void)J_out;
-  return fail(c, ADG_ESTATE, "adg_grad: not available in this build");
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (c->batch) return fail(c, ADG_ESTATE, "adg_grad takes a single-instance context");
+  if (nsteps < 0 || ckpt_every < 1) return fail(c, ADG_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
+  if (!target_dev || !grad_u0_dev || !J_out) return fail(c, ADG_EINVAL, "NULL target, gradient or J");
+  return run_gradient(c, target_dev, nsteps, ckpt_every, grad_u0_dev, J_out);
 }
 
 }  // extern "C"

@@ -44,6 +44,34 @@ struct alignas(16) Inst {
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
 
+// Adjoint of one stage (adg_adjoint.cu): w is the adjoint of the stage output, v the stage
+// input (Burgers), lv receives the adjoint of the stage input (stages 1, 2); lacc collects
+// the adjoint of u^n (stage 2 starts it with alpha w, stage 1 adds alpha w, stage 0 adds the
+// adjoint of its input u^n).
+struct AdjStage {
+  const double *w;
+  const double *v;
+  double *lv;
+  double *lacc;
+  int K, Np;
+  StageConsts C;
+};
+
+// Adjoint of the PE-face pass of one stage. The field names shared with Inst (table, meta,
+// coef, P, q, R) let the delay lookup serve both.
+struct AdjFace {
+  const double *w;
+  const double *v;
+  double *target;       // adjoint of the stage input (lacc for stage 0)
+  double *lring;        // [R][3][P] adjoint of the face values of each stored level
+  const uint8_t *table;
+  const int64_t *meta;
+  const double *coef;
+  int64_t n;
+  int K, Np, P, Kpe, R, q, stage;
+  double lL[kMaxNp], lR[kMaxNp];
+};
+
 // Launchers (adg_kernels.cu). All return cudaGetLastError() after the launch.
 cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
 cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
@@ -70,6 +98,12 @@ cudaError_t launch_reduce(int kind, const double *u, const double *g, int K, int
                           const double *w_or_M, double scale, double *partials,
                           int nblocks, double *out, cudaStream_t s);
 int reduce_blocks(int K);
+
+// Adjoint launchers (adg_adjoint.cu); dir is the sign of the advection speed.
+cudaError_t launch_adj_stage(const AdjStage &A, int pde, int stage, int dir, cudaStream_t s);
+cudaError_t launch_adj_faces(const AdjFace &F, int pde, int dir, cudaStream_t s);
+cudaError_t launch_adj_init(const double *u, const double *g, int K, int Np, const double *M,
+                            double scale, double *lam, cudaStream_t s);
 
 // Host helpers shared by the library's translation units (adg_api.cu).
 void set_last_error(const char *msg);
