@@ -36,7 +36,7 @@ STAGES = 3
 # The large advection workload; its Courant number is not fixed by the workload statement
 # and is set inside the stability bound of the delayed self-feedback (sigma (p+1)^2 k < 1
 # for k <= 7 with the AT extrapolation); the work per step does not depend on it.
-from workloads import ADVECTION_16M as _W16M, batched_instances  # noqa: E402
+from workloads import ADJOINT_64K as _WADJ, ADVECTION_16M as _W16M, batched_instances  # noqa: E402
 
 WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P, L=_W16M.L,
                 q=_W16M.q, cfl=_W16M.cfl, seed=_W16M.seed,
@@ -221,6 +221,42 @@ def batched_timed(steps: int, warmup: int):
     return ndof * STAGES * steps / (ms * 1e-3), ms / steps, ndof, len(ws)
 
 
+def adjoint_cost():
+    """Gradient / forward cost on the adjoint workload (Burgers, K = 65536, p = 3, 1024 PEs,
+    delays in {0..3}, AT order 2, 2000 steps, checkpoints every 50): CUDA-event time of
+    adg_grad against the same 2000 forward steps."""
+    import math as _m
+    import torch
+    import paper_2404_03399_gb300 as adg
+    w = _WADJ
+    cfg = adg.Config(pde="burgers", K=w.K, p=w.p, P=w.P, L=w.L, q=w.q, mode="at", cfl=w.cfl,
+                     seed=w.seed)
+    u0 = adg.eval_modes(cfg, w.modes.amp, w.modes.kappa, w.modes.phase, w.modes.offset)
+    g = adg.eval_modes(cfg, [1.0], [1.0], [-0.003], 0.5)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        fn()
+        ev1.record(stream)
+        ev1.synchronize()
+        return ev0.elapsed_time(ev1)
+
+    fwd, grd = [], []
+    for _ in range(3):
+        s = adg.Solver(cfg, u0)
+        fwd.append(timed(lambda: s.step(w.steps)))
+        s.close()
+        s = adg.Solver(cfg, u0)
+        grd.append(timed(lambda: s.grad(g, w.steps, 50)))
+        s.close()
+    f, gms = min(fwd), min(grd)
+    return {"forward_ms": f, "grad_ms": gms, "grad_over_forward": gms / f, "steps": w.steps,
+            "ckpt_every": 50, "workload": "Burgers K=65536 p=3 1024 PEs L=4 AT2, 2000 steps"}
+
+
 def cpu_oracle_rate(window: int, steps: int):
     """The FP64 oracle as it stands, on the host cores: `steps` SSP-RK3 steps of ADG-AT on
     a contiguous window of `window` elements of the large mesh (its PE faces and delays
@@ -370,6 +406,7 @@ def main():
                            "dof": bdof, "steps": 100,
                            "workload": "512 advection instances, K log-uniform in [1024, 262144], "
                                        "p in 1..4, L in 2..8, AT order min(p+1, 3)"}
+        line["adjoint"] = adjoint_cost()
         ems, nbytes = e2e_timed(args.steps)
         line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,

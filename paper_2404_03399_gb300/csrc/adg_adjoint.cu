@@ -158,13 +158,14 @@ __global__ void __launch_bounds__(256) k_adj_faces(const AdjFace F) {
     nu = fma(F.lL[i], F.w[(size_t)i * K + e], nu);
     nu = fma(F.lR[i], F.w[(size_t)i * K + eL], nu);
   }
-  const DelayAt d = delay_at(F, j, F.n);
+  const int64_t n = F.meta[0] + F.rel;
+  const DelayAt d = delay_at(F, j, n);
   const int s = F.stage;
   for (int i = 0; i < d.qe; ++i) {
     const double ci = d.c[i];
-    if (ci != 0.0) F.lring[(ring_slot(F.n - d.k - i, F.R) * kStages + s) * F.P + j] += ci * (-nu);
+    if (ci != 0.0) F.lring[(ring_slot(n - d.k - i, F.R) * kStages + s) * F.P + j] += ci * (-nu);
   }
-  double *slot = F.lring + (ring_slot(F.n, F.R) * kStages + s) * F.P + j;
+  double *slot = F.lring + (ring_slot(n, F.R) * kStages + s) * F.P + j;
   const double r = *slot;
   *slot = 0.0;
   double tl = 0.0, tr = 0.0;

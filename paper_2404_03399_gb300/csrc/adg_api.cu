@@ -569,21 +569,106 @@ int set_step(adg_ctx *c, InstHost &h, int64_t n) {
   return ADG_OK;
 }
 
-// One forward step whose stage inputs are recorded: u_work is advanced in place, v1 and v2
-// receive the stage-1 and stage-2 inputs.
-int forward_step_recorded(adg_ctx *c, InstHost &h, double *u_work, double *v1, double *v2) {
-  int r = ensure_table(c, h, c->n, 1);
-  if (r) return r;
-  Inst I = h.I;
-  I.u = u_work;
-  I.v1 = v1;
-  I.v2 = v2;
-  for (int s = 0; s < kStages; ++s) {
-    CK(adg::launch_stage(I, s, 0, c->stream));
-    if (I.async) CK(adg::launch_faces(I, s, 0, c->stream));
+// Graph of one segment sweep, captured on the context's capture stream.
+struct GraphExec {
+  cudaGraphExec_t g = nullptr;
+  ~GraphExec() {
+    if (g) cudaGraphExecDestroy(g);
   }
-  CK(adg::launch_advance(c->meta, 2, 1, 1, c->stream));
-  c->n += 1;
+};
+
+template <class F>
+int capture(adg_ctx *c, GraphExec &out, F &&body) {
+  cudaStream_t user = c->stream;
+  c->stream = c->cap;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamBeginCapture(c->cap, cudaStreamCaptureModeThreadLocal);
+  if (e != cudaSuccess) {
+    c->stream = user;
+    return fail(c, ADG_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
+  }
+  int r = body();
+  cudaError_t e2 = cudaStreamEndCapture(c->cap, &graph);
+  c->stream = user;
+  if (r) {
+    if (graph) cudaGraphDestroy(graph);
+    return r;
+  }
+  if (e2 != cudaSuccess) return fail(c, ADG_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
+  e = cudaGraphInstantiate(&out.g, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) {
+    out.g = nullptr;
+    return fail(c, ADG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
+  }
+  return ADG_OK;
+}
+
+// Forward over one segment of `len` steps starting at meta[0], recording the stage inputs
+// of step t in slot t of `seg` (u^n, v1, v2); u is advanced in place.
+int sweep_recompute(adg_ctx *c, InstHost &h, double *seg, int len) {
+  const size_t nd = (size_t)h.I.K * h.I.Np;
+  for (int t = 0; t < len; ++t) {
+    double *slot = seg + (size_t)t * kStages * nd;
+    CK(cudaMemcpyAsync(slot, h.I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    Inst I = h.I;
+    I.v1 = slot + nd;
+    I.v2 = slot + 2 * nd;
+    for (int s = 0; s < kStages; ++s) {
+      CK(adg::launch_stage(I, s, t, c->stream));
+      if (I.async) CK(adg::launch_faces(I, s, t, c->stream));
+    }
+  }
+  return ADG_OK;
+}
+
+// Adjoint sweep over one segment, steps len-1 .. 0 after meta[0]; lam[0..1] hold the
+// adjoint of u at the segment's end on entry (index `par`) and of u at its start on exit.
+int sweep_reverse(adg_ctx *c, InstHost &h, const double *seg, double *lam, double *lring, int len,
+                  int par) {
+  Inst &I = h.I;
+  const size_t nd = (size_t)I.K * I.Np;
+  const int dir = I.a >= 0.0 ? 1 : -1;
+  double *Lv = lam + 2 * nd, *Lv2 = lam + 3 * nd;
+  for (int t = len - 1; t >= 0; --t) {
+    double *Lu = lam + (size_t)par * nd, *Lacc = lam + (size_t)(1 - par) * nd;
+    const double *slot = seg ? seg + (size_t)t * kStages * nd : nullptr;
+    for (int s = kStages - 1; s >= 0; --s) {
+      adg::AdjStage A;
+      A.w = s == 2 ? Lu : (s == 1 ? Lv : Lv2);
+      A.v = slot ? slot + (size_t)s * nd : nullptr;
+      A.lv = s == 2 ? Lv : (s == 1 ? Lv2 : nullptr);
+      A.lacc = Lacc;
+      A.K = I.K;
+      A.Np = I.Np;
+      A.C = I.sc[s];
+      CK(adg::launch_adj_stage(A, I.pde, s, dir, c->stream));
+      if (I.async) {
+        adg::AdjFace F;
+        F.w = A.w;
+        F.v = A.v;
+        F.target = s == 0 ? Lacc : A.lv;
+        F.lring = lring;
+        F.table = I.table;
+        F.meta = I.meta;
+        F.coef = I.coef;
+        F.rel = t;
+        F.K = I.K;
+        F.Np = I.Np;
+        F.P = I.P;
+        F.Kpe = I.Kpe;
+        F.R = I.R;
+        F.q = I.q;
+        F.stage = s;
+        for (int i = 0; i < adg::kMaxNp; ++i) {
+          F.lL[i] = I.sc[s].lL[i];
+          F.lR[i] = I.sc[s].lR[i];
+        }
+        CK(adg::launch_adj_faces(F, I.pde, dir, c->stream));
+      }
+    }
+    par = 1 - par;
+  }
   return ADG_OK;
 }
 
@@ -629,69 +714,42 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
   r = reduce(c, h, 3, g.d(), 0.5 * (h.dx / 2.0), &J);
   if (r) return r;
 
-  double *Lu = lam.d(), *Lacc = lam.d() + nd, *Lv = lam.d() + 2 * nd, *Lv2 = lam.d() + 3 * nd;
-  CK(adg::launch_adj_init(I.u, g.d(), K, Np, h.M, h.dx / 2.0, Lu, c->stream));
+  CK(adg::launch_adj_init(I.u, g.d(), K, Np, h.M, h.dx / 2.0, lam.d(), c->stream));
   if (ring_n) CK(cudaMemsetAsync(lring.p, 0, ring_n * sizeof(double), c->stream));
 
+  // Segment sweeps replay graphs captured once per (segment length, buffer parity).
+  GraphExec rec_full, rec_last, rev[2][2];
+  const int64_t last_len = nseg > 0 ? nsteps - (nseg - 1) * C : 0;
+  int par = 0;
   for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
     const int64_t start = n0 + sidx * C;
-    const int64_t len = std::min<int64_t>(C, nsteps - sidx * C);
+    const int len = (int)std::min<int64_t>(C, nsteps - sidx * C);
+    const bool is_last = sidx == nseg - 1 && last_len != C;
+    r = ensure_table(c, h, start, len);
+    if (r) return r;
+    r = set_step(c, h, start);
+    if (r) return r;
     if (states) {
       CK(cudaMemcpyAsync(I.u, ck_u.d() + sidx * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       if (ring_n)
         CK(cudaMemcpyAsync(I.ring, static_cast<double2 *>(ck_ring.p) + sidx * ring_n,
                            ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-      r = set_step(c, h, start);
-      if (r) return r;
-      for (int64_t t = 0; t < len; ++t) {
-        double *slot = seg.d() + (size_t)t * kStages * nd;
-        CK(cudaMemcpyAsync(slot, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-        r = forward_step_recorded(c, h, I.u, slot + nd, slot + 2 * nd);
+      GraphExec &ge = is_last ? rec_last : rec_full;
+      if (!ge.g) {
+        r = capture(c, ge, [&] { return sweep_recompute(c, h, seg.d(), len); });
         if (r) return r;
       }
+      CK(cudaGraphLaunch(ge.g, c->stream));
     }
-    for (int64_t t = len - 1; t >= 0; --t) {
-      const int64_t n = start + t;
-      r = ensure_table_back(c, h, n);
+    GraphExec &gr = rev[is_last ? 1 : 0][par];
+    if (!gr.g) {
+      r = capture(c, gr, [&] { return sweep_reverse(c, h, states ? seg.d() : nullptr, lam.d(), lring.d(), len, par); });
       if (r) return r;
-      const double *slot = states ? seg.d() + (size_t)t * kStages * nd : nullptr;
-      for (int s = kStages - 1; s >= 0; --s) {
-        adg::AdjStage A;
-        A.w = s == 2 ? Lu : (s == 1 ? Lv : Lv2);
-        A.v = slot ? slot + (size_t)s * nd : nullptr;
-        A.lv = s == 2 ? Lv : (s == 1 ? Lv2 : nullptr);
-        A.lacc = Lacc;
-        A.K = K;
-        A.Np = Np;
-        A.C = I.sc[s];
-        CK(adg::launch_adj_stage(A, I.pde, s, dir, c->stream));
-        if (I.async) {
-          adg::AdjFace F;
-          F.w = A.w;
-          F.v = A.v;
-          F.target = s == 0 ? Lacc : A.lv;
-          F.lring = lring.d();
-          F.table = I.table;
-          F.meta = I.meta;
-          F.coef = I.coef;
-          F.n = n;
-          F.K = K;
-          F.Np = Np;
-          F.P = I.P;
-          F.Kpe = I.Kpe;
-          F.R = I.R;
-          F.q = I.q;
-          F.stage = s;
-          for (int i = 0; i < adg::kMaxNp; ++i) {
-            F.lL[i] = I.sc[s].lL[i];
-            F.lR[i] = I.sc[s].lR[i];
-          }
-          CK(adg::launch_adj_faces(F, I.pde, dir, c->stream));
-        }
-      }
-      std::swap(Lu, Lacc);
     }
+    CK(cudaGraphLaunch(gr.g, c->stream));
+    if (len % 2) par = 1 - par;
   }
+  double *Lu = lam.d() + (size_t)par * nd;
   CK(adg::launch_to_external(Lu, grad_dev, K, Np, c->stream));
   if (nseg > 0) {
     CK(cudaMemcpyAsync(I.u, ck_u.d(), nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));

@@ -67,7 +67,7 @@ struct AdjFace {
   const uint8_t *table;
   const int64_t *meta;
   const double *coef;
-  int64_t n;
+  int rel;              // step index = meta[0] + rel (one graph replays for every segment)
   int K, Np, P, Kpe, R, q, stage;
   double lL[kMaxNp], lR[kMaxNp];
 };
