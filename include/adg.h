@@ -52,6 +52,7 @@ enum { ADG_ADVECTION = 0, ADG_BURGERS = 1 };          /* f(u) = a u  |  f(u) = u
 enum { ADG_UPWIND = 0, ADG_LLF = 1 };                 /* Section 6.1 fluxes */
 enum { ADG_SSPRK3 = 3 };                               /* time integrator */
 enum { ADG_SYNC = 0, ADG_ASYNC = 1, ADG_ASYNC_AT = 2 };/* DG | ADG | ADG-AT */
+enum { ADG_VARIANT_AUTO = 0, ADG_VARIANT_STAGED = 1, ADG_VARIANT_COMPOSED = 2 };
 
 #define ADG_MAX_P 4        /* polynomial degree 1..4 (2..5 LGL nodes) */
 #define ADG_MAX_L 16       /* delays 0..L-1 with L <= 16 */
@@ -76,6 +77,11 @@ enum { ADG_SYNC = 0, ADG_ASYNC = 1, ADG_ASYNC_AT = 2 };/* DG | ADG | ADG-AT */
  *   delay_table, table_steps: optional caller table, uint8 [table_steps][P], host memory,
  *               used periodically (row n mod table_steps at step n); overrides the seed.
  *               Every entry must be < L.
+ *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
+ *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
+ *               composed into one stencil per step, with the elements next to PE faces
+ *               recomputed stage by stage (needs K/P >= 8 when there are PE faces). AUTO picks
+ *               COMPOSED where it applies. Both give the same scheme up to rounding.
  */
 typedef struct {
   int32_t pde;
@@ -92,6 +98,7 @@ typedef struct {
   const double *probs;
   const uint8_t *delay_table;
   int64_t table_steps;
+  int32_t variant;
 } adg_config;
 
 /* Fill cfg with defaults: advection, upwind, SSP-RK3, [0, 2 pi], a = 1, cfl = 0.1, sync. */

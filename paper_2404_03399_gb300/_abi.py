@@ -12,6 +12,7 @@ ADG_ADVECTION, ADG_BURGERS = 0, 1
 ADG_UPWIND, ADG_LLF = 0, 1
 ADG_SSPRK3 = 3
 ADG_SYNC, ADG_ASYNC, ADG_ASYNC_AT = 0, 1, 2
+ADG_VARIANT_AUTO, ADG_VARIANT_STAGED, ADG_VARIANT_COMPOSED = 0, 1, 2
 
 STATUS_NAMES = {0: "ADG_OK", -1: "ADG_EINVAL", -2: "ADG_ENOMEM", -3: "ADG_ECUDA",
                 -4: "ADG_ENONFINITE", -5: "ADG_ETIMEOUT", -6: "ADG_ESTATE"}
@@ -34,6 +35,7 @@ class AdgConfig(C.Structure):
         ("mode", C.c_int32), ("L", C.c_int32), ("at_order", C.c_int32),
         ("seed", C.c_uint64), ("probs", C.POINTER(C.c_double)),
         ("delay_table", C.POINTER(C.c_uint8)), ("table_steps", C.c_int64),
+        ("variant", C.c_int32),
     ]
 
 

@@ -239,6 +239,7 @@ std::string check_config(const adg_config *c) {
   if (c->mode != ADG_SYNC && c->mode != ADG_ASYNC && c->mode != ADG_ASYNC_AT) return "bad mode";
   if (c->L < 1 || c->L > ADG_MAX_L) return "L must be in 1..16";
   if (c->at_order < 0 || c->at_order > ADG_MAX_Q) return "at_order must be in 0..5";
+  if (c->variant < ADG_VARIANT_AUTO || c->variant > ADG_VARIANT_COMPOSED) return "bad variant";
   if (c->probs) {
     double s = 0;
     for (int k = 0; k < c->L; ++k) {
@@ -360,6 +361,75 @@ void fold_constants(InstHost &h) {
   }
 }
 
+// Composed step constants (StepConsts in adg_internal.h), built in long double from the
+// unrounded stage constants of upwind advection with a > 0.
+void fold_step_constants(InstHost &h) {
+  const Ops &o = h.ops;
+  const int Np = o.Np;
+  const ld c2 = -2.0L * (ld)h.dt / (ld)h.dx;
+  const ld a = (ld)h.cfg.a;
+  const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
+  const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
+  typedef std::vector<ld> Mat;
+  auto mul = [&](const Mat &X, const Mat &Y) {
+    Mat Z(Np * Np, 0);
+    for (int i = 0; i < Np; ++i)
+      for (int k = 0; k < Np; ++k)
+        for (int j = 0; j < Np; ++j) Z[i * Np + j] += X[i * Np + k] * Y[k * Np + j];
+    return Z;
+  };
+  auto mulv = [&](const Mat &X, const std::vector<ld> &v) {
+    std::vector<ld> z(Np, 0);
+    for (int i = 0; i < Np; ++i)
+      for (int k = 0; k < Np; ++k) z[i] += X[i * Np + k] * v[k];
+    return z;
+  };
+  Mat M[3];
+  std::vector<ld> cv[3];
+  for (int s = 0; s < 3; ++s) {
+    M[s].assign(Np * Np, 0);
+    cv[s].assign(Np, 0);
+    for (int i = 0; i < Np; ++i) {
+      const ld lL = beta[s] * c2 * a * o.Minv[i * Np + 0];
+      for (int j = 0; j < Np; ++j)
+        M[s][i * Np + j] = beta[s] * ((i == j ? 1.0L : 0.0L) + c2 * a * o.D[i * Np + j]);
+      M[s][i * Np + 0] += lL;
+      cv[s][i] = -lL;
+    }
+  }
+  const int p = Np - 1;
+  Mat I(Np * Np, 0);
+  for (int i = 0; i < Np; ++i) I[i * Np + i] = 1;
+  Mat M10 = mul(M[1], M[0]);
+  Mat inner = M10;
+  for (int i = 0; i < Np; ++i) inner[i * Np + i] += alpha[1];
+  Mat G = mul(M[2], inner);
+  for (int i = 0; i < Np; ++i) G[i * Np + i] += alpha[2];
+  std::vector<ld> h0 = mulv(mul(M[2], M[1]), cv[0]);
+  std::vector<ld> h1 = mulv(M[2], cv[1]);
+  std::vector<ld> h2 = cv[2];
+  std::vector<ld> M1c0 = mulv(M[1], cv[0]);
+  std::vector<ld> h3(Np), h4(Np), h5(Np);
+  for (int i = 0; i < Np; ++i) {
+    h3[i] = h1[i] * cv[0][p] + cv[2][i] * M1c0[p];
+    h4[i] = cv[2][i] * cv[1][p];
+    h5[i] = cv[2][i] * cv[1][p] * cv[0][p];
+  }
+  adg::StepConsts &S = h.I.st;
+  std::memset(&S, 0, sizeof(S));
+  for (int i = 0; i < Np; ++i) {
+    for (int j = 0; j < Np; ++j) S.G[i * Np + j] = (double)G[i * Np + j];
+    S.r1[i] = (double)M[0][p * Np + i];
+    S.r2[i] = (double)(M10[p * Np + i] + (i == p ? alpha[1] : 0.0L));
+    S.h[0][i] = (double)h0[i];
+    S.h[1][i] = (double)h1[i];
+    S.h[2][i] = (double)h2[i];
+    S.h[3][i] = (double)h3[i];
+    S.h[4][i] = (double)h4[i];
+    S.h[5][i] = (double)h5[i];
+  }
+}
+
 int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out) {
   const int nb = adg::reduce_blocks(h.I.K);
   const double *wm = kind == 3 ? h.M : h.w;
@@ -459,6 +529,14 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     h.dt = (cfg->cfl * h.dx) / speed;
   }
   fold_constants(h);
+  {
+    const bool eligible = cfg->pde == ADG_ADVECTION && cfg->a > 0 && K >= 8 &&
+                          (!I.async || I.Kpe >= 8);
+    if (cfg->variant == ADG_VARIANT_COMPOSED && !eligible)
+      return fail(c, ADG_EINVAL, "the composed step needs advection with a > 0, K >= 8 and K/P >= 8");
+    I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED && !c->batch) ? 1 : 0;
+    if (I.fused) fold_step_constants(h);
+  }
 
   if (I.async) {
     const int q = h.q_eff, L = cfg->L;
@@ -482,7 +560,10 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   return ADG_OK;
 }
 
+int launch_fused_steps(adg_ctx *c, int nsteps);
+
 int launch_steps(adg_ctx *c, int nsteps) {
+  if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps);
   for (int rel = 0; rel < nsteps; ++rel) {
     for (int s = 0; s < kStages; ++s) {
       if (c->batch) {
@@ -495,6 +576,21 @@ int launch_steps(adg_ctx *c, int nsteps) {
       }
     }
   }
+  CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
+  return ADG_OK;
+}
+
+// Composed steps ping-pong between u and v1; an odd count ends with a copy back into u.
+int launch_fused_steps(adg_ctx *c, int nsteps) {
+  const Inst &I = c->inst[0].I;
+  for (int rel = 0; rel < nsteps; ++rel) {
+    const double *uin = (rel % 2 == 0) ? I.u : I.v1;
+    double *uout = (rel % 2 == 0) ? I.v1 : I.u;
+    CK(adg::launch_fused_step(I, uin, uout, rel, c->stream));
+  }
+  if (nsteps % 2)
+    CK(cudaMemcpyAsync(I.u, I.v1, (size_t)I.K * I.Np * sizeof(double), cudaMemcpyDeviceToDevice,
+                       c->stream));
   CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
   return ADG_OK;
 }

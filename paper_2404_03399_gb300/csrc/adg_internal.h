@@ -29,6 +29,22 @@ struct StageConsts {
   double alpha, beta;
 };
 
+// The three stages of one SSP-RK3 step of upwind advection (a > 0) composed into one
+// stencil over the element and its three upstream neighbours. With M_s = A_s + lL_s e_0^T
+// and c_s = -lL_s (stage s of the folded form above, all faces synchronous):
+//   v1 = M_0 u^e + c_0 p^{e-1},  v2 = alpha_1 u^e + M_1 v1 + c_1 v1_p^{e-1},
+//   u' = alpha_2 u^e + M_2 v2 + c_2 v2_p^{e-1},
+// which expands to
+//   u'^e = G u^e + h_0 p^{e-1} + h_1 s1^{e-1} + h_2 s2^{e-1} + h_3 p^{e-2} + h_4 s1^{e-2}
+//          + h_5 p^{e-3},
+// p^m = u^m_p (right trace), s1^m = r1 . u^m (own part of v1_p^m), s2^m = r2 . u^m (own
+// part of v2_p^m). Cost: Np^2 + 8 Np multiply-adds per element and step.
+struct StepConsts {
+  double G[kMaxNp * kMaxNp];
+  double r1[kMaxNp], r2[kMaxNp];
+  double h[6][kMaxNp];
+};
+
 // One DG instance as the kernels see it. Nodal fields are node-major: field[i*K + e].
 struct alignas(16) Inst {
   double *u;            // u^n, updated in place by stage 3
@@ -39,7 +55,9 @@ struct alignas(16) Inst {
   const double *coef;   // AT coefficients [L][q][q]: coef[(k*q + (q'-1))*q + i]
   double a;
   int K, Np, P, Kpe, R, L, q, pde, async, table_rows;
+  int fused;            // 1: steps use the composed stencil (StepConsts) + PE-face fix-up
   StageConsts sc[kStages];
+  StepConsts st;
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
@@ -83,6 +101,10 @@ cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int 
                                int rel, cudaStream_t s);
 cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t by,
                            cudaStream_t s);
+// Composed step uin -> uout (rel: step offset from meta[0]) and, with PE faces, the fix-up
+// of the elements next to each PE face with the delayed / AT flux.
+cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
+                              cudaStream_t s);
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,
                                int Np, cudaStream_t s);
 cudaError_t launch_to_external(const double *src_nodemajor, double *dst_rowmajor, int K,

@@ -27,12 +27,22 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
   const StageConsts &C = inst.sc[STAGE];
 
   double v[NP];
+  {
+    const double *q = vin + ec;
 #pragma unroll
-  for (int i = 0; i < NP; ++i) v[i] = __ldg(vin + (size_t)i * K + ec);
+    for (int i = 0; i < NP; ++i) {
+      v[i] = __ldg(q);
+      q += K;
+    }
+  }
   double u[NP];
   if (STAGE > 0) {
+    const double *q = inst.u + ec;
 #pragma unroll
-    for (int i = 0; i < NP; ++i) u[i] = inst.u[(size_t)i * K + ec];
+    for (int i = 0; i < NP; ++i) {
+      u[i] = *q;
+      q += K;
+    }
   }
 
   const unsigned full = 0xffffffffu;
@@ -41,7 +51,7 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
   double vLm = 0.0, vRp = 0.0;
   if (PDE == 1 || DIR > 0) {
     vLm = __shfl_up_sync(full, v[NP - 1], 1);
-    if (lane == 0) vLm = __ldg(vin + (size_t)(NP - 1) * K + (ec == 0 ? K - 1 : ec - 1));
+    if (lane == 0) vLm = __ldg(vin + (NP - 1) * K + (ec == 0 ? K - 1 : ec - 1));
   }
   if (PDE == 1 || DIR < 0) {
     vRp = __shfl_down_sync(full, v[0], 1);
@@ -89,14 +99,168 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
     for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], jR, out[i]);
   }
   if (e < K) {
+    double *q = vout + e;
 #pragma unroll
-    for (int i = 0; i < NP; ++i) vout[(size_t)i * K + e] = out[i];
+    for (int i = 0; i < NP; ++i) {
+      *q = out[i];
+      q += K;
+    }
   }
 }
 
 template <int NP, int PDE, int STAGE, int DIR>
 __global__ void __launch_bounds__(kTile) k_stage(const Inst inst) {
   stage_body<NP, PDE, STAGE, DIR>(inst, blockIdx.x * kTile + threadIdx.x);
+}
+
+// Composed SSP-RK3 step of upwind advection (a > 0), all faces synchronous: one thread per
+// element computes p, s1, s2 of its own element (shared with the block through shared
+// memory) and u'^e = G u^e + the rank-6 upstream coupling (StepConsts). The first three
+// threads of a block form the upstream values of the previous block's elements themselves,
+// with the same arithmetic.
+template <int NP>
+__device__ __forceinline__ void own_scalars(const StepConsts &S, const double *u, double &sp,
+                                            double &s1, double &s2) {
+  sp = u[NP - 1];
+  s1 = S.r1[0] * u[0];
+  s2 = S.r2[0] * u[0];
+#pragma unroll
+  for (int j = 1; j < NP; ++j) {
+    s1 = fma(S.r1[j], u[j], s1);
+    s2 = fma(S.r2[j], u[j], s2);
+  }
+}
+
+// Loads the Np nodal values of element e from a node-major field by pointer steps of K
+// (no per-node 64-bit index products).
+template <int NP>
+__device__ __forceinline__ void load_elem(const double *__restrict__ f, int K, int e, double *u) {
+  const double *q = f + e;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    u[i] = __ldg(q);
+    q += K;
+  }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const double *__restrict__ uin,
+                                                      double *__restrict__ uout) {
+  // slots 0..2: the three elements before the block; slot t+3: this thread's element
+  __shared__ double shp[kTile + 3], sh1[kTile + 3], sh2[kTile + 3];
+  const int K = inst.K;
+  const int t = threadIdx.x;
+  const int e0 = blockIdx.x * kTile;
+  const int e = e0 + t;
+  const int ec = e < K ? e : K - 1;
+  const StepConsts &S = inst.st;
+  if (t < 3) {
+    int m = e0 - 3 + t;
+    if (m < 0) m += K;     // K >= 8 on this path
+    double w[NP], a, b, c;
+    load_elem<NP>(uin, K, m, w);
+    own_scalars<NP>(S, w, a, b, c);
+    shp[t] = a;
+    sh1[t] = b;
+    sh2[t] = c;
+  }
+  double u[NP];
+  load_elem<NP>(uin, K, ec, u);
+  double sp, s1, s2;
+  own_scalars<NP>(S, u, sp, s1, s2);
+  shp[t + 3] = sp;
+  sh1[t + 3] = s1;
+  sh2[t + 3] = s2;
+  __syncthreads();
+  const double p1 = shp[t + 2], p2 = shp[t + 1], p3 = shp[t];
+  const double q1 = sh1[t + 2], q2 = sh1[t + 1];
+  const double r1 = sh2[t + 2];
+  double *o = uout + e;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    double acc = S.G[i * NP] * u[0];
+#pragma unroll
+    for (int j = 1; j < NP; ++j) acc = fma(S.G[i * NP + j], u[j], acc);
+    acc = fma(S.h[0][i], p1, acc);
+    acc = fma(S.h[1][i], q1, acc);
+    acc = fma(S.h[2][i], r1, acc);
+    acc = fma(S.h[3][i], p2, acc);
+    acc = fma(S.h[4][i], q2, acc);
+    acc = fma(S.h[5][i], p3, acc);
+    if (e < K) *o = acc;
+    o += K;
+  }
+}
+
+// One stage for one element with the arithmetic of stage_body (advection, a > 0):
+// out = alpha u + A x + lL (x_0 - xl) where xl is the left neighbour's right trace.
+template <int NP, int STAGE>
+__device__ __forceinline__ void stage_elem(const StageConsts &C, const double *u, const double *x,
+                                           double xl, double *out) {
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    double acc = STAGE == 0 ? C.A[i * NP] * x[0] : fma(C.A[i * NP], x[0], C.alpha * u[i]);
+#pragma unroll
+    for (int jj = 1; jj < NP; ++jj) acc = fma(C.A[i * NP + jj], x[jj], acc);
+    out[i] = acc;
+  }
+  const double jL = __dsub_rn(x[0], xl);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], jL, out[i]);
+}
+
+// Stage s over window slots w = s+1 .. 6 with the PE face between slots 3 and 4: the
+// synchronous stage followed by the face correction of k_faces (same arithmetic), and the
+// ring write of the stage-input traces.
+template <int NP, int STAGE>
+__device__ __forceinline__ void fixup_stage(const Inst &I, int j, int64_t n, double (*U)[NP],
+                                            double (*X)[NP], double (*Y)[NP]) {
+  const StageConsts &C = I.sc[STAGE];
+  for (int w = STAGE + 1; w < 7; ++w) stage_elem<NP, STAGE>(C, U[w], X[w], X[w - 1][NP - 1], Y[w]);
+  const double tl = X[3][NP - 1], tr = X[4][0];
+  const double V = pe_value<0, 1>(I, j, n, STAGE, tl, tr, true);
+  const double d = __dsub_rn(face_value<0, 1>(I, tl, tr), V);
+  if (nonzero(d)) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) Y[4][i] = fma(C.lL[i], d, Y[4][i]);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) Y[3][i] = fma(C.lR[i], d, Y[3][i]);
+  }
+}
+
+// PE-face fix-up of a composed step: thread j recomputes, stage by stage, the elements
+// e-1 .. e+2 around PE face j (e = j Kpe) from u of e-4 .. e+2 (no other PE face lies in that
+// window when Kpe >= 8), with the delayed / AT flux at the face, writes the ring entries of
+// the three stages, and overwrites those four elements when the face's delay is nonzero
+// (with zero delay the composed result already holds the synchronous step).
+template <int NP>
+__global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *__restrict__ uin,
+                                                   double *__restrict__ uout, int rel) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= I.P) return;
+  const int K = I.K;
+  const int e = j * I.Kpe;
+  const int64_t n = I.meta[0] + rel;
+  double U[7][NP], V1[7][NP], V2[7][NP], W[7][NP];
+  for (int w = 0; w < 7; ++w) {
+    int m = e - 4 + w;
+    if (m < 0) m += K;
+    if (m >= K) m -= K;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) U[w][i] = uin[(size_t)i * K + m];
+  }
+  fixup_stage<NP, 0>(I, j, n, U, U, V1);
+  fixup_stage<NP, 1>(I, j, n, U, V1, V2);
+  fixup_stage<NP, 2>(I, j, n, U, V2, W);
+  if (delay_at(I, j, n).k != 0) {
+    for (int w = 3; w < 7; ++w) {
+      int m = e - 4 + w;
+      if (m < 0) m += K;
+      if (m >= K) m -= K;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) uout[(size_t)i * K + m] = W[w][i];
+    }
+  }
 }
 
 // Face pass of one stage, run after the stage kernel. For PE face j (between elements
@@ -363,6 +527,26 @@ cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int 
                                int rel, cudaStream_t s) {
   if (nwork > 0) k_batch_faces<<<nwork, 256, 0, s>>>(insts_dev, work_dev, stage, rel);
   return cudaGetLastError();
+}
+
+namespace {
+template <int NP>
+cudaError_t fused_np(const Inst &I, const double *uin, double *uout, int rel, cudaStream_t s) {
+  k_step_fused<NP><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout);
+  if (I.async) k_step_fixup<NP><<<(unsigned)((I.P + 63) / 64), 64, 0, s>>>(I, uin, uout, rel);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
+                              cudaStream_t s) {
+  switch (I.Np) {
+    case 2: return fused_np<2>(I, uin, uout, rel, s);
+    case 3: return fused_np<3>(I, uin, uout, rel, s);
+    case 4: return fused_np<4>(I, uin, uout, rel, s);
+    case 5: return fused_np<5>(I, uin, uout, rel, s);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_advance(int64_t *meta, int stride, int ninst, int64_t by, cudaStream_t s) {

@@ -52,7 +52,8 @@ def test_small_batch_matches_oracle_and_single_runs():
     b.step(steps)
     for i, (c, w) in enumerate(zip(cfgs, ws)):
         got = b.state(i).cpu().numpy()
-        s = adg.Solver(c, u0s[i])
+        cs = adg.Config(**{**c.__dict__, "variant": "staged"})
+        s = adg.Solver(cs, u0s[i])
         s.step(steps)
         single = s.state().cpu().numpy()
         dt = s.dt

@@ -76,23 +76,27 @@ def test_advection_small_stated_config(mode, q):
     assert rel_linf(got, ref) < TOL
 
 
+@pytest.mark.parametrize("variant", ["staged", "composed"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("mode,q", [("sync", 0), ("async", 0), ("at", 0)])
-def test_advection_degrees_and_modes(p, mode, q):
+def test_advection_degrees_and_modes(p, mode, q, variant):
     # AT order p+1 = 5 at p = 4 needs sigma well inside the delayed-feedback bound.
     cfl = 0.002 if p == 4 else 0.01
     cfg = adg.Config(pde="advection", K=96, p=p, P=8, cfl=cfl, mode=mode, L=3, q=q, seed=11,
-                     probs=[0.3, 0.4, 0.3])
+                     probs=[0.3, 0.4, 0.3], variant=variant)
     u0 = dg.modes_initial(PAPER_FIG6, 96, p)
     got, ref, _ = run_pair(cfg, u0, 70)
     assert rel_linf(got, ref) < TOL
 
 
-@pytest.mark.parametrize("K,P", [(300, 10), (257, 1), (1000, 8), (33, 33), (4096 + 768, 19)])
-def test_ragged_sizes(K, P):
+@pytest.mark.parametrize("variant", ["staged", "auto"])
+@pytest.mark.parametrize("K,P", [(300, 10), (257, 1), (1000, 8), (33, 33), (4096 + 768, 19), (8, 1)])
+def test_ragged_sizes(K, P, variant):
     # K not a multiple of the 256-element tile or of the 32-lane warp; P = 1 (no PE
-    # faces, the periodic wrap is interior); P = K (every face a PE face).
-    cfg = adg.Config(pde="advection", K=K, p=3, P=P, cfl=0.01, mode="at", L=4, q=3, seed=5)
+    # faces, the periodic wrap is interior); P = K (every face a PE face, composed step not
+    # applicable); K = 8 (the upstream window wraps around the whole mesh).
+    cfg = adg.Config(pde="advection", K=K, p=3, P=P, cfl=0.01, mode="at", L=4, q=3, seed=5,
+                     variant=variant)
     u0 = random_nodal(K, 3, 17)
     got, ref, _ = run_pair(cfg, u0, 45)
     assert rel_linf(got, ref) < TOL
@@ -124,13 +128,15 @@ def test_caller_tables(kind):
     assert rel_linf(got, ref) < TOL
 
 
-@pytest.mark.parametrize("pde", ["advection", "burgers"])
-def test_zero_delay_is_bitwise_sync(pde):
+@pytest.mark.parametrize("pde,variant", [("advection", "staged"), ("advection", "composed"),
+                                         ("burgers", "auto")])
+def test_zero_delay_is_bitwise_sync(pde, variant):
     K, p, P = 512, 3, 16
     u0 = torch.tensor(dg.modes_initial(HALF_PLUS_SIN if pde == "burgers" else PAPER_FIG6, K, p), device="cuda")
     outs = []
     for mode, table in [("sync", None), ("at", constant_table(1, P, 0)), ("async", constant_table(1, P, 0))]:
-        cfg = adg.Config(pde=pde, K=K, p=p, P=P, cfl=0.02, mode=mode, L=2, q=3, table=table)
+        cfg = adg.Config(pde=pde, K=K, p=p, P=P, cfl=0.02, mode=mode, L=2, q=3, table=table,
+                         variant=variant)
         s = adg.Solver(cfg, u0)
         s.step(70)
         outs.append(s.state().cpu().numpy())
@@ -196,14 +202,15 @@ def _window_oracle(cfg, u0_full_fn, e, steps, dt, table_rows, both_sides):
     return out[r]
 
 
-@pytest.mark.parametrize("which", ["advection_16m", "burgers_1m"])
+@pytest.mark.parametrize("which", ["advection_16m", "advection_16m_staged", "burgers_1m"])
 def test_full_size_sampled(which):
     # Full-size meshes in the launch configuration the benchmark times (graph replay of
     # 32-step chunks plus a direct remainder), checked at sampled elements against the
     # oracle run on a window wide enough to contain each sample's dependence cone.
-    if which == "advection_16m":
+    if which.startswith("advection_16m"):
         w = ADVECTION_16M
-        cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=0.002, mode="at", L=w.L, q=w.q, seed=w.seed)
+        cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode="at", L=w.L, q=w.q,
+                         seed=w.seed, variant="staged" if which.endswith("staged") else "auto")
         modes, steps, both = SIN, 40, False
     else:
         w = BURGERS_1M
