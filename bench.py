@@ -42,9 +42,16 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
                 q=_W16M.q, cfl=_W16M.cfl, seed=_W16M.seed,
                 modes=(list(_W16M.modes.amp), list(_W16M.modes.kappa), list(_W16M.modes.phase),
                        _W16M.modes.offset))
-# Algorithmic FP64 work per DOF-stage of upwind advection: (Np + 2) multiply-adds
-# (volume D u, the left lift, the stage combine) = 2 (Np + 2) flops.
-FLOP_PER_DOF_STAGE = 2 * (WORKLOAD["p"] + 1 + 2)
+# Algorithmic FP64 work of the kernel that runs the bench step (the composed SSP-RK3 step of
+# upwind advection): Np^2 + 8 Np multiply-adds per element and step = 2 (Np + 8) flop per
+# DOF-step. The staged formulation counts (Np + 2) multiply-adds per DOF-stage
+# (= 2 (Np + 2) flop), 1.5x more at p = 3; both figures are reported.
+NP = WORKLOAD["p"] + 1
+FLOP_PER_DOF_STEP = 2 * (NP + 8)
+FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
+# DRAM bytes per launch of k_step_fused measured by ncu on this workload (read + write), or
+# None when the kernel has changed since the counters were taken.
+TRAFFIC_BYTES_PER_LAUNCH = None
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 GRAPH_STEPS = 32
@@ -366,19 +373,17 @@ def main():
 
     hbm_gbs, hbm_src, fp64_tflops = peaks()
     ms_step = ms / args.steps
-    launch_ms = ms_step / STAGES
-    flop_per_launch = ndof * FLOP_PER_DOF_STAGE
+    # one k_step_fused launch (plus its PE-face fix-up, charged to it) per step
+    launch_ms = ms_step
+    flop_per_launch = ndof * FLOP_PER_DOF_STEP
     achieved_tflops = flop_per_launch / (launch_ms * 1e-3) / 1e12
-    traffic = None
-    try:
-        with open(os.path.join(ROOT, "profiles", "stage_kernel_traffic.json")) as f:
-            traffic = json.load(f).get("bytes_per_launch")
-    except Exception:
-        pass
+    staged_equiv = ndof * STAGES * FLOP_PER_DOF_STAGE_STAGED / (ms_step * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / fp64_tflops, "traffic": traffic,
-                "kernel": "k_stage (fused RHS + SSP-RK3 stage combine, FP64); achieved uses step time / 3, "
-                          "so the PE-face passes (about 1%) are charged to it",
+                "frac": achieved_tflops / fp64_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
+                "kernel": "k_step_fused (composed SSP-RK3 step, FP64, Np^2+8Np FMA per element); "
+                          "the PE-face fix-up launch (about 2%) is charged to it",
+                "flop_per_dof_step": FLOP_PER_DOF_STEP,
+                "staged_count_equivalent_tflops": staged_equiv,
                 "peak_source": "FP64 from unit counts x max SM clock (152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
     hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / (ms_step * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -392,8 +397,9 @@ def main():
             "roofline": roofline,
             "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
                     "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
-            # per step: 3 stage kernels + 3 PE-face passes; one step-counter kernel per chunk
-            "gpu_launches": 2 * STAGES * args.steps + math.ceil(args.steps / GRAPH_STEPS),
+            # per step: the composed-step kernel and the PE-face fix-up; one step-counter
+            # kernel per chunk of GRAPH_STEPS steps
+            "gpu_launches": 2 * args.steps + math.ceil(args.steps / GRAPH_STEPS),
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:

@@ -311,6 +311,7 @@ struct adg_ctx {
   int nwork = 0;
   int2 *fwork_dev = nullptr;   // (instance, first PE face) items of the batched face pass
   int nfwork = 0;
+  bool batch_fused = false;     // every instance runs composed steps
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -534,7 +535,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
                           (!I.async || I.Kpe >= 8);
     if (cfg->variant == ADG_VARIANT_COMPOSED && !eligible)
       return fail(c, ADG_EINVAL, "the composed step needs advection with a > 0, K >= 8 and K/P >= 8");
-    I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED && !c->batch) ? 1 : 0;
+    I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED) ? 1 : 0;
     if (I.fused) fold_step_constants(h);
   }
 
@@ -564,6 +565,14 @@ int launch_fused_steps(adg_ctx *c, int nsteps);
 
 int launch_steps(adg_ctx *c, int nsteps) {
   if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps);
+  if (c->batch && c->batch_fused) {
+    for (int rel = 0; rel < nsteps; ++rel)
+      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
+                                      rel % 2, rel, c->stream));
+    if (nsteps % 2) CK(adg::launch_batch_copy_back(c->insts_dev, c->work_dev, c->nwork, c->stream));
+    CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
+    return ADG_OK;
+  }
   for (int rel = 0; rel < nsteps; ++rel) {
     for (int s = 0; s < kStages; ++s) {
       if (c->batch) {
@@ -978,6 +987,10 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
   if (!r) {
     std::vector<Inst> hi(n);
     std::vector<int2> work, fwork;
+    c->batch_fused = true;
+    for (int i = 0; i < n; ++i) c->batch_fused = c->batch_fused && c->inst[i].I.fused;
+    if (!c->batch_fused)
+      for (int i = 0; i < n; ++i) c->inst[i].I.fused = 0;
     for (int i = 0; i < n; ++i) {
       hi[i] = c->inst[i].I;
       for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));

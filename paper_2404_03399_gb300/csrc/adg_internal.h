@@ -105,6 +105,13 @@ cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t b
 // of the elements next to each PE face with the delayed / AT flux.
 cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
                               cudaStream_t s);
+// Batched composed steps over all instances (parity 0: u -> v1, 1: v1 -> u) and the copy
+// of v1 into u after an odd count.
+cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                                    const int2 *fwork_dev, int nfwork, int parity, int rel,
+                                    cudaStream_t s);
+cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                                   cudaStream_t s);
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,
                                int Np, cudaStream_t s);
 cudaError_t launch_to_external(const double *src_nodemajor, double *dst_rowmajor, int K,

@@ -143,14 +143,16 @@ __device__ __forceinline__ void load_elem(const double *__restrict__ f, int K, i
   }
 }
 
-template <int NP>
-__global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const double *__restrict__ uin,
-                                                      double *__restrict__ uout) {
-  // slots 0..2: the three elements before the block; slot t+3: this thread's element
-  __shared__ double shp[kTile + 3], sh1[kTile + 3], sh2[kTile + 3];
+struct FusedShared {
+  // slots 0..2: the three elements before the block; slot t+3: thread t's element
+  double p[kTile + 3], s1[kTile + 3], s2[kTile + 3];
+};
+
+template <int NP, class I>
+__device__ __forceinline__ void fused_body(const I &inst, const double *__restrict__ uin,
+                                           double *__restrict__ uout, int e0, FusedShared &sh) {
   const int K = inst.K;
   const int t = threadIdx.x;
-  const int e0 = blockIdx.x * kTile;
   const int e = e0 + t;
   const int ec = e < K ? e : K - 1;
   const StepConsts &S = inst.st;
@@ -160,21 +162,21 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
     double w[NP], a, b, c;
     load_elem<NP>(uin, K, m, w);
     own_scalars<NP>(S, w, a, b, c);
-    shp[t] = a;
-    sh1[t] = b;
-    sh2[t] = c;
+    sh.p[t] = a;
+    sh.s1[t] = b;
+    sh.s2[t] = c;
   }
   double u[NP];
   load_elem<NP>(uin, K, ec, u);
   double sp, s1, s2;
   own_scalars<NP>(S, u, sp, s1, s2);
-  shp[t + 3] = sp;
-  sh1[t + 3] = s1;
-  sh2[t + 3] = s2;
+  sh.p[t + 3] = sp;
+  sh.s1[t + 3] = s1;
+  sh.s2[t + 3] = s2;
   __syncthreads();
-  const double p1 = shp[t + 2], p2 = shp[t + 1], p3 = shp[t];
-  const double q1 = sh1[t + 2], q2 = sh1[t + 1];
-  const double r1 = sh2[t + 2];
+  const double p1 = sh.p[t + 2], p2 = sh.p[t + 1], p3 = sh.p[t];
+  const double q1 = sh.s1[t + 2], q2 = sh.s1[t + 1];
+  const double r1 = sh.s2[t + 2];
   double *o = uout + e;
 #pragma unroll
   for (int i = 0; i < NP; ++i) {
@@ -190,6 +192,13 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
     if (e < K) *o = acc;
     o += K;
   }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const double *__restrict__ uin,
+                                                      double *__restrict__ uout) {
+  __shared__ FusedShared sh;
+  fused_body<NP>(inst, uin, uout, blockIdx.x * kTile, sh);
 }
 
 // One stage for one element with the arithmetic of stage_body (advection, a > 0):
@@ -234,10 +243,8 @@ __device__ __forceinline__ void fixup_stage(const Inst &I, int j, int64_t n, dou
 // the three stages, and overwrites those four elements when the face's delay is nonzero
 // (with zero delay the composed result already holds the synchronous step).
 template <int NP>
-__global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *__restrict__ uin,
-                                                   double *__restrict__ uout, int rel) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= I.P) return;
+__device__ __forceinline__ void fixup_body(const Inst &I, int j, const double *__restrict__ uin,
+                                           double *__restrict__ uout, int rel) {
   const int K = I.K;
   const int e = j * I.Kpe;
   const int64_t n = I.meta[0] + rel;
@@ -246,8 +253,12 @@ __global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *_
     int m = e - 4 + w;
     if (m < 0) m += K;
     if (m >= K) m -= K;
+    const double *q = uin + m;
 #pragma unroll
-    for (int i = 0; i < NP; ++i) U[w][i] = uin[(size_t)i * K + m];
+    for (int i = 0; i < NP; ++i) {
+      U[w][i] = *q;
+      q += K;
+    }
   }
   fixup_stage<NP, 0>(I, j, n, U, U, V1);
   fixup_stage<NP, 1>(I, j, n, U, V1, V2);
@@ -257,10 +268,73 @@ __global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *_
       int m = e - 4 + w;
       if (m < 0) m += K;
       if (m >= K) m -= K;
+      double *q = uout + m;
 #pragma unroll
-      for (int i = 0; i < NP; ++i) uout[(size_t)i * K + m] = W[w][i];
+      for (int i = 0; i < NP; ++i) {
+        *q = W[w][i];
+        q += K;
+      }
     }
   }
+}
+
+template <int NP>
+__global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *__restrict__ uin,
+                                                   double *__restrict__ uout, int rel) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= I.P) return;
+  fixup_body<NP>(I, j, uin, uout, rel);
+}
+
+// Batched composed steps: block b takes work item (instance, first element); `parity`
+// selects the ping-pong direction (0: u -> v1, 1: v1 -> u) shared by every instance.
+__global__ void __launch_bounds__(kTile) k_batch_fused(const Inst *__restrict__ insts,
+                                                       const int2 *__restrict__ work, int parity) {
+  __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
+  __shared__ FusedShared sh;
+  const int2 w = work[blockIdx.x];
+  {
+    const int4 *src = reinterpret_cast<const int4 *>(insts + w.x);
+    int4 *dst = reinterpret_cast<int4 *>(smem);
+    for (int t = threadIdx.x; t < (int)(sizeof(Inst) / sizeof(int4)); t += blockDim.x)
+      dst[t] = __ldg(src + t);
+  }
+  __syncthreads();
+  const Inst &I = *reinterpret_cast<const Inst *>(smem);
+  const double *uin = parity ? I.v1 : I.u;
+  double *uout = parity ? I.u : I.v1;
+  switch (I.Np) {
+    case 2: fused_body<2>(I, uin, uout, w.y, sh); break;
+    case 3: fused_body<3>(I, uin, uout, w.y, sh); break;
+    case 4: fused_body<4>(I, uin, uout, w.y, sh); break;
+    default: fused_body<5>(I, uin, uout, w.y, sh); break;
+  }
+}
+
+__global__ void __launch_bounds__(64) k_batch_fixup(const Inst *__restrict__ insts,
+                                                    const int2 *__restrict__ fwork, int parity,
+                                                    int rel) {
+  const int2 w = fwork[blockIdx.y];
+  const Inst &I = insts[w.x];
+  const int j = w.y + blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= I.P || blockIdx.x * blockDim.x + threadIdx.x >= 256) return;
+  const double *uin = parity ? I.v1 : I.u;
+  double *uout = parity ? I.u : I.v1;
+  switch (I.Np) {
+    case 2: fixup_body<2>(I, j, uin, uout, rel); break;
+    case 3: fixup_body<3>(I, j, uin, uout, rel); break;
+    case 4: fixup_body<4>(I, j, uin, uout, rel); break;
+    default: fixup_body<5>(I, j, uin, uout, rel); break;
+  }
+}
+
+// Copies v1 into u for every instance (after an odd number of batched composed steps).
+__global__ void k_batch_copy_back(const Inst *__restrict__ insts, const int2 *__restrict__ work) {
+  const int2 w = work[blockIdx.x];
+  const Inst &I = insts[w.x];
+  const int e = w.y + threadIdx.x;
+  if (e >= I.K) return;
+  for (int i = 0; i < I.Np; ++i) I.u[(size_t)i * I.K + e] = I.v1[(size_t)i * I.K + e];
 }
 
 // Face pass of one stage, run after the stage kernel. For PE face j (between elements
@@ -547,6 +621,20 @@ cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, in
     case 5: return fused_np<5>(I, uin, uout, rel, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                                    const int2 *fwork_dev, int nfwork, int parity, int rel,
+                                    cudaStream_t s) {
+  k_batch_fused<<<nwork, kTile, 0, s>>>(insts_dev, work_dev, parity);
+  if (nfwork > 0) k_batch_fixup<<<dim3(4, nfwork), 64, 0, s>>>(insts_dev, fwork_dev, parity, rel);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                                   cudaStream_t s) {
+  k_batch_copy_back<<<nwork, kTile, 0, s>>>(insts_dev, work_dev);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_advance(int64_t *meta, int stride, int ninst, int64_t by, cudaStream_t s) {

@@ -43,8 +43,24 @@ def _small_batch():
     return ws
 
 
-def test_small_batch_matches_oracle_and_single_runs():
-    ws = _small_batch()
+def _eligible_batch():
+    # every instance admits the composed step (a > 0, K/P >= 8): the batch runs it
+    rng = np.random.default_rng(5)
+    from workloads import Workload
+    ws = []
+    for i, (K, p, P, a, L) in enumerate([(512, 1, 8, 0.7, 3), (2048, 4, 16, 1.9, 5), (777 * 8, 3, 8, 1.1, 8),
+                                          (1024, 2, 1, 1.3, 2), (4096, 3, 64, 0.5, 4)]):
+        modes = Modes(amp=tuple(rng.uniform(0.25, 1.0, 3)), kappa=tuple(float(k) for k in rng.integers(1, 9, 3)),
+                      phase=tuple(rng.uniform(0, 2 * math.pi, 3)))
+        ws.append(Workload(name=f"c{i}", pde="advection", K=K, p=p, P=P, modes=modes, a=a, cfl=0.002,
+                           mode="at", L=L, q=min(p + 1, 3), seed=int(rng.integers(0, 2**62))))
+    return ws
+
+
+@pytest.mark.parametrize("kind", ["mixed", "composed"])
+def test_small_batch_matches_oracle_and_single_runs(kind):
+    ws = _small_batch() if kind == "mixed" else _eligible_batch()
+    single_variant = "staged" if kind == "mixed" else "composed"
     steps = 70
     cfgs = [_cfg(w) for w in ws]
     u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
@@ -52,7 +68,7 @@ def test_small_batch_matches_oracle_and_single_runs():
     b.step(steps)
     for i, (c, w) in enumerate(zip(cfgs, ws)):
         got = b.state(i).cpu().numpy()
-        cs = adg.Config(**{**c.__dict__, "variant": "staged"})
+        cs = adg.Config(**{**c.__dict__, "variant": single_variant})
         s = adg.Solver(cs, u0s[i])
         s.step(steps)
         single = s.state().cpu().numpy()
