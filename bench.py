@@ -228,10 +228,10 @@ def batched_timed(steps: int, warmup: int):
     return ndof * STAGES * steps / (ms * 1e-3), ms / steps, ndof, len(ws)
 
 
-def adjoint_cost():
+def adjoint_cost(steps: int = 0, repeats: int = 3):
     """Gradient / forward cost on the adjoint workload (Burgers, K = 65536, p = 3, 1024 PEs,
     delays in {0..3}, AT order 2, 2000 steps, checkpoints every 50): CUDA-event time of
-    adg_grad against the same 2000 forward steps."""
+    adg_grad against the same forward steps."""
     import math as _m
     import torch
     import paper_2404_03399_gb300 as adg
@@ -251,16 +251,17 @@ def adjoint_cost():
         ev1.synchronize()
         return ev0.elapsed_time(ev1)
 
+    nsteps = steps or w.steps
     fwd, grd = [], []
-    for _ in range(3):
+    for _ in range(repeats):
         s = adg.Solver(cfg, u0)
-        fwd.append(timed(lambda: s.step(w.steps)))
+        fwd.append(timed(lambda: s.step(nsteps)))
         s.close()
         s = adg.Solver(cfg, u0)
-        grd.append(timed(lambda: s.grad(g, w.steps, 50)))
+        grd.append(timed(lambda: s.grad(g, nsteps, 50)))
         s.close()
     f, gms = min(fwd), min(grd)
-    return {"forward_ms": f, "grad_ms": gms, "grad_over_forward": gms / f, "steps": w.steps,
+    return {"forward_ms": f, "grad_ms": gms, "grad_over_forward": gms / f, "steps": nsteps,
             "ckpt_every": 50, "workload": "Burgers K=65536 p=3 1024 PEs L=4 AT2, 2000 steps"}
 
 
@@ -349,6 +350,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip sync-DG and e2e runs")
     ap.add_argument("--ref-window", type=int, default=1 << 22)
+    ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
+                    help="only time adg_grad against the forward on the adjoint workload for STEPS "
+                         "steps (one repeat) and print that dict (for profiling runs)")
     args = ap.parse_args()
 
     rank, ws, local, dist = dist_setup()
@@ -362,6 +366,9 @@ def main():
     import paper_2404_03399_gb300 as adg
     torch.cuda.set_device(local)
     adg.load()
+    if args.adjoint_only:
+        print(json.dumps(adjoint_cost(args.adjoint_only, 1)), flush=True)
+        return
     barrier = (lambda: dist.barrier()) if dist is not None else (lambda: None)
 
     K, p = WORKLOAD["K"], WORKLOAD["p"]

@@ -20,12 +20,12 @@ namespace {
 //   F = 1/2 (uL^2/2 + uR^2/2) - 1/2 lam (uR - uL),  lam = max(|uL|, |uR|),
 // with lam taken from uL when |uL| >= |uR| and d|u|/du = +1 for u >= 0, -1 otherwise.
 __device__ __forceinline__ void llf_partials(double uL, double uR, double &dL, double &dR) {
-  const double aL = fabs(uL), aR = fabs(uR);
-  const double lam = fmax(aL, aR);
+  const bool fromL = abs_bits(uL) >= abs_bits(uR);
+  const double lam = fromL ? fabs(uL) : fabs(uR);
   const double jump = uR - uL;
   double gL = 0.0, gR = 0.0;
-  if (aL >= aR) gL = uL >= 0.0 ? 1.0 : -1.0;
-  else gR = uR >= 0.0 ? 1.0 : -1.0;
+  if (fromL) gL = nonneg(uL) ? 1.0 : -1.0;
+  else gR = nonneg(uR) ? 1.0 : -1.0;
   dL = 0.5 * uL + 0.5 * lam - 0.5 * gL * jump;
   dR = 0.5 * uR - 0.5 * lam - 0.5 * gR * jump;
 }
@@ -41,10 +41,10 @@ __device__ __forceinline__ void value_partials(double tl, double tr, double &dL,
   }
 }
 
-template <int NP, int PDE, int STAGE, int DIR>
+template <int NP, int PDE, int STAGE, int DIR, bool FACES>
 __global__ void __launch_bounds__(kTile) k_adj_stage(const AdjStage A) {
   const int K = A.K;
-  const int e = blockIdx.x * kTile + threadIdx.x;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   const int ec = e < K ? e : K - 1;
   const bool edge = (lane == 31) || (ec + 1 >= K);
@@ -127,6 +127,85 @@ __global__ void __launch_bounds__(kTile) k_adj_stage(const AdjStage A) {
     lv[NP - 1] += fromRight;
   }
 
+  if (FACES) {
+    // PE faces among this block's faces (K/P >= 8). Element e is right of PE face j (peL)
+    // or left of PE face jr (peR); both elements form the face's adjoint g themselves:
+    //   nu = sL^e + sR^{e-1}, g = nu + r - [k == 0] nu, r = ring entry of (n, s, j),
+    // and add g times the value's partial derivative to their trace node. The owner (right
+    // element) posts c_i (-nu) to the delayed levels (never to level n) and clears the ring
+    // entry the previous adjoint kernel read (it is read no more).
+    __shared__ int s_first, s_jfirst;
+    const int e0 = blockIdx.x * blockDim.x;
+    if (threadIdx.x == 0) {
+      const int jf = (e0 + A.Kpe - 1) / A.Kpe;
+      s_jfirst = jf;
+      s_first = jf * A.Kpe;
+    }
+    __syncthreads();
+    int jL = -1, jR = -1;
+    {
+      int f = s_first, jf = s_jfirst;
+      for (; f <= e0 + (int)blockDim.x && f < K; f += A.Kpe, ++jf) {
+        if (f == ec) jL = jf;
+        if (f == ec + 1) jR = jf;
+      }
+      if (ec + 1 == K) jR = 0;
+    }
+    if ((jL >= 0 || jR >= 0) && e < K) {
+      const int64_t n = A.meta[0] + A.rel;
+      const int nm = (int)(n % A.R);
+      auto slot_of = [&](int m) {   // ring slot of level n - m
+        int sl = nm - m;
+        if (sl < 0) sl += A.R;
+        return sl;
+      };
+      // neighbour adjoint scalars and traces (direct loads: this branch is rare)
+      double sRm = 0.0, sLp = 0.0;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        sRm = fma(C.lR[i], __ldg(A.w + (size_t)i * K + eL), sRm);
+        sLp = fma(C.lL[i], __ldg(A.w + (size_t)i * K + eR), sLp);
+      }
+      if (jL >= 0) {
+        const double nu = sL + sRm;
+        const DelayAt d = delay_at(A, jL, n);
+        const double r = A.lring[((size_t)nm * kStages + STAGE) * A.P + jL];
+        const double g = d.k == 0 ? r : nu + r;
+        double tl = 0.0, tr = 0.0;
+        if (PDE == 1) {
+          tl = __ldg(A.v + (size_t)(NP - 1) * K + eL);
+          tr = v[0];
+        }
+        double dL, dR;
+        value_partials<PDE, DIR>(tl, tr, dL, dR);
+        lv[0] = fma(g, dR, lv[0]);
+        for (int i = 0; i < d.qe; ++i) {
+          const double ci = d.c[i];
+          if (ci != 0.0 && d.k + i >= 1)
+            A.lring[((size_t)slot_of(d.k + i) * kStages + STAGE) * A.P + jL] += ci * (-nu);
+        }
+        // clear the entry the previous adjoint kernel read: (n, s+1), or (n+1, 0) for s = 2
+        const int pst = STAGE == 2 ? 0 : STAGE + 1;
+        const int psl = STAGE == 2 ? (nm + 1 == A.R ? 0 : nm + 1) : nm;
+        A.lring[((size_t)psl * kStages + pst) * A.P + jL] = 0.0;
+      }
+      if (jR >= 0) {
+        const double nu = sLp + sR;
+        const DelayAt d = delay_at(A, jR, n);
+        const double r = A.lring[((size_t)nm * kStages + STAGE) * A.P + jR];
+        const double g = d.k == 0 ? r : nu + r;
+        double tl = 0.0, tr = 0.0;
+        if (PDE == 1) {
+          tl = v[NP - 1];
+          tr = __ldg(A.v + eR);
+        }
+        double dL, dR;
+        value_partials<PDE, DIR>(tl, tr, dL, dR);
+        lv[NP - 1] = fma(g, dL, lv[NP - 1]);
+      }
+    }
+  }
+
   if (e < K) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
@@ -193,13 +272,19 @@ __global__ void k_adj_init(const double *__restrict__ u, const double *__restric
   }
 }
 
+template <int NP, int PDE, int STAGE, bool FACES>
+cudaError_t adj_launch(const AdjStage &A, int dir, cudaStream_t s) {
+  const int bs = stage_block(A.K);
+  const unsigned grid = (unsigned)((A.K + bs - 1) / bs);
+  if (PDE == 1) k_adj_stage<NP, 1, STAGE, 0, FACES><<<grid, bs, 0, s>>>(A);
+  else if (dir > 0) k_adj_stage<NP, 0, STAGE, 1, FACES><<<grid, bs, 0, s>>>(A);
+  else k_adj_stage<NP, 0, STAGE, -1, FACES><<<grid, bs, 0, s>>>(A);
+  return cudaGetLastError();
+}
+
 template <int NP, int PDE, int STAGE>
 cudaError_t adj_np_pde_stage(const AdjStage &A, int dir, cudaStream_t s) {
-  const unsigned grid = (unsigned)((A.K + kTile - 1) / kTile);
-  if (PDE == 1) k_adj_stage<NP, 1, STAGE, 0><<<grid, kTile, 0, s>>>(A);
-  else if (dir > 0) k_adj_stage<NP, 0, STAGE, 1><<<grid, kTile, 0, s>>>(A);
-  else k_adj_stage<NP, 0, STAGE, -1><<<grid, kTile, 0, s>>>(A);
-  return cudaGetLastError();
+  return A.faces ? adj_launch<NP, PDE, STAGE, true>(A, dir, s) : adj_launch<NP, PDE, STAGE, false>(A, dir, s);
 }
 
 template <int NP, int PDE>

@@ -498,6 +498,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   const size_t nd = (size_t)K * Np;
   CK(cudaMalloc(&h.fields, 3 * nd * sizeof(double)));
   I.u = h.fields;
+  I.unext = h.fields;
   I.v1 = h.fields + nd;
   I.v2 = h.fields + 2 * nd;
   CK(adg::launch_to_internal(u0_dev, I.u, K, Np, c->stream));
@@ -710,15 +711,17 @@ int capture(adg_ctx *c, GraphExec &out, F &&body) {
 }
 
 // Forward over one segment of `len` steps starting at meta[0], recording the stage inputs
-// of step t in slot t of `seg` (u^n, v1, v2); u is advanced in place.
+// of step t in slot t of `seg` (u^n, v1, v2); slot t+1's u receives u^{n+1}, so slot 0's u
+// must hold the segment's first state and slot len's u holds the last.
 int sweep_recompute(adg_ctx *c, InstHost &h, double *seg, int len) {
   const size_t nd = (size_t)h.I.K * h.I.Np;
   for (int t = 0; t < len; ++t) {
     double *slot = seg + (size_t)t * kStages * nd;
-    CK(cudaMemcpyAsync(slot, h.I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
     Inst I = h.I;
+    I.u = slot;
     I.v1 = slot + nd;
     I.v2 = slot + 2 * nd;
+    I.unext = slot + kStages * nd;
     for (int s = 0; s < kStages; ++s) {
       CK(adg::launch_stage(I, s, t, c->stream));
       if (I.async) CK(adg::launch_faces(I, s, t, c->stream));
@@ -747,8 +750,19 @@ int sweep_reverse(adg_ctx *c, InstHost &h, const double *seg, double *lam, doubl
       A.K = I.K;
       A.Np = I.Np;
       A.C = I.sc[s];
+      A.lring = lring;
+      A.table = I.table;
+      A.meta = I.meta;
+      A.coef = I.coef;
+      A.rel = t;
+      A.stage = s;
+      A.P = I.P;
+      A.Kpe = I.Kpe;
+      A.R = I.R;
+      A.q = I.q;
+      A.faces = (I.async && I.Kpe >= 8) ? 1 : 0;
       CK(adg::launch_adj_stage(A, I.pde, s, dir, c->stream));
-      if (I.async) {
+      if (I.async && !A.faces) {
         adg::AdjFace F;
         F.w = A.w;
         F.v = A.v;
@@ -798,13 +812,16 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
   int r = dev_alloc(c, g, nd * sizeof(double));
   if (!r) r = dev_alloc(c, ck_u, (size_t)nck * nd * sizeof(double));
   if (!r) r = dev_alloc(c, ck_ring, (size_t)nck * ring_n * sizeof(double2));
-  if (!r && states) r = dev_alloc(c, seg, (size_t)C * kStages * nd * sizeof(double));
+  if (!r && states) r = dev_alloc(c, seg, ((size_t)C * kStages + 1) * nd * sizeof(double));
   if (!r) r = dev_alloc(c, lam, 4 * nd * sizeof(double));
   if (!r) r = dev_alloc(c, lring, ring_n * sizeof(double));
   if (r) return r;
   CK(adg::launch_to_internal(target_dev, g.d(), K, Np, c->stream));
 
-  // Forward pass with checkpoints (u^n and the forward ring at each segment start).
+  // Forward pass with checkpoints (u^n and the forward ring at each segment start). The last
+  // segment's stage inputs are recorded on the way, so it is not recomputed.
+  GraphExec rec_full, rec_last;
+  const int64_t last_len = nseg > 0 ? nsteps - (nseg - 1) * C : 0;
   for (int64_t sidx = 0; sidx < nseg; ++sidx) {
     if (sidx < nck) {
       CK(cudaMemcpyAsync(ck_u.d() + sidx * nd, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
@@ -812,8 +829,24 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
         CK(cudaMemcpyAsync(static_cast<double2 *>(ck_ring.p) + sidx * ring_n, I.ring,
                            ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
     }
-    r = adg_step(c, std::min<int64_t>(C, nsteps - sidx * C));
-    if (r) return r;
+    const int len = (int)std::min<int64_t>(C, nsteps - sidx * C);
+    if (states && sidx == nseg - 1) {
+      r = ensure_table(c, h, c->n, len);
+      if (!r) r = set_step(c, h, c->n);
+      if (r) return r;
+      CK(cudaMemcpyAsync(seg.d(), I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+      GraphExec &ge = len == C ? rec_full : rec_last;
+      r = capture(c, ge, [&] { return sweep_recompute(c, h, seg.d(), len); });
+      if (r) return r;
+      CK(cudaGraphLaunch(ge.g, c->stream));
+      CK(cudaMemcpyAsync(I.u, seg.d() + (size_t)len * kStages * nd, nd * sizeof(double),
+                         cudaMemcpyDeviceToDevice, c->stream));
+      r = set_step(c, h, c->n + len);
+      if (r) return r;
+    } else {
+      r = adg_step(c, len);
+      if (r) return r;
+    }
   }
   double J = 0.0;
   r = reduce(c, h, 3, g.d(), 0.5 * (h.dx / 2.0), &J);
@@ -823,8 +856,7 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
   if (ring_n) CK(cudaMemsetAsync(lring.p, 0, ring_n * sizeof(double), c->stream));
 
   // Segment sweeps replay graphs captured once per (segment length, buffer parity).
-  GraphExec rec_full, rec_last, rev[2][2];
-  const int64_t last_len = nseg > 0 ? nsteps - (nseg - 1) * C : 0;
+  GraphExec rev[2][2];
   int par = 0;
   for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
     const int64_t start = n0 + sidx * C;
@@ -834,8 +866,8 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
     if (r) return r;
     r = set_step(c, h, start);
     if (r) return r;
-    if (states) {
-      CK(cudaMemcpyAsync(I.u, ck_u.d() + sidx * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    if (states && sidx != nseg - 1) {
+      CK(cudaMemcpyAsync(seg.d(), ck_u.d() + sidx * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
       if (ring_n)
         CK(cudaMemcpyAsync(I.ring, static_cast<double2 *>(ck_ring.p) + sidx * ring_n,
                            ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));

@@ -16,10 +16,24 @@ __device__ __forceinline__ double phys_flux(double a, double u) {
 
 // Numerical flux (Section 6.1): upwind a u^- (a >= 0) or a u^+ (a < 0); local
 // Lax-Friedrichs 1/2 (f(u^-) + f(u^+)) - 1/2 max(|u^-|, |u^+|) (u^+ - u^-) for Burgers.
+// Comparisons and max/abs on FP64 values done on their IEEE bit patterns with integer
+// instructions (exact for finite values; on this part FP64 compares and min/max occupy the
+// FP64 pipe). |x| as bits, max(|a|, |b|), and "x >= 0" (true for +0 and -0).
+__device__ __forceinline__ unsigned long long abs_bits(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffULL;
+}
+__device__ __forceinline__ double abs_max(double a, double b) {
+  const unsigned long long ia = abs_bits(a), ib = abs_bits(b);
+  return __longlong_as_double((long long)(ia >= ib ? ia : ib));
+}
+__device__ __forceinline__ bool nonneg(double x) {
+  return __double_as_longlong(x) >= 0 || abs_bits(x) == 0;
+}
+
 template <int PDE>
 __device__ __forceinline__ double num_flux(double a, double uL, double uR) {
   if (PDE == 0) return __dmul_rn(a, a >= 0.0 ? uL : uR);
-  const double lam = fmax(fabs(uL), fabs(uR));
+  const double lam = abs_max(uL, uR);
   const double avg = __dmul_rn(0.5, __dadd_rn(phys_flux<1>(a, uL), phys_flux<1>(a, uR)));
   return __dsub_rn(avg, __dmul_rn(__dmul_rn(0.5, lam), __dsub_rn(uR, uL)));
 }
@@ -65,30 +79,59 @@ __device__ __forceinline__ double face_value(const I &inst, double uL, double uR
   return num_flux<1>(0.0, uL, uR);
 }
 
+// Ring levels prefetched by pe_value (rings with more levels fall back to dependent loads).
+constexpr int kPrefetchR = 12;
+
 template <int PDE, int DIR, class I>
 __device__ __forceinline__ double pe_value(const I &inst, int j, int64_t n, int s, double tl,
                                         double tr, bool owner) {
   const int P = inst.P;
   const int R = inst.R;
+  // Every slot of this face and stage is loaded up front, in parallel with the delay-table
+  // lookup that decides which of them the sum uses.
+  double2 *col = inst.ring + (size_t)s * P + j;
+  const bool pre = R <= kPrefetchR;
+  double2 T[kPrefetchR];
+  if (pre) {
+    const double2 *q = col;
+#pragma unroll
+    for (int r = 0; r < kPrefetchR; ++r) {
+      if (r < R) T[r] = *q;
+      q += kStages * P;
+    }
+  }
+  const int nm = (int)(n % R);
+  auto fetch = [&](int m) -> double2 {   // traces of level n - m, 1 <= m < R
+    int slot = nm - m;
+    if (slot < 0) slot += R;
+    if (pre) {
+      double2 x = T[0];
+#pragma unroll
+      for (int r = 1; r < kPrefetchR; ++r)
+        if (r == slot) x = T[r];
+      return x;
+    }
+    return col[(size_t)slot * kStages * P];
+  };
   const DelayAt d = delay_at(inst, j, n);
-  const int64_t k = d.k;
+  const int k = d.k;
   const int qe = d.qe;
   const double *c = d.c;
   double V;
   if (k == 0) {
     V = __dmul_rn(c[0], face_value<PDE, DIR>(inst, tl, tr));
   } else {
-    const double2 T = inst.ring[(ring_slot(n - k, R) * kStages + s) * P + j];
-    V = __dmul_rn(c[0], face_value<PDE, DIR>(inst, T.x, T.y));
+    const double2 t0 = fetch(k);
+    V = __dmul_rn(c[0], face_value<PDE, DIR>(inst, t0.x, t0.y));
   }
   for (int i = 1; i < qe; ++i) {
     const double ci = c[i];
     if (ci != 0.0) {
-      const double2 T = inst.ring[(ring_slot(n - k - i, R) * kStages + s) * P + j];
-      V = __dadd_rn(V, __dmul_rn(ci, face_value<PDE, DIR>(inst, T.x, T.y)));
+      const double2 ti = fetch(k + i);
+      V = __dadd_rn(V, __dmul_rn(ci, face_value<PDE, DIR>(inst, ti.x, ti.y)));
     }
   }
-  if (owner) inst.ring[(ring_slot(n, R) * kStages + s) * P + j] = make_double2(tl, tr);
+  if (owner) col[(size_t)nm * kStages * P] = make_double2(tl, tr);
   return V;
 }
 

@@ -12,6 +12,11 @@ constexpr int kMaxQ = 5;
 constexpr int kStages = 3;
 constexpr int kTile = 256;      // elements (threads) per block
 
+// Block size of the one-thread-per-element stage kernels: 256, or 128 when the mesh gives
+// fewer than two 256-blocks per SM of the 152 (small meshes are latency-bound, and smaller
+// blocks spread them over every SM).
+inline int stage_block(int K) { return K < 2 * 152 * 256 ? 128 : 256; }
+
 // Folded constants of one SSP-RK3 stage in Shu-Osher form, v_out = alpha u + beta (v + dt L(v)),
 // with the strong form of Eq. DGscheme
 //   dt L(v) = c2 [ D f(v) + LIFT_L (f(v_0) - F_L) - LIFT_R (f(v_p) - F_R) ],  c2 = -2 dt/dx.
@@ -49,6 +54,7 @@ struct StepConsts {
 struct alignas(16) Inst {
   double *u;            // u^n, updated in place by stage 3
   double *v1, *v2;      // stage outputs 1 and 2
+  double *unext;        // where stage 3 writes u^{n+1}: u itself, except in recorded sweeps
   double2 *ring;        // [R][3][P] traces (u^-, u^+) of stage inputs at PE faces
   const uint8_t *table; // [table_rows][P] delays
   const int64_t *meta;  // meta[0] = step index of rel 0; meta[1] = first table row's step
@@ -73,6 +79,14 @@ struct AdjStage {
   double *lacc;
   int K, Np;
   StageConsts C;
+  // PE faces handled inside the stage kernel (K/P >= 8): the delay lookup fields (names
+  // shared with Inst), the adjoint ring, and the stage index of this kernel.
+  double *lring;
+  const uint8_t *table;
+  const int64_t *meta;
+  const double *coef;
+  int rel, stage, P, Kpe, R, q;
+  int faces;            // 1: this kernel applies the PE-face adjoint (no separate face pass)
 };
 
 // Adjoint of the PE-face pass of one stage. The field names shared with Inst (table, meta,

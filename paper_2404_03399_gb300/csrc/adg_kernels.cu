@@ -23,7 +23,7 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
   const int lane = threadIdx.x & 31;
   const int ec = e < K ? e : K - 1;
   const double *vin = STAGE == 0 ? inst.u : (STAGE == 1 ? inst.v1 : inst.v2);
-  double *vout = STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.u);
+  double *vout = STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.unext);
   const StageConsts &C = inst.sc[STAGE];
 
   double v[NP];
@@ -110,7 +110,7 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
 
 template <int NP, int PDE, int STAGE, int DIR>
 __global__ void __launch_bounds__(kTile) k_stage(const Inst inst) {
-  stage_body<NP, PDE, STAGE, DIR>(inst, blockIdx.x * kTile + threadIdx.x);
+  stage_body<NP, PDE, STAGE, DIR>(inst, blockIdx.x * blockDim.x + threadIdx.x);
 }
 
 // Composed SSP-RK3 step of upwind advection (a > 0), all faces synchronous: one thread per
@@ -367,14 +367,31 @@ __device__ __forceinline__ void apply_delta(const I &inst, double *out, int e, c
 template <int PDE, int DIR, class I>
 __device__ __forceinline__ void face_body(const I &inst, int stage, int j, int64_t n) {
   const double *vin = stage == 0 ? inst.u : (stage == 1 ? inst.v1 : inst.v2);
-  double *out = stage == 0 ? inst.v1 : (stage == 1 ? inst.v2 : inst.u);
+  double *out = stage == 0 ? inst.v1 : (stage == 1 ? inst.v2 : inst.unext);
   const StageConsts &C = inst.sc[stage];
   const int K = inst.K;
   if (inst.Kpe > 1) {
-    const double d = face_delta<PDE, DIR>(inst, vin, j, n, stage, true);
+    // The two elements' outputs are loaded before the ring work so the loads overlap it.
     const int e = j * inst.Kpe;
-    apply_delta(inst, out, e, C.lL, d);
-    apply_delta(inst, out, e == 0 ? K - 1 : e - 1, C.lR, d);
+    const int eL = e == 0 ? K - 1 : e - 1;
+    double oe[kMaxNp], ol[kMaxNp];
+#pragma unroll
+    for (int i = 0; i < kMaxNp; ++i) {
+      if (i < inst.Np) {
+        oe[i] = out[(size_t)i * K + e];
+        ol[i] = out[(size_t)i * K + eL];
+      }
+    }
+    const double d = face_delta<PDE, DIR>(inst, vin, j, n, stage, true);
+    if (nonzero(d)) {
+#pragma unroll
+      for (int i = 0; i < kMaxNp; ++i) {
+        if (i < inst.Np) {
+          out[(size_t)i * K + e] = fma(C.lL[i], d, oe[i]);
+          out[(size_t)i * K + eL] = fma(C.lR[i], d, ol[i]);
+        }
+      }
+    }
   } else {
     // element j borders faces j (left) and j+1 (right); the right face's value is formed
     // again here with the same arithmetic as by its owner, so both agree bit for bit.
@@ -546,8 +563,9 @@ __global__ void __launch_bounds__(kRedThreads)
 template <int NP, int PDE, int STAGE, int DIR>
 cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
   (void)rel;
-  const unsigned grid = (unsigned)((I.K + kTile - 1) / kTile);
-  k_stage<NP, PDE, STAGE, DIR><<<grid, kTile, 0, s>>>(I);
+  const int bs = stage_block(I.K);
+  const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
+  k_stage<NP, PDE, STAGE, DIR><<<grid, bs, 0, s>>>(I);
   return cudaGetLastError();
 }
 
