@@ -469,6 +469,45 @@ int ensure_table_back(adg_ctx *c, InstHost &h, int64_t n) {
   return fill_table(c, h, std::max<int64_t>(0, n - h.TR + 1));
 }
 
+// Autotuner of the composed-step kernel: times one and two elements per thread on a copy
+// of u0 held in the instance's v1/v2 fields (free at this point) and keeps the faster. Both
+// choices compute every element with the same arithmetic, so results do not depend on it.
+int autotune_fused(adg_ctx *c, InstHost &h) {
+  Inst &I = h.I;
+  const size_t nd = (size_t)I.K * I.Np;
+  if (I.K < 4 * 2 * adg::kTile) return ADG_OK;   // tiny meshes: one element per thread
+  CK(cudaMemcpyAsync(I.v1, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  cudaEvent_t a = nullptr, b = nullptr;
+  CK(cudaEventCreate(&a));
+  CK(cudaEventCreate(&b));
+  float best = 1e30f;
+  int best_ept = 1;
+  for (int ept = 1; ept <= 2; ++ept) {
+    Inst T = I;
+    T.ept = ept;
+    float ms = 0.0f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(a, c->stream);
+      for (int k = 0; k < 2; ++k) {
+        CK(adg::launch_fused_step(T, k ? I.v2 : I.v1, k ? I.v1 : I.v2, 0, c->stream, false));
+      }
+      cudaEventRecord(b, c->stream);
+      CK(cudaEventSynchronize(b));
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, a, b);
+      if (rep > 0) ms += t;   // the first repetition warms up
+    }
+    if (ms < best) {
+      best = ms;
+      best_ept = ept;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  I.ept = best_ept;
+  return ADG_OK;
+}
+
 int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double *u0_dev,
                    int64_t *meta_slot) {
   h.cfg = *cfg;
@@ -537,7 +576,14 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     if (cfg->variant == ADG_VARIANT_COMPOSED && !eligible)
       return fail(c, ADG_EINVAL, "the composed step needs advection with a > 0, K >= 8 and K/P >= 8");
     I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED) ? 1 : 0;
-    if (I.fused) fold_step_constants(h);
+    I.ept = 1;
+    if (I.fused) {
+      fold_step_constants(h);
+      if (!c->batch) {
+        int r2 = autotune_fused(c, h);
+        if (r2) return r2;
+      }
+    }
   }
 
   if (I.async) {

@@ -62,6 +62,7 @@ struct alignas(16) Inst {
   double a;
   int K, Np, P, Kpe, R, L, q, pde, async, table_rows;
   int fused;            // 1: steps use the composed stencil (StepConsts) + PE-face fix-up
+  int ept;              // elements per thread of the composed-step kernel (1 or 2, autotuned)
   StageConsts sc[kStages];
   StepConsts st;
 };
@@ -118,7 +119,7 @@ cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t b
 // Composed step uin -> uout (rel: step offset from meta[0]) and, with PE faces, the fix-up
 // of the elements next to each PE face with the delayed / AT flux.
 cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
-                              cudaStream_t s);
+                              cudaStream_t s, bool with_fixup = true);
 // Batched composed steps over all instances (parity 0: u -> v1, 1: v1 -> u) and the copy
 // of v1 into u after an odd count.
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,

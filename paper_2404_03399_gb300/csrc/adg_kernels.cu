@@ -143,18 +143,19 @@ __device__ __forceinline__ void load_elem(const double *__restrict__ f, int K, i
   }
 }
 
+// Scalars of the elements of one block: slots 0..2 hold the three elements before the
+// block, slot 3+m the block's element m (up to 2 kTile elements per block).
 struct FusedShared {
-  // slots 0..2: the three elements before the block; slot t+3: thread t's element
-  double p[kTile + 3], s1[kTile + 3], s2[kTile + 3];
+  double p[2 * kTile + 3], s1[2 * kTile + 3], s2[2 * kTile + 3];
 };
 
-template <int NP, class I>
+// Composed step for EPT elements per thread: thread t owns elements e0 + t + h kTile,
+// h < EPT, so the loads and FMA chains of EPT elements are in flight together.
+template <int NP, int EPT, class I>
 __device__ __forceinline__ void fused_body(const I &inst, const double *__restrict__ uin,
                                            double *__restrict__ uout, int e0, FusedShared &sh) {
   const int K = inst.K;
   const int t = threadIdx.x;
-  const int e = e0 + t;
-  const int ec = e < K ? e : K - 1;
   const StepConsts &S = inst.st;
   if (t < 3) {
     int m = e0 - 3 + t;
@@ -166,39 +167,52 @@ __device__ __forceinline__ void fused_body(const I &inst, const double *__restri
     sh.s1[t] = b;
     sh.s2[t] = c;
   }
-  double u[NP];
-  load_elem<NP>(uin, K, ec, u);
-  double sp, s1, s2;
-  own_scalars<NP>(S, u, sp, s1, s2);
-  sh.p[t + 3] = sp;
-  sh.s1[t + 3] = s1;
-  sh.s2[t + 3] = s2;
+  double u[EPT][NP];
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    const int e = e0 + t + h * kTile;
+    load_elem<NP>(uin, K, e < K ? e : K - 1, u[h]);
+  }
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    double sp, s1, s2;
+    own_scalars<NP>(S, u[h], sp, s1, s2);
+    const int sl = t + h * kTile + 3;
+    sh.p[sl] = sp;
+    sh.s1[sl] = s1;
+    sh.s2[sl] = s2;
+  }
   __syncthreads();
-  const double p1 = sh.p[t + 2], p2 = sh.p[t + 1], p3 = sh.p[t];
-  const double q1 = sh.s1[t + 2], q2 = sh.s1[t + 1];
-  const double r1 = sh.s2[t + 2];
-  double *o = uout + e;
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    double acc = S.G[i * NP] * u[0];
+  for (int h = 0; h < EPT; ++h) {
+    const int b = t + h * kTile;
+    const int e = e0 + b;
+    const double p1 = sh.p[b + 2], p2 = sh.p[b + 1], p3 = sh.p[b];
+    const double q1 = sh.s1[b + 2], q2 = sh.s1[b + 1];
+    const double r1 = sh.s2[b + 2];
+    double *o = uout + e;
 #pragma unroll
-    for (int j = 1; j < NP; ++j) acc = fma(S.G[i * NP + j], u[j], acc);
-    acc = fma(S.h[0][i], p1, acc);
-    acc = fma(S.h[1][i], q1, acc);
-    acc = fma(S.h[2][i], r1, acc);
-    acc = fma(S.h[3][i], p2, acc);
-    acc = fma(S.h[4][i], q2, acc);
-    acc = fma(S.h[5][i], p3, acc);
-    if (e < K) *o = acc;
-    o += K;
+    for (int i = 0; i < NP; ++i) {
+      double acc = S.G[i * NP] * u[h][0];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) acc = fma(S.G[i * NP + j], u[h][j], acc);
+      acc = fma(S.h[0][i], p1, acc);
+      acc = fma(S.h[1][i], q1, acc);
+      acc = fma(S.h[2][i], r1, acc);
+      acc = fma(S.h[3][i], p2, acc);
+      acc = fma(S.h[4][i], q2, acc);
+      acc = fma(S.h[5][i], p3, acc);
+      if (e < K) *o = acc;
+      o += K;
+    }
   }
 }
 
-template <int NP>
+template <int NP, int EPT>
 __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const double *__restrict__ uin,
                                                       double *__restrict__ uout) {
   __shared__ FusedShared sh;
-  fused_body<NP>(inst, uin, uout, blockIdx.x * kTile, sh);
+  fused_body<NP, EPT>(inst, uin, uout, blockIdx.x * (kTile * EPT), sh);
 }
 
 // One stage for one element with the arithmetic of stage_body (advection, a > 0):
@@ -304,10 +318,10 @@ __global__ void __launch_bounds__(kTile) k_batch_fused(const Inst *__restrict__ 
   const double *uin = parity ? I.v1 : I.u;
   double *uout = parity ? I.u : I.v1;
   switch (I.Np) {
-    case 2: fused_body<2>(I, uin, uout, w.y, sh); break;
-    case 3: fused_body<3>(I, uin, uout, w.y, sh); break;
-    case 4: fused_body<4>(I, uin, uout, w.y, sh); break;
-    default: fused_body<5>(I, uin, uout, w.y, sh); break;
+    case 2: fused_body<2, 1>(I, uin, uout, w.y, sh); break;
+    case 3: fused_body<3, 1>(I, uin, uout, w.y, sh); break;
+    case 4: fused_body<4, 1>(I, uin, uout, w.y, sh); break;
+    default: fused_body<5, 1>(I, uin, uout, w.y, sh); break;
   }
 }
 
@@ -623,20 +637,25 @@ cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int 
 
 namespace {
 template <int NP>
-cudaError_t fused_np(const Inst &I, const double *uin, double *uout, int rel, cudaStream_t s) {
-  k_step_fused<NP><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout);
-  if (I.async) k_step_fixup<NP><<<(unsigned)((I.P + 63) / 64), 64, 0, s>>>(I, uin, uout, rel);
+cudaError_t fused_np(const Inst &I, const double *uin, double *uout, int rel, cudaStream_t s,
+                     bool with_fixup) {
+  if (I.ept == 2)
+    k_step_fused<NP, 2><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, uin, uout);
+  else
+    k_step_fused<NP, 1><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout);
+  if (I.async && with_fixup)
+    k_step_fixup<NP><<<(unsigned)((I.P + 63) / 64), 64, 0, s>>>(I, uin, uout, rel);
   return cudaGetLastError();
 }
 }  // namespace
 
 cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool with_fixup) {
   switch (I.Np) {
-    case 2: return fused_np<2>(I, uin, uout, rel, s);
-    case 3: return fused_np<3>(I, uin, uout, rel, s);
-    case 4: return fused_np<4>(I, uin, uout, rel, s);
-    case 5: return fused_np<5>(I, uin, uout, rel, s);
+    case 2: return fused_np<2>(I, uin, uout, rel, s, with_fixup);
+    case 3: return fused_np<3>(I, uin, uout, rel, s, with_fixup);
+    case 4: return fused_np<4>(I, uin, uout, rel, s, with_fixup);
+    case 5: return fused_np<5>(I, uin, uout, rel, s, with_fixup);
     default: return cudaErrorInvalidValue;
   }
 }
