@@ -43,11 +43,12 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
                 modes=(list(_W16M.modes.amp), list(_W16M.modes.kappa), list(_W16M.modes.phase),
                        _W16M.modes.offset))
 # Algorithmic FP64 work of the kernel that runs the bench step (the composed SSP-RK3 step of
-# upwind advection): Np^2 + 8 Np multiply-adds per element and step = 2 (Np + 8) flop per
-# DOF-step. The staged formulation counts (Np + 2) multiply-adds per DOF-stage
-# (= 2 (Np + 2) flop), 1.5x more at p = 3; both figures are reported.
+# upwind advection): Np^2 + 5 Np + 3 multiply-adds per element and step, i.e.
+# 2 (Np^2 + 5 Np + 3) / Np flop per DOF-step (19.5 at p = 3). The staged formulation counts
+# (Np + 2) multiply-adds per DOF-stage (= 2 (Np + 2) flop), 1.85x more at p = 3; both
+# figures are reported.
 NP = WORKLOAD["p"] + 1
-FLOP_PER_DOF_STEP = 2 * (NP + 8)
+FLOP_PER_DOF_STEP = 2 * (NP * NP + 5 * NP + 3) / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # DRAM bytes per launch of k_step_fused measured by ncu on this workload (read + write), or
 # None when the kernel has changed since the counters were taken.
@@ -387,7 +388,7 @@ def main():
     staged_equiv = ndof * STAGES * FLOP_PER_DOF_STAGE_STAGED / (ms_step * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
                 "frac": achieved_tflops / fp64_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-                "kernel": "k_step_fused (composed SSP-RK3 step, FP64, Np^2+8Np FMA per element); "
+                "kernel": "k_step_fused (composed SSP-RK3 step, FP64, Np^2+5Np+3 FMA per element); "
                           "the PE-face fix-up launch (about 2%) is charged to it",
                 "flop_per_dof_step": FLOP_PER_DOF_STEP,
                 "staged_count_equivalent_tflops": staged_equiv,

@@ -399,8 +399,6 @@ void fold_step_constants(InstHost &h) {
     }
   }
   const int p = Np - 1;
-  Mat I(Np * Np, 0);
-  for (int i = 0; i < Np; ++i) I[i * Np + i] = 1;
   Mat M10 = mul(M[1], M[0]);
   Mat inner = M10;
   for (int i = 0; i < Np; ++i) inner[i * Np + i] += alpha[1];
@@ -410,12 +408,6 @@ void fold_step_constants(InstHost &h) {
   std::vector<ld> h1 = mulv(M[2], cv[1]);
   std::vector<ld> h2 = cv[2];
   std::vector<ld> M1c0 = mulv(M[1], cv[0]);
-  std::vector<ld> h3(Np), h4(Np), h5(Np);
-  for (int i = 0; i < Np; ++i) {
-    h3[i] = h1[i] * cv[0][p] + cv[2][i] * M1c0[p];
-    h4[i] = cv[2][i] * cv[1][p];
-    h5[i] = cv[2][i] * cv[1][p] * cv[0][p];
-  }
   adg::StepConsts &S = h.I.st;
   std::memset(&S, 0, sizeof(S));
   for (int i = 0; i < Np; ++i) {
@@ -425,10 +417,10 @@ void fold_step_constants(InstHost &h) {
     S.h[0][i] = (double)h0[i];
     S.h[1][i] = (double)h1[i];
     S.h[2][i] = (double)h2[i];
-    S.h[3][i] = (double)h3[i];
-    S.h[4][i] = (double)h4[i];
-    S.h[5][i] = (double)h5[i];
   }
+  S.k[0] = (double)cv[0][p];
+  S.k[1] = (double)M1c0[p];
+  S.k[2] = (double)cv[1][p];
 }
 
 int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out) {
@@ -469,9 +461,10 @@ int ensure_table_back(adg_ctx *c, InstHost &h, int64_t n) {
   return fill_table(c, h, std::max<int64_t>(0, n - h.TR + 1));
 }
 
-// Autotuner of the composed-step kernel: times one and two elements per thread on a copy
-// of u0 held in the instance's v1/v2 fields (free at this point) and keeps the faster. Both
-// choices compute every element with the same arithmetic, so results do not depend on it.
+// Autotuner of the composed-step kernel: times one, two and four elements per thread on a
+// copy of u0 held in the instance's v1/v2 fields (free at this point) and keeps the fastest.
+// Every choice computes every element with the same arithmetic, so results do not depend on
+// it.
 int autotune_fused(adg_ctx *c, InstHost &h) {
   Inst &I = h.I;
   const size_t nd = (size_t)I.K * I.Np;
@@ -482,7 +475,7 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   CK(cudaEventCreate(&b));
   float best = 1e30f;
   int best_ept = 1;
-  for (int ept = 1; ept <= 2; ++ept) {
+  for (int ept = 1; ept <= 4; ept *= 2) {
     Inst T = I;
     T.ept = ept;
     float ms = 0.0f;
@@ -628,7 +621,6 @@ int launch_steps(adg_ctx *c, int nsteps) {
           CK(adg::launch_batch_faces(c->insts_dev, c->fwork_dev, c->nfwork, s, rel, c->stream));
       } else {
         CK(adg::launch_stage(c->inst[0].I, s, rel, c->stream));
-        if (c->inst[0].I.async) CK(adg::launch_faces(c->inst[0].I, s, rel, c->stream));
       }
     }
   }
@@ -770,7 +762,6 @@ int sweep_recompute(adg_ctx *c, InstHost &h, double *seg, int len) {
     I.unext = slot + kStages * nd;
     for (int s = 0; s < kStages; ++s) {
       CK(adg::launch_stage(I, s, t, c->stream));
-      if (I.async) CK(adg::launch_faces(I, s, t, c->stream));
     }
   }
   return ADG_OK;

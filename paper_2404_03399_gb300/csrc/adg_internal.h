@@ -35,19 +35,23 @@ struct StageConsts {
 };
 
 // The three stages of one SSP-RK3 step of upwind advection (a > 0) composed into one
-// stencil over the element and its three upstream neighbours. With M_s = A_s + lL_s e_0^T
-// and c_s = -lL_s (stage s of the folded form above, all faces synchronous):
-//   v1 = M_0 u^e + c_0 p^{e-1},  v2 = alpha_1 u^e + M_1 v1 + c_1 v1_p^{e-1},
-//   u' = alpha_2 u^e + M_2 v2 + c_2 v2_p^{e-1},
-// which expands to
-//   u'^e = G u^e + h_0 p^{e-1} + h_1 s1^{e-1} + h_2 s2^{e-1} + h_3 p^{e-2} + h_4 s1^{e-2}
-//          + h_5 p^{e-3},
-// p^m = u^m_p (right trace), s1^m = r1 . u^m (own part of v1_p^m), s2^m = r2 . u^m (own
-// part of v2_p^m). Cost: Np^2 + 8 Np multiply-adds per element and step.
+// stencil. With M_s = A_s + lL_s e_0^T and c_s = -lL_s (stage s of the folded form above,
+// all faces synchronous) and x^m_p the right trace of x on element m:
+//   v1 = M_0 u^e + c_0 P0,  v2 = alpha_1 u^e + M_1 v1 + c_1 P1,  u' = alpha_2 u^e + M_2 v2 + c_2 P2,
+// where P0 = u^{e-1}_p, P1 = v1^{e-1}_p, P2 = v2^{e-1}_p are the three channel scalars of
+// the left neighbour. Hence
+//   u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2,   G = alpha_2 I + M_2 (alpha_1 I + M_1 M_0),
+//   h_0 = M_2 M_1 c_0,  h_1 = M_2 c_1,  h_2 = c_2,
+// and every element forms its own channel scalars from its neighbour's:
+//   v1^e_p = r1 . u^e + k_0 P0,  v2^e_p = r2 . u^e + k_1 P0 + k_2 P1,
+//   r1 = M_0^T e_p, r2 = (alpha_1 I + M_1 M_0)^T e_p, k_0 = c_0[p], k_1 = (M_1 c_0)[p],
+//   k_2 = c_1[p].
+// Cost: Np^2 + 5 Np + 3 multiply-adds per element and step.
 struct StepConsts {
   double G[kMaxNp * kMaxNp];
   double r1[kMaxNp], r2[kMaxNp];
-  double h[6][kMaxNp];
+  double h[3][kMaxNp];
+  double k[3];
 };
 
 // One DG instance as the kernels see it. Nodal fields are node-major: field[i*K + e].
@@ -62,7 +66,7 @@ struct alignas(16) Inst {
   double a;
   int K, Np, P, Kpe, R, L, q, pde, async, table_rows;
   int fused;            // 1: steps use the composed stencil (StepConsts) + PE-face fix-up
-  int ept;              // elements per thread of the composed-step kernel (1 or 2, autotuned)
+  int ept;              // elements per thread of the composed-step kernel (1, 2 or 4, autotuned)
   StageConsts sc[kStages];
   StepConsts st;
 };
@@ -106,12 +110,14 @@ struct AdjFace {
 };
 
 // Launchers (adg_kernels.cu). All return cudaGetLastError() after the launch.
+// One stage over all elements; for an asynchronous instance the same kernel applies the
+// PE-face correction (delayed / AT flux) and writes the ring (step meta[0] + rel).
 cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
 cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                int stage, int rel, int tile, cudaStream_t s);
-// PE-face pass after each stage: ring write of the stage-input traces and replacement of
-// the synchronous flux by the delayed / AT flux in the elements next to each PE face.
-cudaError_t launch_faces(const Inst &I, int stage, int rel, cudaStream_t s);
+// Batched PE-face pass after each batched stage: ring write of the stage-input traces and
+// replacement of the synchronous flux by the delayed / AT flux in the elements next to each
+// PE face.
 cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int nwork, int stage,
                                int rel, cudaStream_t s);
 cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t by,

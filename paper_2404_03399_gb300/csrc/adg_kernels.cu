@@ -14,11 +14,27 @@ namespace adg {
 
 namespace {
 
+// Vs - V at PE face j, stage `stage`, step n, from the face's traces (tl, tr): the
+// synchronous face value minus the delayed / AT value; the owner writes the traces into the
+// ring slot of step n.
+template <int PDE, int DIR, class I>
+__device__ __forceinline__ double pe_face_delta(const I &inst, int j, int64_t n, int stage,
+                                                double tl, double tr, bool owner) {
+  const double Vs = face_value<PDE, DIR>(inst, tl, tr);
+  const double V = pe_value<PDE, DIR>(inst, j, n, stage, tl, tr, owner);
+  return __dsub_rn(Vs, V);
+}
+
 // One SSP-RK3 stage for element e (all 32 lanes of the warp take part; lanes past the
 // end duplicate element K-1 and store nothing). DIR is the upwind side for advection
-// (+1: a > 0, -1: a < 0) and 0 for Burgers.
-template <int NP, int PDE, int STAGE, int DIR, class I>
-__device__ __forceinline__ void stage_body(const I &inst, int e) {
+// (+1: a > 0, -1: a < 0) and 0 for Burgers. With FACES, the PE-face correction of the
+// delayed / AT flux is applied here too (step n): the element right of PE face j
+// (e = j Kpe) owns the face, writes its ring entry and adds lL (Vs - V); the element left
+// of it (e = j Kpe - 1) forms the same value with the same arithmetic and adds lR (Vs - V).
+// The synchronous output is rounded first, so the result is bit-identical to a stage
+// followed by a separate face pass.
+template <int NP, int PDE, int STAGE, int DIR, bool FACES, class I>
+__device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) {
   const int K = inst.K;
   const int lane = threadIdx.x & 31;
   const int ec = e < K ? e : K - 1;
@@ -98,6 +114,29 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], jR, out[i]);
   }
+  if (FACES && e < K) {
+    const int Kpe = inst.Kpe;
+    const int jq = e / Kpe;
+    const int r = e - jq * Kpe;
+    if (r == 0) {   // left face is PE face jq; this element owns it
+      const double tl = (PDE == 1 || DIR > 0) ? vLm
+                        : __ldg(vin + (NP - 1) * K + (e == 0 ? K - 1 : e - 1));
+      const double d = pe_face_delta<PDE, DIR>(inst, jq, n, STAGE, tl, v[0], true);
+      if (nonzero(d)) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], d, out[i]);
+      }
+    }
+    if (r == Kpe - 1) {   // right face is PE face jq + 1 (face 0 for the last element)
+      const double tr = (PDE == 1 || DIR < 0) ? vRp : __ldg(vin + (e + 1 == K ? 0 : e + 1));
+      const int jr = jq + 1 == inst.P ? 0 : jq + 1;
+      const double d = pe_face_delta<PDE, DIR>(inst, jr, n, STAGE, v[NP - 1], tr, false);
+      if (nonzero(d)) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], d, out[i]);
+      }
+    }
+  }
   if (e < K) {
     double *q = vout + e;
 #pragma unroll
@@ -108,16 +147,18 @@ __device__ __forceinline__ void stage_body(const I &inst, int e) {
   }
 }
 
-template <int NP, int PDE, int STAGE, int DIR>
-__global__ void __launch_bounds__(kTile) k_stage(const Inst inst) {
-  stage_body<NP, PDE, STAGE, DIR>(inst, blockIdx.x * blockDim.x + threadIdx.x);
+template <int NP, int PDE, int STAGE, int DIR, bool FACES>
+__global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
+  const int64_t n = FACES ? inst.meta[0] + rel : 0;
+  stage_body<NP, PDE, STAGE, DIR, FACES>(inst, blockIdx.x * blockDim.x + threadIdx.x, n);
 }
 
-// Composed SSP-RK3 step of upwind advection (a > 0), all faces synchronous: one thread per
-// element computes p, s1, s2 of its own element (shared with the block through shared
-// memory) and u'^e = G u^e + the rank-6 upstream coupling (StepConsts). The first three
-// threads of a block form the upstream values of the previous block's elements themselves,
-// with the same arithmetic.
+// Composed SSP-RK3 step of upwind advection (a > 0), all faces synchronous (StepConsts):
+// one thread per element forms its right trace p = u_p and the own parts r1 . u, r2 . u of
+// its channel scalars, then, in two rounds through shared memory, v1_p and v2_p from its
+// left neighbour's, and finally u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2 from the left
+// neighbour's three channel scalars. The first three threads of a block form the scalars of
+// the three elements before the block themselves, with the same arithmetic.
 template <int NP>
 __device__ __forceinline__ void own_scalars(const StepConsts &S, const double *u, double &sp,
                                             double &s1, double &s2) {
@@ -143,31 +184,32 @@ __device__ __forceinline__ void load_elem(const double *__restrict__ f, int K, i
   }
 }
 
-// Scalars of the elements of one block: slots 0..2 hold the three elements before the
-// block, slot 3+m the block's element m (up to 2 kTile elements per block).
+// Channel scalars of the elements of one block: slots 0..2 hold the three elements before
+// the block, slot 3+m the block's element m (EPT kTile elements per block).
+template <int EPT>
 struct FusedShared {
-  double p[2 * kTile + 3], s1[2 * kTile + 3], s2[2 * kTile + 3];
+  double p[EPT * kTile + 3], q1[EPT * kTile + 3], q2[EPT * kTile + 3];
 };
 
 // Composed step for EPT elements per thread: thread t owns elements e0 + t + h kTile,
 // h < EPT, so the loads and FMA chains of EPT elements are in flight together.
 template <int NP, int EPT, class I>
 __device__ __forceinline__ void fused_body(const I &inst, const double *__restrict__ uin,
-                                           double *__restrict__ uout, int e0, FusedShared &sh) {
+                                           double *__restrict__ uout, int e0,
+                                           FusedShared<EPT> &sh) {
   const int K = inst.K;
   const int t = threadIdx.x;
   const StepConsts &S = inst.st;
+  double hs1 = 0.0, hs2 = 0.0;   // own parts of the halo element's channel scalars
   if (t < 3) {
     int m = e0 - 3 + t;
     if (m < 0) m += K;     // K >= 8 on this path
-    double w[NP], a, b, c;
+    double w[NP], a;
     load_elem<NP>(uin, K, m, w);
-    own_scalars<NP>(S, w, a, b, c);
+    own_scalars<NP>(S, w, a, hs1, hs2);
     sh.p[t] = a;
-    sh.s1[t] = b;
-    sh.s2[t] = c;
   }
-  double u[EPT][NP];
+  double u[EPT][NP], s1[EPT], s2[EPT];
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
     const int e = e0 + t + h * kTile;
@@ -175,33 +217,41 @@ __device__ __forceinline__ void fused_body(const I &inst, const double *__restri
   }
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
-    double sp, s1, s2;
-    own_scalars<NP>(S, u[h], sp, s1, s2);
+    double sp;
+    own_scalars<NP>(S, u[h], sp, s1[h], s2[h]);
+    sh.p[t + h * kTile + 3] = sp;
+  }
+  __syncthreads();
+  // v1_p = r1 . u + k_0 P0 (the halo's first element needs none)
+  if (t == 1 || t == 2) sh.q1[t] = fma(S.k[0], sh.p[t - 1], hs1);
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
     const int sl = t + h * kTile + 3;
-    sh.p[sl] = sp;
-    sh.s1[sl] = s1;
-    sh.s2[sl] = s2;
+    sh.q1[sl] = fma(S.k[0], sh.p[sl - 1], s1[h]);
+  }
+  __syncthreads();
+  // v2_p = r2 . u + k_1 P0 + k_2 P1 (of the halo, only the element just before the block)
+  if (t == 2) sh.q2[2] = fma(S.k[2], sh.q1[1], fma(S.k[1], sh.p[1], hs2));
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    const int sl = t + h * kTile + 3;
+    sh.q2[sl] = fma(S.k[2], sh.q1[sl - 1], fma(S.k[1], sh.p[sl - 1], s2[h]));
   }
   __syncthreads();
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
-    const int b = t + h * kTile;
+    const int b = t + h * kTile;   // left neighbour's slot is b + 2
     const int e = e0 + b;
-    const double p1 = sh.p[b + 2], p2 = sh.p[b + 1], p3 = sh.p[b];
-    const double q1 = sh.s1[b + 2], q2 = sh.s1[b + 1];
-    const double r1 = sh.s2[b + 2];
+    const double P0 = sh.p[b + 2], P1 = sh.q1[b + 2], P2 = sh.q2[b + 2];
     double *o = uout + e;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       double acc = S.G[i * NP] * u[h][0];
 #pragma unroll
       for (int j = 1; j < NP; ++j) acc = fma(S.G[i * NP + j], u[h][j], acc);
-      acc = fma(S.h[0][i], p1, acc);
-      acc = fma(S.h[1][i], q1, acc);
-      acc = fma(S.h[2][i], r1, acc);
-      acc = fma(S.h[3][i], p2, acc);
-      acc = fma(S.h[4][i], q2, acc);
-      acc = fma(S.h[5][i], p3, acc);
+      acc = fma(S.h[0][i], P0, acc);
+      acc = fma(S.h[1][i], P1, acc);
+      acc = fma(S.h[2][i], P2, acc);
       if (e < K) *o = acc;
       o += K;
     }
@@ -211,7 +261,7 @@ __device__ __forceinline__ void fused_body(const I &inst, const double *__restri
 template <int NP, int EPT>
 __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const double *__restrict__ uin,
                                                       double *__restrict__ uout) {
-  __shared__ FusedShared sh;
+  __shared__ FusedShared<EPT> sh;
   fused_body<NP, EPT>(inst, uin, uout, blockIdx.x * (kTile * EPT), sh);
 }
 
@@ -233,8 +283,8 @@ __device__ __forceinline__ void stage_elem(const StageConsts &C, const double *u
 }
 
 // Stage s over window slots w = s+1 .. 6 with the PE face between slots 3 and 4: the
-// synchronous stage followed by the face correction of k_faces (same arithmetic), and the
-// ring write of the stage-input traces.
+// synchronous stage followed by the PE-face correction of the staged kernels (same
+// arithmetic), and the ring write of the stage-input traces.
 template <int NP, int STAGE>
 __device__ __forceinline__ void fixup_stage(const Inst &I, int j, int64_t n, double (*U)[NP],
                                             double (*X)[NP], double (*Y)[NP]) {
@@ -305,7 +355,7 @@ __global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *_
 __global__ void __launch_bounds__(kTile) k_batch_fused(const Inst *__restrict__ insts,
                                                        const int2 *__restrict__ work, int parity) {
   __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
-  __shared__ FusedShared sh;
+  __shared__ FusedShared<1> sh;
   const int2 w = work[blockIdx.x];
   {
     const int4 *src = reinterpret_cast<const int4 *>(insts + w.x);
@@ -351,7 +401,7 @@ __global__ void k_batch_copy_back(const Inst *__restrict__ insts, const int2 *__
   for (int i = 0; i < I.Np; ++i) I.u[(size_t)i * I.K + e] = I.v1[(size_t)i * I.K + e];
 }
 
-// Face pass of one stage, run after the stage kernel. For PE face j (between elements
+// Face pass of one batched stage, run after the stage kernel. For PE face j (between elements
 // e-1 = j Kpe - 1 and e = j Kpe) it reads the stage-input traces, forms the synchronous
 // face value Vs and the delayed / AT value V from the ring, writes the traces into the ring
 // slot of step n, and replaces the synchronous flux by the delayed one in both elements:
@@ -365,9 +415,7 @@ __device__ __forceinline__ double face_delta(const I &inst, const double *vin, i
   const int e = j * inst.Kpe;
   const double tl = vin[(size_t)(inst.Np - 1) * K + (e == 0 ? K - 1 : e - 1)];
   const double tr = vin[e];
-  const double Vs = face_value<PDE, DIR>(inst, tl, tr);
-  const double V = pe_value<PDE, DIR>(inst, j, n, stage, tl, tr, owner);
-  return __dsub_rn(Vs, V);
+  return pe_face_delta<PDE, DIR>(inst, j, n, stage, tl, tr, owner);
 }
 
 template <class I>
@@ -423,13 +471,6 @@ __device__ __forceinline__ void face_body(const I &inst, int stage, int j, int64
   }
 }
 
-template <int PDE, int DIR>
-__global__ void __launch_bounds__(256) k_faces(const Inst inst, int stage, int rel) {
-  const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= inst.P) return;
-  face_body<PDE, DIR>(inst, stage, j, inst.meta[0] + rel);
-}
-
 __global__ void __launch_bounds__(256) k_batch_faces(const Inst *__restrict__ insts,
                                                      const int2 *__restrict__ work, int stage,
                                                      int rel) {
@@ -446,10 +487,10 @@ __global__ void __launch_bounds__(256) k_batch_faces(const Inst *__restrict__ in
 template <int STAGE, int NP>
 __device__ __forceinline__ void batch_dispatch_pde(const Inst &I, int e) {
   if (I.pde == 0) {
-    if (I.a >= 0.0) stage_body<NP, 0, STAGE, 1>(I, e);
-    else stage_body<NP, 0, STAGE, -1>(I, e);
+    if (I.a >= 0.0) stage_body<NP, 0, STAGE, 1, false>(I, e);
+    else stage_body<NP, 0, STAGE, -1, false>(I, e);
   } else {
-    stage_body<NP, 1, STAGE, 0>(I, e);
+    stage_body<NP, 1, STAGE, 0, false>(I, e);
   }
 }
 
@@ -576,10 +617,10 @@ __global__ void __launch_bounds__(kRedThreads)
 
 template <int NP, int PDE, int STAGE, int DIR>
 cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
-  (void)rel;
   const int bs = stage_block(I.K);
   const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
-  k_stage<NP, PDE, STAGE, DIR><<<grid, bs, 0, s>>>(I);
+  if (I.async) k_stage<NP, PDE, STAGE, DIR, true><<<grid, bs, 0, s>>>(I, rel);
+  else k_stage<NP, PDE, STAGE, DIR, false><<<grid, bs, 0, s>>>(I, rel);
   return cudaGetLastError();
 }
 
@@ -621,14 +662,6 @@ cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int 
   return cudaGetLastError();
 }
 
-cudaError_t launch_faces(const Inst &I, int stage, int rel, cudaStream_t s) {
-  const unsigned grid = (unsigned)((I.P + 255) / 256);
-  if (I.pde == 1) k_faces<1, 0><<<grid, 256, 0, s>>>(I, stage, rel);
-  else if (I.a >= 0.0) k_faces<0, 1><<<grid, 256, 0, s>>>(I, stage, rel);
-  else k_faces<0, -1><<<grid, 256, 0, s>>>(I, stage, rel);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int nwork, int stage,
                                int rel, cudaStream_t s) {
   if (nwork > 0) k_batch_faces<<<nwork, 256, 0, s>>>(insts_dev, work_dev, stage, rel);
@@ -639,7 +672,9 @@ namespace {
 template <int NP>
 cudaError_t fused_np(const Inst &I, const double *uin, double *uout, int rel, cudaStream_t s,
                      bool with_fixup) {
-  if (I.ept == 2)
+  if (I.ept == 4)
+    k_step_fused<NP, 4><<<(unsigned)((I.K + 4 * kTile - 1) / (4 * kTile)), kTile, 0, s>>>(I, uin, uout);
+  else if (I.ept == 2)
     k_step_fused<NP, 2><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, uin, uout);
   else
     k_step_fused<NP, 1><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout);
