@@ -751,7 +751,9 @@ int capture(adg_ctx *c, GraphExec &out, F &&body) {
 // Forward over one segment of `len` steps starting at meta[0], recording the stage inputs
 // of step t in slot t of `seg` (u^n, v1, v2); slot t+1's u receives u^{n+1}, so slot 0's u
 // must hold the segment's first state and slot len's u holds the last.
-int sweep_recompute(adg_ctx *c, InstHost &h, double *seg, int len) {
+// rel0 shifts the step indices: a segment that starts rel0 steps after meta[0] (the
+// overlapped recompute runs the segment before the one meta[0] names, rel0 = -len).
+int sweep_recompute(adg_ctx *c, InstHost &h, double *seg, int len, int rel0 = 0) {
   const size_t nd = (size_t)h.I.K * h.I.Np;
   for (int t = 0; t < len; ++t) {
     double *slot = seg + (size_t)t * kStages * nd;
@@ -761,7 +763,7 @@ int sweep_recompute(adg_ctx *c, InstHost &h, double *seg, int len) {
     I.v2 = slot + 2 * nd;
     I.unext = slot + kStages * nd;
     for (int s = 0; s < kStages; ++s) {
-      CK(adg::launch_stage(I, s, t, c->stream));
+      CK(adg::launch_stage(I, s, rel0 + t, c->stream));
     }
   }
   return ADG_OK;
@@ -828,10 +830,33 @@ int sweep_reverse(adg_ctx *c, InstHost &h, const double *seg, double *lam, doubl
   return ADG_OK;
 }
 
+// Second stream and events of the overlapped recompute (released on every exit path).
+struct SideStream {
+  cudaStream_t s = nullptr;
+  cudaEvent_t meta_set = nullptr, rec_done = nullptr;
+  ~SideStream() {
+    if (meta_set) cudaEventDestroy(meta_set);
+    if (rec_done) cudaEventDestroy(rec_done);
+    if (s) cudaStreamDestroy(s);
+  }
+};
+
 // adg_grad: forward with checkpoints every C steps, misfit, then segments in reverse: restore
 // the checkpoint, recompute the segment recording the stage inputs (Burgers; the linear
 // advection adjoint needs no forward state), and run the adjoint stages from the last step
 // of the segment to its first. The state of the context is restored at the end.
+//
+// Burgers with two or more segments: the recompute of segment s-1 runs on a second stream
+// into a second segment buffer while the adjoint of segment s runs on the context's stream
+// (the two share only read-only data, the delay table and meta[0]; the recompute's step
+// indices are taken relative to segment s's start, so meta[0] changes only once both are
+// done). Order per segment s on the context's stream: wait for the recompute of s, refill
+// the delay table if it does not cover steps [start(s) - C, end(s)), set meta[0] = start(s),
+// record `meta_set`, run the adjoint of s; on the second stream: wait for `meta_set` (which
+// also orders it after the adjoint of s+1, the last reader of the buffer it overwrites),
+// restore checkpoint s-1 and its ring, recompute s-1, record `rec_done`. Without room for
+// the second buffer, or with 2C larger than the delay table, segments run one after the
+// other on the context's stream.
 int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, double *grad_dev,
                  double *J_out) {
   InstHost &h = c->inst[0];
@@ -892,36 +917,88 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
   CK(adg::launch_adj_init(I.u, g.d(), K, Np, h.M, h.dx / 2.0, lam.d(), c->stream));
   if (ring_n) CK(cudaMemsetAsync(lring.p, 0, ring_n * sizeof(double), c->stream));
 
-  // Segment sweeps replay graphs captured once per (segment length, buffer parity).
-  GraphExec rev[2][2];
-  int par = 0;
+  // Overlapped recompute: a second segment buffer and stream when there is room for them.
+  DevBuf seg2;
+  SideStream side;
+  bool overlap = states && nseg >= 2 && (!I.async || 2 * (int64_t)C <= h.TR);
+  if (overlap) {
+    if (cudaMalloc(&seg2.p, ((size_t)C * kStages + 1) * nd * sizeof(double)) != cudaSuccess) {
+      seg2.p = nullptr;
+      (void)cudaGetLastError();   // clear the failed allocation; run segments serially
+      overlap = false;
+    }
+  }
+  if (overlap) {
+    CK(cudaStreamCreateWithFlags(&side.s, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&side.meta_set, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&side.rec_done, cudaEventDisableTiming));
+  }
+  double *segb[2] = {seg.d(), seg2.d()};
+
+  // Segment sweeps replay graphs captured once per (segment length, buffer parity, segment
+  // buffer); the overlapped recompute has one graph per segment buffer.
+  GraphExec rev[2][2][2], rec_prev[2];
+  int par = 0, cur = 0;
   for (int64_t sidx = nseg - 1; sidx >= 0; --sidx) {
     const int64_t start = n0 + sidx * C;
     const int len = (int)std::min<int64_t>(C, nsteps - sidx * C);
     const bool is_last = sidx == nseg - 1 && last_len != C;
-    r = ensure_table(c, h, start, len);
-    if (r) return r;
-    r = set_step(c, h, start);
-    if (r) return r;
-    if (states && sidx != nseg - 1) {
-      CK(cudaMemcpyAsync(seg.d(), ck_u.d() + sidx * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-      if (ring_n)
-        CK(cudaMemcpyAsync(I.ring, static_cast<double2 *>(ck_ring.p) + sidx * ring_n,
-                           ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
-      GraphExec &ge = is_last ? rec_last : rec_full;
-      if (!ge.g) {
-        r = capture(c, ge, [&] { return sweep_recompute(c, h, seg.d(), len); });
-        if (r) return r;
+    if (overlap) {
+      if (sidx != nseg - 1) CK(cudaStreamWaitEvent(c->stream, side.rec_done, 0));
+      if (I.async) {
+        const int64_t lo = sidx > 0 ? start - C : start, hi = start + len;
+        if (!(lo >= h.tbase && hi <= h.tbase + h.TR)) {
+          r = fill_table(c, h, std::max<int64_t>(0, hi - h.TR));
+          if (r) return r;
+        }
       }
-      CK(cudaGraphLaunch(ge.g, c->stream));
+      r = set_step(c, h, start);
+      if (r) return r;
+      if (sidx > 0) {
+        // recompute of segment sidx-1 (full length C) into the other buffer
+        double *nb = segb[1 - cur];
+        CK(cudaEventRecord(side.meta_set, c->stream));
+        CK(cudaStreamWaitEvent(side.s, side.meta_set, 0));
+        CK(cudaMemcpyAsync(nb, ck_u.d() + (sidx - 1) * nd, nd * sizeof(double),
+                           cudaMemcpyDeviceToDevice, side.s));
+        if (ring_n)
+          CK(cudaMemcpyAsync(I.ring, static_cast<double2 *>(ck_ring.p) + (sidx - 1) * ring_n,
+                             ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, side.s));
+        GraphExec &gp = rec_prev[1 - cur];
+        if (!gp.g) {
+          r = capture(c, gp, [&] { return sweep_recompute(c, h, nb, C, -C); });
+          if (r) return r;
+        }
+        CK(cudaGraphLaunch(gp.g, side.s));
+        CK(cudaEventRecord(side.rec_done, side.s));
+      }
+    } else {
+      r = ensure_table(c, h, start, len);
+      if (r) return r;
+      r = set_step(c, h, start);
+      if (r) return r;
+      if (states && sidx != nseg - 1) {
+        CK(cudaMemcpyAsync(seg.d(), ck_u.d() + sidx * nd, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+        if (ring_n)
+          CK(cudaMemcpyAsync(I.ring, static_cast<double2 *>(ck_ring.p) + sidx * ring_n,
+                             ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
+        GraphExec &ge = is_last ? rec_last : rec_full;
+        if (!ge.g) {
+          r = capture(c, ge, [&] { return sweep_recompute(c, h, seg.d(), len); });
+          if (r) return r;
+        }
+        CK(cudaGraphLaunch(ge.g, c->stream));
+      }
     }
-    GraphExec &gr = rev[is_last ? 1 : 0][par];
+    double *sb = states ? segb[cur] : nullptr;
+    GraphExec &gr = rev[is_last ? 1 : 0][par][cur];
     if (!gr.g) {
-      r = capture(c, gr, [&] { return sweep_reverse(c, h, states ? seg.d() : nullptr, lam.d(), lring.d(), len, par); });
+      r = capture(c, gr, [&] { return sweep_reverse(c, h, sb, lam.d(), lring.d(), len, par); });
       if (r) return r;
     }
     CK(cudaGraphLaunch(gr.g, c->stream));
     if (len % 2) par = 1 - par;
+    if (overlap) cur = 1 - cur;
   }
   double *Lu = lam.d() + (size_t)par * nd;
   CK(adg::launch_to_external(Lu, grad_dev, K, Np, c->stream));
