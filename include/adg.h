@@ -52,7 +52,12 @@ enum { ADG_ADVECTION = 0, ADG_BURGERS = 1 };          /* f(u) = a u  |  f(u) = u
 enum { ADG_UPWIND = 0, ADG_LLF = 1 };                 /* Section 6.1 fluxes */
 enum { ADG_SSPRK3 = 3 };                               /* time integrator */
 enum { ADG_SYNC = 0, ADG_ASYNC = 1, ADG_ASYNC_AT = 2 };/* DG | ADG | ADG-AT */
-enum { ADG_VARIANT_AUTO = 0, ADG_VARIANT_STAGED = 1, ADG_VARIANT_COMPOSED = 2 };
+enum {
+  ADG_VARIANT_AUTO = 0,
+  ADG_VARIANT_STAGED = 1,
+  ADG_VARIANT_COMPOSED = 2,
+  ADG_VARIANT_COMPOSED_FIXED = 3
+};
 
 #define ADG_MAX_P 4        /* polynomial degree 1..4 (2..5 LGL nodes) */
 #define ADG_MAX_L 16       /* delays 0..L-1 with L <= 16 */
@@ -80,8 +85,15 @@ enum { ADG_VARIANT_AUTO = 0, ADG_VARIANT_STAGED = 1, ADG_VARIANT_COMPOSED = 2 };
  *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
  *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
  *               composed into one stencil per step, with the elements next to PE faces
- *               recomputed stage by stage (needs K/P >= 8 when there are PE faces). AUTO picks
- *               COMPOSED where it applies. Both give the same scheme up to rounding.
+ *               recomputed stage by stage (needs K/P >= 8 when there are PE faces), or
+ *               ADG_VARIANT_COMPOSED_FIXED (3): the same composed step evaluated exactly in
+ *               64-bit fixed-point integer arithmetic at one scale per step (the largest
+ *               exponent of u^n; resolution 2^-56 of max|u^n| or finer), then rounded to FP64;
+ *               it needs every composed coefficient below 2 in magnitude (small Courant
+ *               numbers; ADG_EINVAL otherwise). Results below 2^-1022 are flushed to zero,
+ *               and a NaN or infinity anywhere in u^n makes all of u^{n+1} NaN. AUTO picks
+ *               COMPOSED_FIXED, else COMPOSED, where they apply (a single instance; batches
+ *               use COMPOSED). All give the same scheme up to rounding.
  */
 typedef struct {
   int32_t pde;

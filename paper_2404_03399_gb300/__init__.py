@@ -48,7 +48,7 @@ class Config:
     seed: int = 0
     probs: Optional[Sequence[float]] = None
     table: Optional[np.ndarray] = None   # uint8 (T, P), used periodically
-    variant: str = "auto"       # "auto" | "staged" | "composed"
+    variant: str = "auto"       # "auto" | "staged" | "composed" | "fixed"
 
     def to_c(self):
         c = _abi.AdgConfig()
@@ -63,7 +63,7 @@ class Config:
         c.L = int(self.L)
         c.at_order = int(self.q)
         c.seed = int(self.seed) & ((1 << 64) - 1)
-        c.variant = {"auto": 0, "staged": 1, "composed": 2}[self.variant]
+        c.variant = {"auto": 0, "staged": 1, "composed": 2, "fixed": 3}[self.variant]
         keep = []
         if self.probs is not None:
             arr = (C.c_double * len(self.probs))(*[float(v) for v in self.probs])

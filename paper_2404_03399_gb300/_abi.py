@@ -12,7 +12,7 @@ ADG_ADVECTION, ADG_BURGERS = 0, 1
 ADG_UPWIND, ADG_LLF = 0, 1
 ADG_SSPRK3 = 3
 ADG_SYNC, ADG_ASYNC, ADG_ASYNC_AT = 0, 1, 2
-ADG_VARIANT_AUTO, ADG_VARIANT_STAGED, ADG_VARIANT_COMPOSED = 0, 1, 2
+ADG_VARIANT_AUTO, ADG_VARIANT_STAGED, ADG_VARIANT_COMPOSED, ADG_VARIANT_COMPOSED_FIXED = 0, 1, 2, 3
 
 STATUS_NAMES = {0: "ADG_OK", -1: "ADG_EINVAL", -2: "ADG_ENOMEM", -3: "ADG_ECUDA",
                 -4: "ADG_ENONFINITE", -5: "ADG_ETIMEOUT", -6: "ADG_ESTATE"}

@@ -239,7 +239,7 @@ std::string check_config(const adg_config *c) {
   if (c->mode != ADG_SYNC && c->mode != ADG_ASYNC && c->mode != ADG_ASYNC_AT) return "bad mode";
   if (c->L < 1 || c->L > ADG_MAX_L) return "L must be in 1..16";
   if (c->at_order < 0 || c->at_order > ADG_MAX_Q) return "at_order must be in 0..5";
-  if (c->variant < ADG_VARIANT_AUTO || c->variant > ADG_VARIANT_COMPOSED) return "bad variant";
+  if (c->variant < ADG_VARIANT_AUTO || c->variant > ADG_VARIANT_COMPOSED_FIXED) return "bad variant";
   if (c->probs) {
     double s = 0;
     for (int k = 0; k < c->L; ++k) {
@@ -295,6 +295,8 @@ struct InstHost {
   uint8_t *table = nullptr;
   double *coef = nullptr;
   double *w = nullptr, *M = nullptr;
+  int *emax = nullptr;       // exponent slots of the fixed-point composed step
+  bool fixed_ok = false;     // the composed coefficients fit the fixed-point bounds
   std::vector<uint8_t> host_rows;
 };
 
@@ -421,6 +423,37 @@ void fold_step_constants(InstHost &h) {
   S.k[0] = (double)cv[0][p];
   S.k[1] = (double)M1c0[p];
   S.k[2] = (double)cv[1][p];
+
+  // Fixed-point limbs of the same coefficients (from the long double values) and the bounds
+  // of the integer step: every |c| < 2 (limbs within 32 bits), and channel scalars v1_p,
+  // v2_p at most twice the input bound (|X| < 2^58 as multiplicands; inputs are < 2^57).
+  adg::StepFixed &F = h.I.sf;
+  std::memset(&F, 0, sizeof(F));
+  bool ok = true;
+  auto limbs = [&](ld c) {
+    if (!(fabsl(c) < 1.999L)) ok = false;
+    const long long C = ok ? llroundl(ldexpl(c, 58)) : 0;
+    int2 r;
+    r.x = (int)(C >> 29);
+    r.y = (int)(C & 0x1FFFFFFF);
+    return r;
+  };
+  ld b1 = fabsl(cv[0][p]), b2 = fabsl(M1c0[p]);
+  for (int i = 0; i < Np; ++i) {
+    for (int j = 0; j < Np; ++j) F.G[i * Np + j] = limbs(G[i * Np + j]);
+    F.r1[i] = limbs(M[0][p * Np + i]);
+    F.r2[i] = limbs(M10[p * Np + i] + (i == p ? alpha[1] : 0.0L));
+    F.h[0][i] = limbs(h0[i]);
+    F.h[1][i] = limbs(h1[i]);
+    F.h[2][i] = limbs(h2[i]);
+    b1 += fabsl(M[0][p * Np + i]);
+    b2 += fabsl(M10[p * Np + i] + (i == p ? alpha[1] : 0.0L));
+  }
+  F.k[0] = limbs(cv[0][p]);
+  F.k[1] = limbs(M1c0[p]);
+  F.k[2] = limbs(cv[1][p]);
+  b2 += fabsl(cv[1][p]) * b1;
+  h.fixed_ok = ok && b1 < 1.999L && b2 < 1.999L;
 }
 
 int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out) {
@@ -459,6 +492,16 @@ int ensure_table_back(adg_ctx *c, InstHost &h, int64_t n) {
   if (!h.I.async) return ADG_OK;
   if (n >= h.tbase && n < h.tbase + h.TR) return ADG_OK;
   return fill_table(c, h, std::max<int64_t>(0, n - h.TR + 1));
+}
+
+// Scale of the fixed-point composed step for the current state: slot (n mod 3) of the
+// exponent slots gets the largest biased exponent of u^n, the other two are cleared.
+int reset_exponent(adg_ctx *c, InstHost &h) {
+  if (h.I.fused != 2) return ADG_OK;
+  CK(cudaMemsetAsync(h.emax, 0, 3 * sizeof(int), c->stream));
+  const int64_t n = c->n;
+  CK(adg::launch_exponent_max(h.I.u, (size_t)h.I.K * h.I.Np, h.emax + (int)(n % 3), c->stream));
+  return ADG_OK;
 }
 
 // Autotuner of the composed-step kernel: times one, two and four elements per thread on a
@@ -566,14 +609,35 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   {
     const bool eligible = cfg->pde == ADG_ADVECTION && cfg->a > 0 && K >= 8 &&
                           (!I.async || I.Kpe >= 8);
-    if (cfg->variant == ADG_VARIANT_COMPOSED && !eligible)
+    const bool want_composed = cfg->variant == ADG_VARIANT_COMPOSED ||
+                               cfg->variant == ADG_VARIANT_COMPOSED_FIXED;
+    if (want_composed && !eligible)
       return fail(c, ADG_EINVAL, "the composed step needs advection with a > 0, K >= 8 and K/P >= 8");
     I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED) ? 1 : 0;
     I.ept = 1;
     if (I.fused) {
       fold_step_constants(h);
+      if (cfg->variant == ADG_VARIANT_COMPOSED_FIXED && (c->batch || !h.fixed_ok))
+        return fail(c, ADG_EINVAL,
+                    c->batch ? "the fixed-point composed step runs single instances only"
+                             : "the fixed-point composed step needs every composed coefficient "
+                               "below 2 in magnitude (a smaller Courant number)");
+      const bool fixed = !c->batch && h.fixed_ok &&
+                         (cfg->variant == ADG_VARIANT_AUTO ||
+                          cfg->variant == ADG_VARIANT_COMPOSED_FIXED);
+      if (fixed) {
+        I.fused = 2;
+        CK(cudaMalloc(&h.emax, 3 * sizeof(int)));
+        I.emax = h.emax;
+        int r2 = reset_exponent(c, h);
+        if (r2) return r2;
+      }
       if (!c->batch) {
         int r2 = autotune_fused(c, h);
+        if (r2) return r2;
+      }
+      if (fixed) {   // the autotuner's launches moved the exponent slots
+        int r2 = reset_exponent(c, h);
         if (r2) return r2;
       }
     }
@@ -1007,6 +1071,7 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
     if (ring_n)
       CK(cudaMemcpyAsync(I.ring, ck_ring.p, ring_n * sizeof(double2), cudaMemcpyDeviceToDevice, c->stream));
     r = set_step(c, h, n0);
+    if (!r) r = reset_exponent(c, h);
     if (r) return r;
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -1061,6 +1126,7 @@ void adg_destroy(adg_ctx *c) {
     cudaFree(h.coef);
     cudaFree(h.w);
     cudaFree(h.M);
+    cudaFree(h.emax);
   }
   cudaFree(c->meta);
   cudaFree(c->insts_dev);

@@ -54,6 +54,16 @@ struct StepConsts {
   double k[3];
 };
 
+// The StepConsts in fixed point for the integer composed step: each coefficient c
+// (|c| < 2) is C = round(c 2^58), split into limbs C = x 2^29 + y with 0 <= y < 2^29
+// (int2 {x, y}).
+struct StepFixed {
+  int2 G[kMaxNp * kMaxNp];
+  int2 r1[kMaxNp], r2[kMaxNp];
+  int2 h[3][kMaxNp];
+  int2 k[3];
+};
+
 // One DG instance as the kernels see it. Nodal fields are node-major: field[i*K + e].
 struct alignas(16) Inst {
   double *u;            // u^n, updated in place by stage 3
@@ -65,10 +75,13 @@ struct alignas(16) Inst {
   const double *coef;   // AT coefficients [L][q][q]: coef[(k*q + (q'-1))*q + i]
   double a;
   int K, Np, P, Kpe, R, L, q, pde, async, table_rows;
-  int fused;            // 1: steps use the composed stencil (StepConsts) + PE-face fix-up
+  int fused;            // 0: staged; composed stencil + PE-face fix-up in 1: FP64 (StepConsts),
+                        // 2: fixed-point integer arithmetic (StepFixed)
   int ept;              // elements per thread of the composed-step kernel (1, 2 or 4, autotuned)
+  int *emax;            // fused == 2: [3] largest biased FP64 exponent of u^n in slot n % 3
   StageConsts sc[kStages];
   StepConsts st;
+  StepFixed sf;
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
@@ -131,6 +144,9 @@ cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, in
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int parity, int rel,
                                     cudaStream_t s);
+// Largest biased FP64 exponent of the n nodal values of f into *slot (0 first, then the
+// maximum), for the fixed-point composed step.
+cudaError_t launch_exponent_max(const double *f, size_t n, int *slot, cudaStream_t s);
 cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                    cudaStream_t s);
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,

@@ -12,7 +12,7 @@ import torch
 
 import paper_2404_03399_gb300 as adg
 from oracle import dg, delays as odelays
-from workloads import (ADVECTION_SMALL, ADVECTION_16M, BURGERS_1M, PAPER_FIG6, SIN,
+from workloads import (ADVECTION_SMALL, ADVECTION_16M, BURGERS_1M, PAPER_FIG6, SIN, Modes,
                        HALF_PLUS_SIN, caa_table, constant_table, random_nodal)
 
 pytestmark = pytest.mark.gpu
@@ -76,7 +76,7 @@ def test_advection_small_stated_config(mode, q):
     assert rel_linf(got, ref) < TOL
 
 
-@pytest.mark.parametrize("variant", ["staged", "composed"])
+@pytest.mark.parametrize("variant", ["staged", "composed", "fixed"])
 @pytest.mark.parametrize("p", [1, 2, 3, 4])
 @pytest.mark.parametrize("mode,q", [("sync", 0), ("async", 0), ("at", 0)])
 def test_advection_degrees_and_modes(p, mode, q, variant):
@@ -129,7 +129,7 @@ def test_caller_tables(kind):
 
 
 @pytest.mark.parametrize("pde,variant", [("advection", "staged"), ("advection", "composed"),
-                                         ("burgers", "auto")])
+                                         ("advection", "fixed"), ("burgers", "auto")])
 def test_zero_delay_is_bitwise_sync(pde, variant):
     K, p, P = 512, 3, 16
     u0 = torch.tensor(dg.modes_initial(HALF_PLUS_SIN if pde == "burgers" else PAPER_FIG6, K, p), device="cuda")
@@ -202,7 +202,8 @@ def _window_oracle(cfg, u0_full_fn, e, steps, dt, table_rows, both_sides):
     return out[r]
 
 
-@pytest.mark.parametrize("which", ["advection_16m", "advection_16m_staged", "burgers_1m"])
+@pytest.mark.parametrize("which", ["advection_16m", "advection_16m_staged", "advection_16m_composed",
+                                   "burgers_1m"])
 def test_full_size_sampled(which):
     # Full-size meshes in the launch configuration the benchmark times (graph replay of
     # 32-step chunks plus a direct remainder), checked at sampled elements against the
@@ -210,7 +211,7 @@ def test_full_size_sampled(which):
     if which.startswith("advection_16m"):
         w = ADVECTION_16M
         cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode="at", L=w.L, q=w.q,
-                         seed=w.seed, variant="staged" if which.endswith("staged") else "auto")
+                         seed=w.seed, variant=which[len("advection_16m_"):] or "auto")
         modes, steps, both = SIN, 40, False
     else:
         w = BURGERS_1M
@@ -237,3 +238,54 @@ def test_full_size_sampled(which):
         ref = _window_oracle(cfg, fn, e, steps, dt, tbl, both)
         worst = max(worst, float(np.max(np.abs(got[e] - ref))) / scale)
     assert worst < TOL
+
+
+@pytest.mark.parametrize("scale", [1e-150, 1.0, 1e150])
+def test_fixed_point_scales(scale):
+    # The integer composed step works at the scale of u^n's largest exponent: tiny and huge
+    # fields give the same relative agreement as unit ones.
+    cfg = adg.Config(pde="advection", K=160, p=3, P=10, cfl=0.01, mode="at", L=4, q=3, seed=4,
+                     variant="fixed")
+    u0 = scale * dg.modes_initial(PAPER_FIG6, 160, 3)
+    got, ref, _ = run_pair(cfg, u0, 60)
+    assert rel_linf(got, ref) < TOL
+
+
+def test_fixed_point_follows_a_decaying_field():
+    # An under-resolved wave (2.7 elements per wavelength at kappa = 24, p = 1) is dissipated
+    # by the upwind flux to about 1e-4 of its size over the run, so the largest exponent of
+    # u^n, and with it the scale of the integer step, falls by 13 binades. The decayed field is
+    # ill-conditioned (a 1e-16 perturbation of u0 moves it by 1e-12 of its final size in the
+    # oracle), so both variants are held to the initial size, and the integer step to the
+    # FP64 composed step's own error.
+    K, p = 64, 1
+    u0 = dg.modes_initial(Modes(amp=(1.0,), kappa=(24.0,), phase=(0.3,)), K, p)
+    errs = {}
+    for variant in ("composed", "fixed"):
+        cfg = adg.Config(pde="advection", K=K, p=p, P=8, cfl=0.05, mode="at", L=3, q=2, seed=6,
+                         variant=variant)
+        got, ref, _ = run_pair(cfg, u0, 1000)
+        assert np.max(np.abs(ref)) < 1e-3 * np.max(np.abs(u0))
+        errs[variant] = float(np.max(np.abs(got - ref))) / np.max(np.abs(u0))
+    assert errs["fixed"] < 1e-14
+    assert errs["fixed"] <= 4 * errs["composed"] + 1e-17
+
+
+def test_fixed_point_matches_fp64_composed():
+    cfg = dict(pde="advection", K=4096 + 300, p=3, P=7, cfl=0.005, mode="at", L=5, q=3, seed=13)
+    u0 = torch.tensor(random_nodal(4396, 3, 8), device="cuda")
+    outs = []
+    for variant in ("composed", "fixed"):
+        s = adg.Solver(adg.Config(variant=variant, **cfg), u0)
+        s.step(77)
+        outs.append(s.state().cpu().numpy())
+        s.close()
+    assert rel_linf(outs[1], outs[0]) < 1e-13
+
+
+def test_fixed_point_rejects_large_coefficients():
+    # At sigma = 0.4 the composed coefficients leave the integer step's bounds.
+    cfg = adg.Config(pde="advection", K=64, p=3, P=8, cfl=0.4, mode="sync", variant="fixed")
+    with pytest.raises(adg.AdgError) as ei:
+        adg.Solver(cfg, adg.eval_modes(cfg, [1.0], [1.0], [0.0]))
+    assert ei.value.code == adg._abi.ADG_EINVAL
