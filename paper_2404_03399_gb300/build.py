@@ -17,7 +17,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libadg.so")
 
-SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_adjoint.cu", "adg_static.cu"]
+SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_fixed.cu", "adg_adjoint.cu", "adg_static.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 
@@ -39,7 +39,7 @@ def _stale(obj: str, deps) -> bool:
 def build(verbose: bool = False, force: bool = False) -> str:
     os.makedirs(BUILD, exist_ok=True)
     headers = [os.path.join(CSRC, "adg_internal.h"), os.path.join(CSRC, "adg_device.cuh"),
-               os.path.join(INCLUDE, "adg.h")]
+               os.path.join(CSRC, "adg_fixed.cuh"), os.path.join(INCLUDE, "adg.h")]
     objs, procs = [], []
     for src in SOURCES:
         path = os.path.join(CSRC, src)

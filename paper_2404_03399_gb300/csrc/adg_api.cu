@@ -295,7 +295,7 @@ struct InstHost {
   uint8_t *table = nullptr;
   double *coef = nullptr;
   double *w = nullptr, *M = nullptr;
-  int *emax = nullptr;       // exponent slots of the fixed-point composed step
+  adg::FxSlot *fx = nullptr; // scale slots of the fixed-point composed step
   bool fixed_ok = false;     // the composed coefficients fit the fixed-point bounds
   std::vector<uint8_t> host_rows;
 };
@@ -494,13 +494,11 @@ int ensure_table_back(adg_ctx *c, InstHost &h, int64_t n) {
   return fill_table(c, h, std::max<int64_t>(0, n - h.TR + 1));
 }
 
-// Scale of the fixed-point composed step for the current state: slot (n mod 3) of the
-// exponent slots gets the largest biased exponent of u^n, the other two are cleared.
+// Scale slots of the fixed-point composed step for the current state: slot (n mod 3) gets
+// the largest biased exponent of u^n (FP64), the other two are cleared.
 int reset_exponent(adg_ctx *c, InstHost &h) {
   if (h.I.fused != 2) return ADG_OK;
-  CK(cudaMemsetAsync(h.emax, 0, 3 * sizeof(int), c->stream));
-  const int64_t n = c->n;
-  CK(adg::launch_exponent_max(h.I.u, (size_t)h.I.K * h.I.Np, h.emax + (int)(n % 3), c->stream));
+  CK(adg::launch_fixed_reset(h.I.u, (size_t)h.I.K * h.I.Np, h.fx, c->n, c->stream));
   return ADG_OK;
 }
 
@@ -512,20 +510,29 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   Inst &I = h.I;
   const size_t nd = (size_t)I.K * I.Np;
   if (I.K < 4 * 2 * adg::kTile) return ADG_OK;   // tiny meshes: one element per thread
-  CK(cudaMemcpyAsync(I.v1, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  // The fixed-point step is timed in its int64 -> int64 form (the bulk of a chunk): one
+  // FP64 -> int64 step fills v1, then v1 and v2 alternate. The FP64 step alternates copies
+  // of u0 in v1 and v2.
+  const bool fixed = I.fused == 2;
+  if (fixed)
+    CK(adg::launch_fused_step(I, I.u, I.v1, 0, c->stream, false, adg::kFmtOutFixed));
+  else
+    CK(cudaMemcpyAsync(I.v1, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+  const int fmt = fixed ? adg::kFmtInFixed | adg::kFmtOutFixed : 0;
+  const int rel = fixed ? 1 : 0;   // the slot the first step wrote
   cudaEvent_t a = nullptr, b = nullptr;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
   float best = 1e30f;
   int best_ept = 1;
-  for (int ept = 1; ept <= 4; ept *= 2) {
+  for (int ept = 1; ept <= (fixed ? 2 : 4); ept *= 2) {
     Inst T = I;
     T.ept = ept;
     float ms = 0.0f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, c->stream);
       for (int k = 0; k < 2; ++k) {
-        CK(adg::launch_fused_step(T, k ? I.v2 : I.v1, k ? I.v1 : I.v2, 0, c->stream, false));
+        CK(adg::launch_fused_step(T, k ? I.v2 : I.v1, k ? I.v1 : I.v2, rel, c->stream, false, fmt));
       }
       cudaEventRecord(b, c->stream);
       CK(cudaEventSynchronize(b));
@@ -627,8 +634,8 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
                           cfg->variant == ADG_VARIANT_COMPOSED_FIXED);
       if (fixed) {
         I.fused = 2;
-        CK(cudaMalloc(&h.emax, 3 * sizeof(int)));
-        I.emax = h.emax;
+        CK(cudaMalloc(&h.fx, 3 * sizeof(adg::FxSlot)));
+        I.fx = h.fx;
         int r2 = reset_exponent(c, h);
         if (r2) return r2;
       }
@@ -695,14 +702,27 @@ int launch_steps(adg_ctx *c, int nsteps) {
 // Composed steps ping-pong between u and v1; an odd count ends with a copy back into u.
 int launch_fused_steps(adg_ctx *c, int nsteps) {
   const Inst &I = c->inst[0].I;
-  for (int rel = 0; rel < nsteps; ++rel) {
-    const double *uin = (rel % 2 == 0) ? I.u : I.v1;
-    double *uout = (rel % 2 == 0) ? I.v1 : I.u;
-    CK(adg::launch_fused_step(I, uin, uout, rel, c->stream));
+  if (I.fused == 2 && nsteps >= 2) {
+    // Fixed point: u (FP64) -> v1 (int64) -> v2 -> v1 ... -> u (FP64); the chunk's interior
+    // steps neither read nor write FP64.
+    CK(adg::launch_fused_step(I, I.u, I.v1, 0, c->stream, true, adg::kFmtOutFixed));
+    void *in = I.v1, *out = I.v2;
+    for (int rel = 1; rel < nsteps - 1; ++rel) {
+      CK(adg::launch_fused_step(I, in, out, rel, c->stream, true,
+                                adg::kFmtInFixed | adg::kFmtOutFixed));
+      std::swap(in, out);
+    }
+    CK(adg::launch_fused_step(I, in, I.u, nsteps - 1, c->stream, true, adg::kFmtInFixed));
+  } else {
+    for (int rel = 0; rel < nsteps; ++rel) {
+      const double *uin = (rel % 2 == 0) ? I.u : I.v1;
+      double *uout = (rel % 2 == 0) ? I.v1 : I.u;
+      CK(adg::launch_fused_step(I, uin, uout, rel, c->stream));
+    }
+    if (nsteps % 2)
+      CK(cudaMemcpyAsync(I.u, I.v1, (size_t)I.K * I.Np * sizeof(double), cudaMemcpyDeviceToDevice,
+                         c->stream));
   }
-  if (nsteps % 2)
-    CK(cudaMemcpyAsync(I.u, I.v1, (size_t)I.K * I.Np * sizeof(double), cudaMemcpyDeviceToDevice,
-                       c->stream));
   CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
   return ADG_OK;
 }
@@ -1126,7 +1146,7 @@ void adg_destroy(adg_ctx *c) {
     cudaFree(h.coef);
     cudaFree(h.w);
     cudaFree(h.M);
-    cudaFree(h.emax);
+    cudaFree(h.fx);
   }
   cudaFree(c->meta);
   cudaFree(c->insts_dev);

@@ -40,6 +40,18 @@ __device__ __forceinline__ double num_flux(double a, double uL, double uR) {
 
 __device__ __forceinline__ int64_t ring_slot(int64_t level, int R) { return level % R; }
 
+// Loads the Np nodal values of element e from a node-major field by pointer steps of K
+// (no per-node 64-bit index products).
+template <int NP, class T>
+__device__ __forceinline__ void load_elem(const T *__restrict__ f, int K, int e, T *u) {
+  const T *q = f + e;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    u[i] = __ldg(q);
+    q += K;
+  }
+}
+
 __device__ __forceinline__ bool nonzero(double x) {
   return (__double_as_longlong(x) << 1) != 0;   // integer test: not +0 or -0
 }

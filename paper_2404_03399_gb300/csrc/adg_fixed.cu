@@ -1,0 +1,263 @@
+// Composed SSP-RK3 step of upwind advection (a > 0) in fixed-point integer arithmetic:
+// the StepConsts stencil (adg_internal.h) evaluated exactly with 32 x 32 -> 64-bit integer
+// multiply-adds on two-limb values (adg_fixed.cuh). Within a chunk of steps the field stays
+// int64 between steps; only the chunk's first step reads FP64 and its last writes FP64.
+#include "adg_device.cuh"
+#include "adg_fixed.cuh"
+
+namespace adg {
+namespace {
+
+template <int EPT>
+struct FixedShared {
+  long long p[EPT * kTile + 3], q1[EPT * kTile + 3], q2[EPT * kTile + 3];
+  unsigned long long wmag[kTile / 32];
+  int wmax[kTile / 32];
+  FxScale sc;
+};
+
+// Working-scale value of node j of an element (FP64 or stored int64 input).
+template <bool FIN>
+__device__ __forceinline__ long long fx_in(double x, long long X, const FxScale &sc) {
+  if (FIN) return fx_rescale(X, sc.shift);
+  return fx_from_double(x, sc.sigma + 1079);
+}
+
+// p = the element's right trace, s1 / s2 = the own parts r1 . u, r2 . u of its channel
+// scalars (unrounded sums), and the limbs of its values for the output rows.
+template <int NP, bool FIN>
+__device__ __forceinline__ void fx_own(const StepFixed &F, const double *ud, const long long *uq,
+                                       const FxScale &sc, long long &p, FxAcc &s1, FxAcc &s2,
+                                       int *xh, int *xl) {
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    const long long X = fx_in<FIN>(FIN ? 0.0 : ud[j], FIN ? uq[j] : 0ll, sc);
+    fx_split(X, xh[j], xl[j]);
+    fx_mac(s1, F.r1[j], xh[j], xl[j]);
+    fx_mac(s2, F.r2[j], xh[j], xl[j]);
+    if (j == NP - 1) p = X;
+  }
+}
+
+// One thread per element (EPT elements per thread, e = e0 + t + h kTile): the right trace and
+// the own parts of the channel scalars, then v1_p = r1 . u + k_0 P0 and
+// v2_p = r2 . u + k_1 P0 + k_2 P1 in two rounds through shared memory, then
+// u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2 from the left neighbour's channel scalars. The first
+// three threads form the scalars of the three elements before the block with the same
+// arithmetic (the working scale is one per field, so every element converts the same way).
+template <int NP, int EPT, int FMT>
+__global__ void __launch_bounds__(kTile) k_step_fixed(const Inst inst, const void *__restrict__ uin_,
+                                                      void *__restrict__ uout_, int rel) {
+  constexpr bool FIN = (FMT & kFmtInFixed) != 0;
+  constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
+  __shared__ FixedShared<EPT> sh;
+  const double *uin_d = static_cast<const double *>(uin_);
+  const long long *uin_q = static_cast<const long long *>(uin_);
+  const int K = inst.K;
+  const int t = threadIdx.x;
+  const int e0 = blockIdx.x * (kTile * EPT);
+  const StepFixed &F = inst.sf;
+
+  // loads first: they do not depend on the scale
+  double hd[NP];
+  long long hq[NP];
+  if (t < 3) {
+    int m = e0 - 3 + t;
+    if (m < 0) m += K;   // K >= 8 on this path
+    if (FIN) load_elem<NP>(uin_q, K, m, hq);
+    else load_elem<NP>(uin_d, K, m, hd);
+  }
+  double ud[EPT][NP];
+  long long uq[EPT][NP];
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    const int e = e0 + t + h * kTile;
+    if (FIN) load_elem<NP>(uin_q, K, e < K ? e : K - 1, uq[h]);
+    else load_elem<NP>(uin_d, K, e < K ? e : K - 1, ud[h]);
+  }
+  if (t == 0) {
+    const FxScale sc = fx_scale(inst.fx, inst.meta[0] + rel, FIN);
+    sh.sc = sc;
+    if (blockIdx.x == 0) {
+      FxSlot &c = inst.fx[fx_clear(sc.slot)];   // the slot of u^{n+2}
+      c.mag = 0;
+      c.E = 0;
+      c.sigma = 0;
+      if (FOUT) {
+        inst.fx[fx_next(sc.slot)].sigma = sc.sigma;
+        if (sc.bad) inst.fx[fx_next(sc.slot)].E = 2047;
+      }
+    }
+  }
+  __syncthreads();
+  const FxScale sc = sh.sc;
+  FxAcc hs1, hs2;
+  if (t < 3) {
+    int xh[NP], xl[NP];
+    long long p;
+    fx_own<NP, FIN>(F, hd, hq, sc, p, hs1, hs2, xh, xl);
+    sh.p[t] = p;
+  }
+  int xh[EPT][NP], xl[EPT][NP];
+  FxAcc s1[EPT], s2[EPT];
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    long long p;
+    fx_own<NP, FIN>(F, ud[h], uq[h], sc, p, s1[h], s2[h], xh[h], xl[h]);
+    sh.p[t + h * kTile + 3] = p;
+  }
+  __syncthreads();
+  // v1_p = r1 . u + k_0 P0, rounded once
+  if (t == 1 || t == 2) {
+    int ph, pl;
+    fx_split(sh.p[t - 1], ph, pl);
+    fx_mac(hs1, F.k[0], ph, pl);
+    sh.q1[t] = fx_round(hs1);
+  }
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    const int sl = t + h * kTile + 3;
+    int ph, pl;
+    fx_split(sh.p[sl - 1], ph, pl);
+    fx_mac(s1[h], F.k[0], ph, pl);
+    sh.q1[sl] = fx_round(s1[h]);
+  }
+  __syncthreads();
+  // v2_p = r2 . u + k_1 P0 + k_2 P1, rounded once
+  if (t == 2) {
+    int ph, pl, qh, ql;
+    fx_split(sh.p[1], ph, pl);
+    fx_split(sh.q1[1], qh, ql);
+    fx_mac(hs2, F.k[1], ph, pl);
+    fx_mac(hs2, F.k[2], qh, ql);
+    sh.q2[2] = fx_round(hs2);
+  }
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    const int sl = t + h * kTile + 3;
+    int ph, pl, qh, ql;
+    fx_split(sh.p[sl - 1], ph, pl);
+    fx_split(sh.q1[sl - 1], qh, ql);
+    fx_mac(s2[h], F.k[1], ph, pl);
+    fx_mac(s2[h], F.k[2], qh, ql);
+    sh.q2[sl] = fx_round(s2[h]);
+  }
+  __syncthreads();
+  unsigned long long mag = 0;   // FOUT: OR of |y|
+  int emax = 0;                 // FP64 output: largest biased exponent
+#pragma unroll
+  for (int h = 0; h < EPT; ++h) {
+    const int b = t + h * kTile;   // left neighbour's slot is b + 2
+    const int e = e0 + b;
+    int P0h, P0l, P1h, P1l, P2h, P2l;
+    fx_split(sh.p[b + 2], P0h, P0l);
+    fx_split(sh.q1[b + 2], P1h, P1l);
+    fx_split(sh.q2[b + 2], P2h, P2l);
+    const size_t base = (size_t)e;
+    double *od = static_cast<double *>(uout_) + base;
+    long long *oq = static_cast<long long *>(uout_) + base;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      FxAcc acc;
+#pragma unroll
+      for (int j = 0; j < NP; ++j) fx_mac(acc, F.G[i * NP + j], xh[h][j], xl[h][j]);
+      fx_mac(acc, F.h[0][i], P0h, P0l);
+      fx_mac(acc, F.h[1][i], P1h, P1l);
+      fx_mac(acc, F.h[2][i], P2h, P2l);
+      const long long y = fx_round(acc);
+      if (FOUT) {
+        if (e < K) {
+          *oq = y;
+          mag |= fx_mag(y);
+        }
+      } else {
+        const double v = sc.bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(y, sc.sigma);
+        if (e < K) {
+          *od = v;
+          const int be = biased_exponent(v);
+          emax = be > emax ? be : emax;
+        }
+      }
+      od += K;
+      oq += K;
+    }
+  }
+  // the scale of u^{n+1}: OR of |y| (int64 output) or largest exponent (FP64 output)
+  const int w = t >> 5;
+  if (FOUT) {
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mag);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mag >> 32));
+    if ((t & 31) == 0) sh.wmag[w] = ((unsigned long long)hi << 32) | lo;
+  } else {
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((t & 31) == 0) sh.wmax[w] = emax;
+  }
+  __syncthreads();
+  if (t == 0) {
+    FxSlot &nx = inst.fx[fx_next(sc.slot)];
+    if (FOUT) {
+      unsigned long long m = 0;
+      for (int k = 0; k < kTile / 32; ++k) m |= sh.wmag[k];
+      or_slot(&nx.mag, m);
+    } else {
+      int m = 0;
+      for (int k = 0; k < kTile / 32; ++k) m = sh.wmax[k] > m ? sh.wmax[k] : m;
+      raise_slot(&nx.E, m);
+    }
+  }
+}
+
+__global__ void k_fixed_reset(const double *__restrict__ f, size_t n, int *E) {
+  int m = 0;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int be = biased_exponent(f[i]);
+    m = be > m ? be : m;
+  }
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) raise_slot(E, m);
+}
+
+template <int NP, int FMT>
+void fixed_np_fmt(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s) {
+  if (I.ept == 2)
+    k_step_fixed<NP, 2, FMT><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, uin, uout, rel);
+  else
+    k_step_fixed<NP, 1, FMT><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout, rel);
+}
+
+template <int NP>
+void fixed_np(const Inst &I, const void *uin, void *uout, int rel, int fmt, cudaStream_t s) {
+  switch (fmt & 3) {
+    case 0: fixed_np_fmt<NP, 0>(I, uin, uout, rel, s); break;
+    case 1: fixed_np_fmt<NP, 1>(I, uin, uout, rel, s); break;
+    case 2: fixed_np_fmt<NP, 2>(I, uin, uout, rel, s); break;
+    default: fixed_np_fmt<NP, 3>(I, uin, uout, rel, s); break;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int rel, int fmt,
+                              cudaStream_t s) {
+  switch (I.Np) {
+    case 2: fixed_np<2>(I, uin, uout, rel, fmt, s); break;
+    case 3: fixed_np<3>(I, uin, uout, rel, fmt, s); break;
+    case 4: fixed_np<4>(I, uin, uout, rel, fmt, s); break;
+    case 5: fixed_np<5>(I, uin, uout, rel, fmt, s); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,
+                               cudaStream_t s) {
+  cudaError_t e = cudaMemsetAsync(fx, 0, 3 * sizeof(FxSlot), s);
+  if (e != cudaSuccess) return e;
+  const size_t want = (n + 255) / 256;
+  const unsigned grid = (unsigned)(want < 4 * 152 ? (want ? want : 1) : 4 * 152);
+  k_fixed_reset<<<grid, 256, 0, s>>>(f, n, &fx[(int)(step % 3)].E);
+  return cudaGetLastError();
+}
+
+}  // namespace adg

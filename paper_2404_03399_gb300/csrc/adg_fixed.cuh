@@ -1,0 +1,147 @@
+// Fixed-point arithmetic of the integer composed step (adg_fixed.cu) and of the PE-face
+// fix-up when it reads or writes fixed-point fields (adg_kernels.cu).
+//
+// On this part a warp's FP64 instruction occupies the FP64 pipe for 16 clocks (2 lanes per
+// clock per SM) while a 32 x 32 -> 64-bit integer multiply-add issues at the integer rate,
+// so the composed step (StepConsts) is evaluated exactly in integers.
+//
+// Representation: a field at step n is either FP64 or int64 values X with one scale for the
+// whole field, value = X 2^sigma. A step first brings its input to the working scale sigma'
+// at which |X| < 2^57:
+//   FP64 input: sigma' = En - 1079, En the largest biased FP64 exponent over u^n
+//               (|x| < 2^(En - 1022)), X = round(x 2^-sigma');
+//   int64 input (|X| < 2^62, bit length b of the OR of all |X|): X' = round(X 2^-(b-57)),
+//               sigma' = sigma + (b - 57).
+// X is split into limbs X = xh 2^29 + xl with 0 <= xl < 2^29, and a coefficient c
+// (|c| < 2) into C = round(c 2^58) = ch 2^29 + cl likewise. Then
+//   c x 2^-sigma' ~ C X 2^-58 = ch xh + (ch xl + cl xh) 2^-29 + cl xl 2^-58,
+// the last term (< 1 unit) is dropped, the others accumulate exactly in two 64-bit sums a and
+// b, and a sum of terms is rounded once: a + round(b 2^-29). With |X| < 2^58 for the channel
+// scalars and at most 8 terms per sum, |a| < 2^62 and |b| < 2^63 (the host checks the
+// coefficient bounds that keep the channel scalars below 2^58), and every result is below
+// 2^62 (|G| rows, |h| at most 20 x 2^57). Results are stored as int64 at sigma' or rounded
+// to FP64 (round to nearest even).
+//
+// Scale bookkeeping: slot n % 3 of the instance's FxSlot[3] describes u^n: E (largest
+// biased exponent when u^n is FP64; 2047 marks a NaN or infinity, carried through int64
+// steps), sigma and mag (OR of |X|) when it is int64. Step n reads slot n % 3, raises slot
+// (n + 1) % 3 and clears slot (n + 2) % 3 (block 0).
+#pragma once
+
+#include "adg_internal.h"
+
+namespace adg {
+namespace {
+
+struct FxAcc {
+  long long a = 0, b = 0;
+};
+
+__device__ __forceinline__ void fx_mac(FxAcc &s, int2 c, int xh, int xl) {
+  s.a += (long long)c.x * xh;
+  s.b += (long long)c.x * xl;
+  s.b += (long long)c.y * xh;
+}
+
+__device__ __forceinline__ long long fx_round(const FxAcc &s) {
+  return s.a + ((s.b + (1ll << 28)) >> 29);
+}
+
+__device__ __forceinline__ void fx_split(long long X, int &xh, int &xl) {
+  xh = (int)(X >> 29);
+  xl = (int)(X & 0x1FFFFFFF);
+}
+
+// FP64 -> int64 at scale sigma = En - 1079 (round half away from zero): |x| < 2^(En-1022)
+// gives |X| < 2^57.
+__device__ __forceinline__ long long fx_from_double(double x, int En) {
+  const long long bits = __double_as_longlong(x);
+  const int e = (int)(((unsigned long long)bits >> 52) & 0x7ff);
+  unsigned long long m = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
+  int d = En - e;
+  if (e) m |= 1ull << 52;
+  else d -= 1;   // subnormal: the scale of exponent 1
+  d = d < 0 ? 0 : (d > 63 ? 63 : d);
+  m <<= 4;
+  const unsigned long long M = (m + ((1ull << d) >> 1)) >> d;
+  return bits < 0 ? -(long long)M : (long long)M;
+}
+
+// int64 at scale sigma -> FP64, round to nearest even; below the normal range the result
+// is a signed zero, above it an infinity.
+__device__ __forceinline__ double fx_to_double(long long y, int sigma) {
+  if (y == 0) return 0.0;
+  const unsigned long long sgn = (unsigned long long)y & 0x8000000000000000ull;
+  const unsigned long long a = y < 0 ? 0ull - (unsigned long long)y : (unsigned long long)y;
+  const int lz = __clzll((long long)a);
+  const unsigned long long nrm = a << lz;
+  unsigned long long m = nrm >> 11;
+  const unsigned rem = (unsigned)nrm & 0x7ffu;
+  m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
+  int ex = 1086 + sigma - lz;
+  if (m >> 53) {
+    m >>= 1;
+    ++ex;
+  }
+  if (ex <= 0) return __longlong_as_double((long long)sgn);
+  if (ex >= 2047) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull));
+  return __longlong_as_double(
+      (long long)(sgn | ((unsigned long long)ex << 52) | (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// int64 X at the stored scale -> working scale (shift = b - 57): rounded right shift when
+// the field has grown past 2^57, exact left shift when it has shrunk.
+__device__ __forceinline__ long long fx_rescale(long long X, int shift) {
+  if (shift > 0) return (X + (1ll << (shift - 1))) >> shift;
+  if (shift < 0) return (long long)((unsigned long long)X << (-shift));
+  return X;
+}
+
+__device__ __forceinline__ int biased_exponent(double x) {
+  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
+}
+
+__device__ __forceinline__ unsigned long long fx_mag(long long y) {
+  return y < 0 ? 0ull - (unsigned long long)y : (unsigned long long)y;
+}
+
+// Raises *slot to v unless it already holds at least v (slots only grow during a step, so
+// a stale read can only cause a redundant atomic).
+__device__ __forceinline__ void raise_slot(int *slot, int v) {
+  if (v > *(volatile int *)slot) atomicMax(slot, v);
+}
+
+__device__ __forceinline__ void or_slot(unsigned long long *slot, unsigned long long v) {
+  const unsigned long long cur = *(volatile unsigned long long *)slot;
+  if ((cur | v) != cur) atomicOr(slot, v);
+}
+
+// Working scale of step n for input format fin (true: int64).
+struct FxScale {
+  int sigma;   // working scale sigma'
+  int shift;   // int64 input: X' = fx_rescale(X, shift)
+  int slot;    // n % 3
+  bool bad;    // u^n holds a NaN or an infinity
+};
+
+__device__ __forceinline__ FxScale fx_scale(const FxSlot *fx, int64_t n, bool fin) {
+  FxScale s;
+  s.slot = (int)(n % 3);
+  const FxSlot &cur = fx[s.slot];
+  s.bad = cur.E >= 2047;
+  if (!fin) {
+    s.sigma = cur.E - 1079;
+    s.shift = 0;
+  } else {
+    const unsigned long long M = cur.mag;
+    s.shift = M ? (64 - __clzll((long long)M)) - 57 : 0;
+    s.sigma = cur.sigma + s.shift;
+  }
+  return s;
+}
+
+__device__ __forceinline__ int fx_next(int slot) { return slot == 2 ? 0 : slot + 1; }
+__device__ __forceinline__ int fx_clear(int slot) { return slot == 0 ? 2 : slot - 1; }
+
+}  // namespace
+}  // namespace adg

@@ -64,6 +64,20 @@ struct StepFixed {
   int2 k[3];
 };
 
+// Formats of a fixed-point composed step (launch_fused_step's fmt): bit 0 the input, bit 1
+// the output is int64 fixed point; FP64 otherwise.
+constexpr int kFmtInFixed = 1;
+constexpr int kFmtOutFixed = 2;
+
+// Scale of a field at one step for the fixed-point composed step (adg_fixed.cuh): E is the
+// largest biased FP64 exponent (2047: a NaN or infinity is present), sigma and mag the scale
+// and the OR of |X| of an int64 field.
+struct FxSlot {
+  unsigned long long mag;
+  int E;
+  int sigma;
+};
+
 // One DG instance as the kernels see it. Nodal fields are node-major: field[i*K + e].
 struct alignas(16) Inst {
   double *u;            // u^n, updated in place by stage 3
@@ -78,7 +92,7 @@ struct alignas(16) Inst {
   int fused;            // 0: staged; composed stencil + PE-face fix-up in 1: FP64 (StepConsts),
                         // 2: fixed-point integer arithmetic (StepFixed)
   int ept;              // elements per thread of the composed-step kernel (1, 2 or 4, autotuned)
-  int *emax;            // fused == 2: [3] largest biased FP64 exponent of u^n in slot n % 3
+  FxSlot *fx;           // fused == 2: [3] scale of u^n in slot n % 3
   StageConsts sc[kStages];
   StepConsts st;
   StepFixed sf;
@@ -136,17 +150,23 @@ cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int 
 cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t by,
                            cudaStream_t s);
 // Composed step uin -> uout (rel: step offset from meta[0]) and, with PE faces, the fix-up
-// of the elements next to each PE face with the delayed / AT flux.
-cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
-                              cudaStream_t s, bool with_fixup = true);
+// of the elements next to each PE face with the delayed / AT flux. fmt (fixed-point step,
+// fused == 2, only): bit 0 the input, bit 1 the output is int64 fixed point (adg_fixed.cuh);
+// otherwise both are FP64.
+cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int rel,
+                              cudaStream_t s, bool with_fixup = true, int fmt = 0);
+// The fixed-point composed step alone (adg_fixed.cu).
+cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int rel, int fmt,
+                              cudaStream_t s);
 // Batched composed steps over all instances (parity 0: u -> v1, 1: v1 -> u) and the copy
 // of v1 into u after an odd count.
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int parity, int rel,
                                     cudaStream_t s);
-// Largest biased FP64 exponent of the n nodal values of f into *slot (0 first, then the
-// maximum), for the fixed-point composed step.
-cudaError_t launch_exponent_max(const double *f, size_t n, int *slot, cudaStream_t s);
+// Scale slots of the fixed-point composed step for an FP64 field f of n values at step
+// index `step`: all three slots cleared, then E of slot step % 3 = largest biased exponent.
+cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,
+                               cudaStream_t s);
 cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                    cudaStream_t s);
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,

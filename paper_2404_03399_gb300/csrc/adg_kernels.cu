@@ -7,6 +7,7 @@
 // at PE faces, the delayed / AT flux (Eqs. asyncEulerDGconserved, at-flux-gen) with the
 // ring-buffer write of the stage-input traces are fused into one kernel per stage.
 #include "adg_device.cuh"
+#include "adg_fixed.cuh"
 
 #include <cstdio>
 
@@ -172,18 +173,6 @@ __device__ __forceinline__ void own_scalars(const StepConsts &S, const double *u
   }
 }
 
-// Loads the Np nodal values of element e from a node-major field by pointer steps of K
-// (no per-node 64-bit index products).
-template <int NP>
-__device__ __forceinline__ void load_elem(const double *__restrict__ f, int K, int e, double *u) {
-  const double *q = f + e;
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    u[i] = __ldg(q);
-    q += K;
-  }
-}
-
 // Channel scalars of the elements of one block: slots 0..2 hold the three elements before
 // the block, slot 3+m the block's element m (EPT kTile elements per block).
 template <int EPT>
@@ -265,240 +254,6 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
   fused_body<NP, EPT>(inst, uin, uout, blockIdx.x * (kTile * EPT), sh);
 }
 
-// ---------------------------------------------------------------------------------------
-// Composed step in fixed-point integer arithmetic (same StepConsts algebra as above).
-//
-// On this part a warp's FP64 instruction occupies the FP64 pipe for 16 clocks (2 lanes per
-// clock per SM) while a 32 x 32 -> 64-bit integer multiply-add issues at the integer rate,
-// so the step is evaluated exactly in integers. A value x of u^n is held as
-// X = round(x 2^(1079 - En)), En the largest biased FP64 exponent over u^n (|x| < 2^(En-1022),
-// so |X| < 2^57; one scale for the whole field, so every element is converted the same way
-// wherever it is read). X is split into limbs X = xh 2^29 + xl with 0 <= xl < 2^29, and a
-// coefficient c (|c| < 2) into C = round(c 2^58) = ch 2^29 + cl likewise. Then
-//   c x 2^(1079 - En) ~ C X 2^-58 = ch xh + (ch xl + cl xh) 2^-29 + cl xl 2^-58,
-// the last term (< 1 unit) is dropped, the others accumulate exactly in two 64-bit sums a and
-// b, and a sum of terms is rounded once: a + round(b 2^-29). With |X| < 2^58 for the channel
-// scalars and at most 8 terms per sum, |a| < 2^62 and |b| < 2^63 (the host checks the
-// coefficient bounds that keep the channel scalars below 2^58). Results go back to FP64 with
-// round-to-nearest-even; the block's largest output exponent updates the scale of u^{n+1}.
-struct FxAcc {
-  long long a = 0, b = 0;
-};
-
-__device__ __forceinline__ void fx_mac(FxAcc &s, int2 c, int xh, int xl) {
-  s.a += (long long)c.x * xh;
-  s.b += (long long)c.x * xl;
-  s.b += (long long)c.y * xh;
-}
-
-__device__ __forceinline__ long long fx_round(const FxAcc &s) {
-  return s.a + ((s.b + (1ll << 28)) >> 29);
-}
-
-__device__ __forceinline__ void fx_split(long long X, int &xh, int &xl) {
-  xh = (int)(X >> 29);
-  xl = (int)(X & 0x1FFFFFFF);
-}
-
-// FP64 -> fixed point at scale En (round half away from zero; |x| < 2^(En-1022) gives
-// |X| < 2^57).
-__device__ __forceinline__ long long fx_from_double(double x, int En) {
-  const long long bits = __double_as_longlong(x);
-  const int e = (int)(((unsigned long long)bits >> 52) & 0x7ff);
-  unsigned long long m = (unsigned long long)bits & 0xFFFFFFFFFFFFFull;
-  int d = En - e;
-  if (e) m |= 1ull << 52;
-  else d -= 1;   // subnormal: the scale of exponent 1
-  d = d < 0 ? 0 : (d > 63 ? 63 : d);
-  m <<= 4;
-  const unsigned long long M = (m + ((1ull << d) >> 1)) >> d;
-  return bits < 0 ? -(long long)M : (long long)M;
-}
-
-// Fixed point at scale En -> FP64, round to nearest even; below the normal range the result
-// is a signed zero, above it an infinity.
-__device__ __forceinline__ double fx_to_double(long long y, int En) {
-  if (y == 0) return 0.0;
-  const unsigned long long sgn = (unsigned long long)y & 0x8000000000000000ull;
-  const unsigned long long a = y < 0 ? 0ull - (unsigned long long)y : (unsigned long long)y;
-  const int lz = __clzll((long long)a);
-  const unsigned long long nrm = a << lz;
-  unsigned long long m = nrm >> 11;
-  const unsigned rem = (unsigned)nrm & 0x7ffu;
-  m += (rem > 0x400u || (rem == 0x400u && (m & 1ull))) ? 1ull : 0ull;
-  int ex = En + 7 - lz;
-  if (m >> 53) {
-    m >>= 1;
-    ++ex;
-  }
-  if (ex <= 0) return __longlong_as_double((long long)sgn);
-  if (ex >= 2047) return __longlong_as_double((long long)(sgn | 0x7ff0000000000000ull));
-  return __longlong_as_double(
-      (long long)(sgn | ((unsigned long long)ex << 52) | (m & 0xFFFFFFFFFFFFFull)));
-}
-
-__device__ __forceinline__ int biased_exponent(double x) {
-  return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
-}
-
-// Raises *slot to v unless it already holds at least v (the slot only grows during a step,
-// so a stale read can only cause a redundant atomic).
-__device__ __forceinline__ void raise_slot(int *slot, int v) {
-  if (v > *(volatile int *)slot) atomicMax(slot, v);
-}
-
-template <int EPT>
-struct FixedShared {
-  long long p[EPT * kTile + 3], q1[EPT * kTile + 3], q2[EPT * kTile + 3];
-  int wmax[kTile / 32];
-  int En, slot;
-};
-
-template <int NP>
-__device__ __forceinline__ void fx_own(const StepFixed &F, const double *u, int En, long long &p,
-                                       FxAcc &s1, FxAcc &s2, int *xh, int *xl) {
-#pragma unroll
-  for (int j = 0; j < NP; ++j) {
-    const long long X = fx_from_double(u[j], En);
-    fx_split(X, xh[j], xl[j]);
-    fx_mac(s1, F.r1[j], xh[j], xl[j]);
-    fx_mac(s2, F.r2[j], xh[j], xl[j]);
-    if (j == NP - 1) p = X;
-  }
-}
-
-template <int NP, int EPT>
-__global__ void __launch_bounds__(kTile) k_step_fixed(const Inst inst, const double *__restrict__ uin,
-                                                      double *__restrict__ uout, int rel) {
-  __shared__ FixedShared<EPT> sh;
-  const int K = inst.K;
-  const int t = threadIdx.x;
-  const int e0 = blockIdx.x * (kTile * EPT);
-  const StepFixed &F = inst.sf;
-  double hw[NP];
-  if (t < 3) {
-    int m = e0 - 3 + t;
-    if (m < 0) m += K;   // K >= 8 on this path
-    load_elem<NP>(uin, K, m, hw);
-  }
-  double u[EPT][NP];
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
-    const int e = e0 + t + h * kTile;
-    load_elem<NP>(uin, K, e < K ? e : K - 1, u[h]);
-  }
-  if (t == 0) {
-    const int64_t n = inst.meta[0] + rel;
-    const int slot = (int)(n % 3);
-    sh.slot = slot;
-    sh.En = inst.emax[slot];
-    if (blockIdx.x == 0) inst.emax[slot == 0 ? 2 : slot - 1] = 0;   // slot of u^{n+2}
-  }
-  __syncthreads();
-  const int En = sh.En;
-  FxAcc hs1, hs2;
-  if (t < 3) {
-    int xh[NP], xl[NP];
-    long long p;
-    fx_own<NP>(F, hw, En, p, hs1, hs2, xh, xl);
-    sh.p[t] = p;
-  }
-  int xh[EPT][NP], xl[EPT][NP];
-  FxAcc s1[EPT], s2[EPT];
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
-    long long p;
-    fx_own<NP>(F, u[h], En, p, s1[h], s2[h], xh[h], xl[h]);
-    sh.p[t + h * kTile + 3] = p;
-  }
-  __syncthreads();
-  // v1_p = r1 . u + k_0 P0, rounded once
-  if (t == 1 || t == 2) {
-    int ph, pl;
-    fx_split(sh.p[t - 1], ph, pl);
-    fx_mac(hs1, F.k[0], ph, pl);
-    sh.q1[t] = fx_round(hs1);
-  }
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
-    const int sl = t + h * kTile + 3;
-    int ph, pl;
-    fx_split(sh.p[sl - 1], ph, pl);
-    fx_mac(s1[h], F.k[0], ph, pl);
-    sh.q1[sl] = fx_round(s1[h]);
-  }
-  __syncthreads();
-  // v2_p = r2 . u + k_1 P0 + k_2 P1, rounded once
-  if (t == 2) {
-    int ph, pl, qh, ql;
-    fx_split(sh.p[1], ph, pl);
-    fx_split(sh.q1[1], qh, ql);
-    fx_mac(hs2, F.k[1], ph, pl);
-    fx_mac(hs2, F.k[2], qh, ql);
-    sh.q2[2] = fx_round(hs2);
-  }
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
-    const int sl = t + h * kTile + 3;
-    int ph, pl, qh, ql;
-    fx_split(sh.p[sl - 1], ph, pl);
-    fx_split(sh.q1[sl - 1], qh, ql);
-    fx_mac(s2[h], F.k[1], ph, pl);
-    fx_mac(s2[h], F.k[2], qh, ql);
-    sh.q2[sl] = fx_round(s2[h]);
-  }
-  __syncthreads();
-  const bool bad = En >= 2047;   // u^n holds a NaN or an infinity
-  int emax = 0;
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
-    const int b = t + h * kTile;   // left neighbour's slot is b + 2
-    const int e = e0 + b;
-    int P0h, P0l, P1h, P1l, P2h, P2l;
-    fx_split(sh.p[b + 2], P0h, P0l);
-    fx_split(sh.q1[b + 2], P1h, P1l);
-    fx_split(sh.q2[b + 2], P2h, P2l);
-    double *o = uout + e;
-#pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      FxAcc acc;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) fx_mac(acc, F.G[i * NP + j], xh[h][j], xl[h][j]);
-      fx_mac(acc, F.h[0][i], P0h, P0l);
-      fx_mac(acc, F.h[1][i], P1h, P1l);
-      fx_mac(acc, F.h[2][i], P2h, P2l);
-      const double y = bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(fx_round(acc), En);
-      if (e < K) {
-        *o = y;
-        const int be = biased_exponent(y);
-        emax = be > emax ? be : emax;
-      }
-      o += K;
-    }
-  }
-  // largest output exponent of the block -> scale of u^{n+1}
-  emax = __reduce_max_sync(0xffffffffu, emax);
-  if ((t & 31) == 0) sh.wmax[t >> 5] = emax;
-  __syncthreads();
-  if (t == 0) {
-    int m = 0;
-    for (int w = 0; w < kTile / 32; ++w) m = sh.wmax[w] > m ? sh.wmax[w] : m;
-    const int slot = sh.slot;
-    raise_slot(inst.emax + (slot == 2 ? 0 : slot + 1), m);
-  }
-}
-
-__global__ void k_exponent_max(const double *__restrict__ f, size_t n, int *slot) {
-  int m = 0;
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (size_t)gridDim.x * blockDim.x) {
-    const int be = biased_exponent(f[i]);
-    m = be > m ? be : m;
-  }
-  m = __reduce_max_sync(0xffffffffu, m);
-  if ((threadIdx.x & 31) == 0) raise_slot(slot, m);
-}
-
 // One stage for one element with the arithmetic of stage_body (advection, a > 0):
 // out = alpha u + A x + lL (x_0 - xl) where xl is the left neighbour's right trace.
 template <int NP, int STAGE>
@@ -539,57 +294,90 @@ __device__ __forceinline__ void fixup_stage(const Inst &I, int j, int64_t n, dou
 // e-1 .. e+2 around PE face j (e = j Kpe) from u of e-4 .. e+2 (no other PE face lies in that
 // window when Kpe >= 8), with the delayed / AT flux at the face, writes the ring entries of
 // the three stages, and overwrites those four elements when the face's delay is nonzero
-// (with zero delay the composed result already holds the synchronous step).
+// (with zero delay the composed result already holds the synchronous step). fmt: the
+// fixed-point composed step's formats (bit 0: uin, bit 1: uout int64 at the step's scale);
+// the arithmetic here is FP64 on u^n rounded to FP64.
 template <int NP>
-__device__ __forceinline__ void fixup_body(const Inst &I, int j, const double *__restrict__ uin,
-                                           double *__restrict__ uout, int rel) {
+__device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__restrict__ uin,
+                                           void *__restrict__ uout, int rel, int fmt) {
   const int K = I.K;
   const int e = j * I.Kpe;
   const int64_t n = I.meta[0] + rel;
+  const bool fin = (fmt & kFmtInFixed) != 0, fout = (fmt & kFmtOutFixed) != 0;
+  FxScale sc{0, 0, 0, false};
+  int sig_in = 0;
+  if (I.fused == 2) {
+    sc = fx_scale(I.fx, n, fin);
+    sig_in = I.fx[sc.slot].sigma;
+  }
   double U[7][NP], V1[7][NP], V2[7][NP], W[7][NP];
   for (int w = 0; w < 7; ++w) {
     int m = e - 4 + w;
     if (m < 0) m += K;
     if (m >= K) m -= K;
-    const double *q = uin + m;
+    if (fin) {
+      const long long *q = static_cast<const long long *>(uin) + m;
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      U[w][i] = *q;
-      q += K;
+      for (int i = 0; i < NP; ++i) {
+        U[w][i] = scalbn((double)*q, sig_in);
+        q += K;
+      }
+    } else {
+      const double *q = static_cast<const double *>(uin) + m;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        U[w][i] = *q;
+        q += K;
+      }
     }
   }
   fixup_stage<NP, 0>(I, j, n, U, U, V1);
   fixup_stage<NP, 1>(I, j, n, U, V1, V2);
   fixup_stage<NP, 2>(I, j, n, U, V2, W);
-  if (delay_at(I, j, n).k != 0) {
+  // with a NaN or infinity in u^n the fixed-point step has already written NaN (or carries
+  // the mark); the recomputed values are not used
+  if (delay_at(I, j, n).k != 0 && !sc.bad) {
     int emax = 0;
+    unsigned long long mag = 0;
     for (int w = 3; w < 7; ++w) {
       int m = e - 4 + w;
       if (m < 0) m += K;
       if (m >= K) m -= K;
-      double *q = uout + m;
+      if (fout) {
+        long long *q = static_cast<long long *>(uout) + m;
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        *q = W[w][i];
-        q += K;
-        const int be = (int)(((unsigned long long)__double_as_longlong(W[w][i]) >> 52) & 0x7ff);
-        emax = be > emax ? be : emax;
+        for (int i = 0; i < NP; ++i) {
+          const long long X = llrint(scalbn(W[w][i], -sc.sigma));
+          *q = X;
+          q += K;
+          mag |= fx_mag(X);
+        }
+      } else {
+        double *q = static_cast<double *>(uout) + m;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          *q = W[w][i];
+          q += K;
+          const int be = biased_exponent(W[w][i]);
+          emax = be > emax ? be : emax;
+        }
       }
     }
     // the fixed-point composed step takes the scale of u^{n+1} from every value written
     if (I.fused == 2) {
-      int *slot = I.emax + (int)((n + 1) % 3);
-      if (emax > *(volatile int *)slot) atomicMax(slot, emax);
+      FxSlot &nx = I.fx[fx_next(sc.slot)];
+      if (fout) or_slot(&nx.mag, mag);
+      else raise_slot(&nx.E, emax);
     }
   }
 }
 
 template <int NP>
-__global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const double *__restrict__ uin,
-                                                   double *__restrict__ uout, int rel) {
+__global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const void *__restrict__ uin,
+                                                   void *__restrict__ uout, int rel, int fmt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= I.P) return;
-  fixup_body<NP>(I, j, uin, uout, rel);
+  fixup_body<NP>(I, j, uin, uout, rel, fmt);
 }
 
 // Batched composed steps: block b takes work item (instance, first element); `parity`
@@ -627,10 +415,10 @@ __global__ void __launch_bounds__(64) k_batch_fixup(const Inst *__restrict__ ins
   const double *uin = parity ? I.v1 : I.u;
   double *uout = parity ? I.u : I.v1;
   switch (I.Np) {
-    case 2: fixup_body<2>(I, j, uin, uout, rel); break;
-    case 3: fixup_body<3>(I, j, uin, uout, rel); break;
-    case 4: fixup_body<4>(I, j, uin, uout, rel); break;
-    default: fixup_body<5>(I, j, uin, uout, rel); break;
+    case 2: fixup_body<2>(I, j, uin, uout, rel, 0); break;
+    case 3: fixup_body<3>(I, j, uin, uout, rel, 0); break;
+    case 4: fixup_body<4>(I, j, uin, uout, rel, 0); break;
+    default: fixup_body<5>(I, j, uin, uout, rel, 0); break;
   }
 }
 
@@ -912,44 +700,37 @@ cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int 
 
 namespace {
 template <int NP>
-cudaError_t fused_np(const Inst &I, const double *uin, double *uout, int rel, cudaStream_t s,
-                     bool with_fixup) {
-  const unsigned g1 = (unsigned)((I.K + kTile - 1) / kTile);
-  const unsigned g2 = (unsigned)((I.K + 2 * kTile - 1) / (2 * kTile));
-  const unsigned g4 = (unsigned)((I.K + 4 * kTile - 1) / (4 * kTile));
+cudaError_t fused_np(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s,
+                     bool with_fixup, int fmt) {
   if (I.fused == 2) {
-    if (I.ept == 4) k_step_fixed<NP, 4><<<g4, kTile, 0, s>>>(I, uin, uout, rel);
-    else if (I.ept == 2) k_step_fixed<NP, 2><<<g2, kTile, 0, s>>>(I, uin, uout, rel);
-    else k_step_fixed<NP, 1><<<g1, kTile, 0, s>>>(I, uin, uout, rel);
+    cudaError_t e = launch_fixed_step(I, uin, uout, rel, fmt, s);
+    if (e != cudaSuccess) return e;
   } else {
-    if (I.ept == 4) k_step_fused<NP, 4><<<g4, kTile, 0, s>>>(I, uin, uout);
-    else if (I.ept == 2) k_step_fused<NP, 2><<<g2, kTile, 0, s>>>(I, uin, uout);
-    else k_step_fused<NP, 1><<<g1, kTile, 0, s>>>(I, uin, uout);
+    const double *ui = static_cast<const double *>(uin);
+    double *uo = static_cast<double *>(uout);
+    fmt = 0;
+    if (I.ept == 4)
+      k_step_fused<NP, 4><<<(unsigned)((I.K + 4 * kTile - 1) / (4 * kTile)), kTile, 0, s>>>(I, ui, uo);
+    else if (I.ept == 2)
+      k_step_fused<NP, 2><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, ui, uo);
+    else
+      k_step_fused<NP, 1><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, ui, uo);
   }
   if (I.async && with_fixup)
-    k_step_fixup<NP><<<(unsigned)((I.P + 63) / 64), 64, 0, s>>>(I, uin, uout, rel);
+    k_step_fixup<NP><<<(unsigned)((I.P + 63) / 64), 64, 0, s>>>(I, uin, uout, rel, fmt);
   return cudaGetLastError();
 }
 }  // namespace
 
-cudaError_t launch_fused_step(const Inst &I, const double *uin, double *uout, int rel,
-                              cudaStream_t s, bool with_fixup) {
+cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int rel,
+                              cudaStream_t s, bool with_fixup, int fmt) {
   switch (I.Np) {
-    case 2: return fused_np<2>(I, uin, uout, rel, s, with_fixup);
-    case 3: return fused_np<3>(I, uin, uout, rel, s, with_fixup);
-    case 4: return fused_np<4>(I, uin, uout, rel, s, with_fixup);
-    case 5: return fused_np<5>(I, uin, uout, rel, s, with_fixup);
+    case 2: return fused_np<2>(I, uin, uout, rel, s, with_fixup, fmt);
+    case 3: return fused_np<3>(I, uin, uout, rel, s, with_fixup, fmt);
+    case 4: return fused_np<4>(I, uin, uout, rel, s, with_fixup, fmt);
+    case 5: return fused_np<5>(I, uin, uout, rel, s, with_fixup, fmt);
     default: return cudaErrorInvalidValue;
   }
-}
-
-cudaError_t launch_exponent_max(const double *f, size_t n, int *slot, cudaStream_t s) {
-  cudaError_t e = cudaMemsetAsync(slot, 0, sizeof(int), s);
-  if (e != cudaSuccess) return e;
-  const size_t want = (n + 255) / 256;
-  const unsigned grid = (unsigned)(want < 4 * 152 ? (want ? want : 1) : 4 * 152);
-  k_exponent_max<<<grid, 256, 0, s>>>(f, n, slot);
-  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,

@@ -289,3 +289,23 @@ def test_fixed_point_rejects_large_coefficients():
     with pytest.raises(adg.AdgError) as ei:
         adg.Solver(cfg, adg.eval_modes(cfg, [1.0], [1.0], [0.0]))
     assert ei.value.code == adg._abi.ADG_EINVAL
+
+
+def test_fixed_point_step_splitting():
+    # The integer step keeps the field in int64 inside each adg_step call (graph chunks of
+    # 32 steps) and rounds it to FP64 at the end of a call or chunk; single-step calls round
+    # every step. Both stay on the oracle, and within rounding of each other.
+    cfg = adg.Config(pde="advection", K=512, p=3, P=16, cfl=0.005, mode="at", L=4, q=3, seed=12,
+                     variant="fixed")
+    u0 = dg.modes_initial(PAPER_FIG6, 512, 3)
+    outs = []
+    for calls in ([96], [1] * 96, [1, 2, 33, 60]):
+        s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
+        for k in calls:
+            s.step(k)
+        outs.append(s.state().cpu().numpy())
+        s.close()
+    _, ref, _ = run_pair(cfg, u0, 96)
+    for got in outs:
+        assert rel_linf(got, ref) < TOL
+        assert rel_linf(got, outs[0]) < 1e-13
