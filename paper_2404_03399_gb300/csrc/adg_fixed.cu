@@ -11,15 +11,14 @@ namespace {
 template <int EPT>
 struct FixedShared {
   long long p[EPT * kTile + 3], q1[EPT * kTile + 3], q2[EPT * kTile + 3];
-  unsigned long long wmag[kTile / 32];
-  int wmax[kTile / 32];
   FxScale sc;
 };
 
-// Working-scale value of node j of an element (FP64 or stored int64 input).
+// Working-scale value of node j of an element (FP64 input, or int64 input already brought
+// to the working scale).
 template <bool FIN>
 __device__ __forceinline__ long long fx_in(double x, long long X, const FxScale &sc) {
-  if (FIN) return fx_rescale(X, sc.shift);
+  if (FIN) return X;
   return fx_from_double(x, sc.sigma + 1079);
 }
 
@@ -45,8 +44,10 @@ __device__ __forceinline__ void fx_own(const StepFixed &F, const double *ud, con
 // u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2 from the left neighbour's channel scalars. The first
 // three threads form the scalars of the three elements before the block with the same
 // arithmetic (the working scale is one per field, so every element converts the same way).
+// One element per thread runs at full occupancy (8 blocks of 256 threads per SM, at most 32
+// registers); two per thread keep 64 registers for the second element's values.
 template <int NP, int EPT, int FMT>
-__global__ void __launch_bounds__(kTile) k_step_fixed(const Inst inst, const void *__restrict__ uin_,
+__global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4) k_step_fixed(const Inst inst, const void *__restrict__ uin_,
                                                       void *__restrict__ uout_, int rel) {
   constexpr bool FIN = (FMT & kFmtInFixed) != 0;
   constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
@@ -91,6 +92,14 @@ __global__ void __launch_bounds__(kTile) k_step_fixed(const Inst inst, const voi
   }
   __syncthreads();
   const FxScale sc = sh.sc;
+  if (FIN && sc.shift != 0) {   // block-uniform: the field grew past 2^57 or shrank
+#pragma unroll
+    for (int j = 0; j < NP; ++j) hq[j] = fx_rescale(hq[j], sc.shift);
+#pragma unroll
+    for (int h = 0; h < EPT; ++h)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) uq[h][j] = fx_rescale(uq[h][j], sc.shift);
+  }
   FxAcc hs1, hs2;
   if (t < 3) {
     int xh[NP], xl[NP];
@@ -182,28 +191,16 @@ __global__ void __launch_bounds__(kTile) k_step_fixed(const Inst inst, const voi
       oq += K;
     }
   }
-  // the scale of u^{n+1}: OR of |y| (int64 output) or largest exponent (FP64 output)
-  const int w = t >> 5;
+  // the scale of u^{n+1}: OR of |y| (int64 output) or largest exponent (FP64 output), one
+  // slot update per warp
+  FxSlot &nx = inst.fx[fx_next(sc.slot)];
   if (FOUT) {
     const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mag);
     const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mag >> 32));
-    if ((t & 31) == 0) sh.wmag[w] = ((unsigned long long)hi << 32) | lo;
+    if ((t & 31) == 0) or_slot(&nx.mag, ((unsigned long long)hi << 32) | lo);
   } else {
     emax = __reduce_max_sync(0xffffffffu, emax);
-    if ((t & 31) == 0) sh.wmax[w] = emax;
-  }
-  __syncthreads();
-  if (t == 0) {
-    FxSlot &nx = inst.fx[fx_next(sc.slot)];
-    if (FOUT) {
-      unsigned long long m = 0;
-      for (int k = 0; k < kTile / 32; ++k) m |= sh.wmag[k];
-      or_slot(&nx.mag, m);
-    } else {
-      int m = 0;
-      for (int k = 0; k < kTile / 32; ++k) m = sh.wmax[k] > m ? sh.wmax[k] : m;
-      raise_slot(&nx.E, m);
-    }
+    if ((t & 31) == 0) raise_slot(&nx.E, emax);
   }
 }
 
