@@ -42,19 +42,23 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
                 q=_W16M.q, cfl=_W16M.cfl, seed=_W16M.seed,
                 modes=(list(_W16M.modes.amp), list(_W16M.modes.kappa), list(_W16M.modes.phase),
                        _W16M.modes.offset))
-# Algorithmic FP64 work of the kernel that runs the bench step (the composed SSP-RK3 step of
-# upwind advection): Np^2 + 5 Np + 3 multiply-adds per element and step, i.e.
-# 2 (Np^2 + 5 Np + 3) / Np flop per DOF-step (19.5 at p = 3). The staged formulation counts
-# (Np + 2) multiply-adds per DOF-stage (= 2 (Np + 2) flop), 1.85x more at p = 3; both
-# figures are reported.
+# Algorithmic work of the kernels that can run the bench step (the composed SSP-RK3 step of
+# upwind advection, Np^2 + 5 Np + 3 multiply-adds per element and step):
+#  - fixed-point integer step (picked where the coefficients fit, as here): each
+#    multiply-add is three 32 x 32 -> 64-bit integer products, 3 (Np^2 + 5 Np + 3) per element
+#    (117 at p = 3); the bound is the integer multiply pipe;
+#  - FP64 composed step: 2 (Np^2 + 5 Np + 3) / Np flop per DOF-step (19.5 at p = 3);
+#  - staged FP64 kernels: 2 (Np + 2) flop per DOF-stage.
 NP = WORKLOAD["p"] + 1
-FLOP_PER_DOF_STEP = 2 * (NP * NP + 5 * NP + 3) / NP
+MACS_PER_ELEMENT_STEP = NP * NP + 5 * NP + 3
+INT_PRODUCTS_PER_ELEMENT_STEP = 3 * MACS_PER_ELEMENT_STEP
+FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
-# DRAM bytes per launch of k_step_fused measured by ncu on this workload (read + write), or
-# None when the kernel has changed since the counters were taken: 537.78 MB read +
-# 482.72 MB written, one launch of the four-elements-per-thread instance (the autotuner's
-# choices differ only in how elements map to threads, not in the bytes moved).
-TRAFFIC_BYTES_PER_LAUNCH = 1_020_501_248
+# DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
+# dominates the step, keyed by variant; a kernel changed since its counters were taken has no
+# entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 536.93 MB read
+# + 489.09 MB written (the chunk's interior steps; the first and last read or write FP64).
+TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_026_015_744}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 GRAPH_STEPS = 32
@@ -63,7 +67,10 @@ GRAPH_STEPS = 32
 def peaks():
     """Roofline denominators: HBM from MEASURED_PEAKS.json (else the recipe's fallback);
     FP64 ALU peak from unit counts and the maximum SM clock: 152 SMs x 2 DFMA/clk x 2 flop
-    x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 of GB300)."""
+    x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 of GB300); integer product peak: 152 SMs x 32
+    wide (32 x 32 -> 64-bit) multiply-adds per clock (the heavy FMA pipe, 16 lanes per clock
+    per SM sub-partition, two passes for a 64-bit result) x 2.07 GHz = 10.07 T/s (28.7 per
+    clock per SM measured in a dependent-chain microbenchmark)."""
     hbm, src = 6800.0, "fallback"
     sm_mhz = 2070.0
     try:
@@ -74,7 +81,8 @@ def peaks():
     except Exception:
         pass
     fp64_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    return hbm, src, fp64_tflops
+    int_tops = 152 * 32 * sm_mhz * 1e6 / 1e12
+    return hbm, src, fp64_tflops, int_tops
 
 
 class ClockSampler:
@@ -173,8 +181,9 @@ def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks
     except adg.AdgError:
         s.check_finite_ok = False
     finite = s.check_finite_ok
+    variant = s.variant
     s.close()
-    return ms, (clocks.summary() if clocks else None), finite
+    return ms, (clocks.summary() if clocks else None), finite, variant
 
 
 def e2e_timed(steps: int):
@@ -376,34 +385,49 @@ def main():
 
     K, p = WORKLOAD["K"], WORKLOAD["p"]
     ndof = K * (p + 1)
-    ms, clocks, finite = device_timed("at", args.steps, args.warmup, barrier, rank == 0, local)
+    ms, clocks, finite, (variant, ept) = device_timed("at", args.steps, args.warmup, barrier,
+                                                      rank == 0, local)
     units = ndof * STAGES * args.steps
     ms_max, units_all = aggregate(dist, ms, units)
     value = units_all / (ms_max * 1e-3)
 
-    hbm_gbs, hbm_src, fp64_tflops = peaks()
+    hbm_gbs, hbm_src, fp64_tflops, int_tops = peaks()
     ms_step = ms / args.steps
-    # one k_step_fused launch (plus its PE-face fix-up, charged to it) per step
-    launch_ms = ms_step
-    flop_per_launch = ndof * FLOP_PER_DOF_STEP
-    achieved_tflops = flop_per_launch / (launch_ms * 1e-3) / 1e12
-    staged_equiv = ndof * STAGES * FLOP_PER_DOF_STAGE_STAGED / (ms_step * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved_tflops, "peak": fp64_tflops, "unit": "TFLOP/s",
-                "frac": achieved_tflops / fp64_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH,
-                "kernel": "k_step_fused (composed SSP-RK3 step, FP64, Np^2+5Np+3 FMA per element); "
-                          "the PE-face fix-up launch (about 2%) is charged to it",
-                "flop_per_dof_step": FLOP_PER_DOF_STEP,
-                "staged_count_equivalent_tflops": staged_equiv,
-                "peak_source": "FP64 from unit counts x max SM clock (152 SM x 2 DFMA/clk x 2 flop x 2.07 GHz)"}
+    # one composed-step launch per step plus the PE-face fix-up launch, charged to it (the
+    # CUDA-event time of the step; ncu puts the fix-up near 10% of it)
+    elements = K
+    if variant == "fixed":
+        achieved = elements * INT_PRODUCTS_PER_ELEMENT_STEP / (ms_step * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": int_tops,
+                    "unit": "T int64-products/s", "frac": achieved / int_tops,
+                    "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fixed"),
+                    "kernel": f"k_step_fixed (composed SSP-RK3 step in two-limb fixed point, "
+                              f"{INT_PRODUCTS_PER_ELEMENT_STEP} 32x32->64-bit products per element, "
+                              f"{ept} element(s) per thread); the PE-face fix-up is charged to it",
+                    "peak_source": "integer unit counts x max SM clock (152 SM x 32 wide "
+                                   "multiply-adds/clk x 2.07 GHz)",
+                    "fp64_equivalent_tflops": ndof * FLOP_PER_DOF_STEP / (ms_step * 1e-3) / 1e12}
+    else:
+        achieved = ndof * FLOP_PER_DOF_STEP / (ms_step * 1e-3) / 1e12
+        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
+                    "frac": achieved / fp64_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(variant),
+                    "kernel": f"k_step_fused / k_stage ({variant}, FP64)",
+                    "peak_source": "FP64 from unit counts x max SM clock (152 SM x 2 DFMA/clk x 2 "
+                                   "flop x 2.07 GHz)"}
     hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / (ms_step * 1e-3) / 1e9
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "int64" if variant == "fixed" else "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD["name"], "K": K, "p": p, "P": WORKLOAD["P"],
                        "L": WORKLOAD["L"], "at_order": WORKLOAD["q"], "cfl": WORKLOAD["cfl"],
                        "dof": ndof, "parallelism": f"replicas x{ws}",
                        "l2": "inputs larger than L2 (537 MB per nodal field)",
-                       "graph_steps": GRAPH_STEPS},
+                       "graph_steps": GRAPH_STEPS, "variant": variant,
+                       "arithmetic": ("exact two-limb fixed point at one scale per step "
+                                      "(resolution 2^-55 of max|u| or finer), int64 state inside "
+                                      "each 32-step chunk, FP64 at chunk ends and in the PE-face "
+                                      "fix-up") if variant == "fixed" else "FP64"},
             "roofline": roofline,
             "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
                     "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
@@ -413,7 +437,7 @@ def main():
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:
-        sms, _, _ = device_timed("sync", args.sync_steps, args.warmup, barrier, False, local)
+        sms, _, _, _ = device_timed("sync", args.sync_steps, args.warmup, barrier, False, local)
         line["sync_dg"] = {"value": ndof * STAGES * args.sync_steps / (sms * 1e-3), "unit": UNIT,
                            "ms_per_step": sms / args.sync_steps}
         line["at_over_sync"] = value / ws / line["sync_dg"]["value"]

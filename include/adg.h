@@ -87,13 +87,16 @@ enum {
  *               composed into one stencil per step, with the elements next to PE faces
  *               recomputed stage by stage (needs K/P >= 8 when there are PE faces), or
  *               ADG_VARIANT_COMPOSED_FIXED (3): the same composed step evaluated exactly in
- *               64-bit fixed-point integer arithmetic at one scale per step (the largest
- *               exponent of u^n; resolution 2^-56 of max|u^n| or finer), then rounded to FP64;
- *               it needs every composed coefficient below 2 in magnitude (small Courant
- *               numbers; ADG_EINVAL otherwise). Results below 2^-1022 are flushed to zero,
- *               and a NaN or infinity anywhere in u^n makes all of u^{n+1} NaN. AUTO picks
- *               COMPOSED_FIXED, else COMPOSED, where they apply (a single instance; batches
- *               use COMPOSED). All give the same scheme up to rounding.
+ *               64-bit fixed-point integer arithmetic at one scale per step (from the largest
+ *               magnitude in u^n; resolution 2^-55 of max|u^n| or finer). The state stays in
+ *               fixed point between the steps of one adg_step call (in chunks of 32 steps) and
+ *               is rounded to FP64 at the end of each chunk, so splitting a run into different
+ *               adg_step calls changes results at the rounding level. It needs every composed
+ *               coefficient below 2 in magnitude (small Courant numbers; ADG_EINVAL
+ *               otherwise). Results below 2^-1022 are flushed to zero, and a NaN or infinity
+ *               anywhere in u^n makes all of u^{n+1} NaN. AUTO picks COMPOSED_FIXED, else
+ *               COMPOSED, where they apply (a single instance; batches use COMPOSED). All give
+ *               the same scheme up to rounding.
  */
 typedef struct {
   int32_t pde;
@@ -148,6 +151,11 @@ int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out);
 
 /* The fixed time step of instance `index`. */
 int adg_get_dt(adg_ctx *c, int32_t index, double *dt_out);
+
+/* How instance `index` steps (not a paper quantity): *variant_out = the ADG_VARIANT_* in use
+ * (STAGED, COMPOSED or COMPOSED_FIXED; AUTO resolved), *ept_out = elements per thread of the
+ * composed-step kernel chosen at init (1 for the staged kernels). Either pointer may be NULL. */
+int adg_get_variant(adg_ctx *c, int32_t index, int32_t *variant_out, int32_t *ept_out);
 
 /*
  * Discrete gradient of the final-time L2 misfit

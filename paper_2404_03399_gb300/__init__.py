@@ -159,6 +159,13 @@ class Solver:
         check(load().adg_get_dt(self.ctx, 0, C.byref(v)), self.ctx)
         return v.value
 
+    @property
+    def variant(self) -> tuple:
+        """(variant in use: "staged" | "composed" | "fixed", elements per thread)."""
+        v, e = C.c_int32(), C.c_int32()
+        check(load().adg_get_variant(self.ctx, 0, C.byref(v), C.byref(e)), self.ctx)
+        return {1: "staged", 2: "composed", 3: "fixed"}[v.value], e.value
+
     def integral(self) -> float:
         v = C.c_double()
         check(load().adg_integral(self.ctx, 0, C.byref(v)), self.ctx)

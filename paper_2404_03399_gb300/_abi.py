@@ -20,7 +20,7 @@ STATUS_NAMES = {0: "ADG_OK", -1: "ADG_EINVAL", -2: "ADG_ENOMEM", -3: "ADG_ECUDA"
 # Every entry point declared in include/adg.h.
 EXPORTS = [
     "adg_config_default", "adg_init", "adg_batch_init", "adg_step", "adg_run",
-    "adg_get_state", "adg_get_dt", "adg_grad", "adg_integral", "adg_check_finite",
+    "adg_get_state", "adg_get_dt", "adg_get_variant", "adg_grad", "adg_integral", "adg_check_finite",
     "adg_delay_table", "adg_eval_modes", "adg_lgl_nodes", "adg_last_error", "adg_destroy",
     "adg_integral_noalloc", "adg_misfit",
 ]
@@ -71,6 +71,7 @@ def load(require: bool = True):
         "adg_run": (C.c_int, [vp, C.c_double]),
         "adg_get_state": (C.c_int, [vp, i32, vp, C.POINTER(i64)]),
         "adg_get_dt": (C.c_int, [vp, i32, dp]),
+        "adg_get_variant": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
         "adg_grad": (C.c_int, [vp, vp, i64, i32, vp, dp]),
         "adg_integral": (C.c_int, [vp, i32, dp]),
         "adg_check_finite": (C.c_int, [vp]),

@@ -1302,6 +1302,17 @@ int adg_get_dt(adg_ctx *c, int32_t index, double *dt_out) {
   return ADG_OK;
 }
 
+int adg_get_variant(adg_ctx *c, int32_t index, int32_t *variant_out, int32_t *ept_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size()) return fail(c, ADG_EINVAL, "bad argument");
+  const Inst &I = c->inst[index].I;
+  if (variant_out)
+    *variant_out = I.fused == 2 ? ADG_VARIANT_COMPOSED_FIXED
+                                : (I.fused == 1 ? ADG_VARIANT_COMPOSED : ADG_VARIANT_STAGED);
+  if (ept_out) *ept_out = I.fused ? I.ept : 1;
+  return ADG_OK;
+}
+
 int adg_integral(adg_ctx *c, int32_t index, double *out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (index < 0 || index >= (int)c->inst.size() || !out) return fail(c, ADG_EINVAL, "bad argument");

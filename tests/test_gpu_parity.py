@@ -309,3 +309,19 @@ def test_fixed_point_step_splitting():
     for got in outs:
         assert rel_linf(got, ref) < TOL
         assert rel_linf(got, outs[0]) < 1e-13
+
+
+@pytest.mark.parametrize("kw,want", [
+    (dict(pde="advection", cfl=0.005), "fixed"),
+    (dict(pde="advection", cfl=0.005, variant="composed"), "composed"),
+    (dict(pde="advection", cfl=0.4), "composed"),
+    (dict(pde="advection", cfl=0.005, a=-1.0), "staged"),
+    (dict(pde="burgers", cfl=0.005), "staged"),
+])
+def test_variant_in_use(kw, want):
+    cfg = adg.Config(K=4096, p=3, P=64, mode="at", L=4, q=3, **kw)
+    s = adg.Solver(cfg, adg.eval_modes(cfg, [1.0], [1.0], [0.0], 0.5))
+    variant, ept = s.variant
+    s.close()
+    assert variant == want
+    assert ept in (1, 2, 4)
