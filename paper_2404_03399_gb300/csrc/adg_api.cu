@@ -424,6 +424,35 @@ void fold_step_constants(InstHost &h) {
   S.k[1] = (double)M1c0[p];
   S.k[2] = (double)cv[1][p];
 
+  // PE-face correction responses: inject lL_s at element e and lR_s at element e-1 after
+  // stage s, then apply the remaining stages' perturbation maps
+  // dx'^m = M_t dx^m + c_t dx^{m-1}_p (t = s+1 .. 2) on elements e-1 .. e+2; rho collects
+  // the right trace of element e-1 seen by the later stages.
+  for (int st = 0; st < 3; ++st) {
+    std::vector<ld> d(4 * Np, 0.0L);   // elements e-1 .. e+2
+    const ld sc = beta[st] * c2 * a;
+    for (int i = 0; i < Np; ++i) {
+      d[1 * Np + i] = sc * o.Minv[i * Np + 0];
+      d[0 * Np + i] = -sc * o.Minv[i * Np + p];
+    }
+    for (int t = st + 1; t < 3; ++t) {
+      if (st == 0 && t == 1) S.rho[0] = (double)d[0 * Np + p];
+      if (st == 0 && t == 2) S.rho[1] = (double)d[0 * Np + p];
+      if (st == 1 && t == 2) S.rho[2] = (double)d[0 * Np + p];
+      std::vector<ld> nd(4 * Np, 0.0L);
+      for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < Np; ++i) {
+          ld acc = 0;
+          for (int k = 0; k < Np; ++k) acc += M[t][i * Np + k] * d[m * Np + k];
+          if (m > 0) acc += cv[t][i] * d[(m - 1) * Np + p];
+          nd[m * Np + i] = acc;
+        }
+      d = nd;
+    }
+    for (int m = 0; m < 4; ++m)
+      for (int i = 0; i < Np; ++i) S.R[st][m][i] = (double)d[m * Np + i];
+  }
+
   // Fixed-point limbs of the same coefficients (from the long double values) and the bounds
   // of the integer step: every |c| < 2 (limbs within 32 bits), and channel scalars v1_p,
   // v2_p at most twice the input bound (|X| < 2^58 as multiplicands; inputs are < 2^57).

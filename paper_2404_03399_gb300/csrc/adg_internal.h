@@ -47,11 +47,23 @@ struct StageConsts {
 //   r1 = M_0^T e_p, r2 = (alpha_1 I + M_1 M_0)^T e_p, k_0 = c_0[p], k_1 = (M_1 c_0)[p],
 //   k_2 = c_1[p].
 // Cost: Np^2 + 5 Np + 3 multiply-adds per element and step.
+//
+// PE-face correction of the composed step (upwind advection is linear): at PE face j
+// (e = j Kpe) stage s replaces the synchronous face value by the delayed / AT one, which
+// adds lL_s d_s to stage s's output on element e and lR_s d_s on element e-1, with
+// d_s = T_s - V_s (T_s the stage-s input's right trace of element e-1, V_s the delayed / AT
+// value). The step's result is the synchronous composed step plus
+//   sum_s R_s d_s  on elements e-1 .. e+2  (R[s][m + 1], m = -1 .. 2),
+// R_s the response of the remaining stages to that injection, and
+//   T_1 = q1^{e-1} + rho[0] d_0,  T_2 = q2^{e-1} + rho[1] d_0 + rho[2] d_1
+// (q1, q2 the synchronous channel scalars v1_p, v2_p of element e-1).
 struct StepConsts {
   double G[kMaxNp * kMaxNp];
   double r1[kMaxNp], r2[kMaxNp];
   double h[3][kMaxNp];
   double k[3];
+  double R[3][4][kMaxNp];
+  double rho[3];
 };
 
 // The StepConsts in fixed point for the integer composed step: each coefficient c
@@ -99,6 +111,7 @@ struct alignas(16) Inst {
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
+static_assert(sizeof(Inst) <= 4000, "Inst is passed by value as a kernel parameter");
 
 // Adjoint of one stage (adg_adjoint.cu): w is the adjoint of the stage output, v the stage
 // input (Burgers), lv receives the adjoint of the stage input (stages 1, 2); lacc collects

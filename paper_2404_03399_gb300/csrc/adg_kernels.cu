@@ -254,49 +254,16 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
   fused_body<NP, EPT>(inst, uin, uout, blockIdx.x * (kTile * EPT), sh);
 }
 
-// One stage for one element with the arithmetic of stage_body (advection, a > 0):
-// out = alpha u + A x + lL (x_0 - xl) where xl is the left neighbour's right trace.
-template <int NP, int STAGE>
-__device__ __forceinline__ void stage_elem(const StageConsts &C, const double *u, const double *x,
-                                           double xl, double *out) {
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    double acc = STAGE == 0 ? C.A[i * NP] * x[0] : fma(C.A[i * NP], x[0], C.alpha * u[i]);
-#pragma unroll
-    for (int jj = 1; jj < NP; ++jj) acc = fma(C.A[i * NP + jj], x[jj], acc);
-    out[i] = acc;
-  }
-  const double jL = __dsub_rn(x[0], xl);
-#pragma unroll
-  for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], jL, out[i]);
-}
-
-// Stage s over window slots w = s+1 .. 6 with the PE face between slots 3 and 4: the
-// synchronous stage followed by the PE-face correction of the staged kernels (same
-// arithmetic), and the ring write of the stage-input traces.
-template <int NP, int STAGE>
-__device__ __forceinline__ void fixup_stage(const Inst &I, int j, int64_t n, double (*U)[NP],
-                                            double (*X)[NP], double (*Y)[NP]) {
-  const StageConsts &C = I.sc[STAGE];
-  for (int w = STAGE + 1; w < 7; ++w) stage_elem<NP, STAGE>(C, U[w], X[w], X[w - 1][NP - 1], Y[w]);
-  const double tl = X[3][NP - 1], tr = X[4][0];
-  const double V = pe_value<0, 1>(I, j, n, STAGE, tl, tr, true);
-  const double d = __dsub_rn(face_value<0, 1>(I, tl, tr), V);
-  if (nonzero(d)) {
-#pragma unroll
-    for (int i = 0; i < NP; ++i) Y[4][i] = fma(C.lL[i], d, Y[4][i]);
-#pragma unroll
-    for (int i = 0; i < NP; ++i) Y[3][i] = fma(C.lR[i], d, Y[3][i]);
-  }
-}
-
-// PE-face fix-up of a composed step: thread j recomputes, stage by stage, the elements
-// e-1 .. e+2 around PE face j (e = j Kpe) from u of e-4 .. e+2 (no other PE face lies in that
-// window when Kpe >= 8), with the delayed / AT flux at the face, writes the ring entries of
-// the three stages, and overwrites those four elements when the face's delay is nonzero
-// (with zero delay the composed result already holds the synchronous step). fmt: the
-// fixed-point composed step's formats (bit 0: uin, bit 1: uout int64 at the step's scale);
-// the arithmetic here is FP64 on u^n rounded to FP64.
+// PE-face correction of a composed step (upwind advection, a > 0; StepConsts): thread j
+// forms, for PE face j (e = j Kpe), the synchronous right traces of element e-1's stage
+// inputs (p, q1 = v1_p, q2 = v2_p, from elements e-3 .. e-1 with the composed step's
+// coefficients), then stage by stage T_s (those traces plus the responses to the earlier
+// corrections), the delayed / AT value V_s from the ring (writing T_s into the ring slot of
+// step n; only the upwind trace is read back for a > 0, the other slot holds 0), and
+// d_s = T_s - V_s. The composed (synchronous) result of elements e-1 .. e+2 then gets
+// sum_s R_s d_s. A zero delay gives d_s = 0 exactly and leaves the composed result as it is.
+// Windows of different faces are disjoint when Kpe >= 8. fmt: the fixed-point step's
+// formats (bit 0: uin, bit 1: uout int64 at the step's scale); the arithmetic here is FP64.
 template <int NP>
 __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__restrict__ uin,
                                            void *__restrict__ uout, int rel, int fmt) {
@@ -304,17 +271,18 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
   const int e = j * I.Kpe;
   const int64_t n = I.meta[0] + rel;
   const bool fin = (fmt & kFmtInFixed) != 0, fout = (fmt & kFmtOutFixed) != 0;
+  const StepConsts &S = I.st;
   FxScale sc{0, 0, 0, false};
   int sig_in = 0;
   if (I.fused == 2) {
     sc = fx_scale(I.fx, n, fin);
     sig_in = I.fx[sc.slot].sigma;
   }
-  double U[7][NP], V1[7][NP], V2[7][NP], W[7][NP];
-  for (int w = 0; w < 7; ++w) {
-    int m = e - 4 + w;
+  // elements e-3 .. e-1 (w = 0 .. 2) of u^n
+  double U[3][NP];
+  for (int w = 0; w < 3; ++w) {
+    int m = e - 3 + w;
     if (m < 0) m += K;
-    if (m >= K) m -= K;
     if (fin) {
       const long long *q = static_cast<const long long *>(uin) + m;
 #pragma unroll
@@ -331,44 +299,59 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       }
     }
   }
-  fixup_stage<NP, 0>(I, j, n, U, U, V1);
-  fixup_stage<NP, 1>(I, j, n, U, V1, V2);
-  fixup_stage<NP, 2>(I, j, n, U, V2, W);
+  // synchronous channel scalars of e-1: q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3},
+  // q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
+  double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    a1 = fma(S.r1[i], U[1][i], a1);
+    b1 = fma(S.r1[i], U[2][i], b1);
+    b2 = fma(S.r2[i], U[2][i], b2);
+  }
+  b2 = fma(S.k[2], a1, b2);
+  const double T0 = U[2][NP - 1];
+  const double d0 = __dsub_rn(T0, pe_value<0, 1>(I, j, n, 0, T0, 0.0, true));
+  const double T1 = fma(S.rho[0], d0, b1);
+  const double d1 = __dsub_rn(T1, pe_value<0, 1>(I, j, n, 1, T1, 0.0, true));
+  const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, b2));
+  const double d2 = __dsub_rn(T2, pe_value<0, 1>(I, j, n, 2, T2, 0.0, true));
   // with a NaN or infinity in u^n the fixed-point step has already written NaN (or carries
-  // the mark); the recomputed values are not used
-  if (delay_at(I, j, n).k != 0 && !sc.bad) {
-    int emax = 0;
-    unsigned long long mag = 0;
-    for (int w = 3; w < 7; ++w) {
-      int m = e - 4 + w;
-      if (m < 0) m += K;
-      if (m >= K) m -= K;
-      if (fout) {
-        long long *q = static_cast<long long *>(uout) + m;
+  // the mark); nothing is added
+  if (!(nonzero(d0) || nonzero(d1) || nonzero(d2)) || sc.bad) return;
+  int emax = 0;
+  unsigned long long mag = 0;
+  for (int w = 0; w < 4; ++w) {   // elements e-1 .. e+2
+    int m = e - 1 + w;
+    if (m < 0) m += K;
+    if (m >= K) m -= K;
+    if (fout) {
+      long long *q = static_cast<long long *>(uout) + m;
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          const long long X = llrint(scalbn(W[w][i], -sc.sigma));
-          *q = X;
-          q += K;
-          mag |= fx_mag(X);
-        }
-      } else {
-        double *q = static_cast<double *>(uout) + m;
+      for (int i = 0; i < NP; ++i) {
+        const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
+        const long long X = *q + llrint(scalbn(c, -sc.sigma));
+        *q = X;
+        q += K;
+        mag |= fx_mag(X);
+      }
+    } else {
+      double *q = static_cast<double *>(uout) + m;
 #pragma unroll
-        for (int i = 0; i < NP; ++i) {
-          *q = W[w][i];
-          q += K;
-          const int be = biased_exponent(W[w][i]);
-          emax = be > emax ? be : emax;
-        }
+      for (int i = 0; i < NP; ++i) {
+        const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
+        const double y = __dadd_rn(*q, c);
+        *q = y;
+        q += K;
+        const int be = biased_exponent(y);
+        emax = be > emax ? be : emax;
       }
     }
-    // the fixed-point composed step takes the scale of u^{n+1} from every value written
-    if (I.fused == 2) {
-      FxSlot &nx = I.fx[fx_next(sc.slot)];
-      if (fout) or_slot(&nx.mag, mag);
-      else raise_slot(&nx.E, emax);
-    }
+  }
+  // the fixed-point composed step takes the scale of u^{n+1} from every value written
+  if (I.fused == 2) {
+    FxSlot &nx = I.fx[fx_next(sc.slot)];
+    if (fout) or_slot(&nx.mag, mag);
+    else raise_slot(&nx.E, emax);
   }
 }
 
