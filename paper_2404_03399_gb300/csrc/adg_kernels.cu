@@ -258,28 +258,42 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
 // forms, for PE face j (e = j Kpe), the synchronous right traces of element e-1's stage
 // inputs (p, q1 = v1_p, q2 = v2_p, from elements e-3 .. e-1 with the composed step's
 // coefficients), then stage by stage T_s (those traces plus the responses to the earlier
-// corrections), the delayed / AT value V_s from the ring (writing T_s into the ring slot of
-// step n; only the upwind trace is read back for a > 0, the other slot holds 0), and
-// d_s = T_s - V_s. The composed (synchronous) result of elements e-1 .. e+2 then gets
-// sum_s R_s d_s. A zero delay gives d_s = 0 exactly and leaves the composed result as it is.
-// Windows of different faces are disjoint when Kpe >= 8. fmt: the fixed-point step's
-// formats (bit 0: uin, bit 1: uout int64 at the step's scale); the arithmetic here is FP64.
+// corrections), the delayed / AT value V_s (Eq. at-flux-gen over the upwind traces of levels
+// n-k-i in the ring; the face's delay k is one per step, so V_s does not depend on T), and
+// d_s = T_s - V_s, writes T_s into the ring slot of step n (only the upwind trace is read back
+// for a > 0; the other slot holds 0), and adds sum_s R_s d_s to the composed (synchronous)
+// result of elements e-1 .. e+2. Every load (delay, ring levels of all three stages, inputs,
+// outputs) is issued before any of them is used. A zero delay gives d_s = 0 exactly and leaves
+// the composed result as it is. Windows of different faces are disjoint when Kpe >= 8. fmt:
+// the fixed-point step's formats (bit 0: uin, bit 1: uout int64 at the step's scale); the
+// arithmetic here is FP64.
 template <int NP>
 __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__restrict__ uin,
                                            void *__restrict__ uout, int rel, int fmt) {
   const int K = I.K;
+  const int P = I.P;
   const int e = j * I.Kpe;
   const int64_t n = I.meta[0] + rel;
   const bool fin = (fmt & kFmtInFixed) != 0, fout = (fmt & kFmtOutFixed) != 0;
   const StepConsts &S = I.st;
+  const DelayAt dl = delay_at(I, j, n);
   FxScale sc{0, 0, 0, false};
   int sig_in = 0;
   if (I.fused == 2) {
     sc = fx_scale(I.fx, n, fin);
     sig_in = I.fx[sc.slot].sigma;
   }
-  // elements e-3 .. e-1 (w = 0 .. 2) of u^n
+  // elements e-3 .. e-1 of u^n (w = 0 .. 2) and the composed result of e-1 .. e+2 (w = 0 .. 3)
+  int mw[4];
+  for (int w = 0; w < 4; ++w) {
+    int m = e - 1 + w;
+    if (m < 0) m += K;
+    if (m >= K) m -= K;
+    mw[w] = m;
+  }
   double U[3][NP];
+  long long Xq[4][NP];
+  double Yd[4][NP];
   for (int w = 0; w < 3; ++w) {
     int m = e - 3 + w;
     if (m < 0) m += K;
@@ -299,6 +313,50 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       }
     }
   }
+  for (int w = 0; w < 4; ++w) {
+    if (fout) {
+      const long long *q = static_cast<const long long *>(uout) + mw[w];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        Xq[w][i] = *q;
+        q += K;
+      }
+    } else {
+      const double *q = static_cast<const double *>(uout) + mw[w];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        Yd[w][i] = *q;
+        q += K;
+      }
+    }
+  }
+  // upwind traces of levels n-k-i (i < q') for the three stages: ring [slot][stage][P]
+  const int R = I.R;
+  const int nm = (int)(n % R);
+  double2 *col = I.ring + j;
+  double Rv[kStages][kMaxQ];
+  const int k = dl.k, qe = dl.qe;
+#pragma unroll
+  for (int i = 0; i < kMaxQ; ++i) {
+    int sl = nm - (k + i);
+    if (sl < 0) sl += R;
+#pragma unroll
+    for (int st = 0; st < kStages; ++st)
+      Rv[st][i] = (k > 0 && i < qe) ? col[((size_t)sl * kStages + st) * P].x : 0.0;
+  }
+  double V[kStages];
+#pragma unroll
+  for (int st = 0; st < kStages; ++st) {
+    double v = __dmul_rn(dl.c[0], Rv[st][0]);
+#pragma unroll
+    for (int i = 1; i < kMaxQ; ++i) {
+      if (i < qe) {
+        const double ci = dl.c[i];
+        if (ci != 0.0) v = __dadd_rn(v, __dmul_rn(ci, Rv[st][i]));
+      }
+    }
+    V[st] = v;
+  }
   // synchronous channel scalars of e-1: q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3},
   // q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
   double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
@@ -309,37 +367,38 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
     b2 = fma(S.r2[i], U[2][i], b2);
   }
   b2 = fma(S.k[2], a1, b2);
+  // with zero delay V_s = T_s (the current traces), so d_s = 0
   const double T0 = U[2][NP - 1];
-  const double d0 = __dsub_rn(T0, pe_value<0, 1>(I, j, n, 0, T0, 0.0, true));
+  const double d0 = k > 0 ? __dsub_rn(T0, V[0]) : 0.0;
   const double T1 = fma(S.rho[0], d0, b1);
-  const double d1 = __dsub_rn(T1, pe_value<0, 1>(I, j, n, 1, T1, 0.0, true));
+  const double d1 = k > 0 ? __dsub_rn(T1, V[1]) : 0.0;
   const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, b2));
-  const double d2 = __dsub_rn(T2, pe_value<0, 1>(I, j, n, 2, T2, 0.0, true));
+  const double d2 = k > 0 ? __dsub_rn(T2, V[2]) : 0.0;
+  col[((size_t)nm * kStages + 0) * P] = make_double2(T0, 0.0);
+  col[((size_t)nm * kStages + 1) * P] = make_double2(T1, 0.0);
+  col[((size_t)nm * kStages + 2) * P] = make_double2(T2, 0.0);
   // with a NaN or infinity in u^n the fixed-point step has already written NaN (or carries
   // the mark); nothing is added
   if (!(nonzero(d0) || nonzero(d1) || nonzero(d2)) || sc.bad) return;
   int emax = 0;
   unsigned long long mag = 0;
   for (int w = 0; w < 4; ++w) {   // elements e-1 .. e+2
-    int m = e - 1 + w;
-    if (m < 0) m += K;
-    if (m >= K) m -= K;
     if (fout) {
-      long long *q = static_cast<long long *>(uout) + m;
+      long long *q = static_cast<long long *>(uout) + mw[w];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
-        const long long X = *q + llrint(scalbn(c, -sc.sigma));
+        const long long X = Xq[w][i] + llrint(scalbn(c, -sc.sigma));
         *q = X;
         q += K;
         mag |= fx_mag(X);
       }
     } else {
-      double *q = static_cast<double *>(uout) + m;
+      double *q = static_cast<double *>(uout) + mw[w];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
-        const double y = __dadd_rn(*q, c);
+        const double y = __dadd_rn(Yd[w][i], c);
         *q = y;
         q += K;
         const int be = biased_exponent(y);
