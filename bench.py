@@ -56,9 +56,9 @@ FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant; a kernel changed since its counters were taken has no
-# entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 536.93 MB read
-# + 489.09 MB written (the chunk's interior steps; the first and last read or write FP64).
-TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_026_015_744}
+# entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.05 MB read
+# + 488.87 MB written (the chunk's interior steps; the first and last read or write FP64).
+TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_025_920_256}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 GRAPH_STEPS = 32
