@@ -236,8 +236,9 @@ def batched_timed(steps: int, warmup: int):
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
     b.check_finite()
+    variant = b.variant(0)[0]
     b.close()
-    return ndof * STAGES * steps / (ms * 1e-3), ms / steps, ndof, len(ws)
+    return ndof * STAGES * steps / (ms * 1e-3), ms / steps, ndof, len(ws), variant
 
 
 def adjoint_cost(steps: int = 0, repeats: int = 3):
@@ -441,9 +442,9 @@ def main():
         line["sync_dg"] = {"value": ndof * STAGES * args.sync_steps / (sms * 1e-3), "unit": UNIT,
                            "ms_per_step": sms / args.sync_steps}
         line["at_over_sync"] = value / ws / line["sync_dg"]["value"]
-        brate, bms, bdof, bn = batched_timed(100, 3)
+        brate, bms, bdof, bn, bvariant = batched_timed(100, 3)
         line["batched"] = {"value": brate, "unit": UNIT, "ms_per_step": bms, "instances": bn,
-                           "dof": bdof, "steps": 100,
+                           "dof": bdof, "steps": 100, "variant": bvariant,
                            "workload": "512 advection instances, K log-uniform in [1024, 262144], "
                                        "p in 1..4, L in 2..8, AT order min(p+1, 3)"}
         line["adjoint"] = adjoint_cost()

@@ -95,8 +95,8 @@ enum {
  *               coefficient below 2 in magnitude (small Courant numbers; ADG_EINVAL
  *               otherwise). Results below 2^-1022 are flushed to zero, and a NaN or infinity
  *               anywhere in u^n makes all of u^{n+1} NaN. AUTO picks COMPOSED_FIXED, else
- *               COMPOSED, where they apply (a single instance; batches use COMPOSED). All give
- *               the same scheme up to rounding.
+ *               COMPOSED, where they apply (in a batch, where every instance admits them). All
+ *               give the same scheme up to rounding.
  */
 typedef struct {
   int32_t pde;

@@ -236,6 +236,12 @@ class BatchSolver:
         check(load().adg_get_dt(self._ctx, int(i), C.byref(v)), self._ctx)
         return v.value
 
+    def variant(self, i: int) -> tuple:
+        """(variant instance i runs: "staged" | "composed" | "fixed", elements per thread)."""
+        v, e = C.c_int32(), C.c_int32()
+        check(load().adg_get_variant(self._ctx, int(i), C.byref(v), C.byref(e)), self._ctx)
+        return {1: "staged", 2: "composed", 3: "fixed"}[v.value], e.value
+
     def check_finite(self) -> None:
         check(load().adg_check_finite(self._ctx), self._ctx)
 

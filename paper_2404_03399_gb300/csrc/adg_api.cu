@@ -314,6 +314,7 @@ struct adg_ctx {
   int2 *fwork_dev = nullptr;   // (instance, first PE face) items of the batched face pass
   int nfwork = 0;
   bool batch_fused = false;     // every instance runs composed steps
+  bool batch_fixed = false;     // ... in fixed point
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -653,14 +654,12 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     I.ept = 1;
     if (I.fused) {
       fold_step_constants(h);
-      if (cfg->variant == ADG_VARIANT_COMPOSED_FIXED && (c->batch || !h.fixed_ok))
+      if (cfg->variant == ADG_VARIANT_COMPOSED_FIXED && !h.fixed_ok)
         return fail(c, ADG_EINVAL,
-                    c->batch ? "the fixed-point composed step runs single instances only"
-                             : "the fixed-point composed step needs every composed coefficient "
-                               "below 2 in magnitude (a smaller Courant number)");
-      const bool fixed = !c->batch && h.fixed_ok &&
-                         (cfg->variant == ADG_VARIANT_AUTO ||
-                          cfg->variant == ADG_VARIANT_COMPOSED_FIXED);
+                    "the fixed-point composed step needs every composed coefficient "
+                    "below 2 in magnitude (a smaller Courant number)");
+      const bool fixed = h.fixed_ok && (cfg->variant == ADG_VARIANT_AUTO ||
+                                        cfg->variant == ADG_VARIANT_COMPOSED_FIXED);
       if (fixed) {
         I.fused = 2;
         CK(cudaMalloc(&h.fx, 3 * sizeof(adg::FxSlot)));
@@ -705,10 +704,26 @@ int launch_fused_steps(adg_ctx *c, int nsteps);
 
 int launch_steps(adg_ctx *c, int nsteps) {
   if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps);
+  if (c->batch && c->batch_fixed && nsteps >= 2) {
+    // as launch_fused_steps: u (FP64) -> v1 (int64) -> v2 -> v1 ... -> u (FP64)
+    const int io = adg::kFmtInFixed | adg::kFmtOutFixed;
+    CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
+                                    0, 1, adg::kFmtOutFixed, true, 0, c->stream));
+    int in = 1;
+    for (int rel = 1; rel < nsteps - 1; ++rel) {
+      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
+                                      in, 3 - in, io, true, rel, c->stream));
+      in = 3 - in;
+    }
+    CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
+                                    in, 0, adg::kFmtInFixed, true, nsteps - 1, c->stream));
+    CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
+    return ADG_OK;
+  }
   if (c->batch && c->batch_fused) {
     for (int rel = 0; rel < nsteps; ++rel)
       CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                      rel % 2, rel, c->stream));
+                                      rel % 2, 1 - rel % 2, 0, c->batch_fixed, rel, c->stream));
     if (nsteps % 2) CK(adg::launch_batch_copy_back(c->insts_dev, c->work_dev, c->nwork, c->stream));
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
@@ -1248,10 +1263,23 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
   if (!r) {
     std::vector<Inst> hi(n);
     std::vector<int2> work, fwork;
+    // one batch runs one kind of step: fixed point if every instance admits it, else the
+    // FP64 composed step if every instance admits that, else the staged kernels
     c->batch_fused = true;
-    for (int i = 0; i < n; ++i) c->batch_fused = c->batch_fused && c->inst[i].I.fused;
-    if (!c->batch_fused)
-      for (int i = 0; i < n; ++i) c->inst[i].I.fused = 0;
+    c->batch_fixed = true;
+    for (int i = 0; i < n; ++i) {
+      c->batch_fused = c->batch_fused && c->inst[i].I.fused;
+      c->batch_fixed = c->batch_fixed && c->inst[i].I.fused == 2;
+    }
+    for (int i = 0; i < n && !r; ++i) {
+      if (c->inst[i].cfg.variant == ADG_VARIANT_COMPOSED_FIXED && !c->batch_fixed)
+        r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) +
+                                    ": the fixed-point composed step needs every instance of the "
+                                    "batch to admit it");
+      if (!c->batch_fused) c->inst[i].I.fused = 0;
+      else if (!c->batch_fixed) c->inst[i].I.fused = 1;
+    }
+    c->batch_fixed = c->batch_fixed && c->batch_fused;
     for (int i = 0; i < n; ++i) {
       hi[i] = c->inst[i].I;
       for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));

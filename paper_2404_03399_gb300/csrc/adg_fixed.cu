@@ -44,19 +44,17 @@ __device__ __forceinline__ void fx_own(const StepFixed &F, const double *ud, con
 // u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2 from the left neighbour's channel scalars. The first
 // three threads form the scalars of the three elements before the block with the same
 // arithmetic (the working scale is one per field, so every element converts the same way).
-// One element per thread runs at full occupancy (8 blocks of 256 threads per SM, at most 32
-// registers); two per thread keep 64 registers for the second element's values.
-template <int NP, int EPT, int FMT>
-__global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4) k_step_fixed(const Inst inst, const void *__restrict__ uin_,
-                                                      void *__restrict__ uout_, int rel) {
+// The block holding element 0 clears the scale slot of u^{n+2}.
+template <int NP, int EPT, int FMT, class I>
+__device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict__ uin_,
+                                           void *__restrict__ uout_, int e0, int rel,
+                                           FixedShared<EPT> &sh) {
   constexpr bool FIN = (FMT & kFmtInFixed) != 0;
   constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
-  __shared__ FixedShared<EPT> sh;
   const double *uin_d = static_cast<const double *>(uin_);
   const long long *uin_q = static_cast<const long long *>(uin_);
   const int K = inst.K;
   const int t = threadIdx.x;
-  const int e0 = blockIdx.x * (kTile * EPT);
   const StepFixed &F = inst.sf;
 
   // loads first: they do not depend on the scale
@@ -79,7 +77,7 @@ __global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4) k_step_fixed(const In
   if (t == 0) {
     const FxScale sc = fx_scale(inst.fx, inst.meta[0] + rel, FIN);
     sh.sc = sc;
-    if (blockIdx.x == 0) {
+    if (e0 == 0) {
       FxSlot &c = inst.fx[fx_clear(sc.slot)];   // the slot of u^{n+2}
       c.mag = 0;
       c.E = 0;
@@ -204,6 +202,47 @@ __global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4) k_step_fixed(const In
   }
 }
 
+// One element per thread runs at full occupancy (8 blocks of 256 threads per SM, at most 32
+// registers); two per thread keep 64 registers for the second element's values.
+template <int NP, int EPT, int FMT>
+__global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4)
+    k_step_fixed(const Inst inst, const void *__restrict__ uin, void *__restrict__ uout, int rel) {
+  __shared__ FixedShared<EPT> sh;
+  fixed_body<NP, EPT, FMT>(inst, uin, uout, blockIdx.x * (kTile * EPT), rel, sh);
+}
+
+__device__ __forceinline__ void *inst_field(const Inst &I, int sel) {
+  return sel == 0 ? (void *)I.u : (sel == 1 ? (void *)I.v1 : (void *)I.v2);
+}
+
+// Batched fixed-point steps: block b takes work item (instance, first element); the
+// instance's descriptor is staged in shared memory; src / dst select u (0), v1 (1) or v2 (2)
+// of every instance, FMT their formats.
+template <int FMT>
+__global__ void __launch_bounds__(kTile)
+    k_batch_fixed(const Inst *__restrict__ insts, const int2 *__restrict__ work, int src, int dst,
+                  int rel) {
+  __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
+  __shared__ FixedShared<1> sh;
+  const int2 w = work[blockIdx.x];
+  {
+    const int4 *from = reinterpret_cast<const int4 *>(insts + w.x);
+    int4 *to = reinterpret_cast<int4 *>(smem);
+    for (int t = threadIdx.x; t < (int)(sizeof(Inst) / sizeof(int4)); t += blockDim.x)
+      to[t] = __ldg(from + t);
+  }
+  __syncthreads();
+  const Inst &I = *reinterpret_cast<const Inst *>(smem);
+  const void *uin = inst_field(I, src);
+  void *uout = inst_field(I, dst);
+  switch (I.Np) {
+    case 2: fixed_body<2, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
+    case 3: fixed_body<3, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
+    case 4: fixed_body<4, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
+    default: fixed_body<5, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
+  }
+}
+
 __global__ void k_fixed_reset(const double *__restrict__ f, size_t n, int *E) {
   int m = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -243,6 +282,18 @@ cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int re
     case 4: fixed_np<4>(I, uin, uout, rel, fmt, s); break;
     case 5: fixed_np<5>(I, uin, uout, rel, fmt, s); break;
     default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                                    int src, int dst, int fmt, int rel, cudaStream_t s) {
+  if (nwork <= 0) return cudaSuccess;
+  switch (fmt & 3) {
+    case 0: k_batch_fixed<0><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
+    case 1: k_batch_fixed<1><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
+    case 2: k_batch_fixed<2><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
+    default: k_batch_fixed<3><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
   }
   return cudaGetLastError();
 }

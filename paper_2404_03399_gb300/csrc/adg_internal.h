@@ -171,15 +171,21 @@ cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int re
 // The fixed-point composed step alone (adg_fixed.cu).
 cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int rel, int fmt,
                               cudaStream_t s);
-// Batched composed steps over all instances (parity 0: u -> v1, 1: v1 -> u) and the copy
-// of v1 into u after an odd count.
+// Batched composed steps over all instances: src / dst select u (0), v1 (1) or v2 (2) of
+// every instance. FP64 (fixed false): u -> v1 or v1 -> u. Fixed point (fixed true): fmt as in
+// launch_fused_step. Then the PE-face correction of every instance.
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
-                                    const int2 *fwork_dev, int nfwork, int parity, int rel,
-                                    cudaStream_t s);
+                                    const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
+                                    bool fixed, int rel, cudaStream_t s);
+// The batched fixed-point step alone (adg_fixed.cu).
+cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
+                                    int src, int dst, int fmt, int rel, cudaStream_t s);
 // Scale slots of the fixed-point composed step for an FP64 field f of n values at step
 // index `step`: all three slots cleared, then E of slot step % 3 = largest biased exponent.
 cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,
                                cudaStream_t s);
+// Copies v1 into u for every instance (after an odd number of FP64 batched composed steps, or
+// a single fixed-point step).
 cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                    cudaStream_t s);
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,

@@ -448,19 +448,19 @@ __global__ void __launch_bounds__(kTile) k_batch_fused(const Inst *__restrict__ 
 }
 
 __global__ void __launch_bounds__(64) k_batch_fixup(const Inst *__restrict__ insts,
-                                                    const int2 *__restrict__ fwork, int parity,
-                                                    int rel) {
+                                                    const int2 *__restrict__ fwork, int src,
+                                                    int dst, int fmt, int rel) {
   const int2 w = fwork[blockIdx.y];
   const Inst &I = insts[w.x];
   const int j = w.y + blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= I.P || blockIdx.x * blockDim.x + threadIdx.x >= 256) return;
-  const double *uin = parity ? I.v1 : I.u;
-  double *uout = parity ? I.u : I.v1;
+  const void *uin = src == 0 ? (const void *)I.u : (src == 1 ? (const void *)I.v1 : (const void *)I.v2);
+  void *uout = dst == 0 ? (void *)I.u : (dst == 1 ? (void *)I.v1 : (void *)I.v2);
   switch (I.Np) {
-    case 2: fixup_body<2>(I, j, uin, uout, rel, 0); break;
-    case 3: fixup_body<3>(I, j, uin, uout, rel, 0); break;
-    case 4: fixup_body<4>(I, j, uin, uout, rel, 0); break;
-    default: fixup_body<5>(I, j, uin, uout, rel, 0); break;
+    case 2: fixup_body<2>(I, j, uin, uout, rel, fmt); break;
+    case 3: fixup_body<3>(I, j, uin, uout, rel, fmt); break;
+    case 4: fixup_body<4>(I, j, uin, uout, rel, fmt); break;
+    default: fixup_body<5>(I, j, uin, uout, rel, fmt); break;
   }
 }
 
@@ -776,10 +776,17 @@ cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int re
 }
 
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
-                                    const int2 *fwork_dev, int nfwork, int parity, int rel,
-                                    cudaStream_t s) {
-  k_batch_fused<<<nwork, kTile, 0, s>>>(insts_dev, work_dev, parity);
-  if (nfwork > 0) k_batch_fixup<<<dim3(4, nfwork), 64, 0, s>>>(insts_dev, fwork_dev, parity, rel);
+                                    const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
+                                    bool fixed, int rel, cudaStream_t s) {
+  if (fixed) {
+    cudaError_t e = launch_batch_fixed_step(insts_dev, work_dev, nwork, src, dst, fmt, rel, s);
+    if (e != cudaSuccess) return e;
+  } else {
+    fmt = 0;
+    k_batch_fused<<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src == 1 ? 1 : 0);
+  }
+  if (nfwork > 0)
+    k_batch_fixup<<<dim3(4, nfwork), 64, 0, s>>>(insts_dev, fwork_dev, src, dst, fmt, rel);
   return cudaGetLastError();
 }
 

@@ -23,9 +23,9 @@ def _built():
     build.build()
 
 
-def _cfg(w, mode=None):
+def _cfg(w, mode=None, variant="auto"):
     return adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, a=w.a, cfl=w.cfl,
-                      mode=mode or w.mode, L=w.L, q=w.q, seed=w.seed)
+                      mode=mode or w.mode, L=w.L, q=w.q, seed=w.seed, variant=variant)
 
 
 def _small_batch():
@@ -57,14 +57,18 @@ def _eligible_batch():
     return ws
 
 
-@pytest.mark.parametrize("kind", ["mixed", "composed"])
-def test_small_batch_matches_oracle_and_single_runs(kind):
+@pytest.mark.parametrize("kind,variant,single_variant", [
+    ("mixed", "auto", "staged"),        # some instances admit no composed step: all staged
+    ("eligible", "composed", "composed"),
+    ("eligible", "auto", "fixed"),      # every instance admits the fixed-point step
+])
+def test_small_batch_matches_oracle_and_single_runs(kind, variant, single_variant):
     ws = _small_batch() if kind == "mixed" else _eligible_batch()
-    single_variant = "staged" if kind == "mixed" else "composed"
     steps = 70
-    cfgs = [_cfg(w) for w in ws]
+    cfgs = [_cfg(w, variant=variant) for w in ws]
     u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
     b = adg.BatchSolver(cfgs, u0s)
+    assert all(b.variant(i)[0] == single_variant for i in range(len(ws)))
     b.step(steps)
     for i, (c, w) in enumerate(zip(cfgs, ws)):
         got = b.state(i).cpu().numpy()
@@ -112,4 +116,24 @@ def test_full_batch_sampled():
             ref = dg.run(prob, u0[idx], steps).numpy()[e - lo]
             err = np.max(np.abs(got[e] - ref)) / np.max(np.abs(got))
             assert err < TOL, (i, e, err)
+    b.close()
+
+
+def test_batch_of_fixed_point_steps_in_calls_of_one_and_two():
+    # single-step calls take the FP64 path of the fixed-point step; two-step calls run one
+    # FP64 -> int64 and one int64 -> FP64 step; both stay on the oracle
+    ws = _eligible_batch()
+    cfgs = [_cfg(w) for w in ws]
+    u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
+    b = adg.BatchSolver(cfgs, u0s)
+    for k in (1, 2, 1, 2, 3):
+        b.step(k)
+    steps = 9
+    for i, (c, w) in enumerate(zip(cfgs, ws)):
+        got = b.state(i).cpu().numpy()
+        tbl = odelays.delay_table(w.seed, w.P, steps, w.L) if w.P > 1 else None
+        prob = dg.Problem(pde="advection", K=w.K, p=w.p, P=w.P, dt=b.dt(i), a=w.a,
+                          mode="adg" if tbl is not None else "sync", q=w.q, delays=tbl)
+        ref = dg.run(prob, u0s[i].cpu().numpy(), steps).numpy()
+        assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < TOL, i
     b.close()
