@@ -366,6 +366,9 @@ def main():
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                     help="only time adg_grad against the forward on the adjoint workload for STEPS "
                          "steps (one repeat) and print that dict (for profiling runs)")
+    ap.add_argument("--batched-only", type=int, default=0, metavar="STEPS",
+                    help="only time the batched workload for STEPS steps and print that dict "
+                         "(for profiling runs)")
     args = ap.parse_args()
 
     rank, ws, local, dist = dist_setup()
@@ -381,6 +384,11 @@ def main():
     adg.load()
     if args.adjoint_only:
         print(json.dumps(adjoint_cost(args.adjoint_only, 1)), flush=True)
+        return
+    if args.batched_only:
+        rate, ms, ndof, n, variant = batched_timed(args.batched_only, 3)
+        print(json.dumps({"batched": rate, "ms_per_step": ms, "dof": ndof, "instances": n,
+                          "variant": variant}), flush=True)
         return
     barrier = (lambda: dist.barrier()) if dist is not None else (lambda: None)
 
