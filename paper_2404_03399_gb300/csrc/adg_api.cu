@@ -500,10 +500,25 @@ int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, dou
 // Refill the device delay table of h with the rows of steps [first, first+TR).
 int fill_table(adg_ctx *c, InstHost &h, int64_t first) {
   h.tbase = first;
-  h.host_rows.resize((size_t)h.TR * h.I.P);
-  h.delays.rows(first, h.TR, h.host_rows.data());
-  CK(cudaMemcpyAsync(h.table, h.host_rows.data(), h.host_rows.size(), cudaMemcpyHostToDevice,
-                     c->stream));
+  const DelaySource &d = h.delays;
+  if (d.caller.empty()) {
+    // seeded rows are generated on the device (the host generator's arithmetic, with the bin
+    // edges as exact integer thresholds: u < e  <=>  (z >> 11) < ceil(e 2^53))
+    adg::DelayGen g{};
+    g.seed = d.seed;
+    g.L = d.L;
+    g.P = d.P;
+    for (int b = 0; b < d.L; ++b) {
+      const double t = std::ceil(std::ldexp(d.edges[b], 53));
+      g.T[b] = t >= 18446744073709551616.0 ? ~0ull : (t <= 0 ? 0ull : (uint64_t)t);
+    }
+    CK(adg::launch_fill_delays(h.table, first, h.TR, g, c->stream));
+  } else {
+    h.host_rows.resize((size_t)h.TR * h.I.P);
+    d.rows(first, h.TR, h.host_rows.data());
+    CK(cudaMemcpyAsync(h.table, h.host_rows.data(), h.host_rows.size(), cudaMemcpyHostToDevice,
+                       c->stream));
+  }
   int64_t tb = first;
   CK(cudaMemcpyAsync((void *)(h.I.meta + 1), &tb, sizeof(int64_t), cudaMemcpyHostToDevice,
                      c->stream));

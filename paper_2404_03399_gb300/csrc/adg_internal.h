@@ -180,6 +180,17 @@ cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev,
 // The batched fixed-point step alone (adg_fixed.cu).
 cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     int src, int dst, int fmt, int rel, cudaStream_t s);
+// Seeded delay-table rows on the device, identical to the host generator: entry (row r,
+// face j) is the bin of output (first + r) P + j of SplitMix64(seed), u = (z >> 11) 2^-53,
+// bin = the first b with u < edges[b] (else L - 1), compared in integers as
+// (z >> 11) < T[b] with T[b] = ceil(edges[b] 2^53) formed exactly on the host.
+struct DelayGen {
+  uint64_t seed;
+  uint64_t T[kMaxL];
+  int L, P;
+};
+cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const DelayGen &g,
+                               cudaStream_t s);
 // Scale slots of the fixed-point composed step for an FP64 field f of n values at step
 // index `step`: all three slots cleared, then E of slot step % 3 = largest biased exponent.
 cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,

@@ -775,6 +775,34 @@ cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int re
   }
 }
 
+namespace {
+__global__ void k_fill_delays(uint8_t *__restrict__ table, int64_t first, int64_t total,
+                              const DelayGen g) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const uint64_t idx = (uint64_t)first * (uint64_t)g.P + (uint64_t)i;   // (first + r) P + j
+    uint64_t z = g.seed + (idx + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    const uint64_t m = z >> 11;
+    int k = g.L - 1;
+    for (int b = g.L - 1; b >= 0; --b)
+      if (m < g.T[b]) k = b;
+    table[i] = (uint8_t)k;
+  }
+}
+}  // namespace
+
+cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const DelayGen &g,
+                               cudaStream_t s) {
+  const int64_t total = (int64_t)rows * g.P;
+  const int64_t want = (total + 255) / 256;
+  const unsigned grid = (unsigned)(want < 8 * 152 ? (want ? want : 1) : 8 * 152);
+  k_fill_delays<<<grid, 256, 0, s>>>(table, first, total, g);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
                                     bool fixed, int rel, cudaStream_t s) {
