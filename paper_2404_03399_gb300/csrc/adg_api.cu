@@ -315,6 +315,8 @@ struct adg_ctx {
   int nfwork = 0;
   bool batch_fused = false;     // every instance runs composed steps
   bool batch_fixed = false;     // ... in fixed point
+  adg::BatchLite *lites_dev = nullptr;
+  std::unique_ptr<adg::BatchUniform> bu;   // shared coefficients per degree, when they are
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
   cudaGraphExec_t gexec = nullptr;
@@ -338,12 +340,22 @@ int fail(adg_ctx *c, int code, const std::string &msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                    \
   } while (0)
 
+// c2 a = -2 dt a / dx of upwind advection. With the step from the Courant number,
+// dt = sigma dx / |a|, it is -2 sigma sign(a) exactly: folded from sigma, every instance with
+// the same degree, sigma and sign of a gets the same constants (the rounded dt differs from
+// sigma dx / |a| by one rounding, 1e-16 relatively).
+long double advection_c2a(const InstHost &h) {
+  const long double a = (long double)h.cfg.a;
+  if (h.cfg.dt > 0) return -2.0L * (long double)h.dt * a / (long double)h.dx;
+  return -2.0L * (long double)h.cfg.cfl * (a > 0 ? 1.0L : -1.0L);
+}
+
 void fold_constants(InstHost &h) {
   const Ops &o = h.ops;
   const int Np = o.Np;
   const ld c2 = -2.0L * (ld)h.dt / (ld)h.dx;
   const bool adv = h.cfg.pde == ADG_ADVECTION;
-  const ld a = (ld)h.cfg.a;
+  const ld c2a = adv ? advection_c2a(h) : 0.0L;
   const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
   const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
   for (int s = 0; s < kStages; ++s) {
@@ -355,10 +367,10 @@ void fold_constants(InstHost &h) {
     for (int i = 0; i < Np; ++i) {
       for (int j = 0; j < Np; ++j) {
         const ld d = o.D[i * Np + j];
-        C.A[i * Np + j] = adv ? (double)(b * ((i == j ? 1.0L : 0.0L) + c2 * a * d))
+        C.A[i * Np + j] = adv ? (double)(b * ((i == j ? 1.0L : 0.0L) + c2a * d))
                               : (double)(b * c2 * 0.5L * d);
       }
-      const ld sc = adv ? b * c2 * a : b * c2;
+      const ld sc = adv ? b * c2a : b * c2;
       C.lL[i] = (double)(sc * o.Minv[i * Np + 0]);
       C.lR[i] = (double)(-sc * o.Minv[i * Np + (Np - 1)]);
     }
@@ -370,8 +382,7 @@ void fold_constants(InstHost &h) {
 void fold_step_constants(InstHost &h) {
   const Ops &o = h.ops;
   const int Np = o.Np;
-  const ld c2 = -2.0L * (ld)h.dt / (ld)h.dx;
-  const ld a = (ld)h.cfg.a;
+  const ld c2a = advection_c2a(h);
   const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
   const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
   typedef std::vector<ld> Mat;
@@ -394,9 +405,9 @@ void fold_step_constants(InstHost &h) {
     M[s].assign(Np * Np, 0);
     cv[s].assign(Np, 0);
     for (int i = 0; i < Np; ++i) {
-      const ld lL = beta[s] * c2 * a * o.Minv[i * Np + 0];
+      const ld lL = beta[s] * c2a * o.Minv[i * Np + 0];
       for (int j = 0; j < Np; ++j)
-        M[s][i * Np + j] = beta[s] * ((i == j ? 1.0L : 0.0L) + c2 * a * o.D[i * Np + j]);
+        M[s][i * Np + j] = beta[s] * ((i == j ? 1.0L : 0.0L) + c2a * o.D[i * Np + j]);
       M[s][i * Np + 0] += lL;
       cv[s][i] = -lL;
     }
@@ -431,7 +442,7 @@ void fold_step_constants(InstHost &h) {
   // the right trace of element e-1 seen by the later stages.
   for (int st = 0; st < 3; ++st) {
     std::vector<ld> d(4 * Np, 0.0L);   // elements e-1 .. e+2
-    const ld sc = beta[st] * c2 * a;
+    const ld sc = beta[st] * c2a;
     for (int i = 0; i < Np; ++i) {
       d[1 * Np + i] = sc * o.Minv[i * Np + 0];
       d[0 * Np + i] = -sc * o.Minv[i * Np + p];
@@ -723,22 +734,24 @@ int launch_steps(adg_ctx *c, int nsteps) {
     // as launch_fused_steps: u (FP64) -> v1 (int64) -> v2 -> v1 ... -> u (FP64)
     const int io = adg::kFmtInFixed | adg::kFmtOutFixed;
     CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                    0, 1, adg::kFmtOutFixed, true, 0, c->stream));
+                                    0, 1, adg::kFmtOutFixed, true, 0, c->stream, c->bu.get()));
     int in = 1;
     for (int rel = 1; rel < nsteps - 1; ++rel) {
       CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                      in, 3 - in, io, true, rel, c->stream));
+                                      in, 3 - in, io, true, rel, c->stream, c->bu.get()));
       in = 3 - in;
     }
     CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                    in, 0, adg::kFmtInFixed, true, nsteps - 1, c->stream));
+                                    in, 0, adg::kFmtInFixed, true, nsteps - 1, c->stream,
+                                    c->bu.get()));
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
   }
   if (c->batch && c->batch_fused) {
     for (int rel = 0; rel < nsteps; ++rel)
       CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                      rel % 2, 1 - rel % 2, 0, c->batch_fixed, rel, c->stream));
+                                      rel % 2, 1 - rel % 2, 0, c->batch_fixed, rel, c->stream,
+                                      c->batch_fixed ? c->bu.get() : nullptr));
     if (nsteps % 2) CK(adg::launch_batch_copy_back(c->insts_dev, c->work_dev, c->nwork, c->stream));
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
@@ -1209,6 +1222,7 @@ void adg_destroy(adg_ctx *c) {
   }
   cudaFree(c->meta);
   cudaFree(c->insts_dev);
+  cudaFree(c->lites_dev);
   cudaFree(c->work_dev);
   cudaFree(c->fwork_dev);
   cudaFree(c->partials);
@@ -1295,6 +1309,43 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       else if (!c->batch_fixed) c->inst[i].I.fused = 1;
     }
     c->batch_fixed = c->batch_fixed && c->batch_fused;
+    // every instance of a degree with the same fixed-point coefficients: pass them per degree
+    if (!r && c->batch_fixed) {
+      bool uniform = true;
+      const adg::StepFixed *ref[adg::kMaxNp - 1] = {nullptr, nullptr, nullptr, nullptr};
+      for (int i = 0; i < n && uniform; ++i) {
+        const adg::StepFixed &f = c->inst[i].I.sf;
+        const int d = c->inst[i].I.Np - 2;
+        if (!ref[d]) ref[d] = &f;
+        else uniform = std::memcmp(ref[d], &f, sizeof(f)) == 0;
+      }
+      if (uniform) {
+        std::vector<adg::BatchLite> lites(n);
+        for (int i = 0; i < n; ++i) {
+          const Inst &I = c->inst[i].I;
+          lites[i].f[0] = I.u;
+          lites[i].f[1] = I.v1;
+          lites[i].f[2] = I.v2;
+          lites[i].meta = I.meta;
+          lites[i].fx = I.fx;
+          lites[i].K = I.K;
+          lites[i].Np = I.Np;
+        }
+        c->bu.reset(new (std::nothrow) adg::BatchUniform());
+        if (!c->bu) {
+          r = fail(c, ADG_ENOMEM, "host allocation failed");
+        } else if (cudaMalloc(&c->lites_dev, sizeof(adg::BatchLite) * n) != cudaSuccess ||
+                   cudaMemcpy(c->lites_dev, lites.data(), sizeof(adg::BatchLite) * n,
+                              cudaMemcpyHostToDevice) != cudaSuccess) {
+          r = fail(c, ADG_ENOMEM, "cudaMalloc(batch records)");
+        } else {
+          std::memset(&c->bu->uf, 0, sizeof(c->bu->uf));
+          for (int d = 0; d < adg::kMaxNp - 1; ++d)
+            if (ref[d]) c->bu->uf.sf[d] = *ref[d];
+          c->bu->lites_dev = c->lites_dev;
+        }
+      }
+    }
     for (int i = 0; i < n; ++i) {
       hi[i] = c->inst[i].I;
       for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));

@@ -243,6 +243,33 @@ __global__ void __launch_bounds__(kTile)
   }
 }
 
+// The fields fixed_body reads, with the coefficients taken from a kernel parameter.
+struct LiteView {
+  int K;
+  const int64_t *meta;
+  FxSlot *fx;
+  const StepFixed &sf;
+};
+
+// Batched fixed-point steps with the coefficients shared per degree (BatchUniform): block b
+// takes work item (instance, first element) and reads only the instance's BatchLite.
+template <int FMT>
+__global__ void __launch_bounds__(kTile)
+    k_batch_fixed_uniform(const BatchLite *__restrict__ lites, const int2 *__restrict__ work,
+                          int src, int dst, int rel, const UniformFixed uf) {
+  __shared__ FixedShared<1> sh;
+  const int2 w = work[blockIdx.x];
+  const BatchLite L = lites[w.x];
+  const void *uin = src == 0 ? L.f[0] : (src == 1 ? L.f[1] : L.f[2]);
+  void *uout = dst == 0 ? L.f[0] : (dst == 1 ? L.f[1] : L.f[2]);
+  switch (L.Np) {
+    case 2: fixed_body<2, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
+    case 3: fixed_body<3, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
+    case 4: fixed_body<4, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
+    default: fixed_body<5, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
+  }
+}
+
 __global__ void k_fixed_reset(const double *__restrict__ f, size_t n, int *E) {
   int m = 0;
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
@@ -294,6 +321,19 @@ cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev,
     case 1: k_batch_fixed<1><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
     case 2: k_batch_fixed<2><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
     default: k_batch_fixed<3><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_dev, int nwork,
+                                       int src, int dst, int fmt, int rel, cudaStream_t s) {
+  if (nwork <= 0) return cudaSuccess;
+  const BatchLite *l = bu.lites_dev;
+  switch (fmt & 3) {
+    case 0: k_batch_fixed_uniform<0><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
+    case 1: k_batch_fixed_uniform<1><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
+    case 2: k_batch_fixed_uniform<2><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
+    default: k_batch_fixed_uniform<3><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
   }
   return cudaGetLastError();
 }

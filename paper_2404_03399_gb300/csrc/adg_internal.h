@@ -171,12 +171,37 @@ cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int re
 // The fixed-point composed step alone (adg_fixed.cu).
 cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int rel, int fmt,
                               cudaStream_t s);
+// What the batched fixed-point step reads of an instance when the coefficients are shared
+// (below): its fields u, v1, v2, step counter, scale slots, K and Np.
+struct BatchLite {
+  void *f[3];
+  const int64_t *meta;
+  FxSlot *fx;
+  int K, Np;
+};
+// One fixed-point coefficient set per degree (sf[Np - 2]), for batches in which every instance
+// of a degree has the same composed coefficients (the same Courant number with a > 0 and the
+// step from the Courant number: the folded constants depend on p and sigma only). Passed as a
+// kernel parameter, so the coefficients are constant-bank operands as in the single-instance
+// step instead of shared-memory loads.
+struct UniformFixed {
+  StepFixed sf[kMaxNp - 1];
+};
+struct BatchUniform {
+  const BatchLite *lites_dev;
+  UniformFixed uf;
+};
+
 // Batched composed steps over all instances: src / dst select u (0), v1 (1) or v2 (2) of
 // every instance. FP64 (fixed false): u -> v1 or v1 -> u. Fixed point (fixed true): fmt as in
-// launch_fused_step. Then the PE-face correction of every instance.
+// launch_fused_step, with the shared coefficients of bu when bu is not null. Then the PE-face
+// correction of every instance.
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
-                                    bool fixed, int rel, cudaStream_t s);
+                                    bool fixed, int rel, cudaStream_t s,
+                                    const BatchUniform *bu = nullptr);
+cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_dev, int nwork,
+                                       int src, int dst, int fmt, int rel, cudaStream_t s);
 // The batched fixed-point step alone (adg_fixed.cu).
 cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     int src, int dst, int fmt, int rel, cudaStream_t s);

@@ -805,9 +805,10 @@ cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const De
 
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
-                                    bool fixed, int rel, cudaStream_t s) {
+                                    bool fixed, int rel, cudaStream_t s, const BatchUniform *bu) {
   if (fixed) {
-    cudaError_t e = launch_batch_fixed_step(insts_dev, work_dev, nwork, src, dst, fmt, rel, s);
+    cudaError_t e = bu ? launch_batch_fixed_uniform(*bu, work_dev, nwork, src, dst, fmt, rel, s)
+                       : launch_batch_fixed_step(insts_dev, work_dev, nwork, src, dst, fmt, rel, s);
     if (e != cudaSuccess) return e;
   } else {
     fmt = 0;

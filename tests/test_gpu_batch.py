@@ -137,3 +137,22 @@ def test_batch_of_fixed_point_steps_in_calls_of_one_and_two():
         ref = dg.run(prob, u0s[i].cpu().numpy(), steps).numpy()
         assert np.max(np.abs(got - ref)) / np.max(np.abs(ref)) < TOL, i
     b.close()
+
+
+def test_fixed_point_batch_with_different_coefficients_per_degree():
+    # Two Courant numbers among instances of the same degree: the coefficients differ, so the
+    # batch reads each instance's own coefficients (the general batched kernel) instead of one
+    # set per degree; every instance still equals its single-instance fixed-point run.
+    ws = _eligible_batch()
+    cfgs = [adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, a=w.a, cfl=0.002 + 0.001 * (i % 2),
+                       mode=w.mode, L=w.L, q=w.q, seed=w.seed) for i, w in enumerate(ws)]
+    u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
+    b = adg.BatchSolver(cfgs, u0s)
+    assert all(b.variant(i)[0] == "fixed" for i in range(len(ws)))
+    b.step(40)
+    for i, c in enumerate(cfgs):
+        s = adg.Solver(adg.Config(**{**c.__dict__, "variant": "fixed"}), u0s[i])
+        s.step(40)
+        assert np.array_equal(b.state(i).cpu().numpy(), s.state().cpu().numpy()), i
+        s.close()
+    b.close()
