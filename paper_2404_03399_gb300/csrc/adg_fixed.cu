@@ -10,7 +10,11 @@ namespace {
 
 template <int EPT>
 struct FixedShared {
-  long long p[EPT * kTile + 3], q1[EPT * kTile + 3], q2[EPT * kTile + 3];
+  // per element slot: the right trace p and the unrounded own parts (a, b) of its channel
+  // scalars r1 . u, r2 . u
+  long long p[EPT * kTile + 3];
+  long long s1a[EPT * kTile + 3], s1b[EPT * kTile + 3];
+  long long s2a[EPT * kTile + 3], s2b[EPT * kTile + 3];
   FxScale sc;
 };
 
@@ -39,11 +43,11 @@ __device__ __forceinline__ void fx_own(const StepFixed &F, const double *ud, con
 }
 
 // One thread per element (EPT elements per thread, e = e0 + t + h kTile): the right trace and
-// the own parts of the channel scalars, then v1_p = r1 . u + k_0 P0 and
-// v2_p = r2 . u + k_1 P0 + k_2 P1 in two rounds through shared memory, then
-// u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2 from the left neighbour's channel scalars. The first
-// three threads form the scalars of the three elements before the block with the same
-// arithmetic (the working scale is one per field, so every element converts the same way).
+// the unrounded own parts of the channel scalars go to shared memory (one barrier); each
+// thread then forms its left neighbour's v1_p and v2_p from those of elements e-3 .. e-1 and
+// u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2. The first three threads publish the three elements
+// before the block with the same arithmetic (the working scale is one per field, so every
+// element converts the same way).
 // The block holding element 0 clears the scale slot of u^{n+2}.
 template <int NP, int EPT, int FMT, class I>
 __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict__ uin_,
@@ -98,68 +102,61 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
 #pragma unroll
       for (int j = 0; j < NP; ++j) uq[h][j] = fx_rescale(uq[h][j], sc.shift);
   }
-  FxAcc hs1, hs2;
+  // publish p and the unrounded own parts of every element's channel scalars (the halo's too)
   if (t < 3) {
     int xh[NP], xl[NP];
     long long p;
+    FxAcc hs1, hs2;
     fx_own<NP, FIN>(F, hd, hq, sc, p, hs1, hs2, xh, xl);
     sh.p[t] = p;
+    sh.s1a[t] = hs1.a;
+    sh.s1b[t] = hs1.b;
+    sh.s2a[t] = hs2.a;
+    sh.s2b[t] = hs2.b;
   }
   int xh[EPT][NP], xl[EPT][NP];
-  FxAcc s1[EPT], s2[EPT];
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
     long long p;
-    fx_own<NP, FIN>(F, ud[h], uq[h], sc, p, s1[h], s2[h], xh[h], xl[h]);
-    sh.p[t + h * kTile + 3] = p;
-  }
-  __syncthreads();
-  // v1_p = r1 . u + k_0 P0, rounded once
-  if (t == 1 || t == 2) {
-    int ph, pl;
-    fx_split(sh.p[t - 1], ph, pl);
-    fx_mac(hs1, F.k[0], ph, pl);
-    sh.q1[t] = fx_round(hs1);
-  }
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
+    FxAcc s1, s2;
+    fx_own<NP, FIN>(F, ud[h], uq[h], sc, p, s1, s2, xh[h], xl[h]);
     const int sl = t + h * kTile + 3;
-    int ph, pl;
-    fx_split(sh.p[sl - 1], ph, pl);
-    fx_mac(s1[h], F.k[0], ph, pl);
-    sh.q1[sl] = fx_round(s1[h]);
-  }
-  __syncthreads();
-  // v2_p = r2 . u + k_1 P0 + k_2 P1, rounded once
-  if (t == 2) {
-    int ph, pl, qh, ql;
-    fx_split(sh.p[1], ph, pl);
-    fx_split(sh.q1[1], qh, ql);
-    fx_mac(hs2, F.k[1], ph, pl);
-    fx_mac(hs2, F.k[2], qh, ql);
-    sh.q2[2] = fx_round(hs2);
-  }
-#pragma unroll
-  for (int h = 0; h < EPT; ++h) {
-    const int sl = t + h * kTile + 3;
-    int ph, pl, qh, ql;
-    fx_split(sh.p[sl - 1], ph, pl);
-    fx_split(sh.q1[sl - 1], qh, ql);
-    fx_mac(s2[h], F.k[1], ph, pl);
-    fx_mac(s2[h], F.k[2], qh, ql);
-    sh.q2[sl] = fx_round(s2[h]);
+    sh.p[sl] = p;
+    sh.s1a[sl] = s1.a;
+    sh.s1b[sl] = s1.b;
+    sh.s2a[sl] = s2.a;
+    sh.s2b[sl] = s2.b;
   }
   __syncthreads();
   unsigned long long mag = 0;   // FOUT: OR of |y|
   int emax = 0;                 // FP64 output: largest biased exponent
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
-    const int b = t + h * kTile;   // left neighbour's slot is b + 2
+    const int b = t + h * kTile;   // slots of the elements e-3, e-2, e-1: b, b+1, b+2
     const int e = e0 + b;
+    // the left neighbour's channel scalars, each rounded once from the published parts:
+    // v1_p^{e-2} = r1 . u^{e-2} + k_0 p^{e-3}, v1_p^{e-1} = r1 . u^{e-1} + k_0 p^{e-2},
+    // v2_p^{e-1} = r2 . u^{e-1} + k_1 p^{e-2} + k_2 v1_p^{e-2} (every thread that needs one of
+    // them forms it from the same values, so all agree bit for bit)
+    int p3h, p3l, p2h, p2l;
+    fx_split(sh.p[b], p3h, p3l);
+    fx_split(sh.p[b + 1], p2h, p2l);
+    FxAcc c1m2{sh.s1a[b + 1], sh.s1b[b + 1]};
+    fx_mac(c1m2, F.k[0], p3h, p3l);
+    const long long q1m2 = fx_round(c1m2);
+    FxAcc c1m1{sh.s1a[b + 2], sh.s1b[b + 2]};
+    fx_mac(c1m1, F.k[0], p2h, p2l);
+    const long long q1m1 = fx_round(c1m1);
+    int qh, ql;
+    fx_split(q1m2, qh, ql);
+    FxAcc c2m1{sh.s2a[b + 2], sh.s2b[b + 2]};
+    fx_mac(c2m1, F.k[1], p2h, p2l);
+    fx_mac(c2m1, F.k[2], qh, ql);
+    const long long q2m1 = fx_round(c2m1);
     int P0h, P0l, P1h, P1l, P2h, P2l;
     fx_split(sh.p[b + 2], P0h, P0l);
-    fx_split(sh.q1[b + 2], P1h, P1l);
-    fx_split(sh.q2[b + 2], P2h, P2l);
+    fx_split(q1m1, P1h, P1l);
+    fx_split(q2m1, P2h, P2l);
     const size_t base = (size_t)e;
     double *od = static_cast<double *>(uout_) + base;
     long long *oq = static_cast<long long *>(uout_) + base;
