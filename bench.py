@@ -46,19 +46,20 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
 # upwind advection, Np^2 + 5 Np + 3 multiply-adds per element and step):
 #  - fixed-point integer step (picked where the coefficients fit, as here): each
 #    multiply-add is three 32 x 32 -> 64-bit integer products, 3 (Np^2 + 5 Np + 3) per element
-#    (117 at p = 3); the bound is the integer multiply pipe;
+#    (117 at p = 3), plus 3 for forming the left neighbour's v1_p^{e-2}; the bound is the
+#    integer multiply pipe;
 #  - FP64 composed step: 2 (Np^2 + 5 Np + 3) / Np flop per DOF-step (19.5 at p = 3);
 #  - staged FP64 kernels: 2 (Np + 2) flop per DOF-stage.
 NP = WORKLOAD["p"] + 1
 MACS_PER_ELEMENT_STEP = NP * NP + 5 * NP + 3
-INT_PRODUCTS_PER_ELEMENT_STEP = 3 * MACS_PER_ELEMENT_STEP
+INT_PRODUCTS_PER_ELEMENT_STEP = 3 * MACS_PER_ELEMENT_STEP + 3   # + the neighbour's v1_p^{e-2}
 FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant; a kernel changed since its counters were taken has no
-# entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.05 MB read
-# + 488.87 MB written (the chunk's interior steps; the first and last read or write FP64).
-TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_025_920_256}
+# entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.06 MB read
+# + 489.28 MB written (the chunk's interior steps; the first and last read or write FP64).
+TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_026_334_976}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 GRAPH_STEPS = 32
