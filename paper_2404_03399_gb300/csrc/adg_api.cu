@@ -587,8 +587,9 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
     float ms = 0.0f;
     for (int rep = 0; rep < 3; ++rep) {
       cudaEventRecord(a, c->stream);
-      for (int k = 0; k < 2; ++k) {
-        CK(adg::launch_fused_step(T, k ? I.v2 : I.v1, k ? I.v1 : I.v2, rel, c->stream, false, fmt));
+      for (int k = 0; k < 4; ++k) {   // an even count: the fields alternate
+        CK(adg::launch_fused_step(T, (k & 1) ? I.v2 : I.v1, (k & 1) ? I.v1 : I.v2, rel, c->stream,
+                                  false, fmt));
       }
       cudaEventRecord(b, c->stream);
       CK(cudaEventSynchronize(b));
@@ -1309,6 +1310,12 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       else if (!c->batch_fixed) c->inst[i].I.fused = 1;
     }
     c->batch_fixed = c->batch_fixed && c->batch_fused;
+    for (int i = 0; i < n; ++i) {
+      hi[i] = c->inst[i].I;
+      for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));
+      if (hi[i].async)
+        for (int j0 = 0; j0 < hi[i].P; j0 += 256) fwork.push_back(make_int2(i, j0));
+    }
     // every instance of a degree with the same fixed-point coefficients: pass them per degree
     if (!r && c->batch_fixed) {
       bool uniform = true;
@@ -1320,37 +1327,35 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
         else uniform = std::memcmp(ref[d], &f, sizeof(f)) == 0;
       }
       if (uniform) {
-        std::vector<adg::BatchLite> lites(n);
-        for (int i = 0; i < n; ++i) {
-          const Inst &I = c->inst[i].I;
-          lites[i].f[0] = I.u;
-          lites[i].f[1] = I.v1;
-          lites[i].f[2] = I.v2;
-          lites[i].meta = I.meta;
-          lites[i].fx = I.fx;
-          lites[i].K = I.K;
-          lites[i].Np = I.Np;
+        // one record per work item, in the work list's order
+        std::vector<adg::BatchLite> lites(work.size());
+        for (size_t wi = 0; wi < work.size(); ++wi) {
+          const Inst &I = c->inst[work[wi].x].I;
+          adg::BatchLite &L = lites[wi];
+          L.f[0] = I.u;
+          L.f[1] = I.v1;
+          L.f[2] = I.v2;
+          L.meta = I.meta;
+          L.fx = I.fx;
+          L.K = I.K;
+          L.Np = I.Np;
+          L.e0 = work[wi].y;
+          L.pad = 0;
         }
         c->bu.reset(new (std::nothrow) adg::BatchUniform());
         if (!c->bu) {
           r = fail(c, ADG_ENOMEM, "host allocation failed");
-        } else if (cudaMalloc(&c->lites_dev, sizeof(adg::BatchLite) * n) != cudaSuccess ||
-                   cudaMemcpy(c->lites_dev, lites.data(), sizeof(adg::BatchLite) * n,
+        } else if (cudaMalloc(&c->lites_dev, sizeof(adg::BatchLite) * lites.size()) != cudaSuccess ||
+                   cudaMemcpy(c->lites_dev, lites.data(), sizeof(adg::BatchLite) * lites.size(),
                               cudaMemcpyHostToDevice) != cudaSuccess) {
           r = fail(c, ADG_ENOMEM, "cudaMalloc(batch records)");
         } else {
           std::memset(&c->bu->uf, 0, sizeof(c->bu->uf));
           for (int d = 0; d < adg::kMaxNp - 1; ++d)
             if (ref[d]) c->bu->uf.sf[d] = *ref[d];
-          c->bu->lites_dev = c->lites_dev;
+          c->bu->items_dev = c->lites_dev;
         }
       }
-    }
-    for (int i = 0; i < n; ++i) {
-      hi[i] = c->inst[i].I;
-      for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));
-      if (hi[i].async)
-        for (int j0 = 0; j0 < hi[i].P; j0 += 256) fwork.push_back(make_int2(i, j0));
     }
     c->nwork = (int)work.size();
     c->nfwork = (int)fwork.size();

@@ -249,14 +249,15 @@ struct LiteView {
 };
 
 // Batched fixed-point steps with the coefficients shared per degree (BatchUniform): block b
-// takes work item (instance, first element) and reads only the instance's BatchLite.
+// reads its work item's record (the instance's fields and the tile's first element; one load
+// ahead of the data instead of a work-list entry and then the instance).
 template <int FMT>
 __global__ void __launch_bounds__(kTile)
-    k_batch_fixed_uniform(const BatchLite *__restrict__ lites, const int2 *__restrict__ work,
-                          int src, int dst, int rel, const UniformFixed uf) {
+    k_batch_fixed_uniform(const BatchLite *__restrict__ items, int src, int dst, int rel,
+                          const UniformFixed uf) {
   __shared__ FixedShared<1> sh;
-  const int2 w = work[blockIdx.x];
-  const BatchLite L = lites[w.x];
+  const BatchLite L = items[blockIdx.x];
+  const int2 w = make_int2(0, L.e0);
   const void *uin = src == 0 ? L.f[0] : (src == 1 ? L.f[1] : L.f[2]);
   void *uout = dst == 0 ? L.f[0] : (dst == 1 ? L.f[1] : L.f[2]);
   switch (L.Np) {
@@ -325,12 +326,13 @@ cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev,
 cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_dev, int nwork,
                                        int src, int dst, int fmt, int rel, cudaStream_t s) {
   if (nwork <= 0) return cudaSuccess;
-  const BatchLite *l = bu.lites_dev;
+  (void)work_dev;
+  const BatchLite *l = bu.items_dev;
   switch (fmt & 3) {
-    case 0: k_batch_fixed_uniform<0><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
-    case 1: k_batch_fixed_uniform<1><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
-    case 2: k_batch_fixed_uniform<2><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
-    default: k_batch_fixed_uniform<3><<<nwork, kTile, 0, s>>>(l, work_dev, src, dst, rel, bu.uf); break;
+    case 0: k_batch_fixed_uniform<0><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+    case 1: k_batch_fixed_uniform<1><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+    case 2: k_batch_fixed_uniform<2><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+    default: k_batch_fixed_uniform<3><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
   }
   return cudaGetLastError();
 }

@@ -178,6 +178,7 @@ struct BatchLite {
   const int64_t *meta;
   FxSlot *fx;
   int K, Np;
+  int e0, pad;   // as a work item: the first element of the block's tile
 };
 // One fixed-point coefficient set per degree (sf[Np - 2]), for batches in which every instance
 // of a degree has the same composed coefficients (the same Courant number with a > 0 and the
@@ -188,7 +189,7 @@ struct UniformFixed {
   StepFixed sf[kMaxNp - 1];
 };
 struct BatchUniform {
-  const BatchLite *lites_dev;
+  const BatchLite *items_dev;   // one record per work item (the instance's fields and e0)
   UniformFixed uf;
 };
 
