@@ -84,8 +84,9 @@ enum {
  *               Every entry must be < L.
  *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
  *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
- *               composed into one stencil per step, with the elements next to PE faces
- *               recomputed stage by stage (needs K/P >= 8 when there are PE faces), or
+ *               composed into one stencil per step, with the delayed / AT flux at PE faces
+ *               added as a correction to the four elements around each face (needs
+ *               K/P >= 8 when there are PE faces), or
  *               ADG_VARIANT_COMPOSED_FIXED (3): the same composed step evaluated exactly in
  *               64-bit fixed-point integer arithmetic at one scale per step (from the largest
  *               magnitude in u^n; resolution 2^-55 of max|u^n| or finer). The state stays in
