@@ -403,8 +403,8 @@ def main():
 
     hbm_gbs, hbm_src, fp64_tflops, int_tops = peaks()
     ms_step = ms / args.steps
-    # one composed-step launch per step plus the PE-face fix-up launch, charged to it (the
-    # CUDA-event time of the step; ncu puts the fix-up near 10% of it)
+    # one composed-step launch per step plus the PE-face launch between steps, charged to it
+    # (the CUDA-event time of the step; ncu puts the PE-face launch near 4% of it)
     elements = K
     if variant == "fixed":
         achieved = elements * INT_PRODUCTS_PER_ELEMENT_STEP / (ms_step * 1e-3) / 1e12
@@ -413,7 +413,7 @@ def main():
                     "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fixed"),
                     "kernel": f"k_step_fixed (composed SSP-RK3 step in two-limb fixed point, "
                               f"{INT_PRODUCTS_PER_ELEMENT_STEP} 32x32->64-bit products per element, "
-                              f"{ept} element(s) per thread); the PE-face fix-up is charged to it",
+                              f"{ept} element(s) per thread); the PE-face correction launch is charged to it",
                     "peak_source": "integer unit counts x max SM clock (152 SM x 32 wide "
                                    "multiply-adds/clk x 2.07 GHz)",
                     "fp64_equivalent_tflops": ndof * FLOP_PER_DOF_STEP / (ms_step * 1e-3) / 1e12}
@@ -437,13 +437,14 @@ def main():
                        "arithmetic": ("exact two-limb fixed point at one scale per step "
                                       "(resolution 2^-55 of max|u| or finer), int64 state inside "
                                       "each 32-step chunk, FP64 at chunk ends and in the PE-face "
-                                      "fix-up") if variant == "fixed" else "FP64"},
+                                      "stage differences") if variant == "fixed" else "FP64"},
             "roofline": roofline,
             "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
                     "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
-            # per step: the composed-step kernel and the PE-face fix-up; one step-counter
-            # kernel per chunk of GRAPH_STEPS steps
-            "gpu_launches": 2 * args.steps + math.ceil(args.steps / GRAPH_STEPS),
+            # per step: the composed-step kernel and one PE-face kernel (correction of the step
+            # before, differences of the next); per chunk of GRAPH_STEPS steps one more PE-face
+            # kernel and one step-counter kernel
+            "gpu_launches": 2 * args.steps + 2 * math.ceil(args.steps / GRAPH_STEPS),
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:

@@ -296,6 +296,7 @@ struct InstHost {
   double *coef = nullptr;
   double *w = nullptr, *M = nullptr;
   adg::FxSlot *fx = nullptr; // scale slots of the fixed-point composed step
+  double *fd = nullptr;      // ... and its PE faces' stage differences [2][P][3]
   bool fixed_ok = false;     // the composed coefficients fit the fixed-point bounds
   std::vector<uint8_t> host_rows;
 };
@@ -436,6 +437,7 @@ void fold_step_constants(InstHost &h) {
   S.k[1] = (double)M1c0[p];
   S.k[2] = (double)cv[1][p];
 
+  ld Rl[3][4][adg::kMaxNp] = {};
   // PE-face correction responses: inject lL_s at element e and lR_s at element e-1 after
   // stage s, then apply the remaining stages' perturbation maps
   // dx'^m = M_t dx^m + c_t dx^{m-1}_p (t = s+1 .. 2) on elements e-1 .. e+2; rho collects
@@ -462,7 +464,10 @@ void fold_step_constants(InstHost &h) {
       d = nd;
     }
     for (int m = 0; m < 4; ++m)
-      for (int i = 0; i < Np; ++i) S.R[st][m][i] = (double)d[m * Np + i];
+      for (int i = 0; i < Np; ++i) {
+        S.R[st][m][i] = (double)d[m * Np + i];
+        Rl[st][m][i] = d[m * Np + i];
+      }
   }
 
   // Fixed-point limbs of the same coefficients (from the long double values) and the bounds
@@ -495,6 +500,13 @@ void fold_step_constants(InstHost &h) {
   F.k[2] = limbs(cv[1][p]);
   b2 += fabsl(cv[1][p]) * b1;
   h.fixed_ok = ok && b1 < 1.999L && b2 < 1.999L;
+  // the PE-face responses likewise (from the long double values), for the integer correction
+  std::memset(h.I.Rf, 0, sizeof(h.I.Rf));
+  ok = true;
+  for (int st = 0; st < 3; ++st)
+    for (int m = 0; m < 4; ++m)
+      for (int i = 0; i < Np; ++i) h.I.Rf[st][m][i] = limbs(Rl[st][m][i]);
+  h.I.face_fx = ok ? 1 : 0;
 }
 
 int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out) {
@@ -691,6 +703,10 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
         I.fused = 2;
         CK(cudaMalloc(&h.fx, 3 * sizeof(adg::FxSlot)));
         I.fx = h.fx;
+        if (I.async && !c->batch) {
+          CK(cudaMalloc(&h.fd, (size_t)2 * I.P * 3 * sizeof(double)));
+          I.fd = h.fd;
+        }
         int r2 = reset_exponent(c, h);
         if (r2) return r2;
       }
@@ -778,14 +794,24 @@ int launch_fused_steps(adg_ctx *c, int nsteps) {
   if (I.fused == 2 && nsteps >= 2) {
     // Fixed point: u (FP64) -> v1 (int64) -> v2 -> v1 ... -> u (FP64); the chunk's interior
     // steps neither read nor write FP64.
-    CK(adg::launch_fused_step(I, I.u, I.v1, 0, c->stream, true, adg::kFmtOutFixed));
+    // With PE faces, one face kernel between consecutive steps adds the earlier step's
+    // correction and forms the next step's differences.
+    const bool faces = I.async != 0;
+    if (faces && !I.fd)
+      return fail(c, ADG_EINVAL, "internal: fixed-point step with PE faces lacks its buffer");
+    if (faces) CK(adg::launch_face_step(I, I.u, 0, 0, 0, adg::kFaceDiff, c->stream));
+    CK(adg::launch_fixed_step(I, I.u, I.v1, 0, adg::kFmtOutFixed, c->stream));
     void *in = I.v1, *out = I.v2;
-    for (int rel = 1; rel < nsteps - 1; ++rel) {
-      CK(adg::launch_fused_step(I, in, out, rel, c->stream, true,
-                                adg::kFmtInFixed | adg::kFmtOutFixed));
+    for (int rel = 1; rel < nsteps; ++rel) {
+      const int fmt = rel < nsteps - 1 ? adg::kFmtInFixed | adg::kFmtOutFixed : adg::kFmtInFixed;
+      if (faces)
+        CK(adg::launch_face_step(I, in, rel, 1, rel > 1 ? 1 : 0,
+                                 adg::kFaceApply | adg::kFaceDiff, c->stream));
+      void *dst = rel < nsteps - 1 ? out : static_cast<void *>(I.u);
+      CK(adg::launch_fixed_step(I, in, dst, rel, fmt, c->stream));
       std::swap(in, out);
     }
-    CK(adg::launch_fused_step(I, in, I.u, nsteps - 1, c->stream, true, adg::kFmtInFixed));
+    if (faces) CK(adg::launch_face_step(I, I.u, nsteps, 0, 1, adg::kFaceApply, c->stream));
   } else {
     for (int rel = 0; rel < nsteps; ++rel) {
       const double *uin = (rel % 2 == 0) ? I.u : I.v1;
@@ -1220,6 +1246,7 @@ void adg_destroy(adg_ctx *c) {
     cudaFree(h.w);
     cudaFree(h.M);
     cudaFree(h.fx);
+    cudaFree(h.fd);
   }
   cudaFree(c->meta);
   cudaFree(c->insts_dev);

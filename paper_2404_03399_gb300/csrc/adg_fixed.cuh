@@ -106,6 +106,13 @@ __device__ __forceinline__ long long fx_rescale(long long X, int shift) {
   return X;
 }
 
+// x 2^e. Where 2^e is a normal FP64 number the product with it is the exactly scaled value,
+// correctly rounded, as scalbn gives it; outside that range scalbn itself.
+__device__ __forceinline__ double pow2_scale(double x, int e) {
+  if ((unsigned)(e + 1022) <= 2045u) return x * __longlong_as_double((long long)(e + 1023) << 52);
+  return scalbn(x, e);
+}
+
 __device__ __forceinline__ int biased_exponent(double x) {
   return (int)(((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ff);
 }

@@ -105,9 +105,15 @@ struct alignas(16) Inst {
                         // 2: fixed-point integer arithmetic (StepFixed)
   int ept;              // elements per thread of the composed-step kernel (1, 2 or 4, autotuned)
   FxSlot *fx;           // fused == 2: [3] scale of u^n in slot n % 3
+  double *fd;           // fused == 2 with PE faces: [2][P][3] stage differences d_s of each
+                        // face, buffer n & 1 for step n
   StageConsts sc[kStages];
   StepConsts st;
   StepFixed sf;
+  // fused == 2: the PE-face responses st.R in fixed point (limbs as in StepFixed), used when
+  // face_fx is set (every |R| < 2)
+  int2 Rf[kStages][4][kMaxNp];
+  int face_fx, pad_[3];
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
@@ -162,6 +168,13 @@ cudaError_t launch_batch_faces(const Inst *insts_dev, const int2 *work_dev, int 
                                int rel, cudaStream_t s);
 cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t by,
                            cudaStream_t s);
+// PE-face work of the fixed-point composed step (fused == 2, with PE faces) on the field u
+// between steps rel-1 and rel: mode bit 0 adds step rel-1's correction (differences in I.fd)
+// to u, bit 1 then forms step rel's differences from u and the ring (ring write, I.fd). fu: u
+// is int64, else FP64; fin_prev: step rel-1 read int64.
+constexpr int kFaceApply = 1, kFaceDiff = 2;
+cudaError_t launch_face_step(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
+                             cudaStream_t s);
 // Composed step uin -> uout (rel: step offset from meta[0]) and, with PE faces, the fix-up
 // of the elements next to each PE face with the delayed / AT flux. fmt (fixed-point step,
 // fused == 2, only): bit 0 the input, bit 1 the output is int64 fixed point (adg_fixed.cuh);

@@ -254,6 +254,87 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
   fused_body<NP, EPT>(inst, uin, uout, blockIdx.x * (kTile * EPT), sh);
 }
 
+// What the PE-face correction of face j at step n reads besides the field: its delay k and
+// order q' (delay_at), the AT coefficients, and the upwind traces of levels n-k-i (i < q')
+// for the three stages from the ring [slot][stage][P] (zero when k = 0).
+struct FaceLoads {
+  double Rv[kStages][kMaxQ];
+  double c[kMaxQ];
+  int k, qe, nm;   // nm: the ring slot of step n
+};
+
+// n mod m for n >= 0, m > 0 (a 32-bit remainder while n fits in 31 bits).
+__device__ __forceinline__ int mod_step(int64_t n, int m) {
+  return n <= 0x7fffffff ? (int)((unsigned)n % (unsigned)m) : (int)(n % m);
+}
+
+__device__ __forceinline__ void face_loads(const Inst &I, int j, int64_t n, FaceLoads &f) {
+  const DelayAt dl = delay_at(I, j, n);
+  const int P = I.P, R = I.R;
+  const int nm = mod_step(n, R);
+  f.nm = nm;
+  const double2 *col = I.ring + j;
+  f.k = dl.k;
+  f.qe = dl.qe;
+#pragma unroll
+  for (int i = 0; i < kMaxQ; ++i) {
+    int sl = nm - (dl.k + i);
+    if (sl < 0) sl += R;
+    const bool use = dl.k > 0 && i < dl.qe;
+    f.c[i] = i < dl.qe ? dl.c[i] : 0.0;
+    const double2 *lv = col + (size_t)sl * (kStages * P);
+#pragma unroll
+    for (int st = 0; st < kStages; ++st) f.Rv[st][i] = use ? lv[st * P].x : 0.0;
+  }
+}
+
+// The stage differences d_s = T_s - V_s at PE face j, step n, from elements e-3 .. e-1 of u^n
+// (U, FP64) and the face's loads, and the ring write of T_s (the PE-face correction below).
+template <int NP>
+__device__ __forceinline__ void face_diffs(const Inst &I, int j, int64_t n, const FaceLoads &f,
+                                           const double (*U)[NP], double &d0, double &d1,
+                                           double &d2) {
+  const int P = I.P;
+  const StepConsts &S = I.st;
+  const int nm = f.nm;
+  double2 *col = I.ring + j;
+  const int k = f.k, qe = f.qe;
+  double V[kStages];
+#pragma unroll
+  for (int st = 0; st < kStages; ++st) {
+    double v = __dmul_rn(f.c[0], f.Rv[st][0]);
+#pragma unroll
+    for (int i = 1; i < kMaxQ; ++i) {
+      if (i < qe) {
+        const double ci = f.c[i];
+        if (ci != 0.0) v = __dadd_rn(v, __dmul_rn(ci, f.Rv[st][i]));
+      }
+    }
+    V[st] = v;
+  }
+  // synchronous channel scalars of e-1: q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3},
+  // q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
+  double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    a1 = fma(S.r1[i], U[1][i], a1);
+    b1 = fma(S.r1[i], U[2][i], b1);
+    b2 = fma(S.r2[i], U[2][i], b2);
+  }
+  b2 = fma(S.k[2], a1, b2);
+  // with zero delay V_s = T_s (the current traces), so d_s = 0
+  const double T0 = U[2][NP - 1];
+  d0 = k > 0 ? __dsub_rn(T0, V[0]) : 0.0;
+  const double T1 = fma(S.rho[0], d0, b1);
+  d1 = k > 0 ? __dsub_rn(T1, V[1]) : 0.0;
+  const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, b2));
+  d2 = k > 0 ? __dsub_rn(T2, V[2]) : 0.0;
+  double2 *lv = col + (size_t)nm * (kStages * P);
+  lv[0] = make_double2(T0, 0.0);
+  lv[P] = make_double2(T1, 0.0);
+  lv[2 * P] = make_double2(T2, 0.0);
+}
+
 // PE-face correction of a composed step (upwind advection, a > 0; StepConsts): thread j
 // forms, for PE face j (e = j Kpe), the synchronous right traces of element e-1's stage
 // inputs (p, q1 = v1_p, q2 = v2_p, from elements e-3 .. e-1 with the composed step's
@@ -271,12 +352,10 @@ template <int NP>
 __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__restrict__ uin,
                                            void *__restrict__ uout, int rel, int fmt) {
   const int K = I.K;
-  const int P = I.P;
   const int e = j * I.Kpe;
   const int64_t n = I.meta[0] + rel;
   const bool fin = (fmt & kFmtInFixed) != 0, fout = (fmt & kFmtOutFixed) != 0;
   const StepConsts &S = I.st;
-  const DelayAt dl = delay_at(I, j, n);
   FxScale sc{0, 0, 0, false};
   int sig_in = 0;
   if (I.fused == 2) {
@@ -301,7 +380,7 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       const long long *q = static_cast<const long long *>(uin) + m;
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        U[w][i] = scalbn((double)*q, sig_in);
+        U[w][i] = pow2_scale((double)*q, sig_in);
         q += K;
       }
     } else {
@@ -330,65 +409,50 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       }
     }
   }
-  // upwind traces of levels n-k-i (i < q') for the three stages: ring [slot][stage][P]
-  const int R = I.R;
-  const int nm = (int)(n % R);
-  double2 *col = I.ring + j;
-  double Rv[kStages][kMaxQ];
-  const int k = dl.k, qe = dl.qe;
-#pragma unroll
-  for (int i = 0; i < kMaxQ; ++i) {
-    int sl = nm - (k + i);
-    if (sl < 0) sl += R;
-#pragma unroll
-    for (int st = 0; st < kStages; ++st)
-      Rv[st][i] = (k > 0 && i < qe) ? col[((size_t)sl * kStages + st) * P].x : 0.0;
-  }
-  double V[kStages];
-#pragma unroll
-  for (int st = 0; st < kStages; ++st) {
-    double v = __dmul_rn(dl.c[0], Rv[st][0]);
-#pragma unroll
-    for (int i = 1; i < kMaxQ; ++i) {
-      if (i < qe) {
-        const double ci = dl.c[i];
-        if (ci != 0.0) v = __dadd_rn(v, __dmul_rn(ci, Rv[st][i]));
-      }
-    }
-    V[st] = v;
-  }
-  // synchronous channel scalars of e-1: q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3},
-  // q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
-  double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    a1 = fma(S.r1[i], U[1][i], a1);
-    b1 = fma(S.r1[i], U[2][i], b1);
-    b2 = fma(S.r2[i], U[2][i], b2);
-  }
-  b2 = fma(S.k[2], a1, b2);
-  // with zero delay V_s = T_s (the current traces), so d_s = 0
-  const double T0 = U[2][NP - 1];
-  const double d0 = k > 0 ? __dsub_rn(T0, V[0]) : 0.0;
-  const double T1 = fma(S.rho[0], d0, b1);
-  const double d1 = k > 0 ? __dsub_rn(T1, V[1]) : 0.0;
-  const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, b2));
-  const double d2 = k > 0 ? __dsub_rn(T2, V[2]) : 0.0;
-  col[((size_t)nm * kStages + 0) * P] = make_double2(T0, 0.0);
-  col[((size_t)nm * kStages + 1) * P] = make_double2(T1, 0.0);
-  col[((size_t)nm * kStages + 2) * P] = make_double2(T2, 0.0);
+  FaceLoads fl;
+  face_loads(I, j, n, fl);
+  double d0, d1, d2;
+  face_diffs<NP>(I, j, n, fl, U, d0, d1, d2);
   // with a NaN or infinity in u^n the fixed-point step has already written NaN (or carries
   // the mark); nothing is added
   if (!(nonzero(d0) || nonzero(d1) || nonzero(d2)) || sc.bad) return;
   int emax = 0;
   unsigned long long mag = 0;
+  if (fout && I.face_fx) {
+    // the fixed-point step's int64 output: the integer correction of k_face_step
+    const double sf = pow2_scale(1.0, -sc.sigma);
+    const long long D0 = llrint(d0 * sf), D1 = llrint(d1 * sf), D2 = llrint(d2 * sf);
+    const long long lim = 1ll << 57;
+    if (D0 > -lim && D0 < lim && D1 > -lim && D1 < lim && D2 > -lim && D2 < lim) {
+      int h0, l0, h1, l1, h2, l2;
+      fx_split(D0, h0, l0);
+      fx_split(D1, h1, l1);
+      fx_split(D2, h2, l2);
+      for (int w = 0; w < 4; ++w) {
+        long long *q = static_cast<long long *>(uout) + mw[w];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          FxAcc acc;
+          fx_mac(acc, I.Rf[0][w][i], h0, l0);
+          fx_mac(acc, I.Rf[1][w][i], h1, l1);
+          fx_mac(acc, I.Rf[2][w][i], h2, l2);
+          const long long X = Xq[w][i] + fx_round(acc);
+          *q = X;
+          q += K;
+          mag |= fx_mag(X);
+        }
+      }
+      or_slot(&I.fx[fx_next(sc.slot)].mag, mag);
+      return;
+    }
+  }
   for (int w = 0; w < 4; ++w) {   // elements e-1 .. e+2
     if (fout) {
       long long *q = static_cast<long long *>(uout) + mw[w];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
         const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
-        const long long X = Xq[w][i] + llrint(scalbn(c, -sc.sigma));
+        const long long X = Xq[w][i] + llrint(pow2_scale(c, -sc.sigma));
         *q = X;
         q += K;
         mag |= fx_mag(X);
@@ -411,6 +475,130 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
     FxSlot &nx = I.fx[fx_next(sc.slot)];
     if (fout) or_slot(&nx.mag, mag);
     else raise_slot(&nx.E, emax);
+  }
+}
+
+// PE-face work of the fixed-point step between two steps, on the field u that is the output
+// of step n-1 and the input of step n (n = meta[0] + rel), for PE face j (e = j Kpe). A block
+// of 128 threads takes 32 faces, warp w element e-1+w of their correction windows (so the
+// FP64 work of the differences runs in full warps):
+//   kFaceApply: adds step n-1's correction sum_s R_s[w] d_s (its differences in I.fd, buffer
+//               (n-1) & 1) to element e-1+w of u at step n-1's working scale, with the scale
+//               bookkeeping of the values written (slot n % 3);
+//   kFaceDiff:  warp 0 then forms step n's differences d_s from elements e-3 .. e-1 of u
+//               (e-1 as corrected) and the ring (face_diffs), writes the ring slot of step n
+//               and I.fd buffer n & 1.
+// fu: u is int64 (at the scale of slot n % 3), else FP64; fin_prev: step n-1 read int64. Every
+// load is issued before any value is used; the windows of different faces are disjoint when
+// Kpe >= 8.
+template <int NP>
+__global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restrict__ u, int rel,
+                                                   int fu, int fin_prev, int mode) {
+  const int j = blockIdx.x * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
+  if (j >= I.P) return;
+  const int K = I.K, P = I.P;
+  const int e = j * I.Kpe;
+  const int64_t n = I.meta[0] + rel;
+  const bool diff = (mode & kFaceDiff) && w == 0;
+  long long *uq = static_cast<long long *>(u);
+  int m = e - 1 + w;   // this thread's element; warp 0 also reads e-3 and e-2
+  if (m < 0) m += K;
+  if (m >= K) m -= K;
+  long long V[3][NP];   // raw 64-bit values (int64, or the bits of FP64): e-3, e-2, own
+  {
+    const long long *q = uq + m;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      V[2][i] = *q;
+      q += K;
+    }
+  }
+  if (diff) {
+#pragma unroll
+    for (int b = 0; b < 2; ++b) {
+      int mb = e - 3 + b;
+      if (mb < 0) mb += K;
+      const long long *q = uq + mb;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        V[b][i] = *q;
+        q += K;
+      }
+    }
+  }
+  FaceLoads fl;
+  if (diff) face_loads(I, j, n, fl);
+  if (mode & kFaceApply) {
+    const double *dd = I.fd + (size_t)((n - 1) & 1) * 3 * P + 3 * (size_t)j;
+    const double d0 = dd[0], d1 = dd[1], d2 = dd[2];
+    const FxScale sc = fx_scale(I.fx, n - 1, fin_prev != 0);
+    if ((nonzero(d0) || nonzero(d1) || nonzero(d2)) && !sc.bad) {
+      bool done = false;
+      if (fu && I.face_fx) {
+        // D_s = round(d_s 2^-sigma) and sum_s R_s D_s in the step's two-limb arithmetic
+        const double sf = pow2_scale(1.0, -sc.sigma);
+        const long long D0 = llrint(d0 * sf), D1 = llrint(d1 * sf), D2 = llrint(d2 * sf);
+        const long long lim = 1ll << 57;
+        if (D0 > -lim && D0 < lim && D1 > -lim && D1 < lim && D2 > -lim && D2 < lim) {
+          int h0, l0, h1, l1, h2, l2;
+          fx_split(D0, h0, l0);
+          fx_split(D1, h1, l1);
+          fx_split(D2, h2, l2);
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            FxAcc acc;
+            fx_mac(acc, I.Rf[0][w][i], h0, l0);
+            fx_mac(acc, I.Rf[1][w][i], h1, l1);
+            fx_mac(acc, I.Rf[2][w][i], h2, l2);
+            V[2][i] += fx_round(acc);
+          }
+          done = true;
+        }
+      }
+      if (!done) {
+        // FP64: an FP64 output, or a difference beyond the integer range
+        const StepConsts &S = I.st;
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
+          if (fu) V[2][i] += llrint(pow2_scale(c, -sc.sigma));
+          else V[2][i] = __double_as_longlong(__dadd_rn(__longlong_as_double(V[2][i]), c));
+        }
+      }
+      int emax = 0;
+      unsigned long long mag = 0;
+      long long *q = uq + m;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        const long long X = V[2][i];
+        *q = X;
+        q += K;
+        if (fu) {
+          mag |= fx_mag(X);
+        } else {
+          const int be = biased_exponent(__longlong_as_double(X));
+          emax = be > emax ? be : emax;
+        }
+      }
+      FxSlot &nx = I.fx[fx_next(sc.slot)];
+      if (fu) or_slot(&nx.mag, mag);
+      else raise_slot(&nx.E, emax);
+    }
+  }
+  if (diff) {
+    const int sig = fu ? I.fx[(int)(n % 3)].sigma : 0;
+    double U[3][NP];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+        U[b][i] = fu ? pow2_scale((double)V[b][i], sig) : __longlong_as_double(V[b][i]);
+    double d0, d1, d2;
+    face_diffs<NP>(I, j, n, fl, U, d0, d1, d2);
+    double *o = I.fd + (size_t)(n & 1) * 3 * P + 3 * (size_t)j;
+    o[0] = d0;
+    o[1] = d1;
+    o[2] = d2;
   }
 }
 
@@ -764,8 +952,29 @@ cudaError_t fused_np(const Inst &I, const void *uin, void *uout, int rel, cudaSt
 }
 }  // namespace
 
+cudaError_t launch_face_step(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
+                             cudaStream_t s) {
+  const unsigned g = (unsigned)((I.P + 31) / 32);   // 32 faces per block of four warps
+  switch (I.Np) {
+    case 2: k_face_step<2><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+    case 3: k_face_step<3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+    case 4: k_face_step<4><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+    case 5: k_face_step<5><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int rel,
                               cudaStream_t s, bool with_fixup, int fmt) {
+  if (I.fused == 2 && I.async && with_fixup && I.fd) {
+    // fixed point with PE faces: the step's differences, the step, its correction
+    const int fin = (fmt & kFmtInFixed) ? 1 : 0, fout = (fmt & kFmtOutFixed) ? 1 : 0;
+    cudaError_t e = launch_face_step(I, const_cast<void *>(uin), rel, fin, 0, kFaceDiff, s);
+    if (e != cudaSuccess) return e;
+    if ((e = launch_fixed_step(I, uin, uout, rel, fmt, s)) != cudaSuccess) return e;
+    return launch_face_step(I, uout, rel + 1, fout, fin, kFaceApply, s);
+  }
   switch (I.Np) {
     case 2: return fused_np<2>(I, uin, uout, rel, s, with_fixup, fmt);
     case 3: return fused_np<3>(I, uin, uout, rel, s, with_fixup, fmt);
