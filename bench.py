@@ -58,7 +58,8 @@ FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant; a kernel changed since its counters were taken has no
 # entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.06 MB read
-# + 489.28 MB written (the chunk's interior steps; the first and last read or write FP64).
+# + 489.28 MB written (the interior steps of an adg_step call; its first step reads FP64 and
+# its last writes FP64).
 TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_026_334_976}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
@@ -436,15 +437,15 @@ def main():
                        "graph_steps": GRAPH_STEPS, "variant": variant,
                        "arithmetic": ("exact two-limb fixed point at one scale per step "
                                       "(resolution 2^-55 of max|u| or finer), int64 state inside "
-                                      "each 32-step chunk, FP64 at chunk ends and in the PE-face "
+                                      "each adg_step call, FP64 at its first input, its last output and in the PE-face "
                                       "stage differences") if variant == "fixed" else "FP64"},
             "roofline": roofline,
             "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
                     "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
             # per step: the composed-step kernel and one PE-face kernel (correction of the step
-            # before, differences of the next); per chunk of GRAPH_STEPS steps one more PE-face
-            # kernel and one step-counter kernel
-            "gpu_launches": 2 * args.steps + 2 * math.ceil(args.steps / GRAPH_STEPS),
+            # before, differences of the next); per chunk of GRAPH_STEPS steps one step-counter
+            # kernel, and per call one more PE-face kernel
+            "gpu_launches": 2 * args.steps + 1 + math.ceil(args.steps / GRAPH_STEPS),
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:

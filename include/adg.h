@@ -90,8 +90,8 @@ enum {
  *               ADG_VARIANT_COMPOSED_FIXED (3): the same composed step evaluated exactly in
  *               64-bit fixed-point integer arithmetic at one scale per step (from the largest
  *               magnitude in u^n; resolution 2^-55 of max|u^n| or finer). The state stays in
- *               fixed point between the steps of one adg_step call (in chunks of 32 steps) and
- *               is rounded to FP64 at the end of each chunk, so splitting a run into different
+ *               fixed point from the first to the last step of one adg_step call and is
+ *               rounded to FP64 at the end of the call, so splitting a run into different
  *               adg_step calls changes results at the rounding level. It needs every composed
  *               coefficient below 2 in magnitude (small Courant numbers; ADG_EINVAL
  *               otherwise). Results below 2^-1022 are flushed to zero, and a NaN or infinity

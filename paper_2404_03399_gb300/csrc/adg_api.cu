@@ -320,7 +320,7 @@ struct adg_ctx {
   std::unique_ptr<adg::BatchUniform> bu;   // shared coefficients per degree, when they are
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
-  cudaGraphExec_t gexec = nullptr;
+  cudaGraphExec_t gexec[4] = {};   // one graph of G steps per chunk kind (kChunk*)
   int G = 32;
   int64_t n = 0;
 };
@@ -593,22 +593,20 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   CK(cudaEventCreate(&b));
   float best = 1e30f;
   int best_ept = 1;
+  // Per choice one untimed launch, then two timed ones (the choices differ by about 10% on
+  // large meshes, far above the event resolution; the autotuner runs inside adg_init, so it is
+  // kept short).
   for (int ept = 1; ept <= (fixed ? 2 : 4); ept *= 2) {
     Inst T = I;
     T.ept = ept;
+    CK(adg::launch_fused_step(T, I.v1, I.v2, rel, c->stream, false, fmt));
+    cudaEventRecord(a, c->stream);
+    for (int k = 0; k < 2; ++k)
+      CK(adg::launch_fused_step(T, k ? I.v1 : I.v2, k ? I.v2 : I.v1, rel, c->stream, false, fmt));
+    cudaEventRecord(b, c->stream);
+    CK(cudaEventSynchronize(b));
     float ms = 0.0f;
-    for (int rep = 0; rep < 3; ++rep) {
-      cudaEventRecord(a, c->stream);
-      for (int k = 0; k < 4; ++k) {   // an even count: the fields alternate
-        CK(adg::launch_fused_step(T, (k & 1) ? I.v2 : I.v1, (k & 1) ? I.v1 : I.v2, rel, c->stream,
-                                  false, fmt));
-      }
-      cudaEventRecord(b, c->stream);
-      CK(cudaEventSynchronize(b));
-      float t = 0.0f;
-      cudaEventElapsedTime(&t, a, b);
-      if (rep > 0) ms += t;   // the first repetition warms up
-    }
+    cudaEventElapsedTime(&ms, a, b);
     if (ms < best) {
       best = ms;
       best_ept = ept;
@@ -743,24 +741,32 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   return ADG_OK;
 }
 
-int launch_fused_steps(adg_ctx *c, int nsteps);
+// Chunks of one adg_step call. The fixed-point step (single instance or batch) keeps the
+// field in int64 from the call's first step to its last: a chunk that is not the call's first
+// reads the int64 state from v2, one that is not its last leaves it there (its step count is
+// even: G). Every other path ignores the kind (each chunk reads and writes u).
+constexpr int kChunkFirst = 1, kChunkLast = 2, kChunkWhole = kChunkFirst | kChunkLast;
 
-int launch_steps(adg_ctx *c, int nsteps) {
-  if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps);
-  if (c->batch && c->batch_fixed && nsteps >= 2) {
-    // as launch_fused_steps: u (FP64) -> v1 (int64) -> v2 -> v1 ... -> u (FP64)
-    const int io = adg::kFmtInFixed | adg::kFmtOutFixed;
-    CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                    0, 1, adg::kFmtOutFixed, true, 0, c->stream, c->bu.get()));
-    int in = 1;
-    for (int rel = 1; rel < nsteps - 1; ++rel) {
+int launch_fused_steps(adg_ctx *c, int nsteps, int kind);
+
+int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
+  if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps, kind);
+  const bool first = (kind & kChunkFirst) != 0, last = (kind & kChunkLast) != 0;
+  if (c->batch && c->batch_fixed && (nsteps >= 2 || !first)) {
+    // as launch_fused_steps: fields 0 (u, FP64), 1 and 2 (v1, v2, int64); each step carries
+    // its own PE-face correction
+    if (!last && nsteps % 2)
+      return fail(c, ADG_EINVAL, "internal: a chunk that carries int64 state needs an even count");
+    int in = first ? 0 : 2;
+    for (int rel = 0; rel < nsteps; ++rel) {
+      const bool fin = rel > 0 || !first;
+      const bool to_u = last && rel == nsteps - 1;
+      const int out = to_u ? 0 : !last ? (((nsteps - 1 - rel) % 2 == 0) ? 2 : 1) : (in == 1 ? 2 : 1);
+      const int fmt = (fin ? adg::kFmtInFixed : 0) | (to_u ? 0 : adg::kFmtOutFixed);
       CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                      in, 3 - in, io, true, rel, c->stream, c->bu.get()));
-      in = 3 - in;
+                                      in, out, fmt, true, rel, c->stream, c->bu.get()));
+      in = out;
     }
-    CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
-                                    in, 0, adg::kFmtInFixed, true, nsteps - 1, c->stream,
-                                    c->bu.get()));
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
   }
@@ -788,30 +794,45 @@ int launch_steps(adg_ctx *c, int nsteps) {
   return ADG_OK;
 }
 
-// Composed steps ping-pong between u and v1; an odd count ends with a copy back into u.
-int launch_fused_steps(adg_ctx *c, int nsteps) {
+// Composed steps. FP64: they ping-pong between u and v1; an odd count ends with a copy back
+// into u. Fixed point: the chunk reads u (FP64, first chunk of a call) or the int64 state in
+// v2, alternates v1 and v2, and writes u (FP64, last chunk) or leaves the int64 state in v2.
+int launch_fused_steps(adg_ctx *c, int nsteps, int kind) {
   const Inst &I = c->inst[0].I;
-  if (I.fused == 2 && nsteps >= 2) {
-    // Fixed point: u (FP64) -> v1 (int64) -> v2 -> v1 ... -> u (FP64); the chunk's interior
-    // steps neither read nor write FP64.
+  const bool first = (kind & kChunkFirst) != 0, last = (kind & kChunkLast) != 0;
+  if (I.fused == 2 && (nsteps >= 2 || !first)) {
+    if (!last && nsteps % 2)
+      return fail(c, ADG_EINVAL, "internal: a chunk that carries int64 state needs an even count");
     // With PE faces, one face kernel between consecutive steps adds the earlier step's
-    // correction and forms the next step's differences.
+    // correction and forms the next step's differences; the one before a chunk's first step
+    // also corrects the previous chunk's last step, the one after the call's last step only
+    // corrects.
     const bool faces = I.async != 0;
     if (faces && !I.fd)
       return fail(c, ADG_EINVAL, "internal: fixed-point step with PE faces lacks its buffer");
-    if (faces) CK(adg::launch_face_step(I, I.u, 0, 0, 0, adg::kFaceDiff, c->stream));
-    CK(adg::launch_fixed_step(I, I.u, I.v1, 0, adg::kFmtOutFixed, c->stream));
-    void *in = I.v1, *out = I.v2;
-    for (int rel = 1; rel < nsteps; ++rel) {
-      const int fmt = rel < nsteps - 1 ? adg::kFmtInFixed | adg::kFmtOutFixed : adg::kFmtInFixed;
-      if (faces)
-        CK(adg::launch_face_step(I, in, rel, 1, rel > 1 ? 1 : 0,
-                                 adg::kFaceApply | adg::kFaceDiff, c->stream));
-      void *dst = rel < nsteps - 1 ? out : static_cast<void *>(I.u);
-      CK(adg::launch_fixed_step(I, in, dst, rel, fmt, c->stream));
-      std::swap(in, out);
+    void *in = first ? static_cast<void *>(I.u) : static_cast<void *>(I.v2);
+    int fin_prev = 1;   // the previous step's input format (int64 but after an FP64 first step)
+    for (int rel = 0; rel < nsteps; ++rel) {
+      const bool fin = rel > 0 || !first;
+      const bool to_u = last && rel == nsteps - 1;
+      void *out;
+      if (to_u) out = I.u;
+      else if (!last) out = ((nsteps - 1 - rel) % 2 == 0) ? I.v2 : I.v1;   // ends in v2
+      else out = (in == I.v1) ? I.v2 : I.v1;
+      const int fmt = (fin ? adg::kFmtInFixed : 0) | (to_u ? 0 : adg::kFmtOutFixed);
+      if (faces) {
+        if (rel == 0 && first)
+          CK(adg::launch_face_step(I, in, 0, 0, 0, adg::kFaceDiff, c->stream));
+        else
+          CK(adg::launch_face_step(I, in, rel, 1, fin_prev, adg::kFaceApply | adg::kFaceDiff,
+                                   c->stream));
+      }
+      CK(adg::launch_fixed_step(I, in, out, rel, fmt, c->stream));
+      fin_prev = fin ? 1 : 0;
+      in = out;
     }
-    if (faces) CK(adg::launch_face_step(I, I.u, nsteps, 0, 1, adg::kFaceApply, c->stream));
+    if (faces && last)
+      CK(adg::launch_face_step(I, I.u, nsteps, 0, fin_prev, adg::kFaceApply, c->stream));
   } else {
     for (int rel = 0; rel < nsteps; ++rel) {
       const double *uin = (rel % 2 == 0) ? I.u : I.v1;
@@ -826,7 +847,7 @@ int launch_fused_steps(adg_ctx *c, int nsteps) {
   return ADG_OK;
 }
 
-int build_graph(adg_ctx *c) {
+int build_graph(adg_ctx *c, int kind) {
   cudaStream_t user = c->stream;
   c->stream = c->cap;
   cudaGraph_t g = nullptr;
@@ -835,7 +856,7 @@ int build_graph(adg_ctx *c) {
     c->stream = user;
     return fail(c, ADG_ECUDA, std::string("cudaStreamBeginCapture: ") + cudaGetErrorString(e));
   }
-  int r = launch_steps(c, c->G);
+  int r = launch_steps(c, c->G, kind);
   cudaError_t e2 = cudaStreamEndCapture(c->cap, &g);
   c->stream = user;
   if (r) {
@@ -843,10 +864,10 @@ int build_graph(adg_ctx *c) {
     return r;
   }
   if (e2 != cudaSuccess) return fail(c, ADG_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(e2));
-  e = cudaGraphInstantiate(&c->gexec, g, 0);
+  e = cudaGraphInstantiate(&c->gexec[kind], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    c->gexec = nullptr;
+    c->gexec[kind] = nullptr;
     return fail(c, ADG_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(e));
   }
   return ADG_OK;
@@ -1237,7 +1258,8 @@ const char *adg_last_error(const adg_ctx *c) {
 void adg_destroy(adg_ctx *c) {
   if (!c) return;
   cudaStreamSynchronize(c->stream);
-  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (auto &ge : c->gexec)
+    if (ge) cudaGraphExecDestroy(ge);
   for (auto &h : c->inst) {
     cudaFree(h.fields);
     cudaFree(h.ring);
@@ -1408,21 +1430,25 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
 int adg_step(adg_ctx *c, int64_t nsteps) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(c, ADG_EINVAL, "nsteps must be >= 0");
+  // int64 state carried from chunk to chunk inside the call (single fixed-point instance)
+  const bool carry = c->batch ? c->batch_fixed : c->inst[0].I.fused == 2;
   int64_t left = nsteps;
   while (left > 0) {
     const int chunk = (int)std::min<int64_t>(left, c->G);
+    const int kind = !carry ? kChunkWhole
+                            : (left == nsteps ? kChunkFirst : 0) | (left == chunk ? kChunkLast : 0);
     for (auto &h : c->inst) {
       int r = ensure_table(c, h, c->n, chunk);
       if (r) return r;
     }
     if (chunk == c->G) {
-      if (!c->gexec) {
-        int r = build_graph(c);
+      if (!c->gexec[kind]) {
+        int r = build_graph(c, kind);
         if (r) return r;
       }
-      CK(cudaGraphLaunch(c->gexec, c->stream));
+      CK(cudaGraphLaunch(c->gexec[kind], c->stream));
     } else {
-      int r = launch_steps(c, chunk);
+      int r = launch_steps(c, chunk, kind);
       if (r) return r;
     }
     c->n += chunk;

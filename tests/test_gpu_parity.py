@@ -291,14 +291,15 @@ def test_fixed_point_rejects_large_coefficients():
 
 
 def test_fixed_point_step_splitting():
-    # The integer step keeps the field in int64 inside each adg_step call (graph chunks of
-    # 32 steps) and rounds it to FP64 at the end of a call or chunk; single-step calls round
-    # every step. Both stay on the oracle, and within rounding of each other.
+    # The integer step keeps the field in int64 from the first to the last step of each
+    # adg_step call (across its 32-step graph chunks: first, middle and a ragged last chunk)
+    # and rounds it to FP64 at the end of the call; single-step calls round every step. All
+    # stay on the oracle, and within rounding of each other.
     cfg = adg.Config(pde="advection", K=512, p=3, P=16, cfl=0.005, mode="at", L=4, q=3, seed=12,
                      variant="fixed")
     u0 = dg.modes_initial(PAPER_FIG6, 512, 3)
     outs = []
-    for calls in ([96], [1] * 96, [1, 2, 33, 60]):
+    for calls in ([96], [1] * 96, [1, 2, 33, 60], [70, 26]):
         s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
         for k in calls:
             s.step(k)
