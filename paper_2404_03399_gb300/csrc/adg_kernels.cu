@@ -288,15 +288,79 @@ __device__ __forceinline__ void face_loads(const Inst &I, int j, int64_t n, Face
   }
 }
 
-// The stage differences d_s = T_s - V_s at PE face j, step n, from elements e-3 .. e-1 of u^n
-// (U, FP64) and the face's loads, and the ring write of T_s (the PE-face correction below).
+// The synchronous traces of element e-1's stage inputs at a PE face (e the face's element):
+// T0 = p^{e-1}, the right trace of u^{e-1}, and the channel scalars
+// b1 = q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, b2 = q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
+// with q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3}, from elements e-3 .. e-1 (w = 0 .. 2).
+struct FaceTraces {
+  double T0, b1, b2;
+};
+
+// From FP64 values.
 template <int NP>
-__device__ __forceinline__ void face_diffs(const Inst &I, int j, int64_t n, const FaceLoads &f,
-                                           const double (*U)[NP], double &d0, double &d1,
+__device__ __forceinline__ FaceTraces face_traces(const Inst &I, const double (*U)[NP]) {
+  const StepConsts &S = I.st;
+  double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    a1 = fma(S.r1[i], U[1][i], a1);
+    b1 = fma(S.r1[i], U[2][i], b1);
+    b2 = fma(S.r2[i], U[2][i], b2);
+  }
+  FaceTraces t;
+  t.T0 = U[2][NP - 1];
+  t.b1 = b1;
+  t.b2 = fma(S.k[2], a1, b2);
+  return t;
+}
+
+// From int64 values X at scale 2^sig: the same sums in the composed step's two-limb integer
+// arithmetic (StepFixed coefficients) at a scale chosen from these three elements alone
+// (|X'| < 2^56, so the result does not depend on any other face), then rounded to FP64. Off
+// the FP64 pipe but for four conversions.
+template <int NP>
+__device__ __forceinline__ FaceTraces face_traces_fixed(const Inst &I, const long long (*X)[NP],
+                                                        int sig) {
+  const StepFixed &F = I.sf;
+  unsigned long long m = 0;
+#pragma unroll
+  for (int w = 0; w < 3; ++w)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) m |= fx_mag(X[w][i]);
+  const int L = m ? 64 - __clzll((long long)m) : 0;   // |X| < 2^(L+1)
+  const int sh = L > 55 ? L - 55 : 0;
+  int xh[3][NP], xl[3][NP];
+#pragma unroll
+  for (int w = 0; w < 3; ++w)
+#pragma unroll
+    for (int i = 0; i < NP; ++i) fx_split(fx_rescale(X[w][i], sh), xh[w][i], xl[w][i]);
+  FxAcc A1, B1, B2;
+  fx_mac(A1, F.k[0], xh[0][NP - 1], xl[0][NP - 1]);
+  fx_mac(B1, F.k[0], xh[1][NP - 1], xl[1][NP - 1]);
+  fx_mac(B2, F.k[1], xh[1][NP - 1], xl[1][NP - 1]);
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    fx_mac(A1, F.r1[i], xh[1][i], xl[1][i]);
+    fx_mac(B1, F.r1[i], xh[2][i], xl[2][i]);
+    fx_mac(B2, F.r2[i], xh[2][i], xl[2][i]);
+  }
+  int ah, al;
+  fx_split(fx_round(A1), ah, al);
+  fx_mac(B2, F.k[2], ah, al);
+  FaceTraces t;
+  t.T0 = pow2_scale((double)X[2][NP - 1], sig);
+  t.b1 = pow2_scale((double)fx_round(B1), sig + sh);
+  t.b2 = pow2_scale((double)fx_round(B2), sig + sh);
+  return t;
+}
+
+// The stage differences d_s = T_s - V_s at PE face j, step n, from the synchronous traces and
+// the face's loads, and the ring write of T_s (the PE-face correction below).
+__device__ __forceinline__ void face_diffs(const Inst &I, int j, const FaceLoads &f,
+                                           const FaceTraces &tr, double &d0, double &d1,
                                            double &d2) {
   const int P = I.P;
   const StepConsts &S = I.st;
-  const int nm = f.nm;
   double2 *col = I.ring + j;
   const int k = f.k, qe = f.qe;
   double V[kStages];
@@ -312,24 +376,15 @@ __device__ __forceinline__ void face_diffs(const Inst &I, int j, int64_t n, cons
     }
     V[st] = v;
   }
-  // synchronous channel scalars of e-1: q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3},
-  // q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
-  double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    a1 = fma(S.r1[i], U[1][i], a1);
-    b1 = fma(S.r1[i], U[2][i], b1);
-    b2 = fma(S.r2[i], U[2][i], b2);
-  }
-  b2 = fma(S.k[2], a1, b2);
-  // with zero delay V_s = T_s (the current traces), so d_s = 0
-  const double T0 = U[2][NP - 1];
+  // T_s: the traces plus the responses to the earlier stages' corrections; with zero delay
+  // V_s = T_s (the current traces), so d_s = 0
+  const double T0 = tr.T0;
   d0 = k > 0 ? __dsub_rn(T0, V[0]) : 0.0;
-  const double T1 = fma(S.rho[0], d0, b1);
+  const double T1 = fma(S.rho[0], d0, tr.b1);
   d1 = k > 0 ? __dsub_rn(T1, V[1]) : 0.0;
-  const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, b2));
+  const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, tr.b2));
   d2 = k > 0 ? __dsub_rn(T2, V[2]) : 0.0;
-  double2 *lv = col + (size_t)nm * (kStages * P);
+  double2 *lv = col + (size_t)f.nm * (kStages * P);
   lv[0] = make_double2(T0, 0.0);
   lv[P] = make_double2(T1, 0.0);
   lv[2 * P] = make_double2(T2, 0.0);
@@ -370,26 +425,17 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
     if (m >= K) m -= K;
     mw[w] = m;
   }
-  double U[3][NP];
+  long long Xr[3][NP];   // raw 64-bit values of e-3 .. e-1: int64, or the bits of FP64
   long long Xq[4][NP];
   double Yd[4][NP];
   for (int w = 0; w < 3; ++w) {
     int m = e - 3 + w;
     if (m < 0) m += K;
-    if (fin) {
-      const long long *q = static_cast<const long long *>(uin) + m;
+    const long long *q = static_cast<const long long *>(uin) + m;
 #pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        U[w][i] = pow2_scale((double)*q, sig_in);
-        q += K;
-      }
-    } else {
-      const double *q = static_cast<const double *>(uin) + m;
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        U[w][i] = *q;
-        q += K;
-      }
+    for (int i = 0; i < NP; ++i) {
+      Xr[w][i] = *q;
+      q += K;
     }
   }
   for (int w = 0; w < 4; ++w) {
@@ -411,8 +457,19 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
   }
   FaceLoads fl;
   face_loads(I, j, n, fl);
+  FaceTraces tr;
+  if (fin) {
+    tr = face_traces_fixed<NP>(I, Xr, sig_in);
+  } else {
+    double U[3][NP];
+#pragma unroll
+    for (int w = 0; w < 3; ++w)
+#pragma unroll
+      for (int i = 0; i < NP; ++i) U[w][i] = __longlong_as_double(Xr[w][i]);
+    tr = face_traces<NP>(I, U);
+  }
   double d0, d1, d2;
-  face_diffs<NP>(I, j, n, fl, U, d0, d1, d2);
+  face_diffs(I, j, fl, tr, d0, d1, d2);
   // with a NaN or infinity in u^n the fixed-point step has already written NaN (or carries
   // the mark); nothing is added
   if (!(nonzero(d0) || nonzero(d1) || nonzero(d2)) || sc.bad) return;
@@ -586,15 +643,19 @@ __global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restric
     }
   }
   if (diff) {
-    const int sig = fu ? I.fx[(int)(n % 3)].sigma : 0;
-    double U[3][NP];
+    FaceTraces tr;
+    if (fu) {
+      tr = face_traces_fixed<NP>(I, V, I.fx[(int)(n % 3)].sigma);
+    } else {
+      double U[3][NP];
 #pragma unroll
-    for (int b = 0; b < 3; ++b)
+      for (int b = 0; b < 3; ++b)
 #pragma unroll
-      for (int i = 0; i < NP; ++i)
-        U[b][i] = fu ? pow2_scale((double)V[b][i], sig) : __longlong_as_double(V[b][i]);
+        for (int i = 0; i < NP; ++i) U[b][i] = __longlong_as_double(V[b][i]);
+      tr = face_traces<NP>(I, U);
+    }
     double d0, d1, d2;
-    face_diffs<NP>(I, j, n, fl, U, d0, d1, d2);
+    face_diffs(I, j, fl, tr, d0, d1, d2);
     double *o = I.fd + (size_t)(n & 1) * 3 * P + 3 * (size_t)j;
     o[0] = d0;
     o[1] = d1;
