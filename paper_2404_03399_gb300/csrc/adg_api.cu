@@ -1376,20 +1376,24 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
         else uniform = std::memcmp(ref[d], &f, sizeof(f)) == 0;
       }
       if (uniform) {
-        // one record per work item, in the work list's order
-        std::vector<adg::BatchLite> lites(work.size());
-        for (size_t wi = 0; wi < work.size(); ++wi) {
-          const Inst &I = c->inst[work[wi].x].I;
-          adg::BatchLite &L = lites[wi];
-          L.f[0] = I.u;
-          L.f[1] = I.v1;
-          L.f[2] = I.v2;
-          L.meta = I.meta;
-          L.fx = I.fx;
-          L.K = I.K;
-          L.Np = I.Np;
-          L.e0 = work[wi].y;
-          L.pad = 0;
+        // one record per work item of two tiles (two elements per thread)
+        const int ept = 2;
+        std::vector<adg::BatchLite> lites;
+        for (int i = 0; i < n; ++i) {
+          const Inst &I = c->inst[i].I;
+          for (int e0 = 0; e0 < I.K; e0 += ept * adg::kTile) {
+            adg::BatchLite L;
+            L.f[0] = I.u;
+            L.f[1] = I.v1;
+            L.f[2] = I.v2;
+            L.meta = I.meta;
+            L.fx = I.fx;
+            L.K = I.K;
+            L.Np = I.Np;
+            L.e0 = e0;
+            L.pad = 0;
+            lites.push_back(L);
+          }
         }
         c->bu.reset(new (std::nothrow) adg::BatchUniform());
         if (!c->bu) {
@@ -1403,6 +1407,8 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
           for (int d = 0; d < adg::kMaxNp - 1; ++d)
             if (ref[d]) c->bu->uf.sf[d] = *ref[d];
           c->bu->items_dev = c->lites_dev;
+          c->bu->nitems = (int)lites.size();
+          c->bu->ept = ept;
         }
       }
     }

@@ -250,21 +250,22 @@ struct LiteView {
 
 // Batched fixed-point steps with the coefficients shared per degree (BatchUniform): block b
 // reads its work item's record (the instance's fields and the tile's first element; one load
-// ahead of the data instead of a work-list entry and then the instance).
-template <int FMT>
-__global__ void __launch_bounds__(kTile)
+// ahead of the data instead of a work-list entry and then the instance) and takes EPT kTile
+// elements.
+template <int FMT, int EPT>
+__global__ void __launch_bounds__(kTile, EPT == 1 ? 6 : 4)
     k_batch_fixed_uniform(const BatchLite *__restrict__ items, int src, int dst, int rel,
                           const UniformFixed uf) {
-  __shared__ FixedShared<1> sh;
+  __shared__ FixedShared<EPT> sh;
   const BatchLite L = items[blockIdx.x];
   const int2 w = make_int2(0, L.e0);
   const void *uin = src == 0 ? L.f[0] : (src == 1 ? L.f[1] : L.f[2]);
   void *uout = dst == 0 ? L.f[0] : (dst == 1 ? L.f[1] : L.f[2]);
   switch (L.Np) {
-    case 2: fixed_body<2, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
-    case 3: fixed_body<3, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
-    case 4: fixed_body<4, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
-    default: fixed_body<5, 1, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
+    case 2: fixed_body<2, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
+    case 3: fixed_body<3, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
+    case 4: fixed_body<4, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
+    default: fixed_body<5, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
   }
 }
 
@@ -325,14 +326,25 @@ cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev,
 
 cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_dev, int nwork,
                                        int src, int dst, int fmt, int rel, cudaStream_t s) {
-  if (nwork <= 0) return cudaSuccess;
   (void)work_dev;
+  (void)nwork;
+  const int n = bu.nitems;
+  if (n <= 0) return cudaSuccess;
   const BatchLite *l = bu.items_dev;
-  switch (fmt & 3) {
-    case 0: k_batch_fixed_uniform<0><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-    case 1: k_batch_fixed_uniform<1><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-    case 2: k_batch_fixed_uniform<2><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-    default: k_batch_fixed_uniform<3><<<nwork, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+  if (bu.ept == 2) {
+    switch (fmt & 3) {
+      case 0: k_batch_fixed_uniform<0, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+      case 1: k_batch_fixed_uniform<1, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+      case 2: k_batch_fixed_uniform<2, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+      default: k_batch_fixed_uniform<3, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+    }
+  } else {
+    switch (fmt & 3) {
+      case 0: k_batch_fixed_uniform<0, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+      case 1: k_batch_fixed_uniform<1, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+      case 2: k_batch_fixed_uniform<2, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+      default: k_batch_fixed_uniform<3, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
+    }
   }
   return cudaGetLastError();
 }

@@ -202,7 +202,8 @@ struct UniformFixed {
   StepFixed sf[kMaxNp - 1];
 };
 struct BatchUniform {
-  const BatchLite *items_dev;   // one record per work item (the instance's fields and e0)
+  const BatchLite *items_dev;   // one record per work item (the instance's fields and e0) of
+  int nitems, ept;              // ept kTile elements each
   UniformFixed uf;
 };
 
