@@ -24,7 +24,9 @@ What it computes, with the readings taken where the paper is silent (listed in D
 * Inside a Runge-Kutta step the delayed face values of stage s are the stage-s inputs of
   the delayed step (stage-consistent reading of Eq. async-dg2-rk2-l2).
 * Time integration: explicit Runge-Kutta in Butcher form, Y_s = u + dt sum_j a_sj k_j,
-  k_s = L(Y_s), u+ = u + dt sum_s b_s k_s.
+  k_s = L(Y_s), u+ = u + dt sum_s b_s k_s. The low-storage (2N) schemes of Section 6 enter
+  through their Butcher form (``two_register_tableau``); their stage inputs are the U_{s-1}
+  of the 2N recurrence.
 
 Everything runs in torch float64 on the CPU, vectorised over elements, so that
 ``gradient`` can take the exact discrete gradient by automatic differentiation.
@@ -43,6 +45,51 @@ from .operators import ref_ops
 
 F64 = torch.float64
 
+def two_register_tableau(A, B):
+    """Butcher form (a, b) of a 2N-storage Runge-Kutta scheme in Williamson's form,
+        dU_s = A_s dU_{s-1} + dt L(U_{s-1}),   U_s = U_{s-1} + B_s dU_s,   s = 1 .. S, A_1 = 0,
+    U_0 = u^n, u^{n+1} = U_S. With k_j = L(U_{j-1}) the recurrence unrolls to
+        dU_s = dt sum_{j<=s} (A_{j+1} ... A_s) k_j,
+        U_s = U_0 + dt sum_{j<=s} k_j sum_{r=j}^{s} B_r (A_{j+1} ... A_r),
+    so stage s+1 (input U_s) has a_{s+1,j} = sum_{r=j}^{s} B_r A_{j+1} ... A_r and b_j is the
+    same sum for s = S. A and B may be Fractions (exact) or floats; entries keep their type."""
+    S = len(A)
+
+    def coef(s, j):   # weight of dt k_j (0-based j) in U_s
+        tot = 0
+        for r in range(j, s):
+            prod = 1
+            for m in range(j + 1, r + 1):
+                prod = prod * A[m]
+            tot = tot + B[r] * prod
+        return tot
+
+    a = [[coef(s, j) if j < s else 0 for j in range(S)] for s in range(S)]
+    b = [coef(S, j) for j in range(S)]
+    return a, b
+
+
+# Low-storage schemes of the kind the paper's experiments use (Section 6, after Williamson
+# 1980 and Kennedy et al. 2000); their published 2N coefficients (A_s, B_s).
+from fractions import Fraction as _Fr  # noqa: E402
+
+TWO_REGISTER = {
+    # Williamson's three-stage, third-order scheme.
+    "lsrk3": ([_Fr(0), _Fr(-5, 9), _Fr(-153, 128)], [_Fr(1, 3), _Fr(15, 16), _Fr(8, 15)]),
+    # Carpenter and Kennedy's five-stage, fourth-order scheme.
+    "lsrk4": ([_Fr(0), _Fr(-567301805773, 1357537059087), _Fr(-2404267990393, 2016746695238),
+               _Fr(-3550918686646, 2091501179385), _Fr(-1275806237668, 842570457699)],
+              [_Fr(1432997174477, 9575080441755), _Fr(5161836677717, 13612068292357),
+               _Fr(1720146321549, 2090206949498), _Fr(3134564353537, 4481467310338),
+               _Fr(2277821191437, 14882151754819)]),
+}
+
+
+def _float_tableau(ab):
+    a, b = ab
+    return [[float(x) for x in row] for row in a], [float(x) for x in b]
+
+
 # Butcher tableaux (a, b).
 TABLEAUX = {
     # Forward Euler, Eq. EulerDG.
@@ -55,6 +102,9 @@ TABLEAUX = {
     # Classical fourth-order RK.
     "rk4": ([[0.0, 0.0, 0.0, 0.0], [0.5, 0.0, 0.0, 0.0], [0.0, 0.5, 0.0, 0.0],
              [0.0, 0.0, 1.0, 0.0]], [1.0 / 6.0, 1.0 / 3.0, 1.0 / 3.0, 1.0 / 6.0]),
+    # The 2N schemes above, in Butcher form.
+    "lsrk3": _float_tableau(two_register_tableau(*TWO_REGISTER["lsrk3"])),
+    "lsrk4": _float_tableau(two_register_tableau(*TWO_REGISTER["lsrk4"])),
 }
 
 

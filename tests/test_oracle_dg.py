@@ -41,7 +41,46 @@ def test_rhs_matches_paper_K_matrix_assembly(a):
     assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
-@pytest.mark.parametrize("rk", ["rk1", "rk2", "ssprk3", "rk4"])
+def _order_residuals(a, b):
+    """Residuals of the Runge-Kutta order conditions up to order four (c_i = sum_j a_ij)."""
+    S = len(b)
+    c = [sum(a[i]) for i in range(S)]
+    Ac = [sum(a[i][j] * c[j] for j in range(S)) for i in range(S)]
+    Ac2 = [sum(a[i][j] * c[j] ** 2 for j in range(S)) for i in range(S)]
+    AAc = [sum(a[i][j] * Ac[j] for j in range(S)) for i in range(S)]
+    from fractions import Fraction as Fr
+    return [sum(b) - 1,
+            sum(b[i] * c[i] for i in range(S)) - Fr(1, 2),
+            sum(b[i] * c[i] ** 2 for i in range(S)) - Fr(1, 3),
+            sum(b[i] * Ac[i] for i in range(S)) - Fr(1, 6),
+            sum(b[i] * c[i] ** 3 for i in range(S)) - Fr(1, 4),
+            sum(b[i] * c[i] * Ac[i] for i in range(S)) - Fr(1, 8),
+            sum(b[i] * Ac2[i] for i in range(S)) - Fr(1, 12),
+            sum(b[i] * AAc[i] for i in range(S)) - Fr(1, 24)]
+
+
+def test_two_register_form_of_the_paper_rk2():
+    # Eq. dg2-rk2 written as a 2N scheme: dU1 = dt L(u), U1 = u + dU1, dU2 = -dU1 + dt L(U1),
+    # u+ = U1 + dU2 / 2; its Butcher form is the two-stage tableau of the equation.
+    from fractions import Fraction as Fr
+    a, b = dg.two_register_tableau([Fr(0), Fr(-1)], [Fr(1), Fr(1, 2)])
+    assert (a, b) == ([[0, 0], [1, 0]], [Fr(1, 2), Fr(1, 2)])
+    assert dg.TABLEAUX["rk2"] == ([[0.0, 0.0], [1.0, 0.0]], [0.5, 0.5])
+
+
+def test_two_register_schemes_meet_their_order_conditions():
+    # Williamson's scheme: third order exactly (rational arithmetic), nodes c = (0, 1/3, 3/4),
+    # and not fourth order; Carpenter and Kennedy's: the eight conditions up to fourth order.
+    from fractions import Fraction as Fr
+    a, b = dg.two_register_tableau(*dg.TWO_REGISTER["lsrk3"])
+    r = _order_residuals(a, b)
+    assert [sum(row) for row in a] == [0, Fr(1, 3), Fr(3, 4)]
+    assert all(x == 0 for x in r[:4]) and any(x != 0 for x in r[4:])
+    a, b = dg.two_register_tableau(*dg.TWO_REGISTER["lsrk4"])
+    assert max(abs(float(x)) for x in _order_residuals(a, b)) < 1e-20
+
+
+@pytest.mark.parametrize("rk", ["rk1", "rk2", "ssprk3", "rk4", "lsrk3", "lsrk4"])
 @pytest.mark.parametrize("p", [1, 3])
 def test_sync_step_equals_amplification_matrix(rk, p):
     K, kap, sigma = 24, 5, 0.1
@@ -151,7 +190,8 @@ def test_exact_period_translation():
     assert np.max(np.abs(uN - dg.modes_initial(SIN, K, p))) < 1e-5
 
 
-@pytest.mark.parametrize("p,rk,sigma", [(1, "rk2", 0.1), (2, "ssprk3", 0.04), (3, "rk4", 0.02)])
+@pytest.mark.parametrize("p,rk,sigma", [(1, "rk2", 0.1), (2, "ssprk3", 0.04), (3, "rk4", 0.02),
+                                        (2, "lsrk3", 0.04), (3, "lsrk4", 0.02)])
 def test_sync_convergence_order(p, rk, sigma):
     # Section 4.3 / Fig. 7: the synchronous DG(p)-RK error falls as dx^{p+1}.
     Ks = (16, 32, 64)
