@@ -55,6 +55,10 @@ MACS_PER_ELEMENT_STEP = NP * NP + 5 * NP + 3
 INT_PRODUCTS_PER_ELEMENT_STEP = 3 * MACS_PER_ELEMENT_STEP + 3   # + the neighbour's v1_p^{e-2}
 FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
+# A 2N low-storage stage: dt L(U) + A_s dU (one multiply and NP + 1 FMA per DOF) and
+# U_s = U_{s-1} + B_s dU_s (one FMA).
+FLOP_PER_DOF_STAGE_LS = 2 * (NP + 2) + 1
+LOW_STORAGE_STAGES = {"rk1": 1, "rk2": 2, "lsrk3": 3, "lsrk4": 5}
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant; a kernel changed since its counters were taken has no
 # entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.06 MB read
@@ -144,17 +148,18 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def make_cfg(mode: str):
+def make_cfg(mode: str, rk: str = "ssprk3"):
     import paper_2404_03399_gb300 as adg
     w = WORKLOAD
     return adg.Config(pde=w["pde"], K=w["K"], p=w["p"], P=w["P"], cfl=w["cfl"], mode=mode,
-                      L=w["L"], q=w["q"] if mode == "at" else 0, seed=w["seed"])
+                      L=w["L"], q=w["q"] if mode == "at" else 0, seed=w["seed"], rk=rk)
 
 
-def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks: bool, dev: int):
+def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks: bool, dev: int,
+                 rk: str = "ssprk3"):
     import torch
     import paper_2404_03399_gb300 as adg
-    cfg = make_cfg(mode)
+    cfg = make_cfg(mode, rk)
     amp, kap, ph, off = WORKLOAD["modes"]
     u0 = adg.eval_modes(cfg, amp, kap, ph, off)
     s = adg.Solver(cfg, u0)
@@ -459,6 +464,20 @@ def main():
                            "workload": "512 advection instances, K log-uniform in [1024, 262144], "
                                        "p in 1..4, L in 2..8, AT order min(p+1, 3)"}
         line["adjoint"] = adjoint_cost()
+        # the 2N low-storage schemes (staged kernels) on the same mesh, ADG-AT3
+        ls = {}
+        for rk, S in LOW_STORAGE_STAGES.items():
+            lms, _, lfin, (lvar, _) = device_timed("at", 10, 3, barrier, False, local, rk)
+            step_s = lms / 10 * 1e-3
+            ls[rk] = {"value": ndof * S / step_s, "unit": UNIT, "ms_per_step": lms / 10,
+                      "stages": S, "variant": lvar, "finite": lfin,
+                      "fp64_tflops": ndof * S * FLOP_PER_DOF_STAGE_LS / step_s / 1e12,
+                      "fp64_frac": ndof * S * FLOP_PER_DOF_STAGE_LS / step_s / 1e12 / fp64_tflops}
+        line["low_storage"] = {"schemes": ls, "steps": 10, "mode": "at",
+                               "kernel": "k_lsrk_stage (one 2N stage: dt L(U), dU and U updates, "
+                                         "PE faces; an odd stage count adds a copy back into u, "
+                                         "charged to the step)",
+                               "peak_source": "FP64 unit counts x max SM clock"}
         ems, nbytes = e2e_timed(args.steps)
         line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,

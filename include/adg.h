@@ -50,7 +50,13 @@ typedef enum {
 
 enum { ADG_ADVECTION = 0, ADG_BURGERS = 1 };          /* f(u) = a u  |  f(u) = u^2/2 */
 enum { ADG_UPWIND = 0, ADG_LLF = 1 };                 /* Section 6.1 fluxes */
-enum { ADG_SSPRK3 = 3 };                               /* time integrator */
+enum {                                                  /* time integrator */
+  ADG_RK1 = 1,      /* forward Euler, Eq. EulerDG */
+  ADG_RK2 = 2,      /* the two-stage RK of Eq. dg2-rk2 */
+  ADG_SSPRK3 = 3,   /* three-stage SSP-RK3 (Shu and Osher) */
+  ADG_LSRK3 = 4,    /* Williamson's three-stage third-order 2N low-storage scheme */
+  ADG_LSRK4 = 5     /* Carpenter and Kennedy's five-stage fourth-order 2N scheme */
+};
 enum { ADG_SYNC = 0, ADG_ASYNC = 1, ADG_ASYNC_AT = 2 };/* DG | ADG | ADG-AT */
 enum {
   ADG_VARIANT_AUTO = 0,
@@ -67,7 +73,14 @@ enum {
  * Run configuration (Section 2: mesh, degree, flux, RK; Section 3: P and L; Section 5:
  * AT order; Section 6.1: probability set and seeded draws).
  *   pde, flux : ADG_ADVECTION with ADG_UPWIND, or ADG_BURGERS with ADG_LLF.
- *   rk        : ADG_SSPRK3.
+ *   rk        : ADG_SSPRK3 (default; every variant, adg_grad and batches), or one of the
+ *               low-storage schemes of the kind Section 6 integrates with, run in Williamson's
+ *               2N form (dU_s = A_s dU_{s-1} + dt L(U_{s-1}), U_s = U_{s-1} + B_s dU_s) by the
+ *               staged kernels: ADG_RK1, ADG_RK2 (Eq. dg2-rk2 as A = (0, -1),
+ *               B = (1, 1/2)), ADG_LSRK3, ADG_LSRK4. At PE faces stage s of a step reads the
+ *               stage-s inputs of the delayed step. A low-storage scheme is a single-instance
+ *               option: adg_batch_init and adg_grad reject it (ADG_EINVAL), and so does a
+ *               composed variant (ADG_VARIANT_COMPOSED, ADG_VARIANT_COMPOSED_FIXED).
  *   K, p, P   : elements, polynomial degree (1..ADG_MAX_P), PEs; K % P == 0, P >= 1.
  *   x0, x1    : periodic domain [x0, x1], x1 > x0.
  *   a         : advection speed (advection only).

@@ -49,13 +49,15 @@ class Config:
     probs: Optional[Sequence[float]] = None
     table: Optional[np.ndarray] = None   # uint8 (T, P), used periodically
     variant: str = "auto"       # "auto" | "staged" | "composed" | "fixed"
+    rk: str = "ssprk3"          # "ssprk3" | "rk1" | "rk2" | "lsrk3" | "lsrk4"
 
     def to_c(self):
         c = _abi.AdgConfig()
         load().adg_config_default(C.byref(c))
         c.pde = _PDE[self.pde]
         c.flux = _abi.ADG_UPWIND if self.pde == "advection" else _abi.ADG_LLF
-        c.rk = _abi.ADG_SSPRK3
+        c.rk = {"rk1": _abi.ADG_RK1, "rk2": _abi.ADG_RK2, "ssprk3": _abi.ADG_SSPRK3,
+                "lsrk3": _abi.ADG_LSRK3, "lsrk4": _abi.ADG_LSRK4}[self.rk]
         c.K, c.p, c.P = int(self.K), int(self.p), int(self.P)
         c.x0, c.x1, c.a = float(self.x0), float(self.x1), float(self.a)
         c.cfl, c.dt = float(self.cfl), float(self.dt)

@@ -10,7 +10,7 @@ ADG_OK, ADG_EINVAL, ADG_ENOMEM, ADG_ECUDA, ADG_ENONFINITE, ADG_ETIMEOUT, ADG_EST
     0, -1, -2, -3, -4, -5, -6
 ADG_ADVECTION, ADG_BURGERS = 0, 1
 ADG_UPWIND, ADG_LLF = 0, 1
-ADG_SSPRK3 = 3
+ADG_RK1, ADG_RK2, ADG_SSPRK3, ADG_LSRK3, ADG_LSRK4 = 1, 2, 3, 4, 5
 ADG_SYNC, ADG_ASYNC, ADG_ASYNC_AT = 0, 1, 2
 ADG_VARIANT_AUTO, ADG_VARIANT_STAGED, ADG_VARIANT_COMPOSED, ADG_VARIANT_COMPOSED_FIXED = 0, 1, 2, 3
 

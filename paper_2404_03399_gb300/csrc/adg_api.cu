@@ -223,12 +223,43 @@ struct DelaySource {
   }
 };
 
+// 2N coefficients (A_s, B_s) in Williamson's form of the low-storage schemes (include/adg.h),
+// as published fractions: forward Euler; Eq. dg2-rk2; Williamson's three-stage third-order
+// scheme; Carpenter and Kennedy's five-stage fourth-order scheme.
+struct Frac {
+  long long n, d;
+};
+struct LsTable {
+  int S;
+  Frac A[adg::kMaxStages], B[adg::kMaxStages];
+};
+
+const LsTable *ls_table(int rk) {
+  static const LsTable rk1 = {1, {{0, 1}}, {{1, 1}}};
+  static const LsTable rk2 = {2, {{0, 1}, {-1, 1}}, {{1, 1}, {1, 2}}};
+  static const LsTable lsrk3 = {3, {{0, 1}, {-5, 9}, {-153, 128}}, {{1, 3}, {15, 16}, {8, 15}}};
+  static const LsTable lsrk4 = {
+      5,
+      {{0, 1}, {-567301805773LL, 1357537059087LL}, {-2404267990393LL, 2016746695238LL},
+       {-3550918686646LL, 2091501179385LL}, {-1275806237668LL, 842570457699LL}},
+      {{1432997174477LL, 9575080441755LL}, {5161836677717LL, 13612068292357LL},
+       {1720146321549LL, 2090206949498LL}, {3134564353537LL, 4481467310338LL},
+       {2277821191437LL, 14882151754819LL}}};
+  switch (rk) {
+    case ADG_RK1: return &rk1;
+    case ADG_RK2: return &rk2;
+    case ADG_LSRK3: return &lsrk3;
+    case ADG_LSRK4: return &lsrk4;
+    default: return nullptr;
+  }
+}
+
 std::string check_config(const adg_config *c) {
   if (!c) return "cfg is NULL";
   if (c->pde != ADG_ADVECTION && c->pde != ADG_BURGERS) return "pde must be ADG_ADVECTION or ADG_BURGERS";
   if (c->pde == ADG_ADVECTION && c->flux != ADG_UPWIND) return "advection uses flux ADG_UPWIND";
   if (c->pde == ADG_BURGERS && c->flux != ADG_LLF) return "Burgers uses flux ADG_LLF";
-  if (c->rk != ADG_SSPRK3) return "rk must be ADG_SSPRK3";
+  if (c->rk < ADG_RK1 || c->rk > ADG_LSRK4) return "rk must be one of ADG_RK1 .. ADG_LSRK4";
   if (c->p < 1 || c->p > ADG_MAX_P) return "p must be in 1..4";
   if (c->K < 1 || c->K > (1 << 30)) return "K must be in 1..2^30";
   if (c->P < 1 || c->K % c->P != 0) return "P must be >= 1 and divide K";
@@ -359,16 +390,19 @@ void fold_constants(InstHost &h) {
   const ld c2a = adv ? advection_c2a(h) : 0.0L;
   const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
   const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
-  for (int s = 0; s < kStages; ++s) {
+  // A 2N low-storage scheme uses one set, sc[0]: dt L alone (beta 1, no identity term).
+  const bool ls = h.I.ls != 0;
+  for (int s = 0; s < (ls ? 1 : kStages); ++s) {
     adg::StageConsts &C = h.I.sc[s];
     std::memset(&C, 0, sizeof(C));
-    C.alpha = (double)alpha[s];
-    C.beta = (double)beta[s];
-    const ld b = beta[s];
+    C.alpha = ls ? 0.0 : (double)alpha[s];
+    C.beta = ls ? 0.0 : (double)beta[s];
+    const ld b = ls ? 1.0L : beta[s];
+    const ld id = ls ? 0.0L : 1.0L;
     for (int i = 0; i < Np; ++i) {
       for (int j = 0; j < Np; ++j) {
         const ld d = o.D[i * Np + j];
-        C.A[i * Np + j] = adv ? (double)(b * ((i == j ? 1.0L : 0.0L) + c2a * d))
+        C.A[i * Np + j] = adv ? (double)(b * ((i == j ? id : 0.0L) + c2a * d))
                               : (double)(b * c2 * 0.5L * d);
       }
       const ld sc = adv ? b * c2a : b * c2;
@@ -642,6 +676,15 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   I.q = h.q_eff;
   I.L = cfg->L;
   I.R = (cfg->L - 1) + h.q_eff;
+  {
+    const LsTable *lt = cfg->rk == ADG_SSPRK3 ? nullptr : ls_table(cfg->rk);
+    I.ls = lt ? 1 : 0;
+    I.ns = lt ? lt->S : kStages;
+    for (int s = 0; s < adg::kMaxStages; ++s) {
+      I.lsA[s] = lt && s < lt->S ? (double)((ld)lt->A[s].n / (ld)lt->A[s].d) : 0.0;
+      I.lsB[s] = lt && s < lt->S ? (double)((ld)lt->B[s].n / (ld)lt->B[s].d) : 0.0;
+    }
+  }
   I.meta = meta_slot;
 
   const size_t nd = (size_t)K * Np;
@@ -682,11 +725,12 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   fold_constants(h);
   {
     const bool eligible = cfg->pde == ADG_ADVECTION && cfg->a > 0 && K >= 8 &&
-                          (!I.async || I.Kpe >= 8);
+                          (!I.async || I.Kpe >= 8) && !I.ls;
     const bool want_composed = cfg->variant == ADG_VARIANT_COMPOSED ||
                                cfg->variant == ADG_VARIANT_COMPOSED_FIXED;
     if (want_composed && !eligible)
-      return fail(c, ADG_EINVAL, "the composed step needs advection with a > 0, K >= 8 and K/P >= 8");
+      return fail(c, ADG_EINVAL, "the composed step needs rk = ADG_SSPRK3, advection with a > 0, "
+                                 "K >= 8 and K/P >= 8");
     I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED) ? 1 : 0;
     I.ept = 1;
     if (I.fused) {
@@ -728,7 +772,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     CK(cudaMalloc(&h.coef, coef.size() * sizeof(double)));
     CK(cudaMemcpy(h.coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice));
     I.coef = h.coef;
-    const size_t ring_n = (size_t)I.R * kStages * I.P;
+    const size_t ring_n = (size_t)I.R * I.ns * I.P;
     CK(cudaMalloc(&h.ring, ring_n * sizeof(double2)));
     CK(cudaMemsetAsync(h.ring, 0, ring_n * sizeof(double2), c->stream));
     I.ring = h.ring;
@@ -776,6 +820,24 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
                                       rel % 2, 1 - rel % 2, 0, c->batch_fixed, rel, c->stream,
                                       c->batch_fixed ? c->bu.get() : nullptr));
     if (nsteps % 2) CK(adg::launch_batch_copy_back(c->insts_dev, c->work_dev, c->nwork, c->stream));
+    CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
+    return ADG_OK;
+  }
+  if (!c->batch && c->inst[0].I.ls) {
+    // 2N low-storage step: U_0 = u, dU in v1, U_s alternately in v2 and u (each stage reads
+    // its input's neighbours, so it writes the other field); an odd stage count ends in v2
+    const Inst &I = c->inst[0].I;
+    for (int rel = 0; rel < nsteps; ++rel) {
+      const double *in = I.u;
+      for (int s = 0; s < I.ns; ++s) {
+        double *out = (s % 2 == 0) ? I.v2 : I.u;
+        CK(adg::launch_lsrk_stage(I, s, rel, in, out, c->stream));
+        in = out;
+      }
+      if (I.ns % 2)
+        CK(cudaMemcpyAsync(I.u, I.v2, (size_t)I.K * I.Np * sizeof(double),
+                           cudaMemcpyDeviceToDevice, c->stream));
+    }
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
   }
@@ -1351,7 +1413,9 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       c->batch_fixed = c->batch_fixed && c->inst[i].I.fused == 2;
     }
     for (int i = 0; i < n && !r; ++i) {
-      if (c->inst[i].cfg.variant == ADG_VARIANT_COMPOSED_FIXED && !c->batch_fixed)
+      if (c->inst[i].I.ls)
+        r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches need rk = ADG_SSPRK3");
+      else if (c->inst[i].cfg.variant == ADG_VARIANT_COMPOSED_FIXED && !c->batch_fixed)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) +
                                     ": the fixed-point composed step needs every instance of the "
                                     "batch to admit it");
@@ -1570,6 +1634,7 @@ int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_
              double *grad_u0_dev, double *J_out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (c->batch) return fail(c, ADG_ESTATE, "adg_grad takes a single-instance context");
+  if (c->inst[0].I.ls) return fail(c, ADG_EINVAL, "adg_grad needs rk = ADG_SSPRK3");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, ADG_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
   if (!target_dev || !grad_u0_dev || !J_out) return fail(c, ADG_EINVAL, "NULL target, gradient or J");
   return run_gradient(c, target_dev, nsteps, ckpt_every, grad_u0_dev, J_out);

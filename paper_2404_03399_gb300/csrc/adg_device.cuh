@@ -109,7 +109,7 @@ __device__ __forceinline__ double pe_value(const I &inst, int j, int64_t n, int 
 #pragma unroll
     for (int r = 0; r < kPrefetchR; ++r) {
       if (r < R) T[r] = *q;
-      q += kStages * P;
+      q += (size_t)inst.ns * P;
     }
   }
   const int nm = (int)(n % R);
@@ -123,7 +123,7 @@ __device__ __forceinline__ double pe_value(const I &inst, int j, int64_t n, int 
         if (r == slot) x = T[r];
       return x;
     }
-    return col[(size_t)slot * kStages * P];
+    return col[(size_t)slot * inst.ns * P];
   };
   const DelayAt d = delay_at(inst, j, n);
   const int k = d.k;
@@ -143,7 +143,7 @@ __device__ __forceinline__ double pe_value(const I &inst, int j, int64_t n, int 
       V = __dadd_rn(V, __dmul_rn(ci, face_value<PDE, DIR>(inst, ti.x, ti.y)));
     }
   }
-  if (owner) col[(size_t)nm * kStages * P] = make_double2(tl, tr);
+  if (owner) col[(size_t)nm * inst.ns * P] = make_double2(tl, tr);
   return V;
 }
 

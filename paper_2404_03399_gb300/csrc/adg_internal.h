@@ -9,7 +9,8 @@ namespace adg {
 constexpr int kMaxNp = 5;
 constexpr int kMaxL = 16;
 constexpr int kMaxQ = 5;
-constexpr int kStages = 3;
+constexpr int kStages = 3;      // SSP-RK3 (the composed and fixed-point steps, the adjoint)
+constexpr int kMaxStages = 5;   // the 2N low-storage schemes (up to five stages)
 constexpr int kTile = 256;      // elements (threads) per block
 
 // Block size of the one-thread-per-element stage kernels: 256, or 128 when the mesh gives
@@ -113,7 +114,11 @@ struct alignas(16) Inst {
   // fused == 2: the PE-face responses st.R in fixed point (limbs as in StepFixed), used when
   // face_fx is set (every |R| < 2)
   int2 Rf[kStages][4][kMaxNp];
-  int face_fx, pad_[3];
+  int face_fx;
+  int ns;               // stages per step: the ring holds [R][ns][P] stage-input traces
+  int ls;               // 1: a 2N low-storage scheme (k_lsrk_stage, coefficients lsA, lsB)
+  int pad_;
+  double lsA[kMaxStages], lsB[kMaxStages];
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
@@ -159,6 +164,11 @@ struct AdjFace {
 // One stage over all elements; for an asynchronous instance the same kernel applies the
 // PE-face correction (delayed / AT flux) and writes the ring (step meta[0] + rel).
 cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
+// Stage s of a 2N low-storage step (I.ls): dU_s = A_s dU_{s-1} + dt L(U_{s-1}) in place in
+// I.v1 (A_1 = 0: dU_0 is not read) and U_s = U_{s-1} + B_s dU_s from uin (U_{s-1}) into uout,
+// with the delayed / AT flux and the ring write of the stage-input traces at PE faces.
+cudaError_t launch_lsrk_stage(const Inst &I, int s, int rel, const double *uin, double *uout,
+                              cudaStream_t st);
 cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                int stage, int rel, int tile, cudaStream_t s);
 // Batched PE-face pass after each batched stage: ring write of the stage-input traces and

@@ -26,22 +26,36 @@ __device__ __forceinline__ double pe_face_delta(const I &inst, int j, int64_t n,
   return __dsub_rn(Vs, V);
 }
 
+// A stage of a 2N low-storage step (LS): its input U_{s-1}, output U_s, stage index (for the
+// ring), coefficients, and whether it is the first (A_1 = 0: dU_0 is not read).
+struct LsArgs {
+  const double *uin;
+  double *uout;
+  int s, first;
+  double As, Bs;
+};
+
 // One SSP-RK3 stage for element e (all 32 lanes of the warp take part; lanes past the
-// end duplicate element K-1 and store nothing). DIR is the upwind side for advection
+// end duplicate element K-1 and store nothing). With LS, stage ls.s of a 2N low-storage step
+// instead: the same right-hand side dt L(U) from the constants sc[0] (no identity and no
+// factor beta), dU_s = A_s dU_{s-1} + dt L(U_{s-1}) in place in v1 and U_s = U_{s-1} + B_s dU_s. DIR is the upwind side for advection
 // (+1: a > 0, -1: a < 0) and 0 for Burgers. With FACES, the PE-face correction of the
 // delayed / AT flux is applied here too (step n): the element right of PE face j
 // (e = j Kpe) owns the face, writes its ring entry and adds lL (Vs - V); the element left
 // of it (e = j Kpe - 1) forms the same value with the same arithmetic and adds lR (Vs - V).
 // The synchronous output is rounded first, so the result is bit-identical to a stage
 // followed by a separate face pass.
-template <int NP, int PDE, int STAGE, int DIR, bool FACES, class I>
-__device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) {
+template <int NP, int PDE, int STAGE, int DIR, bool FACES, bool LS = false, class I>
+__device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0,
+                                           const LsArgs &ls = LsArgs{}) {
   const int K = inst.K;
   const int lane = threadIdx.x & 31;
   const int ec = e < K ? e : K - 1;
-  const double *vin = STAGE == 0 ? inst.u : (STAGE == 1 ? inst.v1 : inst.v2);
-  double *vout = STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.unext);
-  const StageConsts &C = inst.sc[STAGE];
+  const double *vin = LS ? ls.uin : (STAGE == 0 ? inst.u : (STAGE == 1 ? inst.v1 : inst.v2));
+  double *vout = LS ? inst.v1 : (STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.unext));
+  const StageConsts &C = inst.sc[LS ? 0 : STAGE];
+  const double alpha = LS ? ls.As : C.alpha;
+  const int rstage = LS ? ls.s : STAGE;
 
   double v[NP];
   {
@@ -52,13 +66,18 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) 
       q += K;
     }
   }
-  double u[NP];
+  double u[NP];   // the alpha operand: u^n, or dU_{s-1} of a 2N stage
   if (STAGE > 0) {
-    const double *q = inst.u + ec;
+    if (LS && ls.first) {
 #pragma unroll
-    for (int i = 0; i < NP; ++i) {
-      u[i] = *q;
-      q += K;
+      for (int i = 0; i < NP; ++i) u[i] = 0.0;
+    } else {
+      const double *q = (LS ? inst.v1 : inst.u) + ec;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        u[i] = *q;
+        q += K;
+      }
     }
   }
 
@@ -98,9 +117,10 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) 
   for (int i = 0; i < NP; ++i) {
     double acc;
     if (PDE == 0) {
-      acc = STAGE == 0 ? C.A[i * NP] * g[0] : fma(C.A[i * NP], g[0], C.alpha * u[i]);
+      acc = STAGE == 0 ? C.A[i * NP] * g[0] : fma(C.A[i * NP], g[0], alpha * u[i]);
     } else {
-      acc = STAGE == 0 ? v[i] : fma(C.beta, v[i], C.alpha * u[i]);
+      if (LS) acc = alpha * u[i];   // no v term: dt L(U) has none
+      else acc = STAGE == 0 ? v[i] : fma(C.beta, v[i], C.alpha * u[i]);
       acc = fma(C.A[i * NP], g[0], acc);
     }
 #pragma unroll
@@ -122,7 +142,7 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) 
     if (r == 0) {   // left face is PE face jq; this element owns it
       const double tl = (PDE == 1 || DIR > 0) ? vLm
                         : __ldg(vin + (NP - 1) * K + (e == 0 ? K - 1 : e - 1));
-      const double d = pe_face_delta<PDE, DIR>(inst, jq, n, STAGE, tl, v[0], true);
+      const double d = pe_face_delta<PDE, DIR>(inst, jq, n, rstage, tl, v[0], true);
       if (nonzero(d)) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], d, out[i]);
@@ -131,7 +151,7 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) 
     if (r == Kpe - 1) {   // right face is PE face jq + 1 (face 0 for the last element)
       const double tr = (PDE == 1 || DIR < 0) ? vRp : __ldg(vin + (e + 1 == K ? 0 : e + 1));
       const int jr = jq + 1 == inst.P ? 0 : jq + 1;
-      const double d = pe_face_delta<PDE, DIR>(inst, jr, n, STAGE, v[NP - 1], tr, false);
+      const double d = pe_face_delta<PDE, DIR>(inst, jr, n, rstage, v[NP - 1], tr, false);
       if (nonzero(d)) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], d, out[i]);
@@ -145,6 +165,14 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0) 
       *q = out[i];
       q += K;
     }
+    if (LS) {
+      double *w = ls.uout + e;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        *w = fma(ls.Bs, out[i], v[i]);
+        w += K;
+      }
+    }
   }
 }
 
@@ -152,6 +180,13 @@ template <int NP, int PDE, int STAGE, int DIR, bool FACES>
 __global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
   const int64_t n = FACES ? inst.meta[0] + rel : 0;
   stage_body<NP, PDE, STAGE, DIR, FACES>(inst, blockIdx.x * blockDim.x + threadIdx.x, n);
+}
+
+// Stage ls.s of a 2N low-storage step (Williamson's form; I.ls).
+template <int NP, int PDE, int DIR, bool FACES>
+__global__ void __launch_bounds__(kTile) k_lsrk_stage(const Inst inst, int rel, const LsArgs ls) {
+  const int64_t n = FACES ? inst.meta[0] + rel : 0;
+  stage_body<NP, PDE, 1, DIR, FACES, true>(inst, blockIdx.x * blockDim.x + threadIdx.x, n, ls);
 }
 
 // Composed SSP-RK3 step of upwind advection (a > 0), all faces synchronous (StepConsts):
@@ -968,6 +1003,44 @@ cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s) {
     case 3: return launch_np<3>(I, stage, rel, s);
     case 4: return launch_np<4>(I, stage, rel, s);
     case 5: return launch_np<5>(I, stage, rel, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+namespace {
+
+template <int NP, int PDE, int DIR>
+cudaError_t lsrk_np_pde(const Inst &I, int rel, const LsArgs &ls, cudaStream_t s) {
+  const int bs = stage_block(I.K);
+  const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
+  if (I.async) k_lsrk_stage<NP, PDE, DIR, true><<<grid, bs, 0, s>>>(I, rel, ls);
+  else k_lsrk_stage<NP, PDE, DIR, false><<<grid, bs, 0, s>>>(I, rel, ls);
+  return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t lsrk_np(const Inst &I, int rel, const LsArgs &ls, cudaStream_t s) {
+  if (I.pde == 1) return lsrk_np_pde<NP, 1, 0>(I, rel, ls, s);
+  return I.a >= 0.0 ? lsrk_np_pde<NP, 0, 1>(I, rel, ls, s) : lsrk_np_pde<NP, 0, -1>(I, rel, ls, s);
+}
+
+}  // namespace
+
+cudaError_t launch_lsrk_stage(const Inst &I, int s, int rel, const double *uin, double *uout,
+                              cudaStream_t st) {
+  if (!I.ls || s < 0 || s >= I.ns || uin == uout) return cudaErrorInvalidValue;
+  LsArgs ls;
+  ls.uin = uin;
+  ls.uout = uout;
+  ls.s = s;
+  ls.first = s == 0;
+  ls.As = I.lsA[s];
+  ls.Bs = I.lsB[s];
+  switch (I.Np) {
+    case 2: return lsrk_np<2>(I, rel, ls, st);
+    case 3: return lsrk_np<3>(I, rel, ls, st);
+    case 4: return lsrk_np<4>(I, rel, ls, st);
+    case 5: return lsrk_np<5>(I, rel, ls, st);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -51,7 +51,8 @@ def run_pair(cfg: adg.Config, u0: np.ndarray, steps: int, table=None):
     else:
         tbl = None
     prob = dg.Problem(pde=cfg.pde, K=cfg.K, p=cfg.p, P=cfg.P, dt=dt, a=cfg.a, x0=cfg.x0, x1=cfg.x1,
-                      mode=_oracle_mode(cfg.mode) if cfg.P > 1 else "sync", q=q, delays=tbl)
+                      mode=_oracle_mode(cfg.mode) if cfg.P > 1 else "sync", q=q, delays=tbl,
+                      rk=cfg.rk)
     ref = dg.run(prob, u0, steps).numpy()
     return got, ref, dt
 
@@ -190,28 +191,31 @@ def test_run_to_time_and_step_counter():
 
 
 def _window_oracle(cfg, u0_full_fn, e, steps, dt, table_rows, both_sides):
-    """Oracle on a window of the full mesh around element e (sampled parity at full size)."""
-    r = 3 * steps + 2
+    """Oracle on a window of the full mesh around element e (sampled parity at full size); each
+    stage of a step reaches one element further."""
+    r = len(dg.TABLEAUX[cfg.rk][1]) * steps + 2
     lo = e - r
     W = 2 * r + 1 if both_sides else r + 3
     u0w = u0_full_fn(lo, W)
     q = cfg.q if cfg.mode == "at" else 1
     prob = dg.Problem(pde=cfg.pde, K=W, p=cfg.p, P=cfg.P, dt=dt, a=cfg.a, mode="adg", q=q,
-                      delays=table_rows, window_lo=lo, K_global=cfg.K)
+                      delays=table_rows, window_lo=lo, K_global=cfg.K, rk=cfg.rk)
     out = dg.run(prob, u0w, steps).numpy()
     return out[r]
 
 
 @pytest.mark.parametrize("which", ["advection_16m", "advection_16m_staged", "advection_16m_composed",
-                                   "burgers_1m"])
+                                   "advection_16m_lsrk4", "burgers_1m"])
 def test_full_size_sampled(which):
     # Full-size meshes in the launch configuration the benchmark times (graph replay of
     # 32-step chunks plus a direct remainder), checked at sampled elements against the
     # oracle run on a window wide enough to contain each sample's dependence cone.
     if which.startswith("advection_16m"):
         w = ADVECTION_16M
+        suffix = which[len("advection_16m_"):]
+        kw = {"rk": suffix} if suffix == "lsrk4" else {"variant": suffix or "auto"}
         cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode="at", L=w.L, q=w.q,
-                         seed=w.seed, variant=which[len("advection_16m_"):] or "auto")
+                         seed=w.seed, **kw)
         modes, steps, both = SIN, 40, False
     else:
         w = BURGERS_1M
@@ -325,3 +329,72 @@ def test_variant_in_use(kw, want):
     s.close()
     assert variant == want
     assert ept in (1, 2, 4)
+
+
+# --- low-storage (2N) Runge-Kutta schemes: the staged 2N stage kernel against the oracle's
+# Butcher form of the same scheme --------------------------------------------------------------
+
+LOW_STORAGE = ["rk1", "rk2", "lsrk3", "lsrk4"]
+
+
+def _ls_case(case, rk):
+    if case == "advection_at":      # a > 0, ADG-AT3, K not a multiple of the block
+        return adg.Config(pde="advection", K=600, p=3, P=8, a=1.0, cfl=0.02, mode="at", L=4, q=3,
+                          seed=21, rk=rk), dg.modes_initial(PAPER_FIG6, 600, 3)
+    if case == "advection_neg_async":   # a < 0, standard delayed flux
+        return adg.Config(pde="advection", K=320, p=2, P=16, a=-0.8, cfl=0.02, mode="async", L=3,
+                          seed=22, rk=rk), dg.modes_initial(PAPER_FIG6, 320, 2)
+    if case == "burgers_at":        # LLF, ADG-AT2, smooth data before the shock
+        return adg.Config(pde="burgers", K=256, p=4, P=8, cfl=0.01, mode="at", L=3, q=2, seed=23,
+                          rk=rk), dg.modes_initial(HALF_PLUS_SIN, 256, 4)
+    # sync DG(1), the paper's DG(1)-RK2 configuration (Section 4.2) at sigma = 0.1
+    return adg.Config(pde="advection", K=128, p=1, P=4, cfl=0.1 if rk != "rk1" else 0.02,
+                      mode="sync", rk=rk), dg.modes_initial(PAPER_FIG6, 128, 1)
+
+
+@pytest.mark.parametrize("rk", LOW_STORAGE)
+@pytest.mark.parametrize("case", ["advection_at", "advection_neg_async", "burgers_at", "sync_dg1"])
+def test_low_storage_schemes_match_oracle(rk, case):
+    # 40 steps: one 32-step graph chunk and a directly launched remainder.
+    cfg, u0 = _ls_case(case, rk)
+    s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
+    assert s.variant[0] == "staged"
+    s.close()
+    got, ref, _ = run_pair(cfg, u0, 40)
+    assert np.all(np.isfinite(got))
+    assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
+
+
+@pytest.mark.parametrize("rk", ["rk2", "lsrk4"])
+def test_low_storage_zero_delay_is_bitwise_sync(rk):
+    # k = 0 everywhere: the delayed / AT value is the current one, so ADG and ADG-AT reproduce
+    # synchronous DG bit for bit (Section 3) with every stage count.
+    K, p, P = 256, 3, 8
+    u0 = torch.tensor(dg.modes_initial(PAPER_FIG6, K, p), device="cuda")
+    outs = []
+    for mode, table in [("sync", None), ("at", constant_table(1, P, 0)), ("async", constant_table(1, P, 0))]:
+        cfg = adg.Config(pde="advection", K=K, p=p, P=P, cfl=0.02, mode=mode, L=2, q=3,
+                         table=table, rk=rk)
+        s = adg.Solver(cfg, u0)
+        s.step(37)
+        outs.append(s.state().cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1]) and np.array_equal(outs[0], outs[2])
+
+
+def test_low_storage_rejections():
+    # The low-storage schemes are single-instance, staged-kernel options.
+    cfg = adg.Config(pde="advection", K=64, p=2, P=4, cfl=0.02, mode="at", L=2, q=2, rk="lsrk3")
+    u0 = adg.eval_modes(cfg, [1.0], [1.0], [0.0])
+    for variant in ("composed", "fixed"):
+        with pytest.raises(adg.AdgError) as ei:
+            adg.Solver(adg.Config(**{**cfg.__dict__, "variant": variant}), u0)
+        assert ei.value.code == adg._abi.ADG_EINVAL
+    with pytest.raises(adg.AdgError) as ei:
+        adg.BatchSolver([cfg, cfg], [u0, u0])
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    s = adg.Solver(cfg, u0)
+    with pytest.raises(adg.AdgError) as ei:
+        s.grad(u0, 4, 2)
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    s.close()
