@@ -1,6 +1,10 @@
 """Delay emulation (oracle; test infrastructure).
 
-Section 6.1: at each time step a uniform random number in [0, 1] is drawn at each PE
+Two sources of delays. The communication-avoiding cycle of Section 6.3 (``caa_delay``):
+every period of `sync_steps` + L steps starts with `sync_steps` steps that communicate and
+synchronise (delay 0), followed by L steps without communication, whose faces use the levels
+0, 1, ..., L-1 steps old. The random emulation of Section 6.1:
+at each time step a uniform random number in [0, 1] is drawn at each PE
 boundary and matched against L bins of sizes p_0 .. p_{L-1}; bin k gives the delay k.
 The bins are [c_k, c_{k+1}) with c_k = p_0 + ... + p_{k-1} summed left to right in FP64.
 
@@ -59,4 +63,24 @@ def delay_table(seed: int, P: int, steps: int, L: int, probs=None, first_step: i
         n = first_step + r
         for j in range(P):
             out[r, j] = delay_from_uniform(uniform01(seed, n * P + j), edges)
+    return out
+
+
+def caa_delay(n: int, sync_steps: int, L: int) -> int:
+    """Delay of step n under the communication-avoiding cycle (Section 6.3): position
+    m = n mod (sync_steps + L) in the period; 0 for m < sync_steps, else m - sync_steps."""
+    m = n % (sync_steps + L)
+    return 0 if m < sync_steps else m - sync_steps
+
+
+def caa_communicates(n: int, sync_steps: int, L: int) -> bool:
+    """Whether step n of the cycle exchanges PE-face data (its synchronised steps only)."""
+    return n % (sync_steps + L) < sync_steps
+
+
+def caa_table(P: int, steps: int, sync_steps: int, L: int, first_step: int = 0):
+    """uint8 table D[n - first_step][j] of the cycle (the same delay at every PE face)."""
+    out = np.zeros((steps, P), dtype=np.uint8)
+    for r in range(steps):
+        out[r, :] = caa_delay(first_step + r, sync_steps, L)
     return out

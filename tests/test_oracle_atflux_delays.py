@@ -104,3 +104,24 @@ def test_delay_statistics_and_determinism():
     assert np.array_equal(t[300:], t2)
     # Degenerate set {0, 0, 1}: every delay is 2.
     assert np.all(delays.delay_table(1, 8, 20, 3, [0.0, 0.0, 1.0]) == 2)
+
+
+def test_caa_cycle_of_the_2d_experiment():
+    # Section 6.3: with L = 3, of every five steps the first two communicate and synchronise
+    # and the next three do not, so those three use delays 0, 1, 2 and communication falls by
+    # 60% against the synchronous scheme.
+    sync, L = 2, 3
+    rows = [delays.caa_delay(n, sync, L) for n in range(10)]
+    assert rows == [0, 0, 0, 1, 2, 0, 0, 0, 1, 2]
+    comm = [delays.caa_communicates(n, sync, L) for n in range(1000)]
+    assert sum(comm) / len(comm) == pytest.approx(0.4, abs=0)   # 60% fewer exchanges
+    # every step without communication sees its level the number of steps since the last
+    # synchronised one, less one
+    last = None
+    for n in range(40):
+        if delays.caa_communicates(n, sync, L):
+            last = n
+        else:
+            assert delays.caa_delay(n, sync, L) == n - last - 1
+    t = delays.caa_table(4, 7, sync, L, first_step=3)
+    assert t.shape == (7, 4) and (t == np.array(rows[3:10])[:, None]).all()
