@@ -193,6 +193,34 @@ def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks
     return ms, (clocks.summary() if clocks else None), finite, variant
 
 
+def caa_timed(steps: int, warmup: int):
+    """The large advection mesh under the communication-avoiding delay cycle of Section 6.3
+    (L = 3, two synchronised steps of five, ADG-AT2): CUDA-event time of `steps` steps after
+    `warmup`, and the PE-face exchanges a distributed run would make (adg_comm_stats)."""
+    import torch
+    import paper_2404_03399_gb300 as adg
+    w = WORKLOAD
+    cfg = adg.Config(pde=w["pde"], K=w["K"], p=w["p"], P=w["P"], cfl=w["cfl"], mode="at", L=3,
+                     q=2, caa_sync=2)
+    amp, kap, ph, off = w["modes"]
+    u0 = adg.eval_modes(cfg, amp, kap, ph, off)
+    s = adg.Solver(cfg, u0)
+    del u0
+    stream = torch.cuda.current_stream()
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    st = s.comm_stats()
+    variant = s.variant[0]
+    s.close()
+    return ms, st, variant
+
+
 def e2e_timed(steps: int):
     """Public-API run from host buffers: pinned u0 -> device, adg_init, `steps` steps,
     state -> pinned host; all inside one timed region (wall clock around synchronised
@@ -473,6 +501,14 @@ def main():
                       "stages": S, "variant": lvar, "finite": lfin,
                       "fp64_tflops": ndof * S * FLOP_PER_DOF_STAGE_LS / step_s / 1e12,
                       "fp64_frac": ndof * S * FLOP_PER_DOF_STAGE_LS / step_s / 1e12 / fp64_tflops}
+        cms, cst, cvar = caa_timed(args.steps, args.warmup)
+        line["caa"] = {"value": ndof * STAGES * args.steps / (cms * 1e-3), "unit": UNIT,
+                       "ms_per_step": cms / args.steps, "variant": cvar,
+                       "workload": "the same mesh, communication-avoiding cycle of Section 6.3 "
+                                   "(L = 3, 2 synchronised steps of 5), ADG-AT2",
+                       "exchanges": cst["exchanges"], "sync_exchanges": cst["sync_exchanges"],
+                       "exchange_saving": 1.0 - cst["exchanges"] / max(cst["sync_exchanges"], 1),
+                       "steps_counted": cst["steps"]}
         line["low_storage"] = {"schemes": ls, "steps": 10, "mode": "at",
                                "kernel": "k_lsrk_stage (one 2N stage: dt L(U), dU and U updates, "
                                          "PE faces; an odd stage count adds a copy back into u, "

@@ -95,6 +95,12 @@ enum {
  *   delay_table, table_steps: optional caller table, uint8 [table_steps][P], host memory,
  *               used periodically (row n mod table_steps at step n); overrides the seed.
  *               Every entry must be < L.
+ *   caa_sync  : 0 (default), or the communication-avoiding cycle of Section 6.3 as the
+ *               delay source: every period of caa_sync + L steps has caa_sync synchronised
+ *               steps (delay 0), then L steps without communication with delays 0, 1, ..,
+ *               L-1 at every PE face (caa_sync = 2, L = 3: the 2D experiment's cycle).
+ *               Overrides seed and probs; 0 <= caa_sync <= 64; ADG_EINVAL together with a
+ *               caller table.
  *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
  *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
  *               composed into one stencil per step, with the delayed / AT flux at PE faces
@@ -128,6 +134,7 @@ typedef struct {
   const uint8_t *delay_table;
   int64_t table_steps;
   int32_t variant;
+  int32_t caa_sync;
 } adg_config;
 
 /* Fill cfg with defaults: advection, upwind, SSP-RK3, [0, 2 pi], a = 1, cfl = 0.1, sync. */
@@ -221,7 +228,20 @@ int adg_integral_noalloc(int32_t p, int32_t K, double dx, const double *u_dev, d
                          void *stream);
 
 /*
- * Write the delay table the library uses for cfg (seeded or caller table) for steps
+ * Exchanges of PE-face data that a distributed run of the instance `index` over the steps run
+ * so far would make (Section 6.3's accounting), against synchronous DG: one exchange is the
+ * pair of traces of one PE face for one stage of one step. Synchronous DG exchanges at every
+ * step (sync_out = steps * stages * P); under the seeded or caller delays every level is still
+ * sent, only late (exchanges_out = sync_out); under the communication-avoiding cycle only its
+ * synchronised steps exchange. The emulation itself stores every level in its ring either
+ * way. steps_out: steps run since adg_init. Host only (no GPU work); NULL outputs are skipped.
+ * Errors: ADG_EINVAL (NULL ctx, bad index).
+ */
+int adg_comm_stats(const adg_ctx *c, int32_t index, int64_t *steps_out, int64_t *exchanges_out,
+                   int64_t *sync_out);
+
+/*
+ * Write the delay table the library uses for cfg (seeded, cycle or caller table) for steps
  * first_step .. first_step+steps-1 into out_host (uint8 [steps][P]). Host only; needs no
  * GPU. Errors: ADG_EINVAL.
  */

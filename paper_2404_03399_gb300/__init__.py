@@ -50,6 +50,7 @@ class Config:
     table: Optional[np.ndarray] = None   # uint8 (T, P), used periodically
     variant: str = "auto"       # "auto" | "staged" | "composed" | "fixed"
     rk: str = "ssprk3"          # "ssprk3" | "rk1" | "rk2" | "lsrk3" | "lsrk4"
+    caa_sync: int = 0           # > 0: communication-avoiding delay cycle (Section 6.3)
 
     def to_c(self):
         c = _abi.AdgConfig()
@@ -66,6 +67,7 @@ class Config:
         c.at_order = int(self.q)
         c.seed = int(self.seed) & ((1 << 64) - 1)
         c.variant = {"auto": 0, "staged": 1, "composed": 2, "fixed": 3}[self.variant]
+        c.caa_sync = int(self.caa_sync)
         keep = []
         if self.probs is not None:
             arr = (C.c_double * len(self.probs))(*[float(v) for v in self.probs])
@@ -167,6 +169,13 @@ class Solver:
         v, e = C.c_int32(), C.c_int32()
         check(load().adg_get_variant(self.ctx, 0, C.byref(v), C.byref(e)), self.ctx)
         return {1: "staged", 2: "composed", 3: "fixed"}[v.value], e.value
+
+    def comm_stats(self) -> dict:
+        """PE-face exchanges a distributed run of the steps so far would make, against
+        synchronous DG (adg_comm_stats)."""
+        n, ex, sy = C.c_int64(), C.c_int64(), C.c_int64()
+        check(load().adg_comm_stats(self.ctx, 0, C.byref(n), C.byref(ex), C.byref(sy)), self.ctx)
+        return {"steps": n.value, "exchanges": ex.value, "sync_exchanges": sy.value}
 
     def integral(self) -> float:
         v = C.c_double()

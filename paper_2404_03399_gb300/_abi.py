@@ -22,7 +22,7 @@ EXPORTS = [
     "adg_config_default", "adg_init", "adg_batch_init", "adg_step", "adg_run",
     "adg_get_state", "adg_get_dt", "adg_get_variant", "adg_grad", "adg_integral", "adg_check_finite",
     "adg_delay_table", "adg_eval_modes", "adg_lgl_nodes", "adg_last_error", "adg_destroy",
-    "adg_integral_noalloc", "adg_misfit",
+    "adg_integral_noalloc", "adg_misfit", "adg_comm_stats",
 ]
 
 
@@ -35,7 +35,7 @@ class AdgConfig(C.Structure):
         ("mode", C.c_int32), ("L", C.c_int32), ("at_order", C.c_int32),
         ("seed", C.c_uint64), ("probs", C.POINTER(C.c_double)),
         ("delay_table", C.POINTER(C.c_uint8)), ("table_steps", C.c_int64),
-        ("variant", C.c_int32),
+        ("variant", C.c_int32), ("caa_sync", C.c_int32),
     ]
 
 
@@ -82,6 +82,7 @@ def load(require: bool = True):
         "adg_destroy": (None, [vp]),
         "adg_integral_noalloc": (C.c_int, [i32, i32, C.c_double, vp, vp, vp]),
         "adg_misfit": (C.c_int, [vp, i32, vp, dp]),
+        "adg_comm_stats": (C.c_int, [vp, i32, C.POINTER(i64), C.POINTER(i64), C.POINTER(i64)]),
     }
     for name, (res, args) in sig.items():
         f = getattr(L, name)

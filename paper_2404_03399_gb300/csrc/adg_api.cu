@@ -203,10 +203,16 @@ struct DelaySource {
   std::vector<double> edges;          // upper bin edges, summed left to right
   std::vector<uint8_t> caller;        // caller table (periodic) or empty
   int64_t caller_rows = 0;
+  int caa = 0;                        // > 0: the communication-avoiding cycle (Section 6.3)
 
   void rows(int64_t first, int64_t count, uint8_t *out) const {
     for (int64_t r = 0; r < count; ++r) {
       const int64_t n = first + r;
+      if (caa > 0) {
+        const int m = (int)(n % (caa + L));
+        std::memset(out + r * P, m < caa ? 0 : m - caa, P);
+        continue;
+      }
       if (!caller.empty()) {
         const int64_t cr = n % caller_rows;
         std::memcpy(out + r * P, caller.data() + cr * P, P);
@@ -268,6 +274,8 @@ std::string check_config(const adg_config *c) {
   if (!std::isfinite(c->dt) || c->dt < 0) return "dt must be finite and >= 0";
   if (c->dt == 0 && !(std::isfinite(c->cfl) && c->cfl > 0)) return "cfl must be > 0 when dt == 0";
   if (c->mode != ADG_SYNC && c->mode != ADG_ASYNC && c->mode != ADG_ASYNC_AT) return "bad mode";
+  if (c->caa_sync < 0 || c->caa_sync > 64) return "caa_sync must be in 0..64";
+  if (c->caa_sync > 0 && c->delay_table) return "caa_sync and a caller delay table exclude each other";
   if (c->L < 1 || c->L > ADG_MAX_L) return "L must be in 1..16";
   if (c->at_order < 0 || c->at_order > ADG_MAX_Q) return "at_order must be in 0..5";
   if (c->variant < ADG_VARIANT_AUTO || c->variant > ADG_VARIANT_COMPOSED_FIXED) return "bad variant";
@@ -302,6 +310,7 @@ DelaySource make_delay_source(const adg_config *c) {
     d.caller.assign(c->delay_table, c->delay_table + c->table_steps * (int64_t)c->P);
     d.caller_rows = c->table_steps;
   }
+  d.caa = c->caa_sync;
   return d;
 }
 
@@ -559,12 +568,14 @@ int fill_table(adg_ctx *c, InstHost &h, int64_t first) {
   h.tbase = first;
   const DelaySource &d = h.delays;
   if (d.caller.empty()) {
+    // seeded rows and the communication-avoiding cycle are generated on the device
     // seeded rows are generated on the device (the host generator's arithmetic, with the bin
     // edges as exact integer thresholds: u < e  <=>  (z >> 11) < ceil(e 2^53))
     adg::DelayGen g{};
     g.seed = d.seed;
     g.L = d.L;
     g.P = d.P;
+    g.caa = d.caa;
     for (int b = 0; b < d.L; ++b) {
       const double t = std::ceil(std::ldexp(d.edges[b], 53));
       g.T[b] = t >= 18446744073709551616.0 ? ~0ull : (t <= 0 ? 0ull : (uint64_t)t);
@@ -1311,6 +1322,24 @@ void adg_config_default(adg_config *cfg) {
   cfg->cfl = 0.1;
   cfg->mode = ADG_SYNC;
   cfg->L = 1;
+}
+
+int adg_comm_stats(const adg_ctx *c, int32_t index, int64_t *steps_out, int64_t *exchanges_out,
+                   int64_t *sync_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size()) return fail(nullptr, ADG_EINVAL, "bad instance index");
+  const InstHost &h = c->inst[index];
+  const int64_t n = c->n;
+  const int64_t per_step = h.I.async ? (int64_t)h.I.ns * h.I.P : 0;
+  int64_t comm = n;
+  if (h.delays.caa > 0) {   // whole periods, then the partial one
+    const int64_t per = h.delays.caa + h.delays.L;
+    comm = (n / per) * h.delays.caa + std::min<int64_t>(n % per, h.delays.caa);
+  }
+  if (steps_out) *steps_out = n;
+  if (exchanges_out) *exchanges_out = comm * per_step;
+  if (sync_out) *sync_out = n * per_step;
+  return ADG_OK;
 }
 
 const char *adg_last_error(const adg_ctx *c) {

@@ -238,6 +238,8 @@ struct DelayGen {
   uint64_t seed;
   uint64_t T[kMaxL];
   int L, P;
+  int caa;   // > 0: the communication-avoiding cycle instead (the same delay at every face)
+  int pad;
 };
 cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const DelayGen &g,
                                cudaStream_t s);

@@ -1123,6 +1123,11 @@ __global__ void k_fill_delays(uint8_t *__restrict__ table, int64_t first, int64_
                               const DelayGen g) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
        i += (int64_t)gridDim.x * blockDim.x) {
+    if (g.caa > 0) {   // step first + i / P of the cycle
+      const int m = (int)((first + i / g.P) % (g.caa + g.L));
+      table[i] = (uint8_t)(m < g.caa ? 0 : m - g.caa);
+      continue;
+    }
     const uint64_t idx = (uint64_t)first * (uint64_t)g.P + (uint64_t)i;   // (first + r) P + j
     uint64_t z = g.seed + (idx + 1) * 0x9E3779B97F4A7C15ull;
     z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;

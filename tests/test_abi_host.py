@@ -70,6 +70,24 @@ def test_delay_table_matches_oracle(lib, seed, P, L, probs):
     assert np.array_equal(got, ref)
 
 
+@pytest.mark.parametrize("sync,L,first", [(2, 3, 0), (2, 3, 1001), (1, 8, 37), (5, 1, 12)])
+def test_caa_cycle_matches_oracle(lib, sync, L, first):
+    # The communication-avoiding cycle of Section 6.3 as the library's delay source.
+    P = 6
+    cfg = adg.Config(K=P * 4, p=1, P=P, L=L, mode="at", caa_sync=sync, seed=77)
+    got = adg.delay_table(cfg, first, 40)
+    assert np.array_equal(got, odelays.caa_table(P, 40, sync, L, first_step=first))
+
+
+def test_caa_rejects_bad_settings(lib):
+    tbl = np.zeros((2, 2), dtype=np.uint8)
+    for kw in (dict(caa_sync=-1), dict(caa_sync=65), dict(caa_sync=2, table=tbl)):
+        cfg = adg.Config(K=8, p=1, P=2, L=3, mode="async", **kw)
+        with pytest.raises(adg.AdgError) as ei:
+            adg.delay_table(cfg, 0, 4)
+        assert ei.value.code == _abi.ADG_EINVAL
+
+
 def test_caller_table_is_periodic(lib):
     tbl = np.array([[0, 1], [2, 0], [1, 1]], dtype=np.uint8)
     cfg = adg.Config(K=8, p=1, P=2, L=3, mode="async", table=tbl)

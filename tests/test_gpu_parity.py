@@ -46,7 +46,9 @@ def run_pair(cfg: adg.Config, u0: np.ndarray, steps: int, table=None):
     q = cfg.q if cfg.mode == "at" else 1
     if cfg.mode == "at" and q == 0:
         q = min(cfg.p + 1, 5)
-    if cfg.mode != "sync" and cfg.P > 1:
+    if cfg.mode != "sync" and cfg.P > 1 and cfg.caa_sync > 0:
+        tbl = odelays.caa_table(cfg.P, steps, cfg.caa_sync, cfg.L)
+    elif cfg.mode != "sync" and cfg.P > 1:
         tbl = cfg.table if cfg.table is not None else odelays.delay_table(cfg.seed, cfg.P, steps, cfg.L, cfg.probs)
     else:
         tbl = None
@@ -398,3 +400,27 @@ def test_low_storage_rejections():
         s.grad(u0, 4, 2)
     assert ei.value.code == adg._abi.ADG_EINVAL
     s.close()
+
+
+# --- the communication-avoiding delay cycle (Section 6.3) as the library's delay source ----
+
+
+@pytest.mark.parametrize("variant,rk", [("staged", "ssprk3"), ("fixed", "ssprk3"), ("auto", "rk2")])
+def test_caa_cycle_matches_oracle_and_counts_exchanges(variant, rk):
+    # ADG(1)-AT2 of the 2D experiment's cycle (L = 3, two synchronised steps of five), here on
+    # 1D advection: 103 steps (three graph chunks and a remainder) against the oracle run on the
+    # oracle's own cycle table; the exchange count is the cycle's 2 / 5 of synchronous DG.
+    K, p, P = 384, 1, 16
+    cfg = adg.Config(pde="advection", K=K, p=p, P=P, cfl=0.02, mode="at", L=3, q=2, caa_sync=2,
+                     variant=variant, rk=rk)
+    u0 = dg.modes_initial(PAPER_FIG6, K, p)
+    got, ref, _ = run_pair(cfg, u0, 103)
+    assert rel_linf(got, ref) < TOL
+    s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
+    s.step(103)
+    st = s.comm_stats()
+    s.close()
+    stages = len(dg.TABLEAUX[rk][1])
+    comm = sum(odelays.caa_communicates(n, 2, 3) for n in range(103))
+    assert st == {"steps": 103, "exchanges": comm * stages * P, "sync_exchanges": 103 * stages * P}
+    assert comm == 42   # 20 full periods of two, and two of the last three steps
