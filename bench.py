@@ -482,6 +482,11 @@ def main():
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:
+        # end to end first, in the process state the main run left
+        ems, nbytes = e2e_timed(args.steps)
+        line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
+                       "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
+                       "what": "pinned host u0 -> device, adg_init, all steps, state -> pinned host"}
         sms, _, _, _ = device_timed("sync", args.sync_steps, args.warmup, barrier, False, local)
         line["sync_dg"] = {"value": ndof * STAGES * args.sync_steps / (sms * 1e-3), "unit": UNIT,
                            "ms_per_step": sms / args.sync_steps}
@@ -514,10 +519,6 @@ def main():
                                          "PE faces; an odd stage count adds a copy back into u, "
                                          "charged to the step)",
                                "peak_source": "FP64 unit counts x max SM clock"}
-        ems, nbytes = e2e_timed(args.steps)
-        line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
-                       "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
-                       "what": "pinned host u0 -> device, adg_init, all steps, state -> pinned host"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(1 << 22, 3)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
