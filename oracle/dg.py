@@ -12,6 +12,13 @@ What it computes, with the readings taken where the paper is silent (listed in D
 * Numerical fluxes: upwind (Section 6.1: a u^- for a >= 0, a u^+ for a < 0) for linear
   advection; local Lax-Friedrichs (Section 6.1) with lambda = max(|u^-|, |u^+|) for
   inviscid Burgers f = u^2/2.
+* Viscous Burgers u_t + (u^2/2)_x = nu u_xx (Eq. burgers, nu > 0) by the local DG method
+  (Section 6: Lax-Friedrichs for the advective term, alternating fluxes for the viscous
+  one): q = u_x in the weak sense, element by element
+      q^e = (2/dx) M^{-1} [ -S u^e + uhat_R e_p - uhat_L e_0 ],      uhat = u^- ,
+  and the viscous term adds nu [ -S q^e + qhat_R e_p - qhat_L e_0 ] to the bracket above,
+  qhat = q^+ (the alternating pair). At a PE face all three face values (uhat, the
+  Lax-Friedrichs flux, qhat) come from the common delayed level through the AT sum.
 * PE decomposition (Section 2, Fig. 2): P contiguous blocks of K/P elements; the face
   between elements e-1 and e is a PE face iff they lie in different PEs (none for P = 1).
   PE face j sits at element j K/P.
@@ -125,6 +132,7 @@ class Problem:
     delays_minus: Optional[np.ndarray] = None  # naive mode: delay seen by the right element
     window_lo: Optional[int] = None            # window mode: global index of local element 0
     K_global: Optional[int] = None             # window mode: elements of the full mesh
+    nu: float = 0.0                            # Burgers viscosity (LDG for nu > 0)
 
     @property
     def dx(self) -> float:
@@ -255,7 +263,7 @@ class Solver:
             for i in range(qe):
                 if c[i] == 0.0:
                     continue
-                TL, TR = self.history[(n - k - i, s)]
+                TL, TR = self.history[(n - k - i, s)][:2]
                 uL, uR = TL[idx], TR[idx]
                 if side == +1:      # left element's view: own u^- current, far u^+ delayed
                     uL = self.history[(n, s)][0][idx]
@@ -266,11 +274,51 @@ class Solver:
             out.append(acc)
         return torch.stack(out)
 
+    def delayed_value(self, n: int, s: int, pick, table, q: int):
+        """AT sum over the stored levels at the PE faces of one stored face quantity: pick maps
+        a stored entry (u^-, u^+, q^+) to its value (common delayed level)."""
+        ks = self.delay(table, n, self.pe_index)
+        out = []
+        for idx in range(self.pe_local.numel()):
+            k = int(ks[idx])
+            qe = min(q, n - k + 1)
+            c = self.coef(k, qe)
+            acc = None
+            for i in range(qe):
+                if c[i] == 0.0:
+                    continue
+                term = c[i] * pick(self.history[(n - k - i, s)], idx)
+                acc = term if acc is None else acc + term
+            out.append(acc)
+        return torch.stack(out)
+
+    def ldg_q(self, Y, uL, n: int, s: int):
+        """q = u_x of the local DG method with uhat = u^- (delayed / AT at PE faces)."""
+        prob = self.prob
+        uhat = uL
+        if prob.mode == "adg" and self.pe_local.numel() > 0:
+            uhat = uL.index_put((self.pe_local,), self.delayed_value(
+                n, s, lambda h, i: h[0][i], prob.delays, prob.q))
+        uhat_R = torch.roll(uhat, -1)
+        if self.window:
+            uhat_R = torch.cat([uhat_R[:-1], Y[-1:, -1]])
+        body = -_matvec_rows(self.S, Y) + uhat_R[:, None] * self.ep[None, :] \
+            - uhat[:, None] * self.e0[None, :]
+        return (2.0 / self.dx) * _matvec_rows(self.Minv, body)
+
     def L(self, Y, n: int, s: int):
         prob = self.prob
         uL, uR = self.traces(Y)
-        if self.pe_local.numel() > 0:
-            self.history[(n, s)] = (uL[self.pe_local], uR[self.pe_local])
+        viscous = prob.pde == "burgers" and prob.nu != 0.0
+        if viscous and prob.mode == "naive":
+            raise ValueError("the viscous operator takes the common-level scheme")
+        Q = None
+        if self.pe_local.numel() > 0:   # the current level's traces (q^+ once it is formed)
+            self.history[(n, s)] = (uL[self.pe_local], uR[self.pe_local], None)
+        if viscous:
+            Q = self.ldg_q(Y, uL, n, s)
+            if self.pe_local.numel() > 0:
+                self.history[(n, s)] = (uL[self.pe_local], uR[self.pe_local], Q[self.pe_local, 0])
         F = self.fhat(uL, uR)
         FL_view = F          # flux used by element f at its left face f
         FR_view = F          # flux used by element f-1 at its right face f
@@ -293,6 +341,16 @@ class Solver:
         fv = self.f(Y)
         body = _matvec_rows(self.S, fv) + FL_view[:, None] * self.e0[None, :] \
             - FR[:, None] * self.ep[None, :]
+        if viscous:
+            qhat = Q[:, 0]                     # q^+ at every face f: Q[f, 0]
+            if prob.mode == "adg" and self.pe_local.numel() > 0:
+                qhat = qhat.index_put((self.pe_local,), self.delayed_value(
+                    n, s, lambda h, i: h[2][i], prob.delays, prob.q))
+            qhat_R = torch.roll(qhat, -1)
+            if self.window:
+                qhat_R = torch.cat([qhat_R[:-1], Q[-1:, -1]])
+            body = body + prob.nu * (-_matvec_rows(self.S, Q) + qhat_R[:, None] * self.ep[None, :]
+                                     - qhat[:, None] * self.e0[None, :])
         return (2.0 / self.dx) * _matvec_rows(self.Minv, body)
 
     # --- time stepping -------------------------------------------------------------------
