@@ -59,6 +59,10 @@ FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # U_s = U_{s-1} + B_s dU_s (one FMA).
 FLOP_PER_DOF_STAGE_LS = 2 * (NP + 2) + 1
 LOW_STORAGE_STAGES = {"rk1": 1, "rk2": 2, "lsrk3": 3, "lsrk4": 5}
+# Viscous Burgers (LDG), per DOF and stage, counted from the two kernels' multiplies and FMAs:
+# the q pass 2 Np + 3, the stage (Lax-Friedrichs part and viscous part) 4 Np + 14.
+VISC_NP = 3
+FLOP_PER_DOF_STAGE_VISC = 6 * VISC_NP + 17
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant; a kernel changed since its counters were taken has no
 # entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.06 MB read
@@ -219,6 +223,38 @@ def caa_timed(steps: int, warmup: int):
     variant = s.variant[0]
     s.close()
     return ms, st, variant
+
+
+def viscous_timed(steps: int, warmup: int):
+    """ALDG(2)-AT2-RK2 of Section 6's viscous Burgers experiment (nu = 0.1, the multi-scale
+    initial condition, L = 3 with probabilities 0.3 / 0.4 / 0.3) on 2^20 elements and 1024
+    PEs, dt = 0.01 dx^2: CUDA-event time of `steps` steps after `warmup`."""
+    import torch
+    import paper_2404_03399_gb300 as adg
+    K = 1 << 20
+    dx = 2 * math.pi / K
+    cfg = adg.Config(pde="burgers", K=K, p=VISC_NP - 1, P=1024, dt=0.01 * dx * dx, nu=0.1,
+                     mode="at", L=3, q=2, probs=[0.3, 0.4, 0.3], seed=5, rk="rk2")
+    u0 = adg.eval_modes(cfg, [3.0, 2.0, 1.0], [2.0, 3.0, 5.0], [0.3, 1.1, 2.0])
+    s = adg.Solver(cfg, u0)
+    del u0
+    stream = torch.cuda.current_stream()
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    s.check_finite_ok = True
+    try:
+        s.check_finite()
+    except adg.AdgError:
+        s.check_finite_ok = False
+    fin = s.check_finite_ok
+    s.close()
+    return ms, K * VISC_NP, fin
 
 
 def e2e_timed(steps: int):
@@ -514,6 +550,15 @@ def main():
                        "exchanges": cst["exchanges"], "sync_exchanges": cst["sync_exchanges"],
                        "exchange_saving": 1.0 - cst["exchanges"] / max(cst["sync_exchanges"], 1),
                        "steps_counted": cst["steps"]}
+        vms, vdof, vfin = viscous_timed(20, 3)
+        vstep = vms / 20 * 1e-3
+        line["viscous_burgers"] = {
+            "value": vdof * 2 / vstep, "unit": UNIT, "ms_per_step": vms / 20, "finite": vfin,
+            "workload": "ALDG(2)-AT2-RK2, nu = 0.1, K = 2^20, 1024 PEs, L = 3 (0.3/0.4/0.3), "
+                        "dt = 0.01 dx^2 (Section 6 viscous Burgers, scaled up)",
+            "fp64_tflops": vdof * 2 * FLOP_PER_DOF_STAGE_VISC / vstep / 1e12,
+            "fp64_frac": vdof * 2 * FLOP_PER_DOF_STAGE_VISC / vstep / 1e12 / fp64_tflops,
+            "kernels": "k_ldg_q (q = u_x) then k_lsrk_stage with the viscous term, per stage"}
         line["low_storage"] = {"schemes": ls, "steps": 10, "mode": "at",
                                "kernel": "k_lsrk_stage (one 2N stage: dt L(U), dU and U updates, "
                                          "PE faces; an odd stage count adds a copy back into u, "

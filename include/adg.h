@@ -101,6 +101,14 @@ enum {
  *               L-1 at every PE face (caa_sync = 2, L = 3: the 2D experiment's cycle).
  *               Overrides seed and probs; 0 <= caa_sync <= 64; ADG_EINVAL together with a
  *               caller table.
+ *   nu        : 0 (default), or the viscosity of viscous Burgers u_t + u u_x = nu u_xx
+ *               (Eq. burgers; pde ADG_BURGERS, nu > 0, finite) by the local DG method of
+ *               Section 6: q = u_x with the alternating flux uhat = u^-, the viscous flux
+ *               qhat = q^+, Lax-Friedrichs for u u_x; at PE faces uhat, the Lax-Friedrichs
+ *               flux and qhat all take the AT sum over the common delayed level. Staged
+ *               kernels, any rk; dt from cfl uses max|u0| only (the diffusive limit
+ *               nu dt / dx^2 is the caller's: give dt or a small cfl). Single instances only
+ *               (adg_batch_init, adg_grad: ADG_EINVAL).
  *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
  *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
  *               composed into one stencil per step, with the delayed / AT flux at PE faces
@@ -135,6 +143,7 @@ typedef struct {
   int64_t table_steps;
   int32_t variant;
   int32_t caa_sync;
+  double nu;
 } adg_config;
 
 /* Fill cfg with defaults: advection, upwind, SSP-RK3, [0, 2 pi], a = 1, cfl = 0.1, sync. */

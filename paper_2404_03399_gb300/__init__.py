@@ -51,6 +51,7 @@ class Config:
     variant: str = "auto"       # "auto" | "staged" | "composed" | "fixed"
     rk: str = "ssprk3"          # "ssprk3" | "rk1" | "rk2" | "lsrk3" | "lsrk4"
     caa_sync: int = 0           # > 0: communication-avoiding delay cycle (Section 6.3)
+    nu: float = 0.0             # > 0: viscous Burgers by the local DG method (Eq. burgers)
 
     def to_c(self):
         c = _abi.AdgConfig()
@@ -68,6 +69,7 @@ class Config:
         c.seed = int(self.seed) & ((1 << 64) - 1)
         c.variant = {"auto": 0, "staged": 1, "composed": 2, "fixed": 3}[self.variant]
         c.caa_sync = int(self.caa_sync)
+        c.nu = float(self.nu)
         keep = []
         if self.probs is not None:
             arr = (C.c_double * len(self.probs))(*[float(v) for v in self.probs])

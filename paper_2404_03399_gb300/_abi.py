@@ -35,7 +35,7 @@ class AdgConfig(C.Structure):
         ("mode", C.c_int32), ("L", C.c_int32), ("at_order", C.c_int32),
         ("seed", C.c_uint64), ("probs", C.POINTER(C.c_double)),
         ("delay_table", C.POINTER(C.c_uint8)), ("table_steps", C.c_int64),
-        ("variant", C.c_int32), ("caa_sync", C.c_int32),
+        ("variant", C.c_int32), ("caa_sync", C.c_int32), ("nu", C.c_double),
     ]
 
 

@@ -275,6 +275,8 @@ std::string check_config(const adg_config *c) {
   if (c->dt == 0 && !(std::isfinite(c->cfl) && c->cfl > 0)) return "cfl must be > 0 when dt == 0";
   if (c->mode != ADG_SYNC && c->mode != ADG_ASYNC && c->mode != ADG_ASYNC_AT) return "bad mode";
   if (c->caa_sync < 0 || c->caa_sync > 64) return "caa_sync must be in 0..64";
+  if (!std::isfinite(c->nu) || c->nu < 0) return "nu must be finite and >= 0";
+  if (c->nu > 0 && c->pde != ADG_BURGERS) return "nu > 0 needs pde ADG_BURGERS";
   if (c->caa_sync > 0 && c->delay_table) return "caa_sync and a caller delay table exclude each other";
   if (c->L < 1 || c->L > ADG_MAX_L) return "L must be in 1..16";
   if (c->at_order < 0 || c->at_order > ADG_MAX_Q) return "at_order must be in 0..5";
@@ -335,6 +337,8 @@ struct InstHost {
   uint8_t *table = nullptr;
   double *coef = nullptr;
   double *w = nullptr, *M = nullptr;
+  double *qbuf = nullptr;    // viscous Burgers: q = u_x of the stage input
+  double *ringq = nullptr;   // ... and the PE faces' q^+ traces
   adg::FxSlot *fx = nullptr; // scale slots of the fixed-point composed step
   double *fd = nullptr;      // ... and its PE faces' stage differences [2][P][3]
   bool fixed_ok = false;     // the composed coefficients fit the fixed-point bounds
@@ -697,8 +701,24 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     }
   }
   I.meta = meta_slot;
+  I.visc = cfg->nu > 0 ? 1 : 0;
+  I.nu = cfg->nu;
+  if (I.visc) {
+    // q = (2/dx) [ D v + M^{-1} e_p (uhat_R - v_p) - M^{-1} e_0 (uhat_L - v_0) ]
+    const Ops &o = h.ops;
+    const ld s2 = 2.0L / (ld)h.dx;
+    for (int i = 0; i < Np; ++i) {
+      for (int j = 0; j < Np; ++j) I.QD[i * Np + j] = (double)(s2 * o.D[i * Np + j]);
+      I.qlR[i] = (double)(s2 * o.Minv[i * Np + (Np - 1)]);
+      I.qlL[i] = (double)(-s2 * o.Minv[i * Np + 0]);
+    }
+  }
 
   const size_t nd = (size_t)K * Np;
+  if (I.visc) {
+    CK(cudaMalloc(&h.qbuf, nd * sizeof(double)));
+    I.qbuf = h.qbuf;
+  }
   CK(cudaMalloc(&h.fields, 3 * nd * sizeof(double)));
   I.u = h.fields;
   I.unext = h.fields;
@@ -787,6 +807,11 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     CK(cudaMalloc(&h.ring, ring_n * sizeof(double2)));
     CK(cudaMemsetAsync(h.ring, 0, ring_n * sizeof(double2), c->stream));
     I.ring = h.ring;
+    if (I.visc) {
+      CK(cudaMalloc(&h.ringq, ring_n * sizeof(double)));
+      CK(cudaMemsetAsync(h.ringq, 0, ring_n * sizeof(double), c->stream));
+      I.ringq = h.ringq;
+    }
     h.TR = std::max(512, 2 * c->G);
     CK(cudaMalloc(&h.table, (size_t)h.TR * I.P));
     I.table = h.table;
@@ -842,6 +867,7 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
       const double *in = I.u;
       for (int s = 0; s < I.ns; ++s) {
         double *out = (s % 2 == 0) ? I.v2 : I.u;
+        if (I.visc) CK(adg::launch_ldg_q(I, in, s, rel, c->stream));
         CK(adg::launch_lsrk_stage(I, s, rel, in, out, c->stream));
         in = out;
       }
@@ -859,7 +885,9 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
         if (c->nfwork > 0)
           CK(adg::launch_batch_faces(c->insts_dev, c->fwork_dev, c->nfwork, s, rel, c->stream));
       } else {
-        CK(adg::launch_stage(c->inst[0].I, s, rel, c->stream));
+        const Inst &I = c->inst[0].I;
+        if (I.visc) CK(adg::launch_ldg_q(I, s == 0 ? I.u : (s == 1 ? I.v1 : I.v2), s, rel, c->stream));
+        CK(adg::launch_stage(I, s, rel, c->stream));
       }
     }
   }
@@ -1360,6 +1388,8 @@ void adg_destroy(adg_ctx *c) {
     cudaFree(h.M);
     cudaFree(h.fx);
     cudaFree(h.fd);
+    cudaFree(h.qbuf);
+    cudaFree(h.ringq);
   }
   cudaFree(c->meta);
   cudaFree(c->insts_dev);
@@ -1444,6 +1474,8 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
     for (int i = 0; i < n && !r; ++i) {
       if (c->inst[i].I.ls)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches need rk = ADG_SSPRK3");
+      else if (c->inst[i].I.visc)
+        r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches take inviscid equations");
       else if (c->inst[i].cfg.variant == ADG_VARIANT_COMPOSED_FIXED && !c->batch_fixed)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) +
                                     ": the fixed-point composed step needs every instance of the "
@@ -1664,6 +1696,7 @@ int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (c->batch) return fail(c, ADG_ESTATE, "adg_grad takes a single-instance context");
   if (c->inst[0].I.ls) return fail(c, ADG_EINVAL, "adg_grad needs rk = ADG_SSPRK3");
+  if (c->inst[0].I.visc) return fail(c, ADG_EINVAL, "adg_grad covers the inviscid equations");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, ADG_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
   if (!target_dev || !grad_u0_dev || !J_out) return fail(c, ADG_EINVAL, "NULL target, gradient or J");
   return run_gradient(c, target_dev, nsteps, ckpt_every, grad_u0_dev, J_out);

@@ -147,5 +147,29 @@ __device__ __forceinline__ double pe_value(const I &inst, int j, int64_t n, int 
   return V;
 }
 
+// The AT value of q^+ at PE face j for step n, stage s (viscous Burgers, alternating flux
+// qhat = q^+): the same sum as pe_value over the stored q^+ traces of levels n-k-i; level n
+// (k = 0) uses the current q^+ (qcur). The ring write happens in the q pass (k_ldg_q).
+template <class I>
+__device__ __forceinline__ double pe_value_q(const I &inst, int j, int64_t n, int s, double qcur) {
+  const int P = inst.P;
+  const int R = inst.R;
+  const double *col = inst.ringq + (size_t)s * P + j;
+  const int nm = (int)(n % R);
+  const DelayAt d = delay_at(inst, j, n);
+  const int k = d.k;
+  auto fetch = [&](int m) -> double {   // q^+ of level n - m, 1 <= m < R
+    int slot = nm - m;
+    if (slot < 0) slot += R;
+    return col[(size_t)slot * inst.ns * P];
+  };
+  double V = __dmul_rn(d.c[0], k == 0 ? qcur : fetch(k));
+  for (int i = 1; i < d.qe; ++i) {
+    const double ci = d.c[i];
+    if (ci != 0.0) V = __dadd_rn(V, __dmul_rn(ci, fetch(k + i)));
+  }
+  return V;
+}
+
 }  // namespace
 }  // namespace adg

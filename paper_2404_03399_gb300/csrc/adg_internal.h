@@ -117,8 +117,15 @@ struct alignas(16) Inst {
   int face_fx;
   int ns;               // stages per step: the ring holds [R][ns][P] stage-input traces
   int ls;               // 1: a 2N low-storage scheme (k_lsrk_stage, coefficients lsA, lsB)
-  int pad_;
+  int visc;             // 1: viscous Burgers by the local DG method (k_ldg_q, then the stage)
   double lsA[kMaxStages], lsB[kMaxStages];
+  // viscous Burgers: nu, q = u_x of the stage input (node-major like the fields), the PE
+  // faces' q^+ traces [R][ns][P], and q = QD v + qlL (uhat_L - v_0) + qlR (uhat_R - v_p)
+  double nu;
+  double *qbuf;
+  double *ringq;
+  double pad2_;
+  double QD[kMaxNp * kMaxNp], qlL[kMaxNp], qlR[kMaxNp];
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
@@ -169,6 +176,10 @@ cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
 // with the delayed / AT flux and the ring write of the stage-input traces at PE faces.
 cudaError_t launch_lsrk_stage(const Inst &I, int s, int rel, const double *uin, double *uout,
                               cudaStream_t st);
+// Viscous Burgers (I.visc): q = u_x of stage `stage`'s input vin by the local DG method into
+// I.qbuf, with the AT value of uhat at PE faces and the owners' ring writes ((u^-, u^+) into
+// I.ring, q^+ into I.ringq); launched before that stage's kernel.
+cudaError_t launch_ldg_q(const Inst &I, const double *vin, int stage, int rel, cudaStream_t s);
 cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                int stage, int rel, int tile, cudaStream_t s);
 // Batched PE-face pass after each batched stage: ring write of the stage-input traces and

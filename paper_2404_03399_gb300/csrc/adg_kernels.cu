@@ -45,7 +45,8 @@ struct LsArgs {
 // of it (e = j Kpe - 1) forms the same value with the same arithmetic and adds lR (Vs - V).
 // The synchronous output is rounded first, so the result is bit-identical to a stage
 // followed by a separate face pass.
-template <int NP, int PDE, int STAGE, int DIR, bool FACES, bool LS = false, class I>
+template <int NP, int PDE, int STAGE, int DIR, bool FACES, bool LS = false, bool VISC = false,
+          class I>
 __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0,
                                            const LsArgs &ls = LsArgs{}) {
   const int K = inst.K;
@@ -158,6 +159,42 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0,
       }
     }
   }
+  if (VISC && PDE == 1) {
+    // Viscous term nu q_x of the local DG method, alternating flux qhat = q^+ (q from the q
+    // pass, k_ldg_q), in the stage's folded constants (C.A = b c2 D / 2, C.lL, C.lR):
+    //   nu ( -2 C.A q + C.lR (qhat_R - q_p) + C.lL (qhat_L - q_0) ),
+    // with qhat_L = q_0 and qhat_R = q^{e+1}_0 at interior faces and the AT value of the stored
+    // q^+ traces at PE faces (both elements of the face alike).
+    double q[NP];
+    {
+      const double *qq = inst.qbuf + ec;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) {
+        q[i] = *qq;
+        qq += K;
+      }
+    }
+    double qRp = __shfl_down_sync(full, q[0], 1);
+    if (edge) qRp = inst.qbuf[fR];
+    double jqL = 0.0, jqR = __dsub_rn(qRp, q[NP - 1]);
+    if (FACES && e < K) {
+      const int Kpe = inst.Kpe;
+      const int jq = e / Kpe;
+      const int r = e - jq * Kpe;
+      if (r == 0) jqL = __dsub_rn(pe_value_q(inst, jq, n, rstage, q[0]), q[0]);
+      if (r == Kpe - 1) {
+        const int jr = jq + 1 == inst.P ? 0 : jq + 1;
+        jqR = __dsub_rn(pe_value_q(inst, jr, n, rstage, qRp), q[NP - 1]);
+      }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      double vq = C.A[i * NP] * q[0];
+#pragma unroll
+      for (int jj = 1; jj < NP; ++jj) vq = fma(C.A[i * NP + jj], q[jj], vq);
+      out[i] = fma(inst.nu, fma(C.lL[i], jqL, fma(C.lR[i], jqR, -2.0 * vq)), out[i]);
+    }
+  }
   if (e < K) {
     double *q = vout + e;
 #pragma unroll
@@ -176,17 +213,84 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0,
   }
 }
 
-template <int NP, int PDE, int STAGE, int DIR, bool FACES>
+template <int NP, int PDE, int STAGE, int DIR, bool FACES, bool VISC = false>
 __global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
   const int64_t n = FACES ? inst.meta[0] + rel : 0;
-  stage_body<NP, PDE, STAGE, DIR, FACES>(inst, blockIdx.x * blockDim.x + threadIdx.x, n);
+  stage_body<NP, PDE, STAGE, DIR, FACES, false, VISC>(inst, blockIdx.x * blockDim.x + threadIdx.x,
+                                                      n);
 }
 
 // Stage ls.s of a 2N low-storage step (Williamson's form; I.ls).
-template <int NP, int PDE, int DIR, bool FACES>
+template <int NP, int PDE, int DIR, bool FACES, bool VISC = false>
 __global__ void __launch_bounds__(kTile) k_lsrk_stage(const Inst inst, int rel, const LsArgs ls) {
   const int64_t n = FACES ? inst.meta[0] + rel : 0;
-  stage_body<NP, PDE, 1, DIR, FACES, true>(inst, blockIdx.x * blockDim.x + threadIdx.x, n, ls);
+  stage_body<NP, PDE, 1, DIR, FACES, true, VISC>(inst, blockIdx.x * blockDim.x + threadIdx.x, n,
+                                                 ls);
+}
+
+// The q pass of viscous Burgers by the local DG method (Eq. burgers, Section 6): q = u_x of
+// the stage input v with the alternating flux uhat = u^- (the left element's right trace),
+//   q^e = (2/dx) [ D v^e + M^{-1} e_p (uhat_R - v^e_p) - M^{-1} e_0 (uhat_L - v^e_0) ]
+//       = QD v^e + qlR (uhat_R - v^e_p) + qlL (uhat_L - v^e_0),
+// uhat_L = v^{e-1}_p and uhat_R = v^e_p at interior faces (the right term vanishes). At a PE
+// face both elements take uhat as the AT sum of the stored u^- traces (pe_value of the upwind
+// kind); its owner stores the stage input's traces (u^-, u^+) and its q^+ = q^e_0 for the
+// later steps.
+template <int NP, bool FACES>
+__global__ void __launch_bounds__(kTile) k_ldg_q(const Inst inst, const double *__restrict__ vin,
+                                                 int stage, int rel) {
+  const int K = inst.K;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  const int ec = e < K ? e : K - 1;
+  double v[NP];
+  {
+    const double *q = vin + ec;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      v[i] = __ldg(q);
+      q += K;
+    }
+  }
+  double vLm = __shfl_up_sync(0xffffffffu, v[NP - 1], 1);
+  if (lane == 0) vLm = __ldg(vin + (NP - 1) * K + (ec == 0 ? K - 1 : ec - 1));
+  double dL = __dsub_rn(vLm, v[0]), dR = 0.0;
+  int jown = -1;
+  if (FACES && e < K) {
+    const int64_t n = inst.meta[0] + rel;
+    const int Kpe = inst.Kpe;
+    const int jq = e / Kpe;
+    const int r = e - jq * Kpe;
+    if (r == 0) {
+      dL = __dsub_rn(pe_value<0, 1>(inst, jq, n, stage, vLm, v[0], true), v[0]);
+      jown = jq;
+    }
+    if (r == Kpe - 1) {
+      const double tr = __ldg(vin + (e + 1 == K ? 0 : e + 1));
+      const int jr = jq + 1 == inst.P ? 0 : jq + 1;
+      dR = __dsub_rn(pe_value<0, 1>(inst, jr, n, stage, v[NP - 1], tr, false), v[NP - 1]);
+    }
+  }
+  if (e >= K) return;
+  double q[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    double acc = inst.QD[i * NP] * v[0];
+#pragma unroll
+    for (int j = 1; j < NP; ++j) acc = fma(inst.QD[i * NP + j], v[j], acc);
+    acc = fma(inst.qlL[i], dL, acc);
+    q[i] = fma(inst.qlR[i], dR, acc);
+  }
+  double *o = inst.qbuf + e;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    *o = q[i];
+    o += K;
+  }
+  if (FACES && jown >= 0) {
+    const int64_t n = inst.meta[0] + rel;
+    inst.ringq[((size_t)(n % inst.R) * inst.ns + stage) * inst.P + jown] = q[0];
+  }
 }
 
 // Composed SSP-RK3 step of upwind advection (a > 0), all faces synchronous (StepConsts):
@@ -975,8 +1079,14 @@ template <int NP, int PDE, int STAGE, int DIR>
 cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
   const int bs = stage_block(I.K);
   const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
-  if (I.async) k_stage<NP, PDE, STAGE, DIR, true><<<grid, bs, 0, s>>>(I, rel);
-  else k_stage<NP, PDE, STAGE, DIR, false><<<grid, bs, 0, s>>>(I, rel);
+  if (PDE == 1 && I.visc) {
+    if (I.async) k_stage<NP, PDE, STAGE, DIR, true, true><<<grid, bs, 0, s>>>(I, rel);
+    else k_stage<NP, PDE, STAGE, DIR, false, true><<<grid, bs, 0, s>>>(I, rel);
+  } else if (I.async) {
+    k_stage<NP, PDE, STAGE, DIR, true><<<grid, bs, 0, s>>>(I, rel);
+  } else {
+    k_stage<NP, PDE, STAGE, DIR, false><<<grid, bs, 0, s>>>(I, rel);
+  }
   return cudaGetLastError();
 }
 
@@ -1013,8 +1123,23 @@ template <int NP, int PDE, int DIR>
 cudaError_t lsrk_np_pde(const Inst &I, int rel, const LsArgs &ls, cudaStream_t s) {
   const int bs = stage_block(I.K);
   const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
-  if (I.async) k_lsrk_stage<NP, PDE, DIR, true><<<grid, bs, 0, s>>>(I, rel, ls);
-  else k_lsrk_stage<NP, PDE, DIR, false><<<grid, bs, 0, s>>>(I, rel, ls);
+  if (PDE == 1 && I.visc) {
+    if (I.async) k_lsrk_stage<NP, PDE, DIR, true, true><<<grid, bs, 0, s>>>(I, rel, ls);
+    else k_lsrk_stage<NP, PDE, DIR, false, true><<<grid, bs, 0, s>>>(I, rel, ls);
+  } else if (I.async) {
+    k_lsrk_stage<NP, PDE, DIR, true><<<grid, bs, 0, s>>>(I, rel, ls);
+  } else {
+    k_lsrk_stage<NP, PDE, DIR, false><<<grid, bs, 0, s>>>(I, rel, ls);
+  }
+  return cudaGetLastError();
+}
+
+template <int NP>
+cudaError_t ldg_q_np(const Inst &I, const double *vin, int stage, int rel, cudaStream_t s) {
+  const int bs = stage_block(I.K);
+  const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
+  if (I.async) k_ldg_q<NP, true><<<grid, bs, 0, s>>>(I, vin, stage, rel);
+  else k_ldg_q<NP, false><<<grid, bs, 0, s>>>(I, vin, stage, rel);
   return cudaGetLastError();
 }
 
@@ -1025,6 +1150,17 @@ cudaError_t lsrk_np(const Inst &I, int rel, const LsArgs &ls, cudaStream_t s) {
 }
 
 }  // namespace
+
+cudaError_t launch_ldg_q(const Inst &I, const double *vin, int stage, int rel, cudaStream_t s) {
+  if (!I.visc || !I.qbuf || stage < 0 || stage >= I.ns) return cudaErrorInvalidValue;
+  switch (I.Np) {
+    case 2: return ldg_q_np<2>(I, vin, stage, rel, s);
+    case 3: return ldg_q_np<3>(I, vin, stage, rel, s);
+    case 4: return ldg_q_np<4>(I, vin, stage, rel, s);
+    case 5: return ldg_q_np<5>(I, vin, stage, rel, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
 
 cudaError_t launch_lsrk_stage(const Inst &I, int s, int rel, const double *uin, double *uout,
                               cudaStream_t st) {

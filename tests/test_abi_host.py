@@ -79,6 +79,15 @@ def test_caa_cycle_matches_oracle(lib, sync, L, first):
     assert np.array_equal(got, odelays.caa_table(P, 40, sync, L, first_step=first))
 
 
+def test_viscosity_settings_rejected(lib):
+    for kw in (dict(pde="advection", nu=0.1), dict(pde="burgers", nu=-1.0),
+               dict(pde="burgers", nu=float("nan"))):
+        cfg = adg.Config(K=8, p=1, P=2, L=2, mode="async", **kw)
+        with pytest.raises(adg.AdgError) as ei:
+            adg.delay_table(cfg, 0, 4)
+        assert ei.value.code == _abi.ADG_EINVAL
+
+
 def test_caa_rejects_bad_settings(lib):
     tbl = np.zeros((2, 2), dtype=np.uint8)
     for kw in (dict(caa_sync=-1), dict(caa_sync=65), dict(caa_sync=2, table=tbl)):

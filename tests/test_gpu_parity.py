@@ -54,7 +54,7 @@ def run_pair(cfg: adg.Config, u0: np.ndarray, steps: int, table=None):
         tbl = None
     prob = dg.Problem(pde=cfg.pde, K=cfg.K, p=cfg.p, P=cfg.P, dt=dt, a=cfg.a, x0=cfg.x0, x1=cfg.x1,
                       mode=_oracle_mode(cfg.mode) if cfg.P > 1 else "sync", q=q, delays=tbl,
-                      rk=cfg.rk)
+                      rk=cfg.rk, nu=cfg.nu)
     ref = dg.run(prob, u0, steps).numpy()
     return got, ref, dt
 
@@ -424,3 +424,53 @@ def test_caa_cycle_matches_oracle_and_counts_exchanges(variant, rk):
     comm = sum(odelays.caa_communicates(n, 2, 3) for n in range(103))
     assert st == {"steps": 103, "exchanges": comm * stages * P, "sync_exchanges": 103 * stages * P}
     assert comm == 42   # 20 full periods of two, and two of the last three steps
+
+
+# --- viscous Burgers by the local DG method (Eq. burgers, Section 6) ----------------------
+
+PAPER_BURGERS = Modes(amp=(3.0, 2.0, 1.0), kappa=(2.0, 3.0, 5.0), phase=(0.3, 1.1, 2.0))
+
+
+@pytest.mark.parametrize("rk,mode,q,K,p,P", [
+    ("ssprk3", "sync", 0, 96, 2, 4),
+    ("ssprk3", "at", 2, 96, 2, 4),
+    ("rk2", "at", 2, 96, 2, 4),        # ALDG(2)-AT2-RK2 of Fig. burgers-solution
+    ("lsrk4", "async", 0, 96, 3, 8),
+])
+def test_viscous_burgers_matches_oracle(rk, mode, q, K, p, P):
+    # nu = 0.1, the paper's multi-scale data, L = 3 with probabilities 0.3 / 0.4 / 0.3;
+    # dt = 0.01 dx^2 (the AT2 scheme's stable range); 40 steps across a graph chunk.
+    dx = TWO_PI / K
+    cfg = adg.Config(pde="burgers", K=K, p=p, P=P, dt=0.01 * dx * dx, nu=0.1, mode=mode, L=3,
+                     q=q, probs=[0.3, 0.4, 0.3], seed=31, rk=rk)
+    u0 = dg.modes_initial(PAPER_BURGERS, K, p)
+    got, ref, _ = run_pair(cfg, u0, 40)
+    assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
+
+
+def test_viscous_zero_delay_is_bitwise_sync():
+    K, p, P = 128, 2, 8
+    dx = TWO_PI / K
+    u0 = torch.tensor(dg.modes_initial(PAPER_BURGERS, K, p), device="cuda")
+    outs = []
+    for mode, table in [("sync", None), ("at", constant_table(1, P, 0))]:
+        cfg = adg.Config(pde="burgers", K=K, p=p, P=P, dt=0.01 * dx * dx, nu=0.1, mode=mode, L=2,
+                         q=2, table=table)
+        s = adg.Solver(cfg, u0)
+        s.step(37)
+        outs.append(s.state().cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
+
+
+def test_viscous_rejections():
+    cfg = adg.Config(pde="burgers", K=64, p=2, P=4, dt=1e-4, nu=0.1, mode="at", L=2, q=2)
+    u0 = adg.eval_modes(cfg, [1.0], [1.0], [0.0], 0.5)
+    with pytest.raises(adg.AdgError) as ei:
+        adg.BatchSolver([cfg, cfg], [u0, u0])
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    s = adg.Solver(cfg, u0)
+    with pytest.raises(adg.AdgError) as ei:
+        s.grad(u0, 4, 2)
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    s.close()
