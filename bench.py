@@ -257,6 +257,43 @@ def viscous_timed(steps: int, warmup: int):
     return ms, K * VISC_NP, fin
 
 
+def euler_timed(steps: int, warmup: int):
+    """ADG(1)-AT2-RK2 with the limiter for the one-dimensional Euler equations (Section 6's
+    Sod experiment, two Riemann problems on [0, 0.02]) on 2^20 elements and 1024 PEs, L = 3
+    with probabilities 0.3 / 0.4 / 0.3, dt = 0.1 dx: CUDA-event time of `steps` steps."""
+    import numpy as np
+    import torch
+    import paper_2404_03399_gb300 as adg
+    K, p = 1 << 20, 1
+    dx = 0.02 / K
+    cfg = adg.Config(pde="euler", K=K, p=p, P=1024, x0=0.0, x1=0.02, dt=0.1 * dx, rk="rk2",
+                     mode="at", L=3, q=2, probs=[0.3, 0.4, 0.3], seed=3, limiter=True)
+    xi, _ = adg.lgl_nodes(p)
+    x = (np.arange(K)[:, None] + (1.0 + np.asarray(xi)[None, :]) / 2.0) * dx
+    inner = (x >= 0.005) & (x < 0.015)
+    rho = np.where(inner, 1.0, 0.125)
+    pr = np.where(inner, 1.0, 0.1)
+    U0 = torch.tensor(np.stack([rho, 0.0 * rho, pr / 0.4]), device="cuda")
+    s = adg.Solver(cfg, U0)
+    del U0
+    stream = torch.cuda.current_stream()
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    fin = True
+    try:
+        s.check_finite()
+    except adg.AdgError:
+        fin = False
+    s.close()
+    return ms, K * (p + 1), fin
+
+
 def e2e_timed(steps: int):
     """Public-API run from host buffers: pinned u0 -> device, adg_init, `steps` steps,
     state -> pinned host; all inside one timed region (wall clock around synchronised
@@ -559,6 +596,13 @@ def main():
             "fp64_tflops": vdof * 2 * FLOP_PER_DOF_STAGE_VISC / vstep / 1e12,
             "fp64_frac": vdof * 2 * FLOP_PER_DOF_STAGE_VISC / vstep / 1e12 / fp64_tflops,
             "kernels": "k_ldg_q (q = u_x) then k_lsrk_stage with the viscous term, per stage"}
+        ems2, edof, efin = euler_timed(20, 3)
+        line["euler_sod"] = {
+            "value": edof * 2 / (ems2 / 20 * 1e-3), "unit": UNIT, "ms_per_step": ems2 / 20,
+            "finite": efin, "components": 3,
+            "workload": "1D Euler, Sod data (two Riemann problems), DG(1), ADG-AT2-RK2 with the "
+                        "TVB-minmod limiter, K = 2^20, 1024 PEs, L = 3 (0.3/0.4/0.3), dt = 0.1 dx",
+            "kernels": "k_euler_stage then k_euler_limit, per stage"}
         line["low_storage"] = {"schemes": ls, "steps": 10, "mode": "at",
                                "kernel": "k_lsrk_stage (one 2N stage: dt L(U), dU and U updates, "
                                          "PE faces; an odd stage count adds a copy back into u, "

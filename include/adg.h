@@ -48,7 +48,7 @@ typedef enum {
   ADG_ESTATE = -6      /* call not valid in the context's current state */
 } adg_status;
 
-enum { ADG_ADVECTION = 0, ADG_BURGERS = 1 };          /* f(u) = a u  |  f(u) = u^2/2 */
+enum { ADG_ADVECTION = 0, ADG_BURGERS = 1, ADG_EULER = 2 }; /* a u | u^2/2 | 1D Euler */
 enum { ADG_UPWIND = 0, ADG_LLF = 1 };                 /* Section 6.1 fluxes */
 enum {                                                  /* time integrator */
   ADG_RK1 = 1,      /* forward Euler, Eq. EulerDG */
@@ -109,6 +109,16 @@ enum {
  *               kernels, any rk; dt from cfl uses max|u0| only (the diffusive limit
  *               nu dt / dx^2 is the caller's: give dt or a small cfl). Single instances only
  *               (adg_batch_init, adg_grad: ADG_EINVAL).
+ *   pde ADG_EULER (flux ADG_LLF): the one-dimensional Euler equations of Section 6's Sod
+ *               experiment, U = (rho, m, E), E = rho u^2 / 2 + p / 0.4 (gamma = 1.4), local
+ *               Lax-Friedrichs flux, SSP Runge-Kutta in Shu and Osher's form (rk ADG_RK1,
+ *               ADG_RK2 = SSP-RK2 as in the paper, ADG_SSPRK3), AT sums of the delayed flux
+ *               at PE faces. Fields are (3, K, p+1) row-major (u0_dev, adg_get_state; the
+ *               components one after another). limiter = 1 applies the TVB-minmod (MUSCL)
+ *               slope limiter to every stage output, keeping slopes |a1| <= tvb_m dx^2 / 2
+ *               (tvb_m = 0: minmod); its stencil ends at PE faces. dt must be given (> 0).
+ *               adg_integral reports the integral of rho. Single instances, staged kernels;
+ *               batches, adg_grad and the composed variants reject it (ADG_EINVAL).
  *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
  *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
  *               composed into one stencil per step, with the delayed / AT flux at PE faces
@@ -144,6 +154,8 @@ typedef struct {
   int32_t variant;
   int32_t caa_sync;
   double nu;
+  int32_t limiter;
+  double tvb_m;
 } adg_config;
 
 /* Fill cfg with defaults: advection, upwind, SSP-RK3, [0, 2 pi], a = 1, cfl = 0.1, sync. */

@@ -26,7 +26,7 @@ from ._abi import AdgError, check, load
 __all__ = ["Config", "Solver", "BatchSolver", "ADGFunction", "eval_modes", "delay_table",
            "lgl_nodes", "AdgError", "load"]
 
-_PDE = {"advection": _abi.ADG_ADVECTION, "burgers": _abi.ADG_BURGERS}
+_PDE = {"advection": _abi.ADG_ADVECTION, "burgers": _abi.ADG_BURGERS, "euler": _abi.ADG_EULER}
 _MODE = {"sync": _abi.ADG_SYNC, "async": _abi.ADG_ASYNC, "at": _abi.ADG_ASYNC_AT}
 
 
@@ -52,12 +52,16 @@ class Config:
     rk: str = "ssprk3"          # "ssprk3" | "rk1" | "rk2" | "lsrk3" | "lsrk4"
     caa_sync: int = 0           # > 0: communication-avoiding delay cycle (Section 6.3)
     nu: float = 0.0             # > 0: viscous Burgers by the local DG method (Eq. burgers)
+    limiter: bool = True        # Euler: TVB-minmod slope limiter on every stage output
+    tvb_m: float = 0.0          # Euler: TVB constant M (0: minmod)
 
     def to_c(self):
         c = _abi.AdgConfig()
         load().adg_config_default(C.byref(c))
         c.pde = _PDE[self.pde]
         c.flux = _abi.ADG_UPWIND if self.pde == "advection" else _abi.ADG_LLF
+        c.limiter = 1 if self.limiter else 0
+        c.tvb_m = float(self.tvb_m)
         c.rk = {"rk1": _abi.ADG_RK1, "rk2": _abi.ADG_RK2, "ssprk3": _abi.ADG_SSPRK3,
                 "lsrk3": _abi.ADG_LSRK3, "lsrk4": _abi.ADG_LSRK4}[self.rk]
         c.K, c.p, c.P = int(self.K), int(self.p), int(self.P)
@@ -89,12 +93,18 @@ def _stream_ptr(stream) -> Optional[int]:
     return stream.cuda_stream
 
 
-def _as_field(x: torch.Tensor, K: int, Np: int) -> torch.Tensor:
+def _shape(cfg) -> tuple:
+    """Field shape: (K, p+1), or (3, K, p+1) for the Euler equations."""
+    return (3, cfg.K, cfg.p + 1) if cfg.pde == "euler" else (cfg.K, cfg.p + 1)
+
+
+def _as_field(x: torch.Tensor, K: int, Np: int, ncomp: int = 1) -> torch.Tensor:
     if not (isinstance(x, torch.Tensor) and x.is_cuda):
         raise ValueError("expected a CUDA tensor")
     x = x.to(torch.float64).contiguous()
-    if tuple(x.shape) != (K, Np):
-        raise ValueError(f"expected shape ({K}, {Np}), got {tuple(x.shape)}")
+    want = (K, Np) if ncomp == 1 else (ncomp, K, Np)
+    if tuple(x.shape) != want:
+        raise ValueError(f"expected shape {want}, got {tuple(x.shape)}")
     return x
 
 
@@ -132,7 +142,7 @@ class Solver:
     def __init__(self, cfg: Config, u0: torch.Tensor, stream: Optional[torch.cuda.Stream] = None):
         self.cfg = cfg
         self.Np = cfg.p + 1
-        u0 = _as_field(u0, cfg.K, self.Np)
+        u0 = _as_field(u0, cfg.K, self.Np, 3 if cfg.pde == "euler" else 1)
         c, keep = cfg.to_c()
         self._stream = stream
         ctx = C.c_void_p()
@@ -153,7 +163,7 @@ class Solver:
 
     def state(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
         if out is None:
-            out = torch.empty((self.cfg.K, self.Np), dtype=torch.float64, device="cuda")
+            out = torch.empty(_shape(self.cfg), dtype=torch.float64, device="cuda")
         n = C.c_int64()
         check(load().adg_get_state(self.ctx, 0, out.data_ptr(), C.byref(n)), self.ctx)
         self.n = n.value
@@ -189,14 +199,14 @@ class Solver:
 
     def misfit(self, target: torch.Tensor) -> float:
         """J = 1/2 ||u - g||_M^2 of the current state against target g."""
-        g = _as_field(target, self.cfg.K, self.Np)
+        g = _as_field(target, self.cfg.K, self.Np, 3 if self.cfg.pde == "euler" else 1)
         J = C.c_double()
         check(load().adg_misfit(self.ctx, 0, g.data_ptr(), C.byref(J)), self.ctx)
         return J.value
 
     def grad(self, target: torch.Tensor, nsteps: int, ckpt_every: int = 50):
         """(J, dJ/du0) of J = 1/2 ||u_N - g||_M^2 over nsteps from the current state."""
-        g = _as_field(target, self.cfg.K, self.Np)
+        g = _as_field(target, self.cfg.K, self.Np, 3 if self.cfg.pde == "euler" else 1)
         out = torch.empty_like(g)
         J = C.c_double()
         check(load().adg_grad(self.ctx, g.data_ptr(), int(nsteps), int(ckpt_every),
@@ -229,7 +239,7 @@ class BatchSolver:
             c, k = cf.to_c()
             arr[i] = c
             keep.append(k)
-            fields.append(_as_field(u, cf.K, cf.p + 1))
+            fields.append(_as_field(u, cf.K, cf.p + 1, 3 if cf.pde == "euler" else 1))
         ptrs = (C.c_void_p * n)(*[f.data_ptr() for f in fields])
         ctx = C.c_void_p()
         check(load().adg_batch_init(arr, ptrs, n, _stream_ptr(stream), C.byref(ctx)))

@@ -8,7 +8,7 @@ from . import build as _build
 
 ADG_OK, ADG_EINVAL, ADG_ENOMEM, ADG_ECUDA, ADG_ENONFINITE, ADG_ETIMEOUT, ADG_ESTATE = \
     0, -1, -2, -3, -4, -5, -6
-ADG_ADVECTION, ADG_BURGERS = 0, 1
+ADG_ADVECTION, ADG_BURGERS, ADG_EULER = 0, 1, 2
 ADG_UPWIND, ADG_LLF = 0, 1
 ADG_RK1, ADG_RK2, ADG_SSPRK3, ADG_LSRK3, ADG_LSRK4 = 1, 2, 3, 4, 5
 ADG_SYNC, ADG_ASYNC, ADG_ASYNC_AT = 0, 1, 2
@@ -36,6 +36,7 @@ class AdgConfig(C.Structure):
         ("seed", C.c_uint64), ("probs", C.POINTER(C.c_double)),
         ("delay_table", C.POINTER(C.c_uint8)), ("table_steps", C.c_int64),
         ("variant", C.c_int32), ("caa_sync", C.c_int32), ("nu", C.c_double),
+        ("limiter", C.c_int32), ("tvb_m", C.c_double),
     ]
 
 

@@ -17,7 +17,8 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libadg.so")
 
-SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_fixed.cu", "adg_adjoint.cu", "adg_static.cu"]
+SOURCES = ["adg_api.cu", "adg_kernels.cu", "adg_fixed.cu", "adg_adjoint.cu", "adg_static.cu",
+           "adg_euler.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I" + INCLUDE, "-I" + CSRC]
 

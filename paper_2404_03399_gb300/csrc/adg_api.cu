@@ -262,7 +262,16 @@ const LsTable *ls_table(int rk) {
 
 std::string check_config(const adg_config *c) {
   if (!c) return "cfg is NULL";
-  if (c->pde != ADG_ADVECTION && c->pde != ADG_BURGERS) return "pde must be ADG_ADVECTION or ADG_BURGERS";
+  if (c->pde != ADG_ADVECTION && c->pde != ADG_BURGERS && c->pde != ADG_EULER)
+    return "pde must be ADG_ADVECTION, ADG_BURGERS or ADG_EULER";
+  if (c->pde == ADG_EULER) {
+    if (c->flux != ADG_LLF) return "Euler uses flux ADG_LLF";
+    if (!(std::isfinite(c->dt) && c->dt > 0)) return "Euler needs dt > 0";
+    if (c->rk != ADG_RK1 && c->rk != ADG_RK2 && c->rk != ADG_SSPRK3)
+      return "Euler takes rk ADG_RK1, ADG_RK2 or ADG_SSPRK3";
+    if (c->limiter != 0 && c->limiter != 1) return "limiter must be 0 or 1";
+    if (!std::isfinite(c->tvb_m) || c->tvb_m < 0) return "tvb_m must be finite and >= 0";
+  }
   if (c->pde == ADG_ADVECTION && c->flux != ADG_UPWIND) return "advection uses flux ADG_UPWIND";
   if (c->pde == ADG_BURGERS && c->flux != ADG_LLF) return "Burgers uses flux ADG_LLF";
   if (c->rk < ADG_RK1 || c->rk > ADG_LSRK4) return "rk must be one of ADG_RK1 .. ADG_LSRK4";
@@ -556,11 +565,12 @@ void fold_step_constants(InstHost &h) {
   h.I.face_fx = ok ? 1 : 0;
 }
 
-int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out) {
+int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out,
+           const double *field = nullptr) {
   const int nb = adg::reduce_blocks(h.I.K);
   const double *wm = kind == 3 ? h.M : h.w;
-  CK(adg::launch_reduce(kind, h.I.u, g, h.I.K, h.I.Np, wm, scale, c->partials, nb, c->red_out,
-                        c->stream));
+  CK(adg::launch_reduce(kind, field ? field : h.I.u, g, h.I.K, h.I.Np, wm, scale, c->partials, nb,
+                        c->red_out, c->stream));
   CK(cudaMemcpyAsync(c->pinned, c->red_out, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   *host_out = c->pinned[0];
@@ -703,7 +713,27 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   I.meta = meta_slot;
   I.visc = cfg->nu > 0 ? 1 : 0;
   I.nu = cfg->nu;
-  if (I.visc) {
+  I.euler = cfg->pde == ADG_EULER ? 1 : 0;
+  if (I.euler) {
+    // SSP Runge-Kutta in Shu and Osher's form (stage constants below), the limiter's weights
+    I.ls = 0;
+    I.ns = cfg->rk == ADG_RK1 ? 1 : (cfg->rk == ADG_RK2 ? 2 : 3);
+    I.limiter = cfg->limiter;
+    I.tvb_m = cfg->tvb_m;
+    I.dx = h.dx;
+    const Ops &o = h.ops;
+    for (int j = 0; j < Np; ++j) {
+      ld a = 0, b = 0;
+      for (int i = 0; i < Np; ++i) {
+        a += o.M[i * Np + j];
+        b += o.M[j * Np + i] * o.x[i];
+      }
+      I.avg_w[j] = (double)(0.5L * a);
+      I.p1_w[j] = (double)(1.5L * b);
+      I.xi[j] = (double)o.x[j];
+    }
+  }
+  if (I.visc || I.euler) {
     // q = (2/dx) [ D v + M^{-1} e_p (uhat_R - v_p) - M^{-1} e_0 (uhat_L - v_0) ]
     const Ops &o = h.ops;
     const ld s2 = 2.0L / (ld)h.dx;
@@ -719,13 +749,19 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     CK(cudaMalloc(&h.qbuf, nd * sizeof(double)));
     I.qbuf = h.qbuf;
   }
-  CK(cudaMalloc(&h.fields, 3 * nd * sizeof(double)));
+  // u | v1 | v2 (| w: Euler's raw stage output under the limiter), ncomp components each
+  const int ncomp = I.euler ? 3 : 1;
+  const size_t fnd = ncomp * nd;
+  const int nfields = (I.euler && I.limiter) ? 4 : 3;
+  CK(cudaMalloc(&h.fields, nfields * fnd * sizeof(double)));
   I.u = h.fields;
   I.unext = h.fields;
-  I.v1 = h.fields + nd;
-  I.v2 = h.fields + 2 * nd;
-  CK(adg::launch_to_internal(u0_dev, I.u, K, Np, c->stream));
-  CK(cudaMemsetAsync(I.v1, 0, 2 * nd * sizeof(double), c->stream));
+  I.v1 = h.fields + fnd;
+  I.v2 = h.fields + 2 * fnd;
+  I.w = nfields == 4 ? h.fields + 3 * fnd : nullptr;
+  for (int comp = 0; comp < ncomp; ++comp)
+    CK(adg::launch_to_internal(u0_dev + comp * nd, I.u + comp * nd, K, Np, c->stream));
+  CK(cudaMemsetAsync(I.v1, 0, (nfields - 1) * fnd * sizeof(double), c->stream));
 
   // weights and mass matrix for reductions
   std::vector<double> wd(Np), Md(Np * Np);
@@ -737,10 +773,13 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   CK(cudaMemcpyAsync(h.M, Md.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
   CK(cudaStreamSynchronize(c->stream));
 
-  double nonfinite = 0;
-  int r = reduce(c, h, 2, nullptr, 1.0, &nonfinite);
-  if (r) return r;
-  if (nonfinite != 0) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
+  int r = ADG_OK;
+  for (int comp = 0; comp < ncomp; ++comp) {
+    double nonfinite = 0;
+    r = reduce(c, h, 2, nullptr, 1.0, &nonfinite, I.u + comp * nd);
+    if (r) return r;
+    if (nonfinite != 0) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
+  }
 
   if (cfg->dt > 0) {
     h.dt = cfg->dt;
@@ -753,7 +792,16 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     }
     h.dt = (cfg->cfl * h.dx) / speed;
   }
+  I.dt = h.dt;
   fold_constants(h);
+  if (I.euler) {
+    const double so[3][3][2] = {{{0.0, 1.0}}, {{0.0, 1.0}, {0.5, 0.5}},
+                                {{0.0, 1.0}, {0.75, 0.25}, {1.0 / 3.0, 2.0 / 3.0}}};
+    for (int s = 0; s < I.ns; ++s) {
+      I.sc[s].alpha = so[I.ns - 1][s][0];
+      I.sc[s].beta = so[I.ns - 1][s][1];
+    }
+  }
   {
     const bool eligible = cfg->pde == ADG_ADVECTION && cfg->a > 0 && K >= 8 &&
                           (!I.async || I.Kpe >= 8) && !I.ls;
@@ -803,7 +851,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     CK(cudaMalloc(&h.coef, coef.size() * sizeof(double)));
     CK(cudaMemcpy(h.coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice));
     I.coef = h.coef;
-    const size_t ring_n = (size_t)I.R * I.ns * I.P;
+    const size_t ring_n = (size_t)I.R * I.ns * I.P * (I.euler ? 3 : 1);
     CK(cudaMalloc(&h.ring, ring_n * sizeof(double2)));
     CK(cudaMemsetAsync(h.ring, 0, ring_n * sizeof(double2), c->stream));
     I.ring = h.ring;
@@ -856,6 +904,29 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
                                       rel % 2, 1 - rel % 2, 0, c->batch_fixed, rel, c->stream,
                                       c->batch_fixed ? c->bu.get() : nullptr));
     if (nsteps % 2) CK(adg::launch_batch_copy_back(c->insts_dev, c->work_dev, c->nwork, c->stream));
+    CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
+    return ADG_OK;
+  }
+  if (!c->batch && c->inst[0].I.euler) {
+    // Euler: each stage from its input (u, v1, v2) into the raw buffer w and the limiter into
+    // the stage's field (v1, v2; u for the last), or straight into it without the limiter (a
+    // single stage goes through v1: it reads its input's neighbours)
+    const Inst &I = c->inst[0].I;
+    const size_t fbytes = 3 * (size_t)I.K * I.Np * sizeof(double);
+    for (int rel = 0; rel < nsteps; ++rel) {
+      for (int s = 0; s < I.ns; ++s) {
+        double *dst = (s == I.ns - 1) ? I.u : (s == 0 ? I.v1 : I.v2);
+        if (I.limiter) {
+          CK(adg::launch_euler_stage(I, s, rel, I.w, c->stream));
+          CK(adg::launch_euler_limit(I, I.w, dst, c->stream));
+        } else if (I.ns == 1) {
+          CK(adg::launch_euler_stage(I, 0, rel, I.v1, c->stream));
+          CK(cudaMemcpyAsync(I.u, I.v1, fbytes, cudaMemcpyDeviceToDevice, c->stream));
+        } else {
+          CK(adg::launch_euler_stage(I, s, rel, dst, c->stream));
+        }
+      }
+    }
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
   }
@@ -1350,6 +1421,7 @@ void adg_config_default(adg_config *cfg) {
   cfg->cfl = 0.1;
   cfg->mode = ADG_SYNC;
   cfg->L = 1;
+  cfg->limiter = 1;
 }
 
 int adg_comm_stats(const adg_ctx *c, int32_t index, int64_t *steps_out, int64_t *exchanges_out,
@@ -1474,8 +1546,8 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
     for (int i = 0; i < n && !r; ++i) {
       if (c->inst[i].I.ls)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches need rk = ADG_SSPRK3");
-      else if (c->inst[i].I.visc)
-        r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches take inviscid equations");
+      else if (c->inst[i].I.visc || c->inst[i].I.euler)
+        r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches take the inviscid scalar equations");
       else if (c->inst[i].cfg.variant == ADG_VARIANT_COMPOSED_FIXED && !c->batch_fixed)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) +
                                     ": the fixed-point composed step needs every instance of the "
@@ -1601,7 +1673,9 @@ int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out) {
   if (index < 0 || index >= (int)c->inst.size()) return fail(c, ADG_EINVAL, "bad instance index");
   if (!u_dev) return fail(c, ADG_EINVAL, "u_dev is NULL");
   InstHost &h = c->inst[index];
-  CK(adg::launch_to_external(h.I.u, u_dev, h.I.K, h.I.Np, c->stream));
+  const size_t nd = (size_t)h.I.K * h.I.Np;
+  for (int comp = 0; comp < (h.I.euler ? 3 : 1); ++comp)
+    CK(adg::launch_to_external(h.I.u + comp * nd, u_dev + comp * nd, h.I.K, h.I.Np, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (step_out) *step_out = c->n;
   return ADG_OK;
@@ -1648,10 +1722,13 @@ int adg_misfit(adg_ctx *c, int32_t index, const double *target_dev, double *J_ou
 int adg_check_finite(adg_ctx *c) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   for (size_t i = 0; i < c->inst.size(); ++i) {
-    double cnt = 0;
-    int r = reduce(c, c->inst[i], 2, nullptr, 1.0, &cnt);
-    if (r) return r;
-    if (cnt != 0) return fail(c, ADG_ENONFINITE, "instance " + std::to_string(i) + " holds NaN or Inf");
+    InstHost &h = c->inst[i];
+    for (int comp = 0; comp < (h.I.euler ? 3 : 1); ++comp) {
+      double cnt = 0;
+      int r = reduce(c, h, 2, nullptr, 1.0, &cnt, h.I.u + (size_t)comp * h.I.K * h.I.Np);
+      if (r) return r;
+      if (cnt != 0) return fail(c, ADG_ENONFINITE, "instance " + std::to_string(i) + " holds NaN or Inf");
+    }
   }
   return ADG_OK;
 }
@@ -1696,7 +1773,8 @@ int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (c->batch) return fail(c, ADG_ESTATE, "adg_grad takes a single-instance context");
   if (c->inst[0].I.ls) return fail(c, ADG_EINVAL, "adg_grad needs rk = ADG_SSPRK3");
-  if (c->inst[0].I.visc) return fail(c, ADG_EINVAL, "adg_grad covers the inviscid equations");
+  if (c->inst[0].I.visc || c->inst[0].I.euler)
+    return fail(c, ADG_EINVAL, "adg_grad covers the inviscid scalar equations");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, ADG_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
   if (!target_dev || !grad_u0_dev || !J_out) return fail(c, ADG_EINVAL, "NULL target, gradient or J");
   return run_gradient(c, target_dev, nsteps, ckpt_every, grad_u0_dev, J_out);

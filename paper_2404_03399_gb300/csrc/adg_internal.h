@@ -124,8 +124,16 @@ struct alignas(16) Inst {
   double nu;
   double *qbuf;
   double *ringq;
-  double pad2_;
+  double dt;            // the step (viscous Burgers and Euler kernels)
   double QD[kMaxNp * kMaxNp], qlL[kMaxNp], qlR[kMaxNp];
+  // Euler (pde 2): three components per field (component c at field + c K Np), the raw stage
+  // output w when the limiter is on, and the limiter's weights: cell average a0 = avg_w . v,
+  // P_1 coefficient a1 = p1_w . v, nodes xi; TVB constant tvb_m, element width dx
+  int euler, limiter;
+  double tvb_m, dx;
+  double *w;
+  double avg_w[kMaxNp], p1_w[kMaxNp], xi[kMaxNp];
+  double pad3_;
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
@@ -180,6 +188,10 @@ cudaError_t launch_lsrk_stage(const Inst &I, int s, int rel, const double *uin, 
 // I.qbuf, with the AT value of uhat at PE faces and the owners' ring writes ((u^-, u^+) into
 // I.ring, q^+ into I.ringq); launched before that stage's kernel.
 cudaError_t launch_ldg_q(const Inst &I, const double *vin, int stage, int rel, cudaStream_t s);
+// Euler (I.euler, adg_euler.cu): stage `stage` of SSP-RK in Shu and Osher's form from its input
+// (u, v1, v2 by stage) into dst, and the slope limiter src -> dst (src != dst).
+cudaError_t launch_euler_stage(const Inst &I, int stage, int rel, double *dst, cudaStream_t s);
+cudaError_t launch_euler_limit(const Inst &I, const double *src, double *dst, cudaStream_t s);
 cudaError_t launch_batch_stage(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                int stage, int rel, int tile, cudaStream_t s);
 // Batched PE-face pass after each batched stage: ring write of the stage-input traces and

@@ -88,6 +88,14 @@ def test_viscosity_settings_rejected(lib):
         assert ei.value.code == _abi.ADG_EINVAL
 
 
+def test_euler_settings_rejected(lib):
+    for kw in (dict(dt=0.0), dict(dt=1e-6, rk="lsrk4"), dict(dt=1e-6, tvb_m=-1.0)):
+        cfg = adg.Config(pde="euler", K=8, p=1, P=2, L=2, mode="async", **kw)
+        with pytest.raises(adg.AdgError) as ei:
+            adg.delay_table(cfg, 0, 4)
+        assert ei.value.code == _abi.ADG_EINVAL
+
+
 def test_caa_rejects_bad_settings(lib):
     tbl = np.zeros((2, 2), dtype=np.uint8)
     for kw in (dict(caa_sync=-1), dict(caa_sync=65), dict(caa_sync=2, table=tbl)):

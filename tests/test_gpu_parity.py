@@ -474,3 +474,60 @@ def test_viscous_rejections():
         s.grad(u0, 4, 2)
     assert ei.value.code == adg._abi.ADG_EINVAL
     s.close()
+
+
+# --- one-dimensional Euler equations (Section 6, Sod's shock tube) -----------------------
+
+from oracle import euler as oeuler  # noqa: E402
+
+
+def _euler_case(case):
+    if case.startswith("sod"):
+        K, p = 256, 1
+        x = dg.node_coordinates(K, p, 0.0, 0.02)
+        U0 = oeuler.conserved(*oeuler.sod_periodic(x, 0.0))
+        return K, p, U0, True, 0.1 * 0.02 / K
+    K, p = 96, 2
+    x = dg.node_coordinates(K, p, 0.0, 0.02)
+    U0 = oeuler.conserved(1 + 0.2 * np.sin(2 * math.pi * x / 0.02), 1 + 0 * x, 1 + 0 * x)
+    return K, p, U0, False, 0.05 * 0.02 / K
+
+
+@pytest.mark.parametrize("case,rk,mode,q", [
+    ("sod", "rk2", "sync", 0),        # DG(1)-RK2 with the limiter
+    ("sod_at", "rk2", "at", 2),       # ADG(1)-AT2-RK2 with the limiter (L = 3, 0.3/0.4/0.3)
+    ("sod_at3", "ssprk3", "at", 2),
+    ("wave", "ssprk3", "sync", 0),    # smooth wave, no limiter, p = 2
+    ("wave_async", "rk1", "async", 0),
+])
+def test_euler_matches_oracle(case, rk, mode, q):
+    K, p, U0, lim, dt = _euler_case(case)
+    P, L, steps, probs = 8, 3, 60, [0.3, 0.4, 0.3]
+    cfg = adg.Config(pde="euler", K=K, p=p, P=P, x0=0.0, x1=0.02, dt=dt, rk=rk, mode=mode, L=L,
+                     q=q, probs=probs, seed=17, limiter=lim)
+    s = adg.Solver(cfg, torch.tensor(U0, device="cuda"))
+    s.step(steps)
+    got = s.state().cpu().numpy()
+    s.close()
+    tbl = odelays.delay_table(17, P, steps, L, probs) if mode != "sync" else None
+    prob = oeuler.EulerProblem(K=K, p=p, P=P, dt=dt, rk=rk, mode="adg" if mode != "sync" else "sync",
+                               q=q if mode == "at" else 1, delays=tbl, limiter=lim)
+    ref = oeuler.run(prob, U0, steps).numpy()
+    assert np.all(np.isfinite(got))
+    assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
+
+
+def test_euler_rejections():
+    K = 32
+    x = dg.node_coordinates(K, 1, 0.0, 0.02)
+    U0 = torch.tensor(oeuler.conserved(*oeuler.sod_periodic(x, 0.0)), device="cuda")
+    cfg = adg.Config(pde="euler", K=K, p=1, P=4, x0=0.0, x1=0.02, dt=1e-6, rk="rk2", mode="at",
+                     L=2, q=2)
+    with pytest.raises(adg.AdgError) as ei:
+        adg.BatchSolver([cfg, cfg], [U0, U0])
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    s = adg.Solver(cfg, U0)
+    with pytest.raises(adg.AdgError) as ei:
+        s.grad(U0, 2, 1)
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    s.close()
