@@ -474,6 +474,9 @@ def main():
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                     help="only time adg_grad against the forward on the adjoint workload for STEPS "
                          "steps (one repeat) and print that dict (for profiling runs)")
+    ap.add_argument("--extra-only", choices=["lsrk4", "viscous", "euler"], default=None,
+                    help="only time that extra workload (the LSRK4 scheme on the large mesh, "
+                         "viscous Burgers, Euler) and print its dict (for profiling runs)")
     ap.add_argument("--batched-only", type=int, default=0, metavar="STEPS",
                     help="only time the batched workload for STEPS steps and print that dict "
                          "(for profiling runs)")
@@ -492,6 +495,18 @@ def main():
     adg.load()
     if args.adjoint_only:
         print(json.dumps(adjoint_cost(args.adjoint_only, 1)), flush=True)
+        return
+    if args.extra_only:
+        if args.extra_only == "lsrk4":
+            ms, _, fin, (var, _) = device_timed("at", 4, 2, lambda: None, False, local, "lsrk4")
+            out = {"lsrk4_ms_per_step": ms / 4, "finite": fin, "variant": var}
+        elif args.extra_only == "viscous":
+            ms, dof, fin = viscous_timed(4, 2)
+            out = {"viscous_ms_per_step": ms / 4, "dof": dof, "finite": fin}
+        else:
+            ms, dof, fin = euler_timed(4, 2)
+            out = {"euler_ms_per_step": ms / 4, "dof": dof, "finite": fin}
+        print(json.dumps(out), flush=True)
         return
     if args.batched_only:
         rate, ms, ndof, n, variant = batched_timed(args.batched_only, 3)
