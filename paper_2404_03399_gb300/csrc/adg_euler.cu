@@ -21,28 +21,42 @@ namespace {
 
 constexpr double kGamma = 1.4;
 
+// Flux f(U) of a state (u = m / rho through one division 1/rho, as below).
 __device__ __forceinline__ void euler_flux(const double U[3], double f[3]) {
-  const double u = U[1] / U[0];
+  const double u = U[1] * (1.0 / U[0]);
   const double p = (kGamma - 1.0) * (U[2] - 0.5 * U[1] * u);
   f[0] = U[1];
   f[1] = fma(U[1], u, p);
   f[2] = (U[2] + p) * u;
 }
 
-__device__ __forceinline__ double wave_speed(const double U[3]) {
-  const double u = U[1] / U[0];
+// Flux f(U) and wave speed |u| + c of a state, with one division (1/rho) and one square root.
+__device__ __forceinline__ void euler_flux_speed(const double U[3], double f[3], double &speed) {
+  const double r = 1.0 / U[0];
+  const double u = U[1] * r;
   const double p = (kGamma - 1.0) * (U[2] - 0.5 * U[1] * u);
-  return fabs(u) + sqrt(kGamma * p / U[0]);
+  f[0] = U[1];
+  f[1] = fma(U[1], u, p);
+  f[2] = (U[2] + p) * u;
+  speed = fabs(u) + sqrt(kGamma * p * r);
 }
 
-// Local Lax-Friedrichs flux of traces UL = U^-, UR = U^+.
-__device__ __forceinline__ void euler_llf(const double UL[3], const double UR[3], double F[3]) {
-  double fl[3], fr[3];
-  euler_flux(UL, fl);
-  euler_flux(UR, fr);
-  const double lam = fmax(wave_speed(UL), wave_speed(UR));
+// Local Lax-Friedrichs flux from the traces' states, fluxes and wave speeds.
+__device__ __forceinline__ void euler_llf_from(const double UL[3], const double UR[3],
+                                               const double fl[3], const double fr[3], double sl,
+                                               double sr, double F[3]) {
+  const double lam = fmax(sl, sr);
 #pragma unroll
   for (int c = 0; c < 3; ++c) F[c] = 0.5 * (fl[c] + fr[c]) - 0.5 * lam * (UR[c] - UL[c]);
+}
+
+// Local Lax-Friedrichs flux of traces UL = U^-, UR = U^+ (the same arithmetic as the
+// interior faces, so a zero delay reproduces the synchronous flux bit for bit).
+__device__ __forceinline__ void euler_llf(const double UL[3], const double UR[3], double F[3]) {
+  double fl[3], fr[3], sl, sr;
+  euler_flux_speed(UL, fl, sl);
+  euler_flux_speed(UR, fr, sr);
+  euler_llf_from(UL, UR, fl, fr, sl, sr, F);
 }
 
 // AT value of the flux at PE face j, step n, stage s from the ring [R][ns][3][P] of (U^-, U^+)
@@ -108,21 +122,53 @@ __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, do
   const bool edge = (lane == 31) || (ec + 1 >= K);
   const int fR = ec + 1 >= K ? 0 : ec + 1;
   const int fL = ec == 0 ? K - 1 : ec - 1;
-  double VLm[3], VRp[3], V0[3], Vp[3];
+  // node fluxes, and the wave speeds of the two end nodes
+  double f[3][NP], s0 = 0.0, sp = 0.0;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    const double Ui[3] = {V[0][i], V[1][i], V[2][i]};
+    double fi[3];
+    if (i == 0 || i == NP - 1) {
+      double si;
+      euler_flux_speed(Ui, fi, si);
+      if (i == 0) s0 = si;
+      if (i == NP - 1) sp = si;
+    } else {
+      euler_flux(Ui, fi);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) f[c][i] = fi[c];
+  }
+  // left face: U^- with its flux and speed from the left neighbour's last node (lane 0 forms
+  // them from a load), U^+ this element's first node
+  double VLm[3], VRp[3], V0[3], Vp[3], fLm[3], f0[3], fp[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
     V0[c] = V[c][0];
     Vp[c] = V[c][NP - 1];
+    f0[c] = f[c][0];
+    fp[c] = f[c][NP - 1];
     VLm[c] = __shfl_up_sync(full, Vp[c], 1);
-    if (lane == 0) VLm[c] = __ldg(vin + c * nd + (size_t)(NP - 1) * K + fL);
+    fLm[c] = __shfl_up_sync(full, fp[c], 1);
     VRp[c] = __shfl_down_sync(full, V0[c], 1);
-    if (edge) VRp[c] = __ldg(vin + c * nd + fR);
+  }
+  double sLm = __shfl_up_sync(full, sp, 1);
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) VLm[c] = __ldg(vin + c * nd + (size_t)(NP - 1) * K + fL);
+    euler_flux_speed(VLm, fLm, sLm);
   }
   double FL[3], FR[3];
-  euler_llf(VLm, V0, FL);
+  euler_llf_from(VLm, V0, fLm, f0, sLm, s0, FL);
 #pragma unroll
   for (int c = 0; c < 3; ++c) FR[c] = __shfl_down_sync(full, FL[c], 1);
-  if (edge) euler_llf(Vp, VRp, FR);
+  if (edge) {
+    double fRp[3], sRp;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) VRp[c] = __ldg(vin + c * nd + fR);
+    euler_flux_speed(VRp, fRp, sRp);
+    euler_llf_from(Vp, VRp, fp, fRp, sp, sRp, FR);
+  }
   if (FACES && e < K) {
     const int64_t n = I.meta[0] + rel;
     const int Kpe = I.Kpe;
@@ -132,14 +178,6 @@ __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, do
     if (r == Kpe - 1) euler_pe_flux(I, jq + 1 == I.P ? 0 : jq + 1, n, STAGE, Vp, VRp, false, FR);
   }
   if (e >= K) return;
-  double f[3][NP];
-#pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    double Ui[3] = {V[0][i], V[1][i], V[2][i]}, fi[3];
-    euler_flux(Ui, fi);
-#pragma unroll
-    for (int c = 0; c < 3; ++c) f[c][i] = fi[c];
-  }
   const double dt = I.dt;
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -170,22 +208,33 @@ __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, do
   }
 }
 
-// minmod of 2 a1 and the used differences, halved (0 where the signs disagree).
+// Sign of a non-NaN double from its bit pattern (-0 and +0 give 0).
+__device__ __forceinline__ int bit_sign(long long b) { return b > 0 ? 1 : ((b << 1) != 0 ? -1 : 0); }
+
+// minmod of 2 a1 and the used differences, halved (0 where the signs disagree). Signs,
+// magnitudes and minima are taken on the IEEE bit patterns (integer pipe): for non-negative
+// doubles the patterns order like the values.
 __device__ __forceinline__ double limited_slope(double a1, double dp, double dm, bool use_p,
                                                 bool use_m) {
-  const double two = 2.0 * a1;
-  const bool pos = two > 0.0, neg = two < 0.0;
-  double mag = fabs(two);
-  bool ok = pos || neg;
+  const long long mask = 0x7fffffffffffffffLL;
+  const long long bt = __double_as_longlong(2.0 * a1);
+  const int st = bit_sign(bt);
+  long long mag = bt & mask;
+  bool ok = st != 0;
   if (use_p) {
-    ok = ok && ((dp > 0.0) == pos) && ((dp < 0.0) == neg);
-    mag = fmin(mag, fabs(dp));
+    const long long b = __double_as_longlong(dp);
+    ok = ok && bit_sign(b) == st;
+    const long long m = b & mask;
+    mag = m < mag ? m : mag;
   }
   if (use_m) {
-    ok = ok && ((dm > 0.0) == pos) && ((dm < 0.0) == neg);
-    mag = fmin(mag, fabs(dm));
+    const long long b = __double_as_longlong(dm);
+    ok = ok && bit_sign(b) == st;
+    const long long m = b & mask;
+    mag = m < mag ? m : mag;
   }
-  return ok ? 0.5 * (pos ? mag : -mag) : 0.0;
+  const double r = 0.5 * __longlong_as_double(mag);
+  return ok ? (st > 0 ? r : -r) : 0.0;
 }
 
 template <int NP>
@@ -237,7 +286,7 @@ __global__ void __launch_bounds__(kTile) k_euler_limit(const Inst I, const doubl
     }
     if (e >= K) continue;
     double a1n = limited_slope(a1, aR - a0, a0 - aL, use_p, use_m);
-    if (fabs(a1) <= keep) a1n = a1;
+    if ((__double_as_longlong(a1) & 0x7fffffffffffffffLL) <= __double_as_longlong(keep)) a1n = a1;
     double *o = dst + c * nd + e;
     const bool change = a1n != a1;
 #pragma unroll
