@@ -105,6 +105,19 @@ def test_ragged_sizes(K, P, variant):
     assert rel_linf(got, ref) < TOL
 
 
+@pytest.mark.parametrize("seed", [1, 3])
+def test_fixed_point_rough_data_long_delays(seed):
+    # Random nodal data, delays up to 7 and AT3: in the oracle the PE-face differences |T - V|
+    # reach 3.7 (seed 1) and 4.2 (seed 3) times max|u|, past 2^57 units at the integer step's
+    # working scale, so there the integer correction hands over to its FP64 sum.
+    K, p = 512, 3
+    cfg = adg.Config(pde="advection", K=K, p=p, P=16, cfl=0.05, mode="at", L=8, q=3, seed=seed,
+                     variant="fixed")
+    u0 = random_nodal(K, p, 40 + seed)
+    got, ref, _ = run_pair(cfg, u0, 40)
+    assert rel_linf(got, ref) < TOL
+
+
 def test_negative_speed_upwinds_from_the_right():
     cfg = adg.Config(pde="advection", K=128, p=2, P=4, a=-0.8, cfl=0.02, mode="at", L=3, q=2, seed=3)
     u0 = dg.modes_initial(PAPER_FIG6, 128, 2)
