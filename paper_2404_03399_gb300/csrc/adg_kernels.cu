@@ -540,8 +540,10 @@ __device__ __forceinline__ void face_diffs(const Inst &I, int j, const FaceLoads
 // result of elements e-1 .. e+2. Every load (delay, ring levels of all three stages, inputs,
 // outputs) is issued before any of them is used. A zero delay gives d_s = 0 exactly and leaves
 // the composed result as it is. Windows of different faces are disjoint when Kpe >= 8. fmt:
-// the fixed-point step's formats (bit 0: uin, bit 1: uout int64 at the step's scale); the
-// arithmetic here is FP64.
+// the fixed-point step's formats (bit 0: uin, bit 1: uout int64 at the step's scale). The
+// AT sums and the stage-by-stage traces are FP64; with an int64 input the synchronous traces,
+// and with an int64 output the correction itself, are formed in the step's integer limbs (as in
+// k_face_step, so batched and single runs agree bit for bit).
 template <int NP>
 __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__restrict__ uin,
                                            void *__restrict__ uout, int rel, int fmt) {
