@@ -346,6 +346,7 @@ struct InstHost {
   uint8_t *table = nullptr;
   double *coef = nullptr;
   double *w = nullptr, *M = nullptr;
+  int stages = 3;            // stages per step of the RK scheme (the ring may keep more slots)
   double *qbuf = nullptr;    // viscous Burgers: q = u_x of the stage input
   double *ringq = nullptr;   // ... and the PE faces' q^+ traces
   adg::FxSlot *fx = nullptr; // scale slots of the fixed-point composed step
@@ -436,12 +437,40 @@ void fold_constants(InstHost &h) {
 
 // Composed step constants (StepConsts in adg_internal.h), built in long double from the
 // unrounded stage constants of upwind advection with a > 0.
+// Butcher form (a, b) of the 2N scheme of rk (ls_table): with k_j = L(U_{j-1}), stage s+1's
+// input U_s = u + dt sum_{j<=s} a_{s+1,j} k_j, a_{s+1,j} = sum_{r=j}^{s} B_r A_{j+1} ... A_r,
+// and b_j the same sum for s = S.
+void two_register_butcher(int rk, int &S, ld a[adg::kMaxStages][adg::kMaxStages],
+                          ld b[adg::kMaxStages]) {
+  const LsTable *t = ls_table(rk);
+  S = t->S;
+  ld A[adg::kMaxStages], B[adg::kMaxStages];
+  for (int s = 0; s < S; ++s) {
+    A[s] = (ld)t->A[s].n / (ld)t->A[s].d;
+    B[s] = (ld)t->B[s].n / (ld)t->B[s].d;
+  }
+  auto coef = [&](int s, int j) {   // weight of dt k_j in U_s
+    ld tot = 0;
+    for (int r = j; r < s; ++r) {
+      ld prod = 1;
+      for (int m = j + 1; m <= r; ++m) prod *= A[m];
+      tot += B[r] * prod;
+    }
+    return tot;
+  };
+  for (int s = 0; s < adg::kMaxStages; ++s) {
+    b[s] = s < S ? coef(S, s) : 0;
+    for (int jj = 0; jj < adg::kMaxStages; ++jj) a[s][jj] = (s < S && jj < s) ? coef(s, jj) : 0;
+  }
+}
+
+// Composed step constants (StepConsts in adg_internal.h) of upwind advection with a > 0, in
+// long double: from the SSP-RK3 stages in Shu and Osher's form, or, for the low-storage
+// schemes of at most three stages, from their Butcher form (unused channels are zero).
 void fold_step_constants(InstHost &h) {
   const Ops &o = h.ops;
   const int Np = o.Np;
   const ld c2a = advection_c2a(h);
-  const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
-  const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
   typedef std::vector<ld> Mat;
   auto mul = [&](const Mat &X, const Mat &Y) {
     Mat Z(Np * Np, 0);
@@ -456,75 +485,182 @@ void fold_step_constants(InstHost &h) {
       for (int k = 0; k < Np; ++k) z[i] += X[i * Np + k] * v[k];
     return z;
   };
-  Mat M[3];
-  std::vector<ld> cv[3];
-  for (int s = 0; s < 3; ++s) {
-    M[s].assign(Np * Np, 0);
-    cv[s].assign(Np, 0);
-    for (int i = 0; i < Np; ++i) {
-      const ld lL = beta[s] * c2a * o.Minv[i * Np + 0];
-      for (int j = 0; j < Np; ++j)
-        M[s][i * Np + j] = beta[s] * ((i == j ? 1.0L : 0.0L) + c2a * o.D[i * Np + j]);
-      M[s][i * Np + 0] += lL;
-      cv[s][i] = -lL;
-    }
-  }
   const int p = Np - 1;
-  Mat M10 = mul(M[1], M[0]);
-  Mat inner = M10;
-  for (int i = 0; i < Np; ++i) inner[i * Np + i] += alpha[1];
-  Mat G = mul(M[2], inner);
-  for (int i = 0; i < Np; ++i) G[i * Np + i] += alpha[2];
-  std::vector<ld> h0 = mulv(mul(M[2], M[1]), cv[0]);
-  std::vector<ld> h1 = mulv(M[2], cv[1]);
-  std::vector<ld> h2 = cv[2];
-  std::vector<ld> M1c0 = mulv(M[1], cv[0]);
-  adg::StepConsts &S = h.I.st;
-  std::memset(&S, 0, sizeof(S));
-  for (int i = 0; i < Np; ++i) {
-    for (int j = 0; j < Np; ++j) S.G[i * Np + j] = (double)G[i * Np + j];
-    S.r1[i] = (double)M[0][p * Np + i];
-    S.r2[i] = (double)(M10[p * Np + i] + (i == p ? alpha[1] : 0.0L));
-    S.h[0][i] = (double)h0[i];
-    S.h[1][i] = (double)h1[i];
-    S.h[2][i] = (double)h2[i];
-  }
-  S.k[0] = (double)cv[0][p];
-  S.k[1] = (double)M1c0[p];
-  S.k[2] = (double)cv[1][p];
-
+  // the step's constants: u'^e = G u^e + sum_t h_t P_t, channel scalars v1_p = r1 . u + k0 P0,
+  // v2_p = r2 . u + k1 P0 + k2 P1, PE-face responses R and rho
+  Mat Gl(Np * Np, 0);
+  std::vector<ld> r1l(Np, 0), r2l(Np, 0), hl[3];
+  for (auto &v : hl) v.assign(Np, 0);
+  ld kl[3] = {0, 0, 0}, rhol[3] = {0, 0, 0};
   ld Rl[3][4][adg::kMaxNp] = {};
-  // PE-face correction responses: inject lL_s at element e and lR_s at element e-1 after
-  // stage s, then apply the remaining stages' perturbation maps
-  // dx'^m = M_t dx^m + c_t dx^{m-1}_p (t = s+1 .. 2) on elements e-1 .. e+2; rho collects
-  // the right trace of element e-1 seen by the later stages.
-  for (int st = 0; st < 3; ++st) {
-    std::vector<ld> d(4 * Np, 0.0L);   // elements e-1 .. e+2
-    const ld sc = beta[st] * c2a;
-    for (int i = 0; i < Np; ++i) {
-      d[1 * Np + i] = sc * o.Minv[i * Np + 0];
-      d[0 * Np + i] = -sc * o.Minv[i * Np + p];
+
+  if (h.cfg.rk == ADG_SSPRK3) {
+    const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
+    const ld beta[3] = {1.0L, 0.25L, 2.0L / 3.0L};
+    Mat M[3];
+    std::vector<ld> cv[3];
+    for (int s = 0; s < 3; ++s) {
+      M[s].assign(Np * Np, 0);
+      cv[s].assign(Np, 0);
+      for (int i = 0; i < Np; ++i) {
+        const ld lL = beta[s] * c2a * o.Minv[i * Np + 0];
+        for (int j = 0; j < Np; ++j)
+          M[s][i * Np + j] = beta[s] * ((i == j ? 1.0L : 0.0L) + c2a * o.D[i * Np + j]);
+        M[s][i * Np + 0] += lL;
+        cv[s][i] = -lL;
+      }
     }
-    for (int t = st + 1; t < 3; ++t) {
-      if (st == 0 && t == 1) S.rho[0] = (double)d[0 * Np + p];
-      if (st == 0 && t == 2) S.rho[1] = (double)d[0 * Np + p];
-      if (st == 1 && t == 2) S.rho[2] = (double)d[0 * Np + p];
-      std::vector<ld> nd(4 * Np, 0.0L);
+    Mat M10 = mul(M[1], M[0]);
+    Mat inner = M10;
+    for (int i = 0; i < Np; ++i) inner[i * Np + i] += alpha[1];
+    Gl = mul(M[2], inner);
+    for (int i = 0; i < Np; ++i) Gl[i * Np + i] += alpha[2];
+    hl[0] = mulv(mul(M[2], M[1]), cv[0]);
+    hl[1] = mulv(M[2], cv[1]);
+    hl[2] = cv[2];
+    std::vector<ld> M1c0 = mulv(M[1], cv[0]);
+    for (int i = 0; i < Np; ++i) {
+      r1l[i] = M[0][p * Np + i];
+      r2l[i] = M10[p * Np + i] + (i == p ? alpha[1] : 0.0L);
+    }
+    kl[0] = cv[0][p];
+    kl[1] = M1c0[p];
+    kl[2] = cv[1][p];
+    // PE-face correction responses: inject lL_s at element e and lR_s at element e-1 after
+    // stage s, then apply the remaining stages' perturbation maps
+    // dx'^m = M_t dx^m + c_t dx^{m-1}_p (t = s+1 .. 2) on elements e-1 .. e+2; rho collects
+    // the right trace of element e-1 seen by the later stages.
+    for (int st = 0; st < 3; ++st) {
+      std::vector<ld> d(4 * Np, 0.0L);   // elements e-1 .. e+2
+      const ld sc = beta[st] * c2a;
+      for (int i = 0; i < Np; ++i) {
+        d[1 * Np + i] = sc * o.Minv[i * Np + 0];
+        d[0 * Np + i] = -sc * o.Minv[i * Np + p];
+      }
+      for (int t = st + 1; t < 3; ++t) {
+        if (st == 0 && t == 1) rhol[0] = d[0 * Np + p];
+        if (st == 0 && t == 2) rhol[1] = d[0 * Np + p];
+        if (st == 1 && t == 2) rhol[2] = d[0 * Np + p];
+        std::vector<ld> nd(4 * Np, 0.0L);
+        for (int m = 0; m < 4; ++m)
+          for (int i = 0; i < Np; ++i) {
+            ld acc = 0;
+            for (int k = 0; k < Np; ++k) acc += M[t][i * Np + k] * d[m * Np + k];
+            if (m > 0) acc += cv[t][i] * d[(m - 1) * Np + p];
+            nd[m * Np + i] = acc;
+          }
+        d = nd;
+      }
+      for (int m = 0; m < 4; ++m)
+        for (int i = 0; i < Np; ++i) Rl[st][m][i] = d[m * Np + i];
+    }
+  } else {
+    // Butcher form: Y_1 = u, k_s = dt L(Y_s) = W Y_s + w P_s (W = c2a (D + M^{-1} e_0 e_0^T),
+    // w = -c2a M^{-1} e_0, P_s the left neighbour's right trace of Y_s), Y_{s+1} =
+    // u + sum_j a_{s+1,j} k_j, u' = u + sum_j b_j k_j. Every quantity is kept as
+    // A u + sum_t H_t P_t.
+    int S = 0;
+    ld a[adg::kMaxStages][adg::kMaxStages], b[adg::kMaxStages];
+    two_register_butcher(h.cfg.rk, S, a, b);
+    Mat W(Np * Np, 0);
+    std::vector<ld> w(Np);
+    for (int i = 0; i < Np; ++i) {
+      for (int j = 0; j < Np; ++j)
+        W[i * Np + j] = c2a * (o.D[i * Np + j] + (j == 0 ? o.Minv[i * Np + 0] : 0.0L));
+      w[i] = -c2a * o.Minv[i * Np + 0];
+    }
+    Mat I(Np * Np, 0);
+    for (int i = 0; i < Np; ++i) I[i * Np + i] = 1;
+    struct Rep {
+      Mat A;
+      std::vector<ld> H[3];
+    };
+    Rep Y[3], Kr[3];
+    for (int s = 0; s < 3; ++s)
+      for (int t = 0; t < 3; ++t) {
+        Y[s].H[t].assign(Np, 0);
+        Kr[s].H[t].assign(Np, 0);
+      }
+    Y[0].A = I;
+    auto combine = [&](int s, const ld *coef) {   // I u + sum_{j<s} coef_j k_j
+      Rep r;
+      r.A = I;
+      for (int t = 0; t < 3; ++t) r.H[t].assign(Np, 0);
+      for (int j = 0; j < s; ++j) {
+        for (int x = 0; x < Np * Np; ++x) r.A[x] += coef[j] * Kr[j].A[x];
+        for (int t = 0; t < 3; ++t)
+          for (int i = 0; i < Np; ++i) r.H[t][i] += coef[j] * Kr[j].H[t][i];
+      }
+      return r;
+    };
+    for (int s = 0; s < S; ++s) {
+      Kr[s].A = mul(W, Y[s].A);
+      for (int t = 0; t < 3; ++t) Kr[s].H[t] = mulv(W, Y[s].H[t]);
+      for (int i = 0; i < Np; ++i) Kr[s].H[s][i] += w[i];
+      if (s + 1 < S) Y[s + 1] = combine(s + 1, a[s + 1]);
+    }
+    Rep U = combine(S, b);
+    Gl = U.A;
+    for (int t = 0; t < 3; ++t) hl[t] = U.H[t];
+    for (int i = 0; i < Np; ++i) {
+      if (S >= 2) r1l[i] = Y[1].A[p * Np + i];
+      if (S >= 3) r2l[i] = Y[2].A[p * Np + i];
+    }
+    if (S >= 2) kl[0] = Y[1].H[0][p];
+    if (S >= 3) {
+      kl[1] = Y[2].H[0][p];
+      kl[2] = Y[2].H[1][p];
+    }
+    // PE-face responses: the stage-st correction d enters k_st as c2a M^{-1} e_0 d at element e
+    // and -c2a M^{-1} e_p d at element e-1 and spreads through the later stages on elements
+    // e-1 .. e+2; rho is the right trace of element e-1's later stage inputs.
+    for (int st = 0; st < S; ++st) {
+      std::vector<ld> dK[3];
+      for (auto &v : dK) v.assign(4 * Np, 0.0L);
+      for (int i = 0; i < Np; ++i) {
+        dK[st][1 * Np + i] = c2a * o.Minv[i * Np + 0];
+        dK[st][0 * Np + i] = -c2a * o.Minv[i * Np + p];
+      }
+      for (int t = st + 1; t < S; ++t) {
+        std::vector<ld> dY(4 * Np, 0.0L);
+        for (int jj = st; jj < t; ++jj)
+          for (int x = 0; x < 4 * Np; ++x) dY[x] += a[t][jj] * dK[jj][x];
+        const ld r = dY[0 * Np + p];
+        if (st == 0 && t == 1) rhol[0] = r;
+        if (st == 0 && t == 2) rhol[1] = r;
+        if (st == 1 && t == 2) rhol[2] = r;
+        for (int m = 0; m < 4; ++m)
+          for (int i = 0; i < Np; ++i) {
+            ld acc = 0;
+            for (int k = 0; k < Np; ++k) acc += W[i * Np + k] * dY[m * Np + k];
+            if (m > 0) acc += w[i] * dY[(m - 1) * Np + p];
+            dK[t][m * Np + i] = acc;
+          }
+      }
       for (int m = 0; m < 4; ++m)
         for (int i = 0; i < Np; ++i) {
           ld acc = 0;
-          for (int k = 0; k < Np; ++k) acc += M[t][i * Np + k] * d[m * Np + k];
-          if (m > 0) acc += cv[t][i] * d[(m - 1) * Np + p];
-          nd[m * Np + i] = acc;
+          for (int jj = st; jj < S; ++jj) acc += b[jj] * dK[jj][m * Np + i];
+          Rl[st][m][i] = acc;
         }
-      d = nd;
     }
-    for (int m = 0; m < 4; ++m)
-      for (int i = 0; i < Np; ++i) {
-        S.R[st][m][i] = (double)d[m * Np + i];
-        Rl[st][m][i] = d[m * Np + i];
-      }
   }
+
+  adg::StepConsts &Sc = h.I.st;
+  std::memset(&Sc, 0, sizeof(Sc));
+  for (int i = 0; i < Np; ++i) {
+    for (int j = 0; j < Np; ++j) Sc.G[i * Np + j] = (double)Gl[i * Np + j];
+    Sc.r1[i] = (double)r1l[i];
+    Sc.r2[i] = (double)r2l[i];
+    for (int t = 0; t < 3; ++t) Sc.h[t][i] = (double)hl[t][i];
+  }
+  for (int t = 0; t < 3; ++t) {
+    Sc.k[t] = (double)kl[t];
+    Sc.rho[t] = (double)rhol[t];
+  }
+  for (int st = 0; st < 3; ++st)
+    for (int m = 0; m < 4; ++m)
+      for (int i = 0; i < Np; ++i) Sc.R[st][m][i] = (double)Rl[st][m][i];
 
   // Fixed-point limbs of the same coefficients (from the long double values) and the bounds
   // of the integer step: every |c| < 2 (limbs within 32 bits), and channel scalars v1_p,
@@ -540,21 +676,17 @@ void fold_step_constants(InstHost &h) {
     r.y = (int)(C & 0x1FFFFFFF);
     return r;
   };
-  ld b1 = fabsl(cv[0][p]), b2 = fabsl(M1c0[p]);
+  ld b1 = fabsl(kl[0]), b2 = fabsl(kl[1]);
   for (int i = 0; i < Np; ++i) {
-    for (int j = 0; j < Np; ++j) F.G[i * Np + j] = limbs(G[i * Np + j]);
-    F.r1[i] = limbs(M[0][p * Np + i]);
-    F.r2[i] = limbs(M10[p * Np + i] + (i == p ? alpha[1] : 0.0L));
-    F.h[0][i] = limbs(h0[i]);
-    F.h[1][i] = limbs(h1[i]);
-    F.h[2][i] = limbs(h2[i]);
-    b1 += fabsl(M[0][p * Np + i]);
-    b2 += fabsl(M10[p * Np + i] + (i == p ? alpha[1] : 0.0L));
+    for (int j = 0; j < Np; ++j) F.G[i * Np + j] = limbs(Gl[i * Np + j]);
+    F.r1[i] = limbs(r1l[i]);
+    F.r2[i] = limbs(r2l[i]);
+    for (int t = 0; t < 3; ++t) F.h[t][i] = limbs(hl[t][i]);
+    b1 += fabsl(r1l[i]);
+    b2 += fabsl(r2l[i]);
   }
-  F.k[0] = limbs(cv[0][p]);
-  F.k[1] = limbs(M1c0[p]);
-  F.k[2] = limbs(cv[1][p]);
-  b2 += fabsl(cv[1][p]) * b1;
+  for (int t = 0; t < 3; ++t) F.k[t] = limbs(kl[t]);
+  b2 += fabsl(kl[2]) * b1;
   h.fixed_ok = ok && b1 < 1.999L && b2 < 1.999L;
   // the PE-face responses likewise (from the long double values), for the integer correction
   std::memset(h.I.Rf, 0, sizeof(h.I.Rf));
@@ -705,6 +837,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     const LsTable *lt = cfg->rk == ADG_SSPRK3 ? nullptr : ls_table(cfg->rk);
     I.ls = lt ? 1 : 0;
     I.ns = lt ? lt->S : kStages;
+    h.stages = I.ns;
     for (int s = 0; s < adg::kMaxStages; ++s) {
       I.lsA[s] = lt && s < lt->S ? (double)((ld)lt->A[s].n / (ld)lt->A[s].d) : 0.0;
       I.lsB[s] = lt && s < lt->S ? (double)((ld)lt->B[s].n / (ld)lt->B[s].d) : 0.0;
@@ -718,6 +851,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     // SSP Runge-Kutta in Shu and Osher's form (stage constants below), the limiter's weights
     I.ls = 0;
     I.ns = cfg->rk == ADG_RK1 ? 1 : (cfg->rk == ADG_RK2 ? 2 : 3);
+    h.stages = I.ns;
     I.limiter = cfg->limiter;
     I.tvb_m = cfg->tvb_m;
     I.dx = h.dx;
@@ -803,16 +937,20 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     }
   }
   {
+    // the composed step: SSP-RK3, or a low-storage scheme of at most three stages
     const bool eligible = cfg->pde == ADG_ADVECTION && cfg->a > 0 && K >= 8 &&
-                          (!I.async || I.Kpe >= 8) && !I.ls;
+                          (!I.async || I.Kpe >= 8) && (!I.ls || I.ns <= kStages);
     const bool want_composed = cfg->variant == ADG_VARIANT_COMPOSED ||
                                cfg->variant == ADG_VARIANT_COMPOSED_FIXED;
     if (want_composed && !eligible)
-      return fail(c, ADG_EINVAL, "the composed step needs rk = ADG_SSPRK3, advection with a > 0, "
-                                 "K >= 8 and K/P >= 8");
+      return fail(c, ADG_EINVAL, "the composed step needs a scheme of at most three stages, "
+                                 "advection with a > 0, K >= 8 and K/P >= 8");
     I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED) ? 1 : 0;
     I.ept = 1;
     if (I.fused) {
+      // the composed kernels keep three stage slots per ring level whatever the scheme
+      I.ls = 0;
+      I.ns = kStages;
       fold_step_constants(h);
       if (cfg->variant == ADG_VARIANT_COMPOSED_FIXED && !h.fixed_ok)
         return fail(c, ADG_EINVAL,
@@ -1430,7 +1568,7 @@ int adg_comm_stats(const adg_ctx *c, int32_t index, int64_t *steps_out, int64_t 
   if (index < 0 || index >= (int)c->inst.size()) return fail(nullptr, ADG_EINVAL, "bad instance index");
   const InstHost &h = c->inst[index];
   const int64_t n = c->n;
-  const int64_t per_step = h.I.async ? (int64_t)h.I.ns * h.I.P : 0;
+  const int64_t per_step = h.I.async ? (int64_t)h.stages * h.I.P : 0;
   int64_t comm = n;
   if (h.delays.caa > 0) {   // whole periods, then the partial one
     const int64_t per = h.delays.caa + h.delays.L;

@@ -370,13 +370,27 @@ def _ls_case(case, rk):
 @pytest.mark.parametrize("rk", LOW_STORAGE)
 @pytest.mark.parametrize("case", ["advection_at", "advection_neg_async", "burgers_at", "sync_dg1"])
 def test_low_storage_schemes_match_oracle(rk, case):
-    # 40 steps: one 32-step graph chunk and a directly launched remainder.
+    # 40 steps: one 32-step graph chunk and a directly launched remainder. Upwind advection
+    # with a > 0 composes schemes of up to three stages into the fixed-point step; the rest
+    # run the staged 2N kernels.
     cfg, u0 = _ls_case(case, rk)
     s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
-    assert s.variant[0] == "staged"
+    composed = cfg.pde == "advection" and cfg.a > 0 and rk != "lsrk4"
+    assert (s.variant[0] in ("fixed", "composed")) if composed else (s.variant[0] == "staged")
     s.close()
     got, ref, _ = run_pair(cfg, u0, 40)
     assert np.all(np.isfinite(got))
+    assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
+
+
+@pytest.mark.parametrize("rk", ["rk1", "rk2", "lsrk3"])
+@pytest.mark.parametrize("variant", ["staged", "composed"])
+def test_low_storage_forced_variants_match_oracle(rk, variant):
+    # The same schemes on upwind advection through the staged 2N kernels and through the FP64
+    # composed step (the fixed-point one is the default above).
+    cfg, u0 = _ls_case("advection_at", rk)
+    cfg = adg.Config(**{**cfg.__dict__, "variant": variant})
+    got, ref, _ = run_pair(cfg, u0, 40)
     assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
 
 
@@ -398,8 +412,9 @@ def test_low_storage_zero_delay_is_bitwise_sync(rk):
 
 
 def test_low_storage_rejections():
-    # The low-storage schemes are single-instance, staged-kernel options.
-    cfg = adg.Config(pde="advection", K=64, p=2, P=4, cfl=0.02, mode="at", L=2, q=2, rk="lsrk3")
+    # The low-storage schemes are single-instance options; the composed steps take schemes of
+    # at most three stages.
+    cfg = adg.Config(pde="advection", K=64, p=2, P=4, cfl=0.02, mode="at", L=2, q=2, rk="lsrk4")
     u0 = adg.eval_modes(cfg, [1.0], [1.0], [0.0])
     for variant in ("composed", "fixed"):
         with pytest.raises(adg.AdgError) as ei:
