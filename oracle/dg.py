@@ -1,6 +1,6 @@
 """Fully discrete DG / ADG / ADG-AT solver in FP64 (oracle; test infrastructure).
 
-What it computes, with the readings taken where the paper is silent (listed in the design doc):
+What it computes, with the readings taken where the paper is silent:
 
 * Mesh (Section 2): K uniform elements of width dx = (x1 - x0)/K on a periodic domain;
   element e spans [x0 + e dx, x0 + (e+1) dx]; node i of element e sits at

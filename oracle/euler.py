@@ -1,7 +1,7 @@
 """One-dimensional compressible Euler equations by nodal DG (oracle; test infrastructure).
 
 What it computes (Section 6, the Sod shock-tube experiment; Eq. compressible-euler-3d in one
-dimension), with the readings taken where the paper is silent (listed in the design doc):
+dimension), with the readings taken where the paper is silent:
 
 * State U = (rho, m = rho u, E) with E = rho u^2 / 2 + p / (gamma - 1), gamma = 1.4; flux
   f(U) = (m, m u + p, (E + p) u).
