@@ -559,3 +559,39 @@ def test_euler_rejections():
         s.grad(U0, 2, 1)
     assert ei.value.code == adg._abi.ADG_EINVAL
     s.close()
+
+
+# --- the communication-avoiding cycle with the other schemes and equations ----------------
+
+@pytest.mark.parametrize("pde,rk,nu", [("burgers", "rk2", 0.1), ("burgers", "lsrk4", 0.0),
+                                       ("advection", "lsrk4", 0.0)])
+def test_caa_cycle_with_other_schemes(pde, rk, nu):
+    # The cycle's device-generated rows under viscous Burgers (ALDG-AT2-RK2), inviscid Burgers
+    # and upwind advection with the five-stage LSRK4 (staged 2N kernels).
+    K, p, P = 192, 2, 8
+    dx = TWO_PI / K
+    kw = dict(dt=0.01 * dx * dx, nu=nu) if nu else dict(cfl=0.01)
+    cfg = adg.Config(pde=pde, K=K, p=p, P=P, mode="at", L=3, q=2, caa_sync=2, rk=rk, **kw)
+    modes = PAPER_BURGERS if nu else (HALF_PLUS_SIN if pde == "burgers" else PAPER_FIG6)
+    u0 = dg.modes_initial(modes, K, p)
+    got, ref, _ = run_pair(cfg, u0, 37)
+    assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
+
+
+def test_euler_under_caa_cycle():
+    # ADG(1)-AT2-RK2 with the limiter through Sod's shock under the cycle (L = 3, two
+    # synchronised steps of five).
+    K, p, P, steps = 256, 1, 8, 45
+    x = dg.node_coordinates(K, p, 0.0, 0.02)
+    U0 = oeuler.conserved(*oeuler.sod_periodic(x, 0.0))
+    dt = 0.1 * 0.02 / K
+    cfg = adg.Config(pde="euler", K=K, p=p, P=P, x0=0.0, x1=0.02, dt=dt, rk="rk2", mode="at",
+                     L=3, q=2, caa_sync=2, limiter=True)
+    s = adg.Solver(cfg, torch.tensor(U0, device="cuda"))
+    s.step(steps)
+    got = s.state().cpu().numpy()
+    s.close()
+    prob = oeuler.EulerProblem(K=K, p=p, P=P, dt=dt, rk="rk2", mode="adg", q=2,
+                               delays=odelays.caa_table(P, steps, 2, 3), limiter=True)
+    ref = oeuler.run(prob, U0, steps).numpy()
+    assert rel_linf(got, ref) < TOL, rel_linf(got, ref)
