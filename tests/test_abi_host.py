@@ -58,6 +58,7 @@ def test_null_arguments(lib):
     assert lib.adg_step(None, 1) == _abi.ADG_EINVAL
     assert lib.adg_get_state(None, 0, None, None) == _abi.ADG_EINVAL
     assert lib.adg_get_variant(None, 0, None, None) == _abi.ADG_EINVAL
+    assert lib.adg_comm_stats(None, 0, None, None, None) == _abi.ADG_EINVAL
     lib.adg_destroy(None)
 
 
