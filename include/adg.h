@@ -179,9 +179,9 @@ int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx 
 int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t n,
                    void *stream, adg_ctx **out);
 
-/* Advance every instance by nsteps >= 0 SSP-RK3 steps (Section 4.2.1 structure, Eq.
- * EulerDG-style explicit updates; Eq. asyncEulerDGconserved at PE faces). Asynchronous:
- * returns once the work is queued. */
+/* Advance every instance by nsteps >= 0 steps of its Runge-Kutta scheme (SSP-RK3 unless rk
+ * says otherwise; Section 4.2.1 structure, Eq. EulerDG-style explicit updates; Eq.
+ * asyncEulerDGconserved at PE faces). Asynchronous: returns once the work is queued. */
 int adg_step(adg_ctx *c, int64_t nsteps);
 
 /* Advance to time t_end: ceil(t_end/dt - 1e-9) - (current step) steps (none if <= 0). */
