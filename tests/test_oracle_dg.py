@@ -96,7 +96,8 @@ def test_sync_step_equals_amplification_matrix(rk, p):
 
 
 @pytest.mark.parametrize("rk,k,q", [("rk1", 2, 1), ("rk2", 1, 2), ("ssprk3", 0, 3),
-                                    ("ssprk3", 2, 1), ("ssprk3", 1, 2), ("rk4", 1, 3)])
+                                    ("ssprk3", 2, 1), ("ssprk3", 1, 2), ("rk4", 1, 3),
+                                    ("lsrk3", 2, 2), ("lsrk4", 1, 3)])
 def test_delayed_scheme_equals_fourier_recurrence(rk, k, q):
     # P = K: every face is a PE face; a constant delay k turns the scheme into a linear
     # recurrence on the amplitudes of one Fourier mode (block companion, Section 4.2.2).

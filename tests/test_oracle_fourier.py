@@ -34,7 +34,7 @@ def test_adg1_rk2_L2_stability_as_printed():
     assert w333 > 50 * w10 > 50 * w05 / 14
 
 
-@pytest.mark.parametrize("rk", ["rk2", "ssprk3", "rk4"])
+@pytest.mark.parametrize("rk", ["rk2", "ssprk3", "rk4", "lsrk3", "lsrk4"])
 def test_physical_mode_dispersion(rk):
     # The physical mode satisfies Omega_r = K (K = theta/(Np)) for small wavenumbers.
     p, sigma = 2, 0.1
