@@ -99,13 +99,20 @@ __device__ void euler_pe_flux(const Inst &I, int j, int64_t n, int s, const doub
   }
 }
 
+// Elements per warp of k_euler_stage: lanes 1 .. 30 own elements, lanes 0 and 31 hold their
+// left and right neighbours, so every face flux of the warp is formed by the lanes together.
+constexpr int kEulerLanes = 30;
+
 template <int NP, int STAGE, bool FACES>
 __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, double *__restrict__ dst) {
   const int K = I.K;
   const size_t nd = (size_t)K * NP;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int ec = e < K ? e : K - 1;
+  const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int eraw = gw * kEulerLanes - 1 + lane;   // -1 .. K + 30
+  const int ec = (int)(((long long)eraw + K) % K);
+  const bool own = lane >= 1 && lane <= kEulerLanes && eraw < K;
+  const int e = own ? eraw : K;   // K: not this lane's to write
   const double *vin = STAGE == 0 ? I.u : (STAGE == 1 ? I.v1 : I.v2);
   const StageConsts &C = I.sc[STAGE];
   double V[3][NP];
@@ -119,9 +126,6 @@ __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, do
     }
   }
   const unsigned full = 0xffffffffu;
-  const bool edge = (lane == 31) || (ec + 1 >= K);
-  const int fR = ec + 1 >= K ? 0 : ec + 1;
-  const int fL = ec == 0 ? K - 1 : ec - 1;
   // node fluxes, and the wave speeds of the two end nodes
   double f[3][NP], s0 = 0.0, sp = 0.0;
 #pragma unroll
@@ -139,8 +143,8 @@ __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, do
 #pragma unroll
     for (int c = 0; c < 3; ++c) f[c][i] = fi[c];
   }
-  // left face: U^- with its flux and speed from the left neighbour's last node (lane 0 forms
-  // them from a load), U^+ this element's first node
+  // left face: U^- with its flux and speed from the left neighbour's last node (the lane
+  // below), U^+ this element's first node; the right face's flux from the lane above
   double VLm[3], VRp[3], V0[3], Vp[3], fLm[3], f0[3], fp[3];
 #pragma unroll
   for (int c = 0; c < 3; ++c) {
@@ -152,23 +156,11 @@ __global__ void __launch_bounds__(kTile) k_euler_stage(const Inst I, int rel, do
     fLm[c] = __shfl_up_sync(full, fp[c], 1);
     VRp[c] = __shfl_down_sync(full, V0[c], 1);
   }
-  double sLm = __shfl_up_sync(full, sp, 1);
-  if (lane == 0) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) VLm[c] = __ldg(vin + c * nd + (size_t)(NP - 1) * K + fL);
-    euler_flux_speed(VLm, fLm, sLm);
-  }
+  const double sLm = __shfl_up_sync(full, sp, 1);
   double FL[3], FR[3];
   euler_llf_from(VLm, V0, fLm, f0, sLm, s0, FL);
 #pragma unroll
   for (int c = 0; c < 3; ++c) FR[c] = __shfl_down_sync(full, FL[c], 1);
-  if (edge) {
-    double fRp[3], sRp;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) VRp[c] = __ldg(vin + c * nd + fR);
-    euler_flux_speed(VRp, fRp, sRp);
-    euler_llf_from(Vp, VRp, fp, fRp, sp, sRp, FR);
-  }
   if (FACES && e < K) {
     const int64_t n = I.meta[0] + rel;
     const int Kpe = I.Kpe;
@@ -300,7 +292,8 @@ __global__ void __launch_bounds__(kTile) k_euler_limit(const Inst I, const doubl
 template <int NP, int STAGE>
 cudaError_t euler_stage_np(const Inst &I, int rel, double *dst, cudaStream_t s) {
   const int bs = stage_block(I.K);
-  const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
+  const long long threads = (long long)((I.K + kEulerLanes - 1) / kEulerLanes) * 32;
+  const unsigned grid = (unsigned)((threads + bs - 1) / bs);
   if (I.async) k_euler_stage<NP, STAGE, true><<<grid, bs, 0, s>>>(I, rel, dst);
   else k_euler_stage<NP, STAGE, false><<<grid, bs, 0, s>>>(I, rel, dst);
   return cudaGetLastError();
