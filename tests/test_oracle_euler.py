@@ -113,3 +113,18 @@ def test_euler_zero_delay_is_sync():
     b = euler.run(euler.EulerProblem(K=K, p=1, P=4, dt=2e-6, q=2, mode="adg",
                                      delays=np.zeros((1, 4), np.uint8)), U0, 25)
     assert torch.equal(a, b)
+
+
+@pytest.mark.parametrize("left,right", [(euler.SOD_LEFT, euler.SOD_RIGHT),
+                                        ((1.0, 0.75, 1.0), (0.125, 0.0, 0.1)),
+                                        ((1.0, -2.0, 0.4), (1.0, 2.0, 0.4))])
+def test_exact_riemann_solution_is_mirror_symmetric(left, right):
+    # x -> -x swaps the states and negates the velocities: the mirrored problem's solution at
+    # s is the original one at -s with u negated. Sod's problem (left rarefaction, right shock)
+    # thus pins the left-shock and right-rarefaction branches too; the last pair has two
+    # rarefactions.
+    mirror = lambda st: (st[0], -st[1], st[2])
+    for s in np.linspace(-2.5, 2.5, 41):
+        a = euler.sample(left, right, s)
+        b = euler.sample(mirror(right), mirror(left), -s)
+        assert abs(a[0] - b[0]) < 1e-12 and abs(a[1] + b[1]) < 1e-12 and abs(a[2] - b[2]) < 1e-12
