@@ -2,7 +2,8 @@
 // kernels for sm_103a.
 //
 // State U = (rho, m, E), E = rho u^2 / 2 + p / (gamma - 1), gamma = 1.4, three node-major
-// planes per component (component c of a field at field + c K Np). One thread per element.
+// planes per component (component c of a field at field + c K Np). One thread per element;
+// in the stage kernel a warp takes 30 elements with their two neighbours in its edge lanes.
 //   * k_euler_stage: one stage of SSP-RK in Shu and Osher's form,
 //       out = alpha u + beta (v + dt L(v)),   dt L(v) = dt [ -QD f + qlL (f_0 - F_L) + qlR (f_p - F_R) ]
 //     (the strong form of the nodal DG operator, QD = (2/dx) D, qlL = -(2/dx) M^{-1} e_0,
