@@ -36,7 +36,8 @@ STAGES = 3
 # The large advection workload; its Courant number is not fixed by the workload statement
 # and is set inside the stability bound of the delayed self-feedback (sigma (p+1)^2 k < 1
 # for k <= 7 with the AT extrapolation); the work per step does not depend on it.
-from workloads import ADJOINT_64K as _WADJ, ADVECTION_16M as _W16M, batched_instances  # noqa: E402
+from workloads import (ADJOINT_64K as _WADJ, ADVECTION_16M as _W16M, BURGERS_1M,  # noqa: E402
+                       batched_instances)
 
 WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P, L=_W16M.L,
                 q=_W16M.q, cfl=_W16M.cfl, seed=_W16M.seed,
@@ -52,7 +53,10 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
 #  - staged FP64 kernels: 2 (Np + 2) flop per DOF-stage.
 NP = WORKLOAD["p"] + 1
 MACS_PER_ELEMENT_STEP = NP * NP + 5 * NP + 3
-INT_PRODUCTS_PER_ELEMENT_STEP = 3 * MACS_PER_ELEMENT_STEP + 3   # + the neighbour's v1_p^{e-2}
+# fixed point: each multiply-add of the kernel is one 32 x 32 -> 64-bit multiply-add and two
+# high-word multiply-adds (adg_fixed.cuh); the kernel forms Np^2 + 5 Np + 4 of them per element
+# (one more for the left neighbour's v1_p^{e-2})
+FIXED_MACS_PER_ELEMENT_STEP = MACS_PER_ELEMENT_STEP + 1
 FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # A 2N low-storage stage: dt L(U) + A_s dU (one multiply and NP + 1 FMA per DOF) and
@@ -65,22 +69,36 @@ VISC_NP = 3
 FLOP_PER_DOF_STAGE_VISC = 6 * VISC_NP + 17
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant; a kernel changed since its counters were taken has no
-# entry. Fixed point: k_step_fixed<4, 2 elements per thread, int64 -> int64>, 537.06 MB read
-# + 489.28 MB written (the interior steps of an adg_step call; its first step reads FP64 and
-# its last writes FP64).
-TRAFFIC_BYTES_PER_LAUNCH = {"fixed": 1_026_334_976}
+# entry (null in the line).
+TRAFFIC_BYTES_PER_LAUNCH = {}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
+# The staged SSP-RK3 step reads and writes 16 / 24 / 24 B per DOF in its three stages (the
+# Burgers workload's 42 MB fields are largely L2-resident, so its fraction of HBM is a bound
+# on traffic, not a measure of it).
+BYTES_PER_DOF_STEP_STAGED = 64
+# Burgers LLF stage at p = 4 (Np = 5): per node v^2 (one multiply), Np FMA of the volume row,
+# two lifts and the alpha / beta combination: 2 (Np + 4) + 1 flop per DOF-stage.
+FLOP_PER_DOF_STAGE_BURGERS = 2 * (5 + 4) + 1
 GRAPH_STEPS = 32
 
 
+# Issue rates of the heavy integer pipe measured on this part (lanes per clock per SM, all
+# SMs, independent chains): 32 x 32 -> 64-bit multiply-add 33.9, mad.hi.s32 42.3.
+WIDE_PER_CLK_SM = 33.9
+HI_PER_CLK_SM = 42.3
+
+
+def sm_count() -> int:
+    """Streaming multiprocessors of the current device (152 on GB300), read from the device."""
+    import torch
+    return int(torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count)
+
+
 def peaks():
-    """Roofline denominators: HBM from MEASURED_PEAKS.json (else the recipe's fallback);
-    FP64 ALU peak from unit counts and the maximum SM clock: 152 SMs x 2 DFMA/clk x 2 flop
-    x 2.07 GHz (the nominal 1.25 TFLOP/s FP64 of GB300); integer product peak: 152 SMs x 32
-    wide (32 x 32 -> 64-bit) multiply-adds per clock (the heavy FMA pipe, 16 lanes per clock
-    per SM sub-partition, two passes for a 64-bit result) x 2.07 GHz = 10.07 T/s (28.7 per
-    clock per SM measured in a dependent-chain microbenchmark)."""
+    """Roofline denominators: HBM from MEASURED_PEAKS.json (else the recipe's fallback); FP64
+    ALU peak from unit counts: SMs (read from the device) x 2 DFMA/clk x 2 flop x the maximum SM
+    clock (the nominal 1.26 TFLOP/s FP64 of GB300 at 152 SMs and 2.07 GHz)."""
     hbm, src = 6800.0, "fallback"
     sm_mhz = 2070.0
     try:
@@ -90,9 +108,9 @@ def peaks():
         sm_mhz = float(mp.get("sm_max_mhz", sm_mhz))
     except Exception:
         pass
-    fp64_tflops = 152 * 2 * 2 * sm_mhz * 1e6 / 1e12
-    int_tops = 152 * 32 * sm_mhz * 1e6 / 1e12
-    return hbm, src, fp64_tflops, int_tops
+    sms = sm_count()
+    fp64_tflops = sms * 2 * 2 * sm_mhz * 1e6 / 1e12
+    return hbm, src, fp64_tflops, sms, sm_mhz
 
 
 class ClockSampler:
@@ -152,18 +170,54 @@ class ClockSampler:
                 "power_w_max": max(r[2] for r in rows), "samples": len(rows), "reasons": reasons}
 
 
-def make_cfg(mode: str, rk: str = "ssprk3"):
+def make_cfg(mode: str, rk: str = "ssprk3", variant: str = "auto"):
     import paper_2404_03399_gb300 as adg
     w = WORKLOAD
     return adg.Config(pde=w["pde"], K=w["K"], p=w["p"], P=w["P"], cfl=w["cfl"], mode=mode,
-                      L=w["L"], q=w["q"] if mode == "at" else 0, seed=w["seed"], rk=rk)
+                      L=w["L"], q=w["q"] if mode == "at" else 0, seed=w["seed"], rk=rk,
+                      variant=variant)
+
+
+def bench_config(ws: int) -> dict:
+    """The workload of the line, the same for both arms."""
+    w = WORKLOAD
+    return {"workload": w["name"], "K": w["K"], "p": w["p"], "P": w["P"], "L": w["L"],
+            "at_order": w["q"], "cfl": w["cfl"], "dof": w["K"] * (w["p"] + 1),
+            "parallelism": f"replicas x{ws}",
+            "l2": "inputs larger than L2 (537 MB per nodal field)", "graph_steps": GRAPH_STEPS}
+
+
+def host_info() -> dict:
+    """Host cores and CPU model (lscpu, else /proc/cpuinfo)."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() == "Model name":
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if model is None:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    try:
+        avail = len(os.sched_getaffinity(0))
+    except Exception:
+        avail = os.cpu_count()
+    return {"host_cores": os.cpu_count(), "cores_available": avail, "cpu_model": model}
 
 
 def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks: bool, dev: int,
-                 rk: str = "ssprk3"):
+                 rk: str = "ssprk3", variant: str = "auto", exact_error: dict = None):
     import torch
     import paper_2404_03399_gb300 as adg
-    cfg = make_cfg(mode, rk)
+    cfg = make_cfg(mode, rk, variant)
     amp, kap, ph, off = WORKLOAD["modes"]
     u0 = adg.eval_modes(cfg, amp, kap, ph, off)
     s = adg.Solver(cfg, u0)
@@ -193,8 +247,69 @@ def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks
         s.check_finite_ok = False
     finite = s.check_finite_ok
     variant = s.variant
+    if exact_error is not None:
+        exact_error.update(linf_vs_translation(s, cfg, warmup + steps))
     s.close()
     return ms, (clocks.summary() if clocks else None), finite, variant
+
+
+def linf_vs_translation(s, cfg, nsteps: int) -> dict:
+    """Max-norm error of the solver's state against the exact solution of linear advection,
+    u0(x - a t) at t = nsteps dt, evaluated at the library's nodes (relative to max |u_exact|)."""
+    import paper_2404_03399_gb300 as adg
+    amp, kap, ph, off = WORKLOAD["modes"]
+    t = nsteps * s.dt
+    exact = adg.eval_modes(cfg, amp, kap, [f - k * cfg.a * t for f, k in zip(ph, kap)], off)
+    u = s.state()
+    err = float((u - exact).abs().max() / exact.abs().max())
+    del exact, u
+    return {"linf_rel": err, "t": t, "steps": nsteps}
+
+
+def burgers_timed(steps: int, warmup: int, mode: str, cfl: float):
+    """The Burgers workload (K = 2^20, p = 4, LLF, 1024 PEs, delays uniform in {0..3}, AT
+    order 2 for mode "at") at Courant number cfl: CUDA-event time of `steps` steps after
+    `warmup`, finiteness, and the max-norm error against the exact pre-shock solution
+    u = u0(x - u t) (characteristics, Newton per node) after all steps."""
+    import numpy as np
+    import torch
+    import paper_2404_03399_gb300 as adg
+    w = BURGERS_1M
+    cfg = adg.Config(pde="burgers", K=w.K, p=w.p, P=w.P, cfl=cfl, mode=mode, L=w.L,
+                     q=w.q if mode == "at" else 0, seed=w.seed)
+    m = w.modes
+    u0 = adg.eval_modes(cfg, m.amp, m.kappa, m.phase, m.offset)
+    s = adg.Solver(cfg, u0)
+    del u0
+    stream = torch.cuda.current_stream()
+    s.step(warmup)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    s.step(steps)
+    ev1.record(stream)
+    ev1.synchronize()
+    ms = ev0.elapsed_time(ev1)
+    fin = True
+    try:
+        s.check_finite()
+    except adg.AdgError:
+        fin = False
+    variant = s.variant[0]
+    t = (warmup + steps) * s.dt
+    u = s.state()
+    s.close()
+    xi, _ = adg.lgl_nodes(w.p)
+    dx = (cfg.x1 - cfg.x0) / w.K
+    x = cfg.x0 + (torch.arange(w.K, dtype=torch.float64, device="cuda")[:, None]
+                  + (1.0 + torch.tensor(xi, device="cuda"))[None, :] / 2.0) * dx
+    ex = m.offset + m.amp[0] * torch.sin(m.kappa[0] * x + m.phase[0])
+    for _ in range(30):   # u = u0(x - u t): Newton on g(u) = u - u0(x - u t)
+        arg = m.kappa[0] * (x - ex * t) + m.phase[0]
+        g = ex - (m.offset + m.amp[0] * torch.sin(arg))
+        ex = ex - g / (1.0 + m.amp[0] * m.kappa[0] * t * torch.cos(arg))
+    err = float((u - ex).abs().max() / ex.abs().max()) if fin else float("nan")
+    return ms, fin, variant, {"linf_rel": err, "t": t, "steps": warmup + steps}
 
 
 def caa_timed(steps: int, warmup: int):
@@ -386,10 +501,12 @@ def adjoint_cost(steps: int = 0, repeats: int = 3):
             "ckpt_every": 50, "workload": "Burgers K=65536 p=3 1024 PEs L=4 AT2, 2000 steps"}
 
 
-def cpu_oracle_rate(window: int, steps: int):
-    """The FP64 oracle as it stands, on the host cores: `steps` SSP-RK3 steps of ADG-AT on
-    a contiguous window of `window` elements of the large mesh (its PE faces and delays
-    included). Returns (DOF-stage updates/s, threads, sample description)."""
+def oracle_timed(window: int, steps: int, warmup: int = 1, threads: int = 0):
+    """The FP64 oracle as it stands, on the host cores: `warmup` untimed and then `steps` timed
+    SSP-RK3 steps of ADG-AT on a contiguous window of `window` elements of the large mesh (the
+    whole mesh when window = K; its PE faces and delays included). threads > 0 runs torch's
+    CPU ops on that many threads. Returns (DOF-stage updates/s, ms per timed step, threads
+    used, sample description)."""
     import numpy as np
     import torch
     from oracle import dg, delays
@@ -397,21 +514,41 @@ def cpu_oracle_rate(window: int, steps: int):
     K, p = w["K"], w["p"]
     dx = 2 * math.pi / K
     dt = (w["cfl"] * dx) / 1.0
-    tbl = delays.delay_table(w["seed"], w["P"], steps + 2, w["L"])
-    x = dg.node_coordinates(window, p, 0.0, 2 * math.pi, 0, K)
-    u0 = np.sin(x)
-    prob = dg.Problem(pde="advection", K=window, p=p, P=w["P"], dt=dt, mode="adg", q=w["q"],
-                      delays=tbl, window_lo=0, K_global=K)
-    s = dg.Solver(prob, u0)
-    s.step()                                 # untimed first step (setup of the caches)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        s.step()
-    el = time.perf_counter() - t0
+    old_threads = torch.get_num_threads()
+    if threads > 0:
+        torch.set_num_threads(threads)
+    try:
+        used = torch.get_num_threads()
+        tbl = delays.delay_table(w["seed"], w["P"], steps + warmup + 2, w["L"])
+        x = dg.node_coordinates(window, p, 0.0, 2 * math.pi, 0, K)
+        u0 = np.sin(x)
+        full = window == K
+        prob = dg.Problem(pde="advection", K=window, p=p, P=w["P"], dt=dt, mode="adg", q=w["q"],
+                          delays=tbl, window_lo=None if full else 0, K_global=None if full else K)
+        s = dg.Solver(prob, u0)
+        for _ in range(max(warmup, 1)):
+            s.step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            s.step()
+        el = time.perf_counter() - t0
+    finally:
+        torch.set_num_threads(old_threads)
     rate = window * (p + 1) * STAGES * steps / el
-    sample = (f"{steps} SSP-RK3 steps of the oracle on a {window}-element window "
-              f"({window // (K // w['P'])} PE faces) of the K=2^24 mesh")
-    return rate, torch.get_num_threads(), sample
+    where = "the whole K=2^24 mesh" if window == K else \
+        f"a {window}-element window ({window // (K // w['P'])} PE faces) of the K=2^24 mesh"
+    sample = f"{steps} timed SSP-RK3 steps (after {max(warmup, 1)} untimed) of the oracle on {where}"
+    return rate, el / steps * 1e3, used, sample
+
+
+def cpu_baseline(window: int = 1 << 22, steps: int = 3) -> dict:
+    """The oracle on all of torch's CPU threads and on one thread (a 2^20-element window)."""
+    rate, _, used, sample = oracle_timed(window, steps)
+    one, _, _, one_sample = oracle_timed(1 << 20, 2, 1, threads=1)
+    out = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
+           "one_thread": {"value": one, "sample": one_sample}}
+    out.update(host_info())
+    return out
 
 
 def dist_setup():
@@ -441,22 +578,27 @@ def aggregate(dist, ms: float, units: float):
 
 
 def reference_arm(args, rank, ws):
-    """The oracle (the reference for this method) on the host cores, on the same metric:
-    each step is a bounded sample (a window of the mesh)."""
+    """The oracle (the reference for this method) on the host cores, on the same metric, unit
+    and workload as the GPU arm: `--warmup` untimed and `--steps` timed steps, each over the
+    whole mesh when the run fits in about two minutes (about 1.5 s per step on 16 Arm cores),
+    else over a window of whole PEs."""
     if rank != 0:
         return
-    import torch
-    window = args.ref_window
-    rate, cores, sample = cpu_oracle_rate(window, max(1, min(args.steps, 3)))
-    K = WORKLOAD["K"]
-    ms_per_step = (K * (WORKLOAD["p"] + 1) * STAGES) / rate * 1e3
+    K, P = WORKLOAD["K"], WORKLOAD["P"]
+    kpe = K // P
+    n = args.steps + args.warmup
+    window = K if n <= 60 else max(kpe, (K * 60 // n) // kpe * kpe)
+    if args.ref_window > 0:
+        window = min(K, args.ref_window)
+    rate, ms_step, used, sample = oracle_timed(window, args.steps, args.warmup)
+    base = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample}
+    base.update(host_info())
     line = {"impl": "reference", "metric": METRIC, "value": rate, "unit": UNIT, "n_gpus": ws,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+            "ms_per_step_is": "the timed oracle steps (whole mesh)" if window == K else
+                              f"the timed oracle steps on a {window}-element window",
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD["name"], "K": K,
-                                            "p": WORKLOAD["p"], "P": WORKLOAD["P"]},
-            "cpu_baseline": {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                             "sample": sample},
+            "data": "synthetic", "config": bench_config(ws), "cpu_baseline": base,
             "e2e": {"value": rate, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -467,10 +609,11 @@ def main():
     ap.add_argument("--steps", type=int, default=500)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--sync-steps", type=int, default=200)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip sync-DG and e2e runs")
-    ap.add_argument("--ref-window", type=int, default=1 << 22)
+    ap.add_argument("--ref-window", type=int, default=0,
+                    help="reference arm: elements per oracle step (0: the whole mesh when the "
+                         "run fits in about two minutes, else a window of whole PEs)")
     ap.add_argument("--adjoint-only", type=int, default=0, metavar="STEPS",
                     help="only time adg_grad against the forward on the adjoint workload for STEPS "
                          "steps (one repeat) and print that dict (for profiling runs)")
@@ -517,52 +660,50 @@ def main():
 
     K, p = WORKLOAD["K"], WORKLOAD["p"]
     ndof = K * (p + 1)
+    acc_at = {}
     ms, clocks, finite, (variant, ept) = device_timed("at", args.steps, args.warmup, barrier,
-                                                      rank == 0, local)
+                                                      rank == 0, local, exact_error=acc_at)
     units = ndof * STAGES * args.steps
     ms_max, units_all = aggregate(dist, ms, units)
     value = units_all / (ms_max * 1e-3)
 
-    hbm_gbs, hbm_src, fp64_tflops, int_tops = peaks()
+    hbm_gbs, hbm_src, fp64_tflops, sms, sm_mhz = peaks()
     ms_step = ms / args.steps
-    # one composed-step launch per step plus the PE-face launch between steps, charged to it
-    # (the CUDA-event time of the step; ncu puts the PE-face launch near 4% of it)
-    elements = K
+    step_s = ms_step * 1e-3
+    # Roofline of the step against HBM (the metric's roofline): the algorithmic 16 B per DOF
+    # (read u^n, write u^{n+1}) over the CUDA-event time of a step, which is one composed-step
+    # launch plus the PE-face launch between steps (charged to it: the kernel's own share is
+    # the larger one).
+    hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / step_s / 1e9
+    roofline = {"bound": "hbm", "achieved": hbm_algo_gbs, "peak": hbm_gbs, "unit": "GB/s",
+                "frac": hbm_algo_gbs / hbm_gbs, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(variant),
+                "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)",
+                "bytes_per_dof_step": BYTES_PER_DOF_STEP}
     if variant == "fixed":
-        achieved = elements * INT_PRODUCTS_PER_ELEMENT_STEP / (ms_step * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": int_tops,
-                    "unit": "T int64-products/s", "frac": achieved / int_tops,
-                    "traffic": TRAFFIC_BYTES_PER_LAUNCH.get("fixed"),
-                    "kernel": f"k_step_fixed (composed SSP-RK3 step in two-limb fixed point, "
-                              f"{INT_PRODUCTS_PER_ELEMENT_STEP} 32x32->64-bit products per element, "
-                              f"{ept} element(s) per thread); the PE-face correction launch is charged to it",
-                    "peak_source": "integer unit counts x max SM clock (152 SM x 32 wide "
-                                   "multiply-adds/clk x 2.07 GHz)",
-                    "fp64_equivalent_tflops": ndof * FLOP_PER_DOF_STEP / (ms_step * 1e-3) / 1e12}
+        wide, hi = FIXED_MACS_PER_ELEMENT_STEP, 2 * FIXED_MACS_PER_ELEMENT_STEP
+        pipe_s = K * (wide / WIDE_PER_CLK_SM + hi / HI_PER_CLK_SM) / (sms * sm_mhz * 1e6)
+        roofline["kernel"] = (f"k_step_fixed (composed SSP-RK3 step in 58-bit block fixed point, "
+                              f"{ept} element(s) per thread) + k_face_step")
+        roofline["alu"] = {
+            "what": f"heavy integer pipe: {wide} 32x32->64-bit multiply-adds and {hi} high-word "
+                    f"products per element at the measured issue rates ({WIDE_PER_CLK_SM} and "
+                    f"{HI_PER_CLK_SM} per clock per SM, {sms} SMs, {sm_mhz:.0f} MHz)",
+            "pipe_bound_ms": pipe_s * 1e3, "frac": pipe_s / step_s}
     else:
-        achieved = ndof * FLOP_PER_DOF_STEP / (ms_step * 1e-3) / 1e12
-        roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_tflops, "unit": "TFLOP/s",
-                    "frac": achieved / fp64_tflops, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(variant),
-                    "kernel": f"k_step_fused / k_stage ({variant}, FP64)",
-                    "peak_source": "FP64 from unit counts x max SM clock (152 SM x 2 DFMA/clk x 2 "
-                                   "flop x 2.07 GHz)"}
-    hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / (ms_step * 1e-3) / 1e9
+        roofline["kernel"] = f"k_step_fused / k_stage ({variant}, FP64)"
+        roofline["fp64"] = {"achieved_tflops": ndof * FLOP_PER_DOF_STEP / step_s / 1e12,
+                            "peak_tflops": fp64_tflops,
+                            "frac": ndof * FLOP_PER_DOF_STEP / step_s / 1e12 / fp64_tflops}
+    arithmetic = ("58-bit block fixed point (one scale per field per step, 2^-57 of the field's "
+                  "largest value per unit; a few units of error per sum), int64 state inside each "
+                  "adg_step call; FP64 at its first input, its last output and in the PE-face "
+                  "stage differences") if variant == "fixed" else "FP64"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "int64" if variant == "fixed" else "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD["name"], "K": K, "p": p, "P": WORKLOAD["P"],
-                       "L": WORKLOAD["L"], "at_order": WORKLOAD["q"], "cfl": WORKLOAD["cfl"],
-                       "dof": ndof, "parallelism": f"replicas x{ws}",
-                       "l2": "inputs larger than L2 (537 MB per nodal field)",
-                       "graph_steps": GRAPH_STEPS, "variant": variant,
-                       "arithmetic": ("exact two-limb fixed point at one scale per step "
-                                      "(resolution 2^-55 of max|u| or finer), int64 state inside "
-                                      "each adg_step call, FP64 at its first input, its last output and in the PE-face "
-                                      "stage differences") if variant == "fixed" else "FP64"},
+            "config": bench_config(ws), "variant": variant, "arithmetic": arithmetic,
             "roofline": roofline,
-            "hbm": {"algorithmic_gbs": hbm_algo_gbs, "peak_gbs": hbm_gbs, "peak_source": hbm_src,
-                    "frac": hbm_algo_gbs / hbm_gbs, "bytes_per_dof_step": BYTES_PER_DOF_STEP},
             # per step: the composed-step kernel and one PE-face kernel (correction of the step
             # before, differences of the next); per chunk of GRAPH_STEPS steps one step-counter
             # kernel, and per call one more PE-face kernel
@@ -575,10 +716,49 @@ def main():
         line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
                        "what": "pinned host u0 -> device, adg_init, all steps, state -> pinned host"}
-        sms, _, _, _ = device_timed("sync", args.sync_steps, args.warmup, barrier, False, local)
-        line["sync_dg"] = {"value": ndof * STAGES * args.sync_steps / (sms * 1e-3), "unit": UNIT,
-                           "ms_per_step": sms / args.sync_steps}
+        # synchronous DG on the same mesh, the same number of steps in one adg_step call
+        acc_sync = {}
+        sync_ms, _, _, (svar, _) = device_timed("sync", args.steps, args.warmup, barrier, False,
+                                               local, exact_error=acc_sync)
+        line["sync_dg"] = {"value": ndof * STAGES * args.steps / (sync_ms * 1e-3), "unit": UNIT,
+                           "ms_per_step": sync_ms / args.steps, "steps": args.steps,
+                           "variant": svar}
         line["at_over_sync"] = value / ws / line["sync_dg"]["value"]
+        # the accuracy half of the comparison: both schemes against the exact translated
+        # solution after the same steps
+        line["accuracy"] = {"advection_16m": {"at": acc_at, "sync": acc_sync,
+                                              "norm": "max |u - u_exact| / max |u_exact|"}}
+        # the Burgers workload (LLF, K = 2^20, p = 4, 1024 PEs, AT2, L = 4): the staged
+        # stage kernels, at the stated Courant number 0.05 and at 0.005, inside the stability
+        # bound of the delayed self-feedback
+        bline = {"workload": "Burgers u0 = 0.5 + sin x, K = 2^20, p = 4, LLF, SSP-RK3, 1024 PEs, "
+                             "delays uniform in {0..3} (L = 4), AT order 2",
+                 "dof": BURGERS_1M.ndof, "steps": args.steps,
+                 "kernel": "k_stage (one SSP-RK3 stage, PE-face flux and ring write fused), three per step",
+                 "flop_per_dof_stage": FLOP_PER_DOF_STAGE_BURGERS}
+        for cfl in (BURGERS_1M.cfl, 0.005):
+            for mode in ("at", "sync"):
+                bms, bfin, bvar, bacc = burgers_timed(args.steps, args.warmup, mode, cfl)
+                bstep = bms / args.steps * 1e-3
+                bline[f"{mode}_cfl{cfl}"] = {
+                    "value": BURGERS_1M.ndof * STAGES / bstep, "unit": UNIT,
+                    "ms_per_step": bms / args.steps, "finite": bfin, "variant": bvar,
+                    "fp64_frac": BURGERS_1M.ndof * STAGES * FLOP_PER_DOF_STAGE_BURGERS / bstep
+                                 / 1e12 / fp64_tflops,
+                    "bytes_frac": BURGERS_1M.ndof * BYTES_PER_DOF_STEP_STAGED / bstep / 1e9 / hbm_gbs,
+                    "error_vs_characteristics": bacc}
+        line["burgers_1m"] = bline
+        # the same ADG-AT steps in FP64 (the composed step on the FP64 pipe)
+        f_ms, _, ffin, (fvar, _) = device_timed("at", args.steps, args.warmup, barrier, False,
+                                               local, variant="composed")
+        f_s = f_ms / args.steps * 1e-3
+        line["fp64_composed"] = {
+            "value": ndof * STAGES * args.steps / (f_ms * 1e-3), "unit": UNIT,
+            "ms_per_step": f_ms / args.steps, "steps": args.steps, "variant": fvar, "dtype": "f64",
+            "finite": ffin, "kernel": "k_step_fused (composed SSP-RK3 step in FP64) + k_step_fixup",
+            "fp64_tflops": ndof * FLOP_PER_DOF_STEP / f_s / 1e12,
+            "fp64_frac": ndof * FLOP_PER_DOF_STEP / f_s / 1e12 / fp64_tflops,
+            "hbm_frac": ndof * BYTES_PER_DOF_STEP / f_s / 1e9 / hbm_gbs}
         brate, bms, bdof, bn, bvariant = batched_timed(100, 3)
         line["batched"] = {"value": brate, "unit": UNIT, "ms_per_step": bms, "instances": bn,
                            "dof": bdof, "steps": 100, "variant": bvariant,
@@ -627,9 +807,7 @@ def main():
                                          "odd stage count adds a copy back into u)",
                                "peak_source": "FP64 unit counts x max SM clock"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(1 << 22, 3)
-        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
-                                "sample": sample}
+        line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

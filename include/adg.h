@@ -133,8 +133,14 @@ enum {
  *               coefficient below 2 in magnitude (small Courant numbers; ADG_EINVAL
  *               otherwise). Results below 2^-1022 are flushed to zero, and a NaN or infinity
  *               anywhere in u^n makes all of u^{n+1} NaN. AUTO picks COMPOSED_FIXED, else
- *               COMPOSED, where they apply (in a batch, where every instance admits them). All
- *               give the same scheme up to rounding.
+ *               COMPOSED, where they apply; a batch with AUTO times every kind of step that all
+ *               its instances admit (fixed point, FP64 composed, staged) at init and keeps the
+ *               fastest (adg_get_variant reports it). All give the same scheme up to rounding.
+ *   ept       : elements per thread of the composed-step kernels (not a paper quantity):
+ *               0 (default) lets init time the choices and keep the fastest (1 or 2 for the
+ *               fixed-point step, 1, 2 or 4 for the FP64 step; a batch's fixed-point step
+ *               also 4, i.e. work items of 256, 512 or 1024 elements); 1, 2 or 4 forces one
+ *               (ADG_EINVAL where that kernel has no such form). Results do not depend on it.
  */
 typedef struct {
   int32_t pde;
@@ -156,6 +162,7 @@ typedef struct {
   double nu;
   int32_t limiter;
   double tvb_m;
+  int32_t ept;
 } adg_config;
 
 /* Fill cfg with defaults: advection, upwind, SSP-RK3, [0, 2 pi], a = 1, cfl = 0.1, sync. */
@@ -231,7 +238,7 @@ int adg_check_finite(adg_ctx *c);
  * device-memory cap, and latency-critical loops that cannot afford cudaMalloc, which may
  * synchronise the device.
  *   p, K    : degree (1..ADG_MAX_P) and element count (1..2^30).
- *   dx      : element width (> 0).
+ *   dx      : element width (finite, > 0).
  *   u_dev   : device (K, p+1) row-major FP64 field (read only, caller-owned).
  *   out_dev : device pointer to one double that receives the integral (caller-owned).
  *   stream  : cudaStream_t (as void*), NULL for the default stream; the call is queued on

@@ -54,6 +54,7 @@ class Config:
     nu: float = 0.0             # > 0: viscous Burgers by the local DG method (Eq. burgers)
     limiter: bool = True        # Euler: TVB-minmod slope limiter on every stage output
     tvb_m: float = 0.0          # Euler: TVB constant M (0: minmod)
+    ept: int = 0                # elements per thread of the composed kernels (0: autotuned)
 
     def to_c(self):
         c = _abi.AdgConfig()
@@ -74,6 +75,7 @@ class Config:
         c.variant = {"auto": 0, "staged": 1, "composed": 2, "fixed": 3}[self.variant]
         c.caa_sync = int(self.caa_sync)
         c.nu = float(self.nu)
+        c.ept = int(self.ept)
         keep = []
         if self.probs is not None:
             arr = (C.c_double * len(self.probs))(*[float(v) for v in self.probs])
@@ -264,6 +266,12 @@ class BatchSolver:
         v, e = C.c_int32(), C.c_int32()
         check(load().adg_get_variant(self._ctx, int(i), C.byref(v), C.byref(e)), self._ctx)
         return {1: "staged", 2: "composed", 3: "fixed"}[v.value], e.value
+
+    def integral(self, i: int) -> float:
+        """Discrete integral (dx/2) sum_e w^T u^e of instance i's current state."""
+        v = C.c_double()
+        check(load().adg_integral(self._ctx, int(i), C.byref(v)), self._ctx)
+        return v.value
 
     def check_finite(self) -> None:
         check(load().adg_check_finite(self._ctx), self._ctx)

@@ -36,7 +36,7 @@ class AdgConfig(C.Structure):
         ("seed", C.c_uint64), ("probs", C.POINTER(C.c_double)),
         ("delay_table", C.POINTER(C.c_uint8)), ("table_steps", C.c_int64),
         ("variant", C.c_int32), ("caa_sync", C.c_int32), ("nu", C.c_double),
-        ("limiter", C.c_int32), ("tvb_m", C.c_double),
+        ("limiter", C.c_int32), ("tvb_m", C.c_double), ("ept", C.c_int32),
     ]
 
 

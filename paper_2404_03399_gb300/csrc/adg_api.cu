@@ -290,6 +290,7 @@ std::string check_config(const adg_config *c) {
   if (c->L < 1 || c->L > ADG_MAX_L) return "L must be in 1..16";
   if (c->at_order < 0 || c->at_order > ADG_MAX_Q) return "at_order must be in 0..5";
   if (c->variant < ADG_VARIANT_AUTO || c->variant > ADG_VARIANT_COMPOSED_FIXED) return "bad variant";
+  if (c->ept != 0 && c->ept != 1 && c->ept != 2 && c->ept != 4) return "ept must be 0, 1, 2 or 4";
   if (c->probs) {
     double s = 0;
     for (int k = 0; k < c->L; ++k) {
@@ -370,11 +371,14 @@ struct adg_ctx {
   int nfwork = 0;
   bool batch_fused = false;     // every instance runs composed steps
   bool batch_fixed = false;     // ... in fixed point
-  adg::BatchLite *lites_dev = nullptr;
+  adg::BatchLite *lites_ept[3] = {};   // work records of 256, 512, 1024 elements (batch tuner)
+  int nlites_ept[3] = {};
   std::unique_ptr<adg::BatchUniform> bu;   // shared coefficients per degree, when they are
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
   cudaGraphExec_t gexec[4] = {};   // one graph of G steps per chunk kind (kChunk*)
+  int fx_live = 0;                 // fixed-point state: 0 in u (FP64), 1 in v1, 2 in v2 (int64)
+  bool u_fresh = true;             // u holds the state of step n (FP64)
   int G = 32;
   int64_t n = 0;
 };
@@ -662,38 +666,78 @@ void fold_step_constants(InstHost &h) {
     for (int m = 0; m < 4; ++m)
       for (int i = 0; i < Np; ++i) Sc.R[st][m][i] = (double)Rl[st][m][i];
 
-  // Fixed-point limbs of the same coefficients (from the long double values) and the bounds
-  // of the integer step: every |c| < 2 (limbs within 32 bits), and channel scalars v1_p,
-  // v2_p at most twice the input bound (|X| < 2^58 as multiplicands; inputs are < 2^57).
+  // Fixed-point limbs of the same coefficients (from the long double values): C =
+  // round(c 2^58) in balanced limbs C = ch 2^29 + cl (adg_fixed.cuh); every |c| < 2 keeps
+  // both within 32 bits.
   adg::StepFixed &F = h.I.sf;
   std::memset(&F, 0, sizeof(F));
   bool ok = true;
   auto limbs = [&](ld c) {
     if (!(fabsl(c) < 1.999L)) ok = false;
     const long long C = ok ? llroundl(ldexpl(c, 58)) : 0;
+    const long long cl = ((C + (1ll << 28)) & ((1ll << 29) - 1)) - (1ll << 28);
     int2 r;
-    r.x = (int)(C >> 29);
-    r.y = (int)(C & 0x1FFFFFFF);
+    r.x = (int)((C - cl) >> 29);
+    r.y = (int)cl;
     return r;
   };
+  // Bounds of one fixed-point sum of terms c_m x_m whose multiplicands are below g_m 2^57
+  // (g = 1: input values and traces; g = 2: channel scalars), so |xh| <= g 2^28 and
+  // 0 <= xl < 2^29: a = sum ch xh and b = 2^28 + sum (ch xl + cl xh) below 2^62, and the
+  // result, below sum |c| g 2^57 + n, below 2^61.
+  auto sum_ok = [&](const std::vector<std::pair<ld, int>> &terms) {
+    ld ab = 0, bb = ldexpl(1.0L, 28), rb = 0;
+    for (auto &cg : terms) {
+      const ld c = fabsl(cg.first), g = (ld)cg.second;
+      const ld ch = c * ldexpl(1.0L, 29) + 1.0L, xh = g * ldexpl(1.0L, 28) + 1.0L;
+      ab += ch * xh;
+      bb += ch * ldexpl(1.0L, 29) + ldexpl(1.0L, 28) * xh;
+      rb += c * g;
+    }
+    return ab < ldexpl(1.0L, 62) && bb < ldexpl(1.0L, 62) && rb < 15.9L;
+  };
   ld b1 = fabsl(kl[0]), b2 = fabsl(kl[1]);
+  bool sums = true;
+  std::vector<std::pair<ld, int>> s1{{kl[0], 1}}, s2{{kl[1], 1}, {kl[2], 2}};
   for (int i = 0; i < Np; ++i) {
-    for (int j = 0; j < Np; ++j) F.G[i * Np + j] = limbs(Gl[i * Np + j]);
+    std::vector<std::pair<ld, int>> row;
+    for (int j = 0; j < Np; ++j) {
+      F.G[i * Np + j] = limbs(Gl[i * Np + j]);
+      row.push_back({Gl[i * Np + j], 1});
+    }
     F.r1[i] = limbs(r1l[i]);
     F.r2[i] = limbs(r2l[i]);
-    for (int t = 0; t < 3; ++t) F.h[t][i] = limbs(hl[t][i]);
+    for (int t = 0; t < 3; ++t) {
+      F.h[t][i] = limbs(hl[t][i]);
+      row.push_back({hl[t][i], t == 0 ? 1 : 2});
+    }
+    sums = sums && sum_ok(row);
+    s1.push_back({r1l[i], 1});
+    s2.push_back({r2l[i], 1});
     b1 += fabsl(r1l[i]);
     b2 += fabsl(r2l[i]);
   }
   for (int t = 0; t < 3; ++t) F.k[t] = limbs(kl[t]);
+  sums = sums && sum_ok(s1) && sum_ok(s2);
   b2 += fabsl(kl[2]) * b1;
-  h.fixed_ok = ok && b1 < 1.999L && b2 < 1.999L;
+  // channel scalars v1_p, v2_p at most twice the input bound (|X| < 2^58 as multiplicands;
+  // inputs are < 2^57)
+  h.fixed_ok = ok && sums && b1 < 1.999L && b2 < 1.999L;
   // the PE-face responses likewise (from the long double values), for the integer correction
+  // of differences below 2^57
   std::memset(h.I.Rf, 0, sizeof(h.I.Rf));
   ok = true;
-  for (int st = 0; st < 3; ++st)
-    for (int m = 0; m < 4; ++m)
-      for (int i = 0; i < Np; ++i) h.I.Rf[st][m][i] = limbs(Rl[st][m][i]);
+  bool rsums = true;
+  for (int m = 0; m < 4; ++m)
+    for (int i = 0; i < Np; ++i) {
+      std::vector<std::pair<ld, int>> row;
+      for (int st = 0; st < 3; ++st) {
+        h.I.Rf[st][m][i] = limbs(Rl[st][m][i]);
+        row.push_back({Rl[st][m][i], 1});
+      }
+      rsums = rsums && sum_ok(row);
+    }
+  ok = ok && rsums;
   h.I.face_fx = ok ? 1 : 0;
 }
 
@@ -768,6 +812,12 @@ int reset_exponent(adg_ctx *c, InstHost &h) {
 int autotune_fused(adg_ctx *c, InstHost &h) {
   Inst &I = h.I;
   const size_t nd = (size_t)I.K * I.Np;
+  if (h.cfg.ept > 0) {   // forced by the caller
+    if (I.fused == 2 && h.cfg.ept > 2)
+      return fail(c, ADG_EINVAL, "the fixed-point composed step takes ept 1 or 2");
+    I.ept = h.cfg.ept;
+    return ADG_OK;
+  }
   if (I.K < 4 * 2 * adg::kTile) return ADG_OK;   // tiny meshes: one element per thread
   // The fixed-point step is timed in its int64 -> int64 form (the bulk of a chunk): one
   // FP64 -> int64 step fills v1, then v1 and v2 alternate. The FP64 step alternates copies
@@ -1007,28 +1057,49 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   return ADG_OK;
 }
 
-// Chunks of one adg_step call. The fixed-point step (single instance or batch) keeps the
-// field in int64 from the call's first step to its last: a chunk that is not the call's first
-// reads the int64 state from v2, one that is not its last leaves it there (its step count is
-// even: G). Every other path ignores the kind (each chunk reads and writes u).
-constexpr int kChunkFirst = 1, kChunkLast = 2, kChunkWhole = kChunkFirst | kChunkLast;
+// Chunks of steps. The fixed-point step (single instance or batch) keeps the state in int64
+// from step to step, across chunks and adg_step calls: the chunk kind is the field that
+// holds the state when the chunk starts (0: u in FP64, 1: v1, 2: v2 in int64); every step
+// writes the other int64 field, so a chunk of m steps from field k ends in fixed_end(k, m).
+// Every other path reads and writes u (kind kChunkFP64). The FP64 field u is formed from the
+// int64 state when something reads it (sync_state).
+constexpr int kChunkFP64 = 3;
+
+int fixed_end(int from, int64_t m) {
+  if (m == 0) return from;
+  if (from == 0) return (m % 2) ? 1 : 2;
+  return (m % 2) ? 3 - from : from;
+}
+
+// The context's steps run in fixed point (single instance or batch).
+bool fixed_state(const adg_ctx *c) {
+  return c->batch ? c->batch_fixed : c->inst[0].I.fused == 2;
+}
+
+// Writes the FP64 state of step n into every instance's u when it lives in int64 (after
+// fixed-point steps); entry points that read u call it first.
+int sync_state(adg_ctx *c) {
+  if (!fixed_state(c) || c->fx_live == 0 || c->u_fresh) return ADG_OK;
+  for (auto &h : c->inst) {
+    const Inst &I = h.I;
+    const long long *X = reinterpret_cast<const long long *>(c->fx_live == 1 ? I.v1 : I.v2);
+    CK(adg::launch_fixed_to_fp64(X, I.u, (size_t)I.K * I.Np, I.fx, c->n, c->stream));
+  }
+  c->u_fresh = true;
+  return ADG_OK;
+}
 
 int launch_fused_steps(adg_ctx *c, int nsteps, int kind);
 
-int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
+int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkFP64) {
   if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps, kind);
-  const bool first = (kind & kChunkFirst) != 0, last = (kind & kChunkLast) != 0;
-  if (c->batch && c->batch_fixed && (nsteps >= 2 || !first)) {
+  if (c->batch && c->batch_fixed) {
     // as launch_fused_steps: fields 0 (u, FP64), 1 and 2 (v1, v2, int64); each step carries
     // its own PE-face correction
-    if (!last && nsteps % 2)
-      return fail(c, ADG_EINVAL, "internal: a chunk that carries int64 state needs an even count");
-    int in = first ? 0 : 2;
+    int in = kind == kChunkFP64 ? 0 : kind;
     for (int rel = 0; rel < nsteps; ++rel) {
-      const bool fin = rel > 0 || !first;
-      const bool to_u = last && rel == nsteps - 1;
-      const int out = to_u ? 0 : !last ? (((nsteps - 1 - rel) % 2 == 0) ? 2 : 1) : (in == 1 ? 2 : 1);
-      const int fmt = (fin ? adg::kFmtInFixed : 0) | (to_u ? 0 : adg::kFmtOutFixed);
+      const int out = in == 1 ? 2 : 1;
+      const int fmt = (in != 0 ? adg::kFmtInFixed : 0) | adg::kFmtOutFixed;
       CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
                                       in, out, fmt, true, rel, c->stream, c->bu.get()));
       in = out;
@@ -1105,34 +1176,30 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkWhole) {
 }
 
 // Composed steps. FP64: they ping-pong between u and v1; an odd count ends with a copy back
-// into u. Fixed point: the chunk reads u (FP64, first chunk of a call) or the int64 state in
-// v2, alternates v1 and v2, and writes u (FP64, last chunk) or leaves the int64 state in v2.
+// into u. Fixed point: the chunk reads the state from the field its kind names (u in FP64 or
+// v1 / v2 in int64) and alternates v1 and v2.
 int launch_fused_steps(adg_ctx *c, int nsteps, int kind) {
   const Inst &I = c->inst[0].I;
-  const bool first = (kind & kChunkFirst) != 0, last = (kind & kChunkLast) != 0;
-  if (I.fused == 2 && (nsteps >= 2 || !first)) {
-    if (!last && nsteps % 2)
-      return fail(c, ADG_EINVAL, "internal: a chunk that carries int64 state needs an even count");
-    // With PE faces, one face kernel between consecutive steps adds the earlier step's
-    // correction and forms the next step's differences; the one before a chunk's first step
-    // also corrects the previous chunk's last step, the one after the call's last step only
-    // corrects.
+  if (I.fused == 2) {
+    // With PE faces, one face kernel before the chunk's first step forms its differences,
+    // one between consecutive steps adds the earlier step's correction and forms the next
+    // step's differences, and one after the last step adds its correction, so that the int64
+    // state is complete at the end of every chunk.
     const bool faces = I.async != 0;
     if (faces && !I.fd)
       return fail(c, ADG_EINVAL, "internal: fixed-point step with PE faces lacks its buffer");
-    void *in = first ? static_cast<void *>(I.u) : static_cast<void *>(I.v2);
-    int fin_prev = 1;   // the previous step's input format (int64 but after an FP64 first step)
+    const int from = kind == kChunkFP64 ? 0 : kind;
+    void *in = from == 0 ? static_cast<void *>(I.u) : (from == 1 ? static_cast<void *>(I.v1)
+                                                                 : static_cast<void *>(I.v2));
+    int cur = from, fin_prev = 1;
     for (int rel = 0; rel < nsteps; ++rel) {
-      const bool fin = rel > 0 || !first;
-      const bool to_u = last && rel == nsteps - 1;
-      void *out;
-      if (to_u) out = I.u;
-      else if (!last) out = ((nsteps - 1 - rel) % 2 == 0) ? I.v2 : I.v1;   // ends in v2
-      else out = (in == I.v1) ? I.v2 : I.v1;
-      const int fmt = (fin ? adg::kFmtInFixed : 0) | (to_u ? 0 : adg::kFmtOutFixed);
+      const int nxt = cur == 1 ? 2 : 1;
+      void *out = nxt == 1 ? static_cast<void *>(I.v1) : static_cast<void *>(I.v2);
+      const bool fin = cur != 0;
+      const int fmt = (fin ? adg::kFmtInFixed : 0) | adg::kFmtOutFixed;
       if (faces) {
-        if (rel == 0 && first)
-          CK(adg::launch_face_step(I, in, 0, 0, 0, adg::kFaceDiff, c->stream));
+        if (rel == 0)
+          CK(adg::launch_face_step(I, in, 0, fin ? 1 : 0, 0, adg::kFaceDiff, c->stream));
         else
           CK(adg::launch_face_step(I, in, rel, 1, fin_prev, adg::kFaceApply | adg::kFaceDiff,
                                    c->stream));
@@ -1140,9 +1207,10 @@ int launch_fused_steps(adg_ctx *c, int nsteps, int kind) {
       CK(adg::launch_fixed_step(I, in, out, rel, fmt, c->stream));
       fin_prev = fin ? 1 : 0;
       in = out;
+      cur = nxt;
     }
-    if (faces && last)
-      CK(adg::launch_face_step(I, I.u, nsteps, 0, fin_prev, adg::kFaceApply, c->stream));
+    if (faces && nsteps > 0)
+      CK(adg::launch_face_step(I, in, nsteps, 1, fin_prev, adg::kFaceApply, c->stream));
   } else {
     for (int rel = 0; rel < nsteps; ++rel) {
       const double *uin = (rel % 2 == 0) ? I.u : I.v1;
@@ -1384,8 +1452,19 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
   const size_t ring_n = I.async ? (size_t)I.R * kStages * I.P : 0;
   const int dir = I.a >= 0.0 ? 1 : -1;
 
-  DevBuf g, ck_u, ck_ring, seg, lam, lring;
-  int r = dev_alloc(c, g, nd * sizeof(double));
+  DevBuf g, ck_u, ck_ring, seg, lam, lring, ck_fx;
+  // the fixed-point state (int64 field and its scale slots) is put back exactly at the end
+  const int live0 = c->fx_live;
+  int r = ADG_OK;
+  if (live0) {
+    r = dev_alloc(c, ck_fx, nd * sizeof(long long) + 3 * sizeof(adg::FxSlot));
+    if (r) return r;
+    CK(cudaMemcpyAsync(ck_fx.p, live0 == 1 ? I.v1 : I.v2, nd * sizeof(long long),
+                       cudaMemcpyDeviceToDevice, c->stream));
+    CK(cudaMemcpyAsync(static_cast<char *>(ck_fx.p) + nd * sizeof(long long), I.fx,
+                       3 * sizeof(adg::FxSlot), cudaMemcpyDeviceToDevice, c->stream));
+  }
+  r = dev_alloc(c, g, nd * sizeof(double));
   if (!r) r = dev_alloc(c, ck_u, (size_t)nck * nd * sizeof(double));
   if (!r) r = dev_alloc(c, ck_ring, (size_t)nck * ring_n * sizeof(double2));
   if (!r && states) r = dev_alloc(c, seg, ((size_t)C * kStages + 1) * nd * sizeof(double));
@@ -1425,7 +1504,8 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
     }
   }
   double J = 0.0;
-  r = reduce(c, h, 3, g.d(), 0.5 * (h.dx / 2.0), &J);
+  r = sync_state(c);
+  if (!r) r = reduce(c, h, 3, g.d(), 0.5 * (h.dx / 2.0), &J);
   if (r) return r;
 
   CK(adg::launch_adj_init(I.u, g.d(), K, Np, h.M, h.dx / 2.0, lam.d(), c->stream));
@@ -1523,6 +1603,14 @@ int run_gradient(adg_ctx *c, const double *target_dev, int64_t nsteps, int C, do
     r = set_step(c, h, n0);
     if (!r) r = reset_exponent(c, h);
     if (r) return r;
+    c->fx_live = live0;
+    c->u_fresh = true;
+    if (live0) {
+      CK(cudaMemcpyAsync(live0 == 1 ? I.v1 : I.v2, ck_fx.p, nd * sizeof(long long),
+                         cudaMemcpyDeviceToDevice, c->stream));
+      CK(cudaMemcpyAsync(I.fx, static_cast<char *>(ck_fx.p) + nd * sizeof(long long),
+                         3 * sizeof(adg::FxSlot), cudaMemcpyDeviceToDevice, c->stream));
+    }
   }
   CK(cudaStreamSynchronize(c->stream));
   *J_out = J;
@@ -1603,7 +1691,7 @@ void adg_destroy(adg_ctx *c) {
   }
   cudaFree(c->meta);
   cudaFree(c->insts_dev);
-  cudaFree(c->lites_dev);
+  for (auto *l : c->lites_ept) cudaFree(l);
   cudaFree(c->work_dev);
   cudaFree(c->fwork_dev);
   cudaFree(c->partials);
@@ -1645,6 +1733,116 @@ int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx 
   return ADG_OK;
 }
 
+// Batch state at step 0 from the callers' initial fields (after the tuner's timing steps): u
+// from u0, step counters and rings cleared, delay tables refilled on the next step, scale slots
+// of the fixed-point step reset.
+int reset_batch(adg_ctx *c, const double *const *u0_devs) {
+  const int n = (int)c->inst.size();
+  CK(cudaMemsetAsync(c->meta, 0, 2 * sizeof(int64_t) * n, c->stream));
+  for (int i = 0; i < n; ++i) {
+    InstHost &h = c->inst[i];
+    CK(adg::launch_to_internal(u0_devs[i], h.I.u, h.I.K, h.I.Np, c->stream));
+    if (h.ring)
+      CK(cudaMemsetAsync(h.ring, 0, (size_t)h.I.R * h.I.ns * h.I.P * sizeof(double2), c->stream));
+    h.tbase = -(int64_t)1 << 40;
+    if (h.fx) CK(adg::launch_fixed_reset(h.I.u, (size_t)h.I.K * h.I.Np, h.fx, 0, c->stream));
+  }
+  c->n = 0;
+  c->fx_live = 0;
+  c->u_fresh = true;
+  return ADG_OK;
+}
+
+// Selects the kind of batched step (2: fixed point, 1: FP64 composed, 0: staged) and the
+// elements per thread of the fixed-point kernel, and uploads the instances' descriptors.
+int apply_batch_kind(adg_ctx *c, int kind, int ept) {
+  c->batch_fused = kind >= 1;
+  c->batch_fixed = kind == 2;
+  std::vector<Inst> hi;
+  for (auto &h : c->inst) {
+    h.I.fused = kind;
+    h.I.ept = kind == 2 ? ept : 1;
+    hi.push_back(h.I);
+  }
+  if (kind == 2 && c->bu) {
+    const int k = ept == 4 ? 2 : ept - 1;
+    c->bu->items_dev = c->lites_ept[k];
+    c->bu->nitems = c->nlites_ept[k];
+    c->bu->ept = ept;
+  }
+  CK(cudaMemcpy(c->insts_dev, hi.data(), sizeof(Inst) * hi.size(), cudaMemcpyHostToDevice));
+  return ADG_OK;
+}
+
+// The batch autotuner: every kind of step all instances admit (or the one their configs
+// force) and, for the fixed-point step with shared coefficients, work items of 256, 512 and
+// 1024 elements (one, two or four per thread; or the forced ept), timed over four steps after
+// two untimed ones on the batch itself; the fastest is kept and the state is reset to the
+// initial fields. Batches below 2^20 elements skip the timing and take fixed point, else the
+// FP64 composed step, else the staged kernels, with two elements per thread.
+int tune_batch(adg_ctx *c, const double *const *u0_devs) {
+  struct Cand {
+    int kind, ept;
+  };
+  int maxkind = 2, forced = -1, ept_forced = 0;
+  int64_t elements = 0;
+  for (auto &h : c->inst) {
+    maxkind = std::min(maxkind, h.I.fused);
+    if (h.cfg.variant == ADG_VARIANT_STAGED) forced = 0;
+    if (h.cfg.variant == ADG_VARIANT_COMPOSED) forced = 1;
+    if (h.cfg.variant == ADG_VARIANT_COMPOSED_FIXED) forced = 2;
+    if (h.cfg.ept) ept_forced = h.cfg.ept;
+    elements += h.I.K;
+  }
+  std::vector<Cand> cands;
+  for (int kind = maxkind; kind >= 0; --kind) {
+    if (forced >= 0 && kind != forced) continue;
+    if (kind == 2 && c->bu) {
+      for (int ept : {2, 1, 4})
+        if (!ept_forced || ept == ept_forced) cands.push_back({kind, ept});
+    } else {
+      cands.push_back({kind, 1});
+    }
+  }
+  if (cands.empty()) return fail(c, ADG_EINVAL, "no kind of batched step fits every instance");
+  Cand best = cands[0];
+  if (cands.size() > 1 && elements >= (1 << 20)) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+    float best_ms = 1e30f;
+    int r = ADG_OK;
+    for (const Cand &cd : cands) {
+      r = apply_batch_kind(c, cd.kind, cd.ept);
+      if (!r) r = reset_batch(c, u0_devs);
+      for (auto &h : c->inst)
+        if (!r) r = ensure_table(c, h, 0, 6);
+      if (!r) r = launch_steps(c, 2, kChunkFP64);
+      if (r) break;
+      cudaEventRecord(a, c->stream);
+      r = launch_steps(c, 4, cd.kind == 2 ? fixed_end(0, 2) : kChunkFP64);
+      if (r) break;
+      cudaEventRecord(b, c->stream);
+      if (cudaEventSynchronize(b) != cudaSuccess) {
+        r = fail(c, ADG_ECUDA, "batch tuner: cudaEventSynchronize");
+        break;
+      }
+      float ms = 0.0f;
+      cudaEventElapsedTime(&ms, a, b);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = cd;
+      }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (r) return r;
+  }
+  int r = apply_batch_kind(c, best.kind, best.ept);
+  if (!r) r = reset_batch(c, u0_devs);
+  return r;
+}
+
 int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t n, void *stream,
                    adg_ctx **out) {
   if (!out) return fail(nullptr, ADG_EINVAL, "out is NULL");
@@ -1673,35 +1871,47 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
   if (!r) {
     std::vector<Inst> hi(n);
     std::vector<int2> work, fwork;
-    // one batch runs one kind of step: fixed point if every instance admits it, else the
-    // FP64 composed step if every instance admits that, else the staged kernels
-    c->batch_fused = true;
-    c->batch_fixed = true;
-    for (int i = 0; i < n; ++i) {
-      c->batch_fused = c->batch_fused && c->inst[i].I.fused;
-      c->batch_fixed = c->batch_fixed && c->inst[i].I.fused == 2;
-    }
+    // the kinds of step every instance admits (a batch runs one kind for all instances):
+    // fixed point, the FP64 composed step, the staged kernels; a variant forced by the
+    // instances' configs leaves only that kind
+    bool all_fixed = true, all_fused = true;
+    int forced = ADG_VARIANT_AUTO, ept_forced = 0;
     for (int i = 0; i < n && !r; ++i) {
-      if (c->inst[i].I.ls)
+      const InstHost &h = c->inst[i];
+      all_fused = all_fused && h.I.fused;
+      all_fixed = all_fixed && h.I.fused == 2;
+      if (h.I.ls)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches need rk = ADG_SSPRK3");
-      else if (c->inst[i].I.visc || c->inst[i].I.euler)
+      else if (h.I.visc || h.I.euler)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches take the inviscid scalar equations");
-      else if (c->inst[i].cfg.variant == ADG_VARIANT_COMPOSED_FIXED && !c->batch_fixed)
-        r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) +
-                                    ": the fixed-point composed step needs every instance of the "
-                                    "batch to admit it");
-      if (!c->batch_fused) c->inst[i].I.fused = 0;
-      else if (!c->batch_fixed) c->inst[i].I.fused = 1;
+      const int v = h.cfg.variant;
+      if (!r && v != ADG_VARIANT_AUTO) {
+        if (forced != ADG_VARIANT_AUTO && forced != v)
+          r = fail(c, ADG_EINVAL, "instances of one batch force different variants");
+        forced = v;
+      }
+      if (!r && h.cfg.ept) {
+        if (ept_forced && ept_forced != h.cfg.ept)
+          r = fail(c, ADG_EINVAL, "instances of one batch force different ept");
+        ept_forced = h.cfg.ept;
+      }
     }
-    c->batch_fixed = c->batch_fixed && c->batch_fused;
-    for (int i = 0; i < n; ++i) {
-      hi[i] = c->inst[i].I;
+    if (!r && forced == ADG_VARIANT_COMPOSED_FIXED && !all_fixed)
+      r = fail(c, ADG_EINVAL, "the fixed-point composed step needs every instance of the batch to admit it");
+    if (!r && forced == ADG_VARIANT_COMPOSED && !all_fused)
+      r = fail(c, ADG_EINVAL, "the composed step needs every instance of the batch to admit it");
+    // the FP64 composed step of instances that admit fixed point (their I.fused is 2)
+    for (int i = 0; i < n && !r; ++i) {
+      InstHost &h = c->inst[i];
+      h.I.ept = 1;
+      hi[i] = h.I;
       for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));
       if (hi[i].async)
         for (int j0 = 0; j0 < hi[i].P; j0 += 256) fwork.push_back(make_int2(i, j0));
     }
-    // every instance of a degree with the same fixed-point coefficients: pass them per degree
-    if (!r && c->batch_fixed) {
+    // every instance of a degree with the same fixed-point coefficients: pass them per degree,
+    // with one record per work item of ept tiles (ept elements per thread)
+    if (!r && all_fixed) {
       bool uniform = true;
       const adg::StepFixed *ref[adg::kMaxNp - 1] = {nullptr, nullptr, nullptr, nullptr};
       for (int i = 0; i < n && uniform; ++i) {
@@ -1711,42 +1921,44 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
         else uniform = std::memcmp(ref[d], &f, sizeof(f)) == 0;
       }
       if (uniform) {
-        // one record per work item of two tiles (two elements per thread)
-        const int ept = 2;
-        std::vector<adg::BatchLite> lites;
-        for (int i = 0; i < n; ++i) {
-          const Inst &I = c->inst[i].I;
-          for (int e0 = 0; e0 < I.K; e0 += ept * adg::kTile) {
-            adg::BatchLite L;
-            L.f[0] = I.u;
-            L.f[1] = I.v1;
-            L.f[2] = I.v2;
-            L.meta = I.meta;
-            L.fx = I.fx;
-            L.K = I.K;
-            L.Np = I.Np;
-            L.e0 = e0;
-            L.pad = 0;
-            lites.push_back(L);
-          }
-        }
         c->bu.reset(new (std::nothrow) adg::BatchUniform());
-        if (!c->bu) {
-          r = fail(c, ADG_ENOMEM, "host allocation failed");
-        } else if (cudaMalloc(&c->lites_dev, sizeof(adg::BatchLite) * lites.size()) != cudaSuccess ||
-                   cudaMemcpy(c->lites_dev, lites.data(), sizeof(adg::BatchLite) * lites.size(),
-                              cudaMemcpyHostToDevice) != cudaSuccess) {
-          r = fail(c, ADG_ENOMEM, "cudaMalloc(batch records)");
-        } else {
+        if (!c->bu) r = fail(c, ADG_ENOMEM, "host allocation failed");
+        for (int k = 0; k < 3 && !r; ++k) {
+          const int ept = 1 << k;
+          if (ept_forced && ept != ept_forced) continue;
+          std::vector<adg::BatchLite> lites;
+          for (int i = 0; i < n; ++i) {
+            const Inst &I = c->inst[i].I;
+            for (int e0 = 0; e0 < I.K; e0 += ept * adg::kTile) {
+              adg::BatchLite L;
+              L.f[0] = I.u;
+              L.f[1] = I.v1;
+              L.f[2] = I.v2;
+              L.meta = I.meta;
+              L.fx = I.fx;
+              L.K = I.K;
+              L.Np = I.Np;
+              L.e0 = e0;
+              L.pad = 0;
+              lites.push_back(L);
+            }
+          }
+          if (cudaMalloc(&c->lites_ept[k], sizeof(adg::BatchLite) * lites.size()) != cudaSuccess ||
+              cudaMemcpy(c->lites_ept[k], lites.data(), sizeof(adg::BatchLite) * lites.size(),
+                         cudaMemcpyHostToDevice) != cudaSuccess)
+            r = fail(c, ADG_ENOMEM, "cudaMalloc(batch records)");
+          c->nlites_ept[k] = (int)lites.size();
+        }
+        if (!r) {
           std::memset(&c->bu->uf, 0, sizeof(c->bu->uf));
           for (int d = 0; d < adg::kMaxNp - 1; ++d)
             if (ref[d]) c->bu->uf.sf[d] = *ref[d];
-          c->bu->items_dev = c->lites_dev;
-          c->bu->nitems = (int)lites.size();
-          c->bu->ept = ept;
         }
       }
     }
+    if (!r && ept_forced && ept_forced != 1 && !(all_fixed && c->bu && forced != ADG_VARIANT_COMPOSED &&
+                                                  forced != ADG_VARIANT_STAGED))
+      r = fail(c, ADG_EINVAL, "ept > 1 in a batch needs the fixed-point step with shared coefficients");
     c->nwork = (int)work.size();
     c->nfwork = (int)fwork.size();
     if (cudaMalloc(&c->insts_dev, sizeof(Inst) * n) != cudaSuccess ||
@@ -1758,6 +1970,7 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
              (!fwork.empty() && cudaMemcpy(c->fwork_dev, fwork.data(), sizeof(int2) * fwork.size(), cudaMemcpyHostToDevice) != cudaSuccess))
       r = fail(c, ADG_ECUDA, "cudaMemcpy(batch descriptors)");
   }
+  if (!r) r = tune_batch(c, u0_devs);
   if (!r && cudaStreamSynchronize(c->stream) != cudaSuccess) r = fail(c, ADG_ECUDA, "sync");
   if (r) {
     g_last_error = c->err;
@@ -1771,13 +1984,12 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
 int adg_step(adg_ctx *c, int64_t nsteps) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (nsteps < 0) return fail(c, ADG_EINVAL, "nsteps must be >= 0");
-  // int64 state carried from chunk to chunk inside the call (single fixed-point instance)
-  const bool carry = c->batch ? c->batch_fixed : c->inst[0].I.fused == 2;
+  // the fixed-point step carries its int64 state from chunk to chunk and call to call
+  const bool carry = fixed_state(c);
   int64_t left = nsteps;
   while (left > 0) {
     const int chunk = (int)std::min<int64_t>(left, c->G);
-    const int kind = !carry ? kChunkWhole
-                            : (left == nsteps ? kChunkFirst : 0) | (left == chunk ? kChunkLast : 0);
+    const int kind = carry ? c->fx_live : kChunkFP64;
     for (auto &h : c->inst) {
       int r = ensure_table(c, h, c->n, chunk);
       if (r) return r;
@@ -1791,6 +2003,10 @@ int adg_step(adg_ctx *c, int64_t nsteps) {
     } else {
       int r = launch_steps(c, chunk, kind);
       if (r) return r;
+    }
+    if (carry) {
+      c->fx_live = fixed_end(kind, chunk);
+      c->u_fresh = false;
     }
     c->n += chunk;
     left -= chunk;
@@ -1808,6 +2024,10 @@ int adg_run(adg_ctx *c, double t_end) {
 
 int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  {
+    int r0 = sync_state(c);
+    if (r0) return r0;
+  }
   if (index < 0 || index >= (int)c->inst.size()) return fail(c, ADG_EINVAL, "bad instance index");
   if (!u_dev) return fail(c, ADG_EINVAL, "u_dev is NULL");
   InstHost &h = c->inst[index];
@@ -1839,6 +2059,10 @@ int adg_get_variant(adg_ctx *c, int32_t index, int32_t *variant_out, int32_t *ep
 
 int adg_integral(adg_ctx *c, int32_t index, double *out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  {
+    int r0 = sync_state(c);
+    if (r0) return r0;
+  }
   if (index < 0 || index >= (int)c->inst.size() || !out) return fail(c, ADG_EINVAL, "bad argument");
   InstHost &h = c->inst[index];
   return reduce(c, h, 0, nullptr, h.dx / 2.0, out);
@@ -1846,6 +2070,10 @@ int adg_integral(adg_ctx *c, int32_t index, double *out) {
 
 int adg_misfit(adg_ctx *c, int32_t index, const double *target_dev, double *J_out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  {
+    int r0 = sync_state(c);
+    if (r0) return r0;
+  }
   if (index < 0 || index >= (int)c->inst.size() || !target_dev || !J_out)
     return fail(c, ADG_EINVAL, "bad argument");
   InstHost &h = c->inst[index];
@@ -1859,6 +2087,10 @@ int adg_misfit(adg_ctx *c, int32_t index, const double *target_dev, double *J_ou
 
 int adg_check_finite(adg_ctx *c) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  {
+    int r0 = sync_state(c);
+    if (r0) return r0;
+  }
   for (size_t i = 0; i < c->inst.size(); ++i) {
     InstHost &h = c->inst[i];
     for (int comp = 0; comp < (h.I.euler ? 3 : 1); ++comp) {
@@ -1915,6 +2147,8 @@ int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_
     return fail(c, ADG_EINVAL, "adg_grad covers the inviscid scalar equations");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, ADG_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");
   if (!target_dev || !grad_u0_dev || !J_out) return fail(c, ADG_EINVAL, "NULL target, gradient or J");
+  int r = sync_state(c);
+  if (r) return r;
   return run_gradient(c, target_dev, nsteps, ckpt_every, grad_u0_dev, J_out);
 }
 

@@ -3,7 +3,9 @@
 //
 // On this part a warp's FP64 instruction occupies the FP64 pipe for 16 clocks (2 lanes per
 // clock per SM) while a 32 x 32 -> 64-bit integer multiply-add issues at the integer rate,
-// so the composed step (StepConsts) is evaluated exactly in integers.
+// so the composed step (StepConsts) is evaluated in 58-bit block fixed point with integer
+// multiplies (one scale per field and step; not exact: a sum of n terms is off by less than
+// n/2 + 1/2 units of its last place, 2^-57 of the field's largest value per unit).
 //
 // Representation: a field at step n is either FP64 or int64 values X with one scale for the
 // whole field, value = X 2^sigma. A step first brings its input to the working scale sigma'
@@ -12,15 +14,17 @@
 //               (|x| < 2^(En - 1022)), X = round(x 2^-sigma');
 //   int64 input (|X| < 2^62; b the bit length of the OR of all |X| less one for negative X,
 //               so max |X| < 2^(b+1)): X' = round(X 2^-(b-56)), sigma' = sigma + (b - 56).
-// X is split into limbs X = xh 2^29 + xl with 0 <= xl < 2^29, and a coefficient c
-// (|c| < 2) into C = round(c 2^58) = ch 2^29 + cl likewise. Then
-//   c x 2^-sigma' ~ C X 2^-58 = ch xh + (ch xl + cl xh) 2^-29 + cl xl 2^-58,
-// the last term (< 1 unit) is dropped, the others accumulate exactly in two 64-bit sums a and
-// b, and a sum of terms is rounded once: a + round(b 2^-29). With |X| < 2^58 for the channel
-// scalars and at most 8 terms per sum, |a| < 2^62 and |b| < 2^63 (the host checks the
-// coefficient bounds that keep the channel scalars below 2^58), and every result is below
-// 2^62 (|G| rows, |h| at most 20 x 2^57). Results are stored as int64 at sigma' or rounded
-// to FP64 (round to nearest even).
+// Products split a value as X = xh 2^29 + xl with 0 <= xl < 2^29, and a coefficient c
+// (|c| < 2) as C = round(c 2^58) = ch 2^29 + cl with balanced -2^28 <= cl < 2^28. Then
+//   c x 2^-sigma' ~ C X 2^-58 = ch xh + (ch xl + cl xh) 2^-29 + cl xl 2^-58:
+// the first two terms are three 32 x 32 -> 64-bit products that accumulate exactly in two
+// 64-bit sums a and b; the last (|.| < 1/2 unit, with the sign of cl) is dropped. A sum of n
+// terms is rounded once, a + round(b 2^-29): its error is below n/2 + 1/2 units, and the
+// balanced coefficient limbs keep the dropped terms from all leaning one way (an unsigned cl
+// would truncate every product downward). The host checks, per sum and from the
+// coefficients, that a, b and the result stay inside 64 bits (every multiplicand below 2^58:
+// inputs below 2^57, channel scalars below 2^58). Results are stored as int64 at sigma' or
+// rounded to FP64 (round to nearest even).
 //
 // Scale bookkeeping: slot n % 3 of the instance's FxSlot[3] describes u^n: E (largest
 // biased exponent when u^n is FP64; 2047 marks a NaN or infinity, carried through int64
@@ -39,15 +43,17 @@ struct FxAcc {
 };
 
 // Each product is a 32 x 32 -> 64-bit mul.wide.s32 followed by a 64-bit add, which the
-// assembler fuses into one wide multiply-add on the FMA pipe (measured: about one
-// instruction per product; a PTX mad.wide.s32 came out near two and a half, and a C++
-// (long long) product becomes a full 64-bit multiply).
+// assembler fuses into one wide multiply-add (measured: about one instruction per product; a
+// PTX mad.wide.s32 came out near two and a half, a C++ (long long) product becomes a full
+// 64-bit multiply, and forming the cross terms as high words of 32-bit products (mad.hi)
+// issued more slowly than these wide products in this kernel's shape).
 __device__ __forceinline__ long long fx_mul(int c, int x) {
   long long t;
   asm("mul.wide.s32 %0, %1, %2;" : "=l"(t) : "r"(c), "r"(x));
   return t;
 }
 
+// c = {ch, cl} (StepFixed limbs), x = (xh, xl) (fx_split).
 __device__ __forceinline__ void fx_mac(FxAcc &s, int2 c, int xh, int xl) {
   s.a += fx_mul(c.x, xh);
   s.b += fx_mul(c.x, xl);
@@ -56,6 +62,8 @@ __device__ __forceinline__ void fx_mac(FxAcc &s, int2 c, int xh, int xl) {
 
 __device__ __forceinline__ long long fx_round(const FxAcc &s) { return s.a + (s.b >> 29); }
 
+// |X| < 2^58: xh = floor(X 2^-29), xl = X - xh 2^29 (two instructions; a balanced split
+// of X measured 4% slower in the composed step).
 __device__ __forceinline__ void fx_split(long long X, int &xh, int &xl) {
   xh = (int)(X >> 29);
   xl = (int)(X & 0x1FFFFFFF);

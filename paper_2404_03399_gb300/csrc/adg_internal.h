@@ -13,10 +13,14 @@ constexpr int kStages = 3;      // SSP-RK3 (the composed and fixed-point steps, 
 constexpr int kMaxStages = 5;   // the 2N low-storage schemes (up to five stages)
 constexpr int kTile = 256;      // elements (threads) per block
 
+// Streaming multiprocessors of the current device (cudaDevAttrMultiProcessorCount, read once
+// per device and cached; 1 if the query fails).
+int sm_count();
+
 // Block size of the one-thread-per-element stage kernels: 256, or 128 when the mesh gives
-// fewer than two 256-blocks per SM of the 152 (small meshes are latency-bound, and smaller
-// blocks spread them over every SM).
-inline int stage_block(int K) { return K < 2 * 152 * 256 ? 128 : 256; }
+// fewer than two 256-blocks per SM (small meshes are latency-bound, and smaller blocks spread
+// them over every SM).
+inline int stage_block(int K) { return K < 2 * sm_count() * 256 ? 128 : 256; }
 
 // Folded constants of one SSP-RK3 stage in Shu-Osher form, v_out = alpha u + beta (v + dt L(v)),
 // with the strong form of Eq. DGscheme
@@ -68,8 +72,8 @@ struct StepConsts {
 };
 
 // The StepConsts in fixed point for the integer composed step: each coefficient c
-// (|c| < 2) is C = round(c 2^58), split into limbs C = x 2^29 + y with 0 <= y < 2^29
-// (int2 {x, y}).
+// (|c| < 2) is C = round(c 2^58), split into balanced limbs C = ch 2^29 + cl with
+// -2^28 <= cl < 2^28 (int2 {ch, cl}).
 struct StepFixed {
   int2 G[kMaxNp * kMaxNp];
   int2 r1[kMaxNp], r2[kMaxNp];
@@ -270,6 +274,10 @@ cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const De
 // index `step`: all three slots cleared, then E of slot step % 3 = largest biased exponent.
 cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,
                                cudaStream_t s);
+// The FP64 field u (n values) of the int64 fixed-point field X of step `step`, from the scale
+// slot step % 3 of fx (NaN everywhere when it marks a NaN or infinity).
+cudaError_t launch_fixed_to_fp64(const long long *X, double *u, size_t n, const FxSlot *fx,
+                                 int64_t step, cudaStream_t s);
 // Copies v1 into u for every instance (after an odd number of FP64 batched composed steps, or
 // a single fixed-point step).
 cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,

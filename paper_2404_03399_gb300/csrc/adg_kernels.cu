@@ -1284,7 +1284,8 @@ cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const De
                                cudaStream_t s) {
   const int64_t total = (int64_t)rows * g.P;
   const int64_t want = (total + 255) / 256;
-  const unsigned grid = (unsigned)(want < 8 * 152 ? (want ? want : 1) : 8 * 152);
+  const int64_t cap = 8 * (int64_t)sm_count();
+  const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
   k_fill_delays<<<grid, 256, 0, s>>>(table, first, total, g);
   return cudaGetLastError();
 }
@@ -1342,6 +1343,18 @@ cudaError_t launch_eval_modes(double *u, int K, int Np, double x0, double dx, co
   const size_t n = (size_t)K * Np;
   k_eval_modes<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(u, K, Np, x0, dx, m, nmodes, offset);
   return cudaGetLastError();
+}
+
+int sm_count() {
+  constexpr int kMaxDev = 64;
+  static int cached[kMaxDev] = {};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0) return 1;
+  if (dev < kMaxDev && cached[dev] > 0) return cached[dev];
+  int n = 0;
+  if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n < 1) n = 1;
+  if (dev < kMaxDev) cached[dev] = n;
+  return n;
 }
 
 int reduce_blocks(int K) {

@@ -4,6 +4,7 @@
 #include "adg.h"
 #include "adg_internal.h"
 
+#include <cmath>
 #include <mutex>
 #include <string>
 
@@ -88,7 +89,8 @@ extern "C" int adg_integral_noalloc(int32_t p, int32_t K, double dx, const doubl
                                     double *out_dev, void *stream) {
   if (p < 1 || p > ADG_MAX_P) return fail(ADG_EINVAL, "adg_integral_noalloc: p must be in 1..4");
   if (K < 1 || K > (1 << 30)) return fail(ADG_EINVAL, "adg_integral_noalloc: K must be in 1..2^30");
-  if (!(dx > 0.0) || dx != dx) return fail(ADG_EINVAL, "adg_integral_noalloc: dx must be > 0");
+  if (!(dx > 0.0 && std::isfinite(dx)))
+    return fail(ADG_EINVAL, "adg_integral_noalloc: dx must be finite and > 0");
   if (!u_dev || !out_dev) return fail(ADG_EINVAL, "adg_integral_noalloc: NULL field or output");
   double *scratch = nullptr;
   int r = scratch_for_current_device(&scratch);

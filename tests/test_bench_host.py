@@ -52,3 +52,10 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["unit"] == "DOF-stage updates/s"
+    # the same workload description as the GPU arm's line, and the steps it actually timed
+    sys.path.insert(0, ROOT)
+    import bench
+    assert line["config"] == bench.bench_config(1)
+    assert line["steps"] == 1 and line["ms_per_step"] > 0
+    assert "4096-element window" in line["cpu_baseline"]["sample"]
+    assert line["cpu_baseline"]["host_cores"] >= 1

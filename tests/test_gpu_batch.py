@@ -156,3 +156,73 @@ def test_fixed_point_batch_with_different_coefficients_per_degree():
         assert np.array_equal(b.state(i).cpu().numpy(), s.state().cpu().numpy()), i
         s.close()
     b.close()
+
+
+def _tuned_batch_workloads():
+    # 28 instances of the batched workload's distribution, about 1.1 M elements: above the
+    # size at which the batch autotuner times its choices
+    return batched_instances(n=28, seed=7)
+
+
+def test_batch_autotuner_choice_and_forced_choices_agree():
+    # AUTO: the tuner times fixed point (256-, 512- and 1024-element work items), the FP64
+    # composed step and the staged kernels and keeps the fastest; every forced choice runs the
+    # same scheme. The fixed-point choices are bit-identical to each other and to the
+    # single-instance fixed-point run; every choice stays on the oracle.
+    ws = _tuned_batch_workloads()
+    assert sum(w.K for w in ws) >= 1 << 20
+    steps = 12
+    cfgs = [_cfg(w) for w in ws]
+    u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
+    states = {}
+    for variant, ept in [("auto", 0), ("fixed", 1), ("fixed", 2), ("fixed", 4), ("composed", 0),
+                         ("staged", 0)]:
+        cs = [adg.Config(**{**c.__dict__, "variant": variant, "ept": ept}) for c in cfgs]
+        b = adg.BatchSolver(cs, u0s)
+        kinds = {b.variant(i) for i in range(len(ws))}
+        assert len(kinds) == 1, kinds
+        kind, e = kinds.pop()
+        if variant != "auto":
+            assert kind == variant and (ept == 0 or e == ept), (variant, ept, kind, e)
+        b.step(steps)
+        states[(variant, ept)] = ([b.state(i).cpu().numpy() for i in (0, 5, 27)], kind)
+        b.close()
+    base = states[("fixed", 2)][0]
+    for ept in (1, 4):
+        for a, c in zip(states[("fixed", ept)][0], base):
+            assert np.array_equal(a, c)
+    auto_states, auto_kind = states[("auto", 0)]
+    ref_states = states[{"fixed": ("fixed", 2), "composed": ("composed", 0),
+                         "staged": ("staged", 0)}[auto_kind]][0]
+    for a, c in zip(auto_states, ref_states):
+        assert np.array_equal(a, c)
+    for k, i in enumerate((0, 5, 27)):
+        w = ws[i]
+        s = adg.Solver(adg.Config(**{**cfgs[i].__dict__, "variant": "fixed"}), u0s[i])
+        s.step(steps)
+        single = s.state().cpu().numpy()
+        dt = s.dt
+        s.close()
+        assert np.array_equal(base[k], single), i
+        tbl = odelays.delay_table(w.seed, w.P, steps, w.L)
+        prob = dg.Problem(pde="advection", K=w.K, p=w.p, P=w.P, dt=dt, a=w.a, mode="adg", q=w.q,
+                          delays=tbl)
+        ref = dg.run(prob, u0s[i].cpu().numpy(), steps).numpy()
+        for (variant, ept), (sts, _) in states.items():
+            err = np.max(np.abs(sts[k] - ref)) / np.max(np.abs(ref))
+            assert err < TOL, (variant, ept, i, err)
+
+
+def test_batch_rejects_conflicting_forced_choices():
+    ws = _eligible_batch()[:2]
+    cfgs = [_cfg(w) for w in ws]
+    u0s = [adg.eval_modes(c, w.modes.amp, w.modes.kappa, w.modes.phase) for c, w in zip(cfgs, ws)]
+    bad = [adg.Config(**{**cfgs[0].__dict__, "variant": "staged"}),
+           adg.Config(**{**cfgs[1].__dict__, "variant": "composed"})]
+    with pytest.raises(adg.AdgError) as ei:
+        adg.BatchSolver(bad, u0s)
+    assert ei.value.code == adg._abi.ADG_EINVAL
+    bad = [adg.Config(**{**c.__dict__, "variant": "staged", "ept": 2}) for c in cfgs]
+    with pytest.raises(adg.AdgError) as ei:
+        adg.BatchSolver(bad, u0s)
+    assert ei.value.code == adg._abi.ADG_EINVAL

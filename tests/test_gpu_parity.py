@@ -173,6 +173,56 @@ def test_conservation_on_gpu(mode, q):
     assert abs(I1 - I0) < 1e-12 * abs(I0)
 
 
+def _oracle_integral(cfg, field):
+    """The oracle's discrete integral (dx/2) sum_e w^T u^e of a nodal field (Section 4.1's
+    conserved quantity) and the scale sum_e (dx/2) |w|^T |u^e| its rounding is measured
+    against."""
+    prob = dg.Problem(pde=cfg.pde, K=cfg.K, p=cfg.p, P=1, dt=1.0, x0=cfg.x0, x1=cfg.x1)
+    o = dg.Solver(prob, field)
+    return float(o.integral()), float(o.integral(torch.abs(torch.as_tensor(field))))
+
+
+@pytest.mark.parametrize("p,K,x0,x1", [(1, 37, 0.0, TWO_PI), (2, 300, -1.0, 2.5),
+                                      (3, 1017, 0.0, TWO_PI), (4, 4099, -3.0, 0.25)])
+def test_integral_matches_oracle(p, K, x0, x1):
+    # adg_integral against the oracle's integral of the same nodal field: before any step,
+    # and after ADG-AT steps (the field the library holds, read back), on ragged meshes.
+    cfg = adg.Config(pde="advection", K=K, p=p, P=1 if K % 7 else 7, x0=x0, x1=x1, cfl=0.01,
+                     mode="sync")
+    u0 = random_nodal(K, p, 40 + p) + 0.25
+    s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
+    ref, mag = _oracle_integral(cfg, u0)
+    assert abs(s.integral() - ref) <= TOL * mag
+    s.step(9)
+    field = s.state().cpu().numpy()
+    ref, mag = _oracle_integral(cfg, field)
+    assert abs(s.integral() - ref) <= TOL * mag
+    s.close()
+
+
+def test_integral_matches_oracle_after_async_steps_and_in_a_batch():
+    # ADG-AT with PE faces (a run after steps on the fixed-point path, whose state is read
+    # back rounded to FP64), and the same integral for an instance of a batch.
+    cfg = adg.Config(pde="advection", K=1000, p=3, P=10, cfl=0.01, mode="at", L=4, q=3, seed=3)
+    u0 = adg.eval_modes(cfg, PAPER_FIG6.amp, PAPER_FIG6.kappa, PAPER_FIG6.phase, 1.0)
+    s = adg.Solver(cfg, u0)
+    s.step(33)
+    field = s.state().cpu().numpy()
+    ref, mag = _oracle_integral(cfg, field)
+    assert abs(s.integral() - ref) <= TOL * mag
+    s.close()
+    cfgs = [adg.Config(pde="advection", K=K, p=p, P=K // 64, cfl=0.005, mode="at", L=3, q=2,
+                       seed=10 + i) for i, (K, p) in enumerate([(640, 1), (1280, 4), (832, 2)])]
+    u0s = [torch.tensor(random_nodal(c.K, c.p, 70 + i) + 0.5, device="cuda")
+           for i, c in enumerate(cfgs)]
+    b = adg.BatchSolver(cfgs, u0s)
+    b.step(5)
+    for i, c in enumerate(cfgs):
+        ref, mag = _oracle_integral(c, b.state(i).cpu().numpy())
+        assert abs(b.integral(i) - ref) <= TOL * mag, i
+    b.close()
+
+
 def test_nonfinite_detection():
     # Burgers at sigma = 0.05 with p = 4 and delays up to 3 leaves the delayed-feedback
     # stability bound and overflows; the reduction reports ADG_ENONFINITE.
@@ -274,19 +324,57 @@ def test_fixed_point_follows_a_decaying_field():
     # An under-resolved wave (2.7 elements per wavelength at kappa = 24, p = 1) is dissipated
     # by the upwind flux to about 1e-4 of its size over the run, so the largest exponent of
     # u^n, and with it the scale of the integer step, falls by 13 binades. The decayed field is
-    # ill-conditioned (a 1e-16 perturbation of u0 moves it by 1e-12 of its final size in the
-    # oracle, i.e. rounding noise of 1e-16 grows to 1e-12 of the final size), so both variants
-    # are held to 1e-14 of the initial size.
+    # ill-conditioned: rounding noise made while the field was large sits in modes that decay
+    # more slowly than the wave, so errors of 1e-16 of the initial size end as about 1e-12 of
+    # the final size. The bound is therefore the problem's own sensitivity, measured on the
+    # oracle (its final field's change when u0 is perturbed by 1e-16 relative): both variants
+    # stay within a few times it, the fixed-point step within four times the FP64 composed
+    # step, and both within 1e-14 of the initial size.
     K, p = 64, 1
     u0 = dg.modes_initial(Modes(amp=(1.0,), kappa=(24.0,), phase=(0.3,)), K, p)
-    errs = {}
+    errs, errs0 = {}, {}
     for variant in ("composed", "fixed"):
         cfg = adg.Config(pde="advection", K=K, p=p, P=8, cfl=0.05, mode="at", L=3, q=2, seed=6,
                          variant=variant)
-        got, ref, _ = run_pair(cfg, u0, 1000)
+        got, ref, dt = run_pair(cfg, u0, 1000)
         assert np.max(np.abs(ref)) < 1e-3 * np.max(np.abs(u0))
-        errs[variant] = float(np.max(np.abs(got - ref))) / np.max(np.abs(u0))
-    assert errs["fixed"] < 1e-14 and errs["composed"] < 1e-14
+        errs[variant] = rel_linf(got, ref)
+        errs0[variant] = float(np.max(np.abs(got - ref))) / np.max(np.abs(u0))
+    tbl = odelays.delay_table(6, 8, 1000, 3)
+    prob = dg.Problem(pde="advection", K=K, p=p, P=8, dt=dt, mode="adg", q=2, delays=tbl)
+    rng = np.random.default_rng(0)
+    refp = dg.run(prob, u0 * (1.0 + 1e-16 * rng.standard_normal(u0.shape)), 1000).numpy()
+    sens = rel_linf(refp, ref)
+    assert 1e-14 < sens < 1e-10
+    assert errs["fixed"] < 8 * sens and errs["composed"] < 8 * sens, (errs, sens)
+    assert errs["fixed"] <= 4 * errs["composed"], errs
+    assert errs0["fixed"] < 1e-14 and errs0["composed"] < 1e-14
+
+
+def test_fixed_point_error_is_relative_to_the_field_maximum():
+    # A localized pulse whose tail falls to 1e-30 of its peak. The fixed-point step works at
+    # one scale per field and step, so its error is bounded relative to max |u| (here 1e-14 of
+    # it everywhere), not relative to each element: in the tail below 2^-55 max |u| it keeps
+    # no digits. The FP64 composed step keeps relative precision in the tail as well. Both are
+    # the same scheme; the fixed-point variant's contract is the max-normalised error.
+    K, p = 512, 3
+    x = dg.node_coordinates(K, p, 0.0, TWO_PI)
+    u0 = np.exp(-((x - math.pi) / 0.12) ** 2)
+    steps = 50
+    outs = {}
+    for variant in ("fixed", "composed"):
+        cfg = adg.Config(pde="advection", K=K, p=p, P=16, cfl=0.005, mode="at", L=4, q=3, seed=9,
+                         variant=variant)
+        got, ref, _ = run_pair(cfg, u0, steps)
+        outs[variant] = got
+    scale = np.max(np.abs(ref))
+    assert np.max(np.abs(outs["fixed"] - ref)) < 1e-14 * scale
+    tail = (np.abs(ref) > 1e-200) & (np.abs(ref) < 1e-20 * scale)
+    assert tail.sum() > 100
+    rel_tail_fp64 = np.max(np.abs(outs["composed"][tail] - ref[tail]) / np.abs(ref[tail]))
+    rel_tail_fixed = np.max(np.abs(outs["fixed"][tail] - ref[tail]) / np.abs(ref[tail]))
+    assert rel_tail_fp64 < 1e-10
+    assert rel_tail_fixed > 1e-3   # the tail is below the fixed-point step's resolution
 
 
 def test_fixed_point_matches_fp64_composed():
@@ -310,24 +398,47 @@ def test_fixed_point_rejects_large_coefficients():
 
 
 def test_fixed_point_step_splitting():
-    # The integer step keeps the field in int64 from the first to the last step of each
-    # adg_step call (across its 32-step graph chunks: first, middle and a ragged last chunk)
-    # and rounds it to FP64 at the end of the call; single-step calls round every step. All
-    # stay on the oracle, and within rounding of each other.
+    # The integer step keeps the state in int64 from step to step, across its 32-step graph
+    # chunks and across adg_step calls; the FP64 state is formed only when it is read. So
+    # every splitting of a run into calls, and reading the state (or its integral) between
+    # calls, gives bitwise the same result, which stays on the oracle.
     cfg = adg.Config(pde="advection", K=512, p=3, P=16, cfl=0.005, mode="at", L=4, q=3, seed=12,
                      variant="fixed")
     u0 = dg.modes_initial(PAPER_FIG6, 512, 3)
     outs = []
-    for calls in ([96], [1] * 96, [1, 2, 33, 60], [70, 26]):
+    for calls, read in (([96], False), ([1] * 96, False), ([1, 2, 33, 60], True), ([70, 26], True)):
         s = adg.Solver(cfg, torch.tensor(u0, device="cuda"))
         for k in calls:
             s.step(k)
+            if read:
+                s.state()
+                s.integral()
         outs.append(s.state().cpu().numpy())
         s.close()
     _, ref, _ = run_pair(cfg, u0, 96)
     for got in outs:
         assert rel_linf(got, ref) < TOL
-        assert rel_linf(got, outs[0]) < 1e-13
+        assert np.array_equal(got, outs[0])
+
+
+def test_fixed_point_state_kept_across_gradient():
+    # adg_grad runs its own forward steps from the current state and puts the state back: the
+    # int64 state of the fixed-point step is restored exactly, so steps after a gradient equal
+    # steps without it.
+    cfg = adg.Config(pde="advection", K=256, p=2, P=8, cfl=0.005, mode="at", L=3, q=2, seed=2,
+                     variant="fixed")
+    u0 = torch.tensor(dg.modes_initial(PAPER_FIG6, 256, 2), device="cuda")
+    target = torch.zeros_like(u0)
+    outs = []
+    for with_grad in (False, True):
+        s = adg.Solver(cfg, u0)
+        s.step(13)
+        if with_grad:
+            s.grad(target, 9, 4)
+        s.step(20)
+        outs.append(s.state().cpu().numpy())
+        s.close()
+    assert np.array_equal(outs[0], outs[1])
 
 
 @pytest.mark.parametrize("kw,want", [

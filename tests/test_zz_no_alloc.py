@@ -6,7 +6,8 @@ or a latency-critical loop that cannot afford cudaMalloc and the synchronisation
 cause. For them the library offers one entry point whose scratch space is a fixed array
 compiled into the library. This test calls it through the C ABI on two fields in a row and
 checks each result against adg_integral, which uses scratch space owned by a solver
-context. It sits in a file of its own that pytest collects last.
+context, and against the oracle's integral of the same field. It sits in a file of its own
+that pytest collects last.
 """
 import ctypes as C
 import math
@@ -16,6 +17,7 @@ import pytest
 import torch
 
 import paper_2404_03399_gb300 as adg
+from oracle import dg
 from workloads import PAPER_FIG6
 
 pytestmark = pytest.mark.gpu
@@ -51,6 +53,11 @@ def test_noalloc_integral_matches_context_integral_twice():
         ref = s.integral()
         got = _noalloc_integral(lib, p, K, dx, field, out)
         assert abs(got - ref) <= TOL * abs(ref), (call, got, ref)
+        prob = dg.Problem(pde="advection", K=K, p=p, P=1, dt=1.0, x0=cfg.x0, x1=cfg.x1)
+        o = dg.Solver(prob, field.cpu().numpy())
+        orc = float(o.integral())
+        mag = float(o.integral(torch.abs(field.cpu())))
+        assert abs(got - orc) <= TOL * mag, (call, got, orc)
         s.step(7)               # the second call sees a different field
     s.close()
 
@@ -62,4 +69,6 @@ def test_noalloc_rejects_sizes_beyond_limits():
     assert lib.adg_integral_noalloc(5, 4, 0.1, field.data_ptr(), out.data_ptr(), None) == adg._abi.ADG_EINVAL
     assert lib.adg_integral_noalloc(1, (1 << 30) + 1, 0.1, field.data_ptr(), out.data_ptr(), None) == adg._abi.ADG_EINVAL
     assert lib.adg_integral_noalloc(1, 4, 0.0, field.data_ptr(), out.data_ptr(), None) == adg._abi.ADG_EINVAL
+    for bad in (math.inf, math.nan, -1.0):
+        assert lib.adg_integral_noalloc(1, 4, bad, field.data_ptr(), out.data_ptr(), None) == adg._abi.ADG_EINVAL
     assert b"K must be" in lib.adg_last_error(None) or b"dx" in lib.adg_last_error(None)
