@@ -2,8 +2,9 @@
  * adg.h -- C ABI of the GB300 asynchronous discontinuous Galerkin (ADG / ADG-AT) solver.
  *
  * The library advances 1D nodal DG discretisations of u_t + f(u)_x = 0 on a periodic
- * interval with the fully discrete strong-stability-preserving RK3 step, on one GPU, in
- * FP64. Elements are split into P contiguous "processing elements" (PEs); at PE faces the
+ * interval with the fully discrete strong-stability-preserving RK3 step (or the paper's
+ * low-storage schemes), on one GPU, in FP64 (the composed step of upwind advection in 58-bit
+ * block fixed point: adg_config.variant). Elements are split into P contiguous "processing elements" (PEs); at PE faces the
  * numerical flux uses data of a delayed time level taken from a seeded delay table and a
  * device ring buffer, combined by the standard flux or the asynchrony-tolerant (AT) flux.
  *
@@ -120,27 +121,34 @@ enum {
  *               adg_integral reports the integral of rho. Single instances, staged kernels;
  *               batches, adg_grad and the composed variants reject it (ADG_EINVAL).
  *   variant   : ADG_VARIANT_AUTO (0), ADG_VARIANT_STAGED (1): one kernel per RK stage, or
- *               ADG_VARIANT_COMPOSED (2): the three stages of upwind advection with a > 0
- *               composed into one stencil per step, with the delayed / AT flux at PE faces
- *               added as a correction to the four elements around each face (needs
- *               K/P >= 8 when there are PE faces), or
- *               ADG_VARIANT_COMPOSED_FIXED (3): the same composed step evaluated exactly in
- *               64-bit fixed-point integer arithmetic at one scale per step (from the largest
- *               magnitude in u^n; resolution 2^-55 of max|u^n| or finer). The state stays in
- *               fixed point from the first to the last step of one adg_step call and is
- *               rounded to FP64 at the end of the call, so splitting a run into different
- *               adg_step calls changes results at the rounding level. It needs every composed
- *               coefficient below 2 in magnitude (small Courant numbers; ADG_EINVAL
- *               otherwise). Results below 2^-1022 are flushed to zero, and a NaN or infinity
- *               anywhere in u^n makes all of u^{n+1} NaN. AUTO picks COMPOSED_FIXED, else
- *               COMPOSED, where they apply; a batch with AUTO times every kind of step that all
- *               its instances admit (fixed point, FP64 composed, staged) at init and keeps the
- *               fastest (adg_get_variant reports it). All give the same scheme up to rounding.
+ *               ADG_VARIANT_COMPOSED (2): the stages of one step of upwind advection with a > 0
+ *               (SSP-RK3, or a low-storage scheme of up to three stages) composed into one
+ *               stencil per step in FP64, with the delayed / AT flux at PE faces added as a
+ *               correction to the elements around each face (needs K/P >= 8 when there are PE
+ *               faces), or
+ *               ADG_VARIANT_COMPOSED_FIXED (3): the composed step (also for the five-stage
+ *               ADG_LSRK4, which then needs K/P >= 10) evaluated in 58-bit block fixed point:
+ *               int64 values at one scale per field and step (from the largest magnitude in
+ *               u^n), coefficients rounded to 2^-58, 32 x 32 -> 64-bit integer products. A sum
+ *               of n terms is off by less than n/2 + 1/2 units of 2^-57 max|u^n|, so the error is
+ *               bounded relative to the field's maximum (as FP64's is relative to a sum's
+ *               largest term), not per value: values below about 2^-55 max|u^n| keep no
+ *               digits. The state stays in int64 from step to step and across adg_step calls;
+ *               the FP64 state is formed (rounded once) when it is read (adg_get_state,
+ *               adg_integral, adg_misfit, adg_check_finite, adg_grad), so every splitting of a
+ *               run into calls gives the same result. It needs every composed coefficient below
+ *               2 in magnitude (small Courant numbers; ADG_EINVAL otherwise). Results below
+ *               2^-1022 are flushed to zero, and a NaN or infinity anywhere in u^n makes all of
+ *               u^{n+1} NaN. AUTO picks COMPOSED_FIXED, else COMPOSED, where they apply; a
+ *               batch with AUTO times every kind of step that all its instances admit (fixed
+ *               point, FP64 composed, staged) at init and keeps the fastest (adg_get_variant
+ *               reports it). All give the same scheme up to rounding.
  *   ept       : elements per thread of the composed-step kernels (not a paper quantity):
- *               0 (default) lets init time the choices and keep the fastest (1 or 2 for the
- *               fixed-point step, 1, 2 or 4 for the FP64 step; a batch's fixed-point step
- *               also 4, i.e. work items of 256, 512 or 1024 elements); 1, 2 or 4 forces one
- *               (ADG_EINVAL where that kernel has no such form). Results do not depend on it.
+ *               0 (default) lets init time the choices and keep the fastest (1, or 2
+ *               consecutive elements for even K, for the fixed-point step; 1, 2 or 4 for the
+ *               FP64 step; a batch's fixed-point step also 4, i.e. work items of 256, 512 or
+ *               1024 elements); 1, 2 or 4 forces one (ADG_EINVAL where that kernel has no such
+ *               form). Results do not depend on it.
  */
 typedef struct {
   int32_t pde;

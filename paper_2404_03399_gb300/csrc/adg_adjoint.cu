@@ -41,15 +41,21 @@ __device__ __forceinline__ void value_partials(double tl, double tr, double &dL,
   }
 }
 
+// Adjoint of one stage with halo lanes (the layout of the forward k_stage_halo): warp w takes
+// elements 30w .. 30w+29 in lanes 1 .. 30 and lanes 0 and 31 hold the elements on either side
+// (periodic), so every face adjoint is formed by full-warp instructions (lane l forms the
+// adjoint of its left face and hands the left element its part through a shuffle) and a PE
+// face's adjoint g = nu + r (or r) is formed once, by the lane of the element right of the face
+// (which, owned, also posts the delayed levels and clears the ring entry). A warp's FP64
+// instruction costs the same pipe time whatever its active lanes, so the halo lanes' 2/32
+// redundant work is cheaper than single-lane edge and face work.
 template <int NP, int PDE, int STAGE, int DIR, bool FACES>
-__global__ void __launch_bounds__(kTile) k_adj_stage(const AdjStage A) {
+__global__ void __launch_bounds__(kTile) k_adj_stage_halo(const AdjStage A) {
   const int K = A.K;
-  const int e = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int ec = e < K ? e : K - 1;
-  const bool edge = (lane == 31) || (ec + 1 >= K);
-  const int eR = ec + 1 >= K ? 0 : ec + 1;
-  const int eL = ec == 0 ? K - 1 : ec - 1;
+  const int e = 30 * ((blockIdx.x * blockDim.x + threadIdx.x) >> 5) + lane - 1;
+  const bool own = lane >= 1 && lane <= 30 && e < K;
+  const int ec = e < 0 ? e + K : (e < K ? e : 0);
   const StageConsts &C = A.C;
   const unsigned full = 0xffffffffu;
 
@@ -75,83 +81,40 @@ __global__ void __launch_bounds__(kTile) k_adj_stage(const AdjStage A) {
     for (int i = 1; i < NP; ++i) acc = fma(C.A[i * NP + j], w[i], acc);
     lv[j] = PDE == 0 ? acc : fma(C.beta, w[j], 2.0 * v[j] * acc);
   }
-
+  const double sRp = __shfl_up_sync(full, sR, 1);     // sR of the element to the left
   if (PDE == 0) {
     if (DIR > 0) {
-      // jL^e = v_0^e - v_p^{e-1}: own node 0 gets sL^e, node p gets -sL^{e+1}.
       lv[0] += sL;
-      double sLn = __shfl_down_sync(full, sL, 1);
-      if (edge) {
-        sLn = 0.0;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) sLn = fma(C.lL[i], __ldg(A.w + (size_t)i * K + eR), sLn);
-      }
-      lv[NP - 1] -= sLn;
+      lv[NP - 1] -= __shfl_down_sync(full, sL, 1);
     } else {
-      // jR^e = v_p^e - v_0^{e+1}: own node p gets sR^e, node 0 gets -sR^{e-1}.
       lv[NP - 1] += sR;
-      double sRp = __shfl_up_sync(full, sR, 1);
-      if (lane == 0) {
-        sRp = 0.0;
-#pragma unroll
-        for (int i = 0; i < NP; ++i) sRp = fma(C.lR[i], __ldg(A.w + (size_t)i * K + eL), sRp);
-      }
       lv[0] -= sRp;
     }
   } else {
     lv[0] = fma(v[0], sL, lv[0]);
     lv[NP - 1] = fma(v[NP - 1], sR, lv[NP - 1]);
-    // Left face of e: adjoint mu = -sL^e - sR^{e-1}, traces (v_p^{e-1}, v_0^e).
-    double sRp = __shfl_up_sync(full, sR, 1);
-    double vLm = __shfl_up_sync(full, v[NP - 1], 1);
-    if (lane == 0) {
-      sRp = 0.0;
-#pragma unroll
-      for (int i = 0; i < NP; ++i) sRp = fma(C.lR[i], __ldg(A.w + (size_t)i * K + eL), sRp);
-      vLm = __ldg(A.v + (size_t)(NP - 1) * K + eL);
-    }
+    // left face of e: adjoint mu = -sL^e - sR^{e-1}, traces (v_p^{e-1}, v_0^e)
+    const double vLm = __shfl_up_sync(full, v[NP - 1], 1);
     const double muL = -sL - sRp;
     double dL, dR;
     llf_partials(vLm, v[0], dL, dR);
     lv[0] = fma(muL, dR, lv[0]);
-    double fromRight = __shfl_down_sync(full, muL * dL, 1);
-    if (edge) {
-      double sLn = 0.0;
-#pragma unroll
-      for (int i = 0; i < NP; ++i) sLn = fma(C.lL[i], __ldg(A.w + (size_t)i * K + eR), sLn);
-      const double vRp = __ldg(A.v + eR);
-      double dL2, dR2;
-      llf_partials(v[NP - 1], vRp, dL2, dR2);
-      fromRight = (-sLn - sR) * dL2;
-    }
-    lv[NP - 1] += fromRight;
+    lv[NP - 1] += __shfl_down_sync(full, muL * dL, 1);
   }
 
   if (FACES) {
-    // PE faces among this block's faces (K/P >= 8). Element e is right of PE face j (peL)
-    // or left of PE face jr (peR); both elements form the face's adjoint g themselves:
+    // lane l (1 .. 31) forms the adjoint of its left face when its element owns a PE face
+    // (e = j Kpe, or e = K: face 0 seen from element K-1):
     //   nu = sL^e + sR^{e-1}, g = nu + r - [k == 0] nu, r = ring entry of (n, s, j),
-    // and add g times the value's partial derivative to their trace node. The owner (right
-    // element) posts c_i (-nu) to the delayed levels (never to level n) and clears the ring
-    // entry the previous adjoint kernel read (it is read no more).
-    __shared__ int s_first, s_jfirst;
-    const int e0 = blockIdx.x * blockDim.x;
-    if (threadIdx.x == 0) {
-      const int jf = (e0 + A.Kpe - 1) / A.Kpe;
-      s_jfirst = jf;
-      s_first = jf * A.Kpe;
-    }
-    __syncthreads();
-    int jL = -1, jR = -1;
-    {
-      int f = s_first, jf = s_jfirst;
-      for (; f <= e0 + (int)blockDim.x && f < K; f += A.Kpe, ++jf) {
-        if (f == ec) jL = jf;
-        if (f == ec + 1) jR = jf;
-      }
-      if (ec + 1 == K) jR = 0;
-    }
-    if ((jL >= 0 || jR >= 0) && e < K) {
+    // and both elements add g times the value's partial derivative to their trace node (the
+    // left one through a shuffle); an owned lane also posts c_i (-nu) to the delayed levels
+    // (never to level n) and clears the ring entry the previous adjoint kernel read.
+    const double tl = PDE == 1 ? __shfl_up_sync(full, v[NP - 1], 1) : 0.0;
+    const int eo = e < K ? e : e - K;
+    const int jq = eo / A.Kpe;
+    const bool face = lane >= 1 && e <= K && eo - jq * A.Kpe == 0;
+    double g = 0.0, pL = 0.0, pR = 0.0;
+    if (face) {
       const int64_t n = A.meta[0] + A.rel;
       const int nm = (int)(n % A.R);
       auto slot_of = [&](int m) {   // ring slot of level n - m
@@ -159,54 +122,30 @@ __global__ void __launch_bounds__(kTile) k_adj_stage(const AdjStage A) {
         if (sl < 0) sl += A.R;
         return sl;
       };
-      // neighbour adjoint scalars and traces (direct loads: this branch is rare)
-      double sRm = 0.0, sLp = 0.0;
-#pragma unroll
-      for (int i = 0; i < NP; ++i) {
-        sRm = fma(C.lR[i], __ldg(A.w + (size_t)i * K + eL), sRm);
-        sLp = fma(C.lL[i], __ldg(A.w + (size_t)i * K + eR), sLp);
-      }
-      if (jL >= 0) {
-        const double nu = sL + sRm;
-        const DelayAt d = delay_at(A, jL, n);
-        const double r = A.lring[((size_t)nm * kStages + STAGE) * A.P + jL];
-        const double g = d.k == 0 ? r : nu + r;
-        double tl = 0.0, tr = 0.0;
-        if (PDE == 1) {
-          tl = __ldg(A.v + (size_t)(NP - 1) * K + eL);
-          tr = v[0];
-        }
-        double dL, dR;
-        value_partials<PDE, DIR>(tl, tr, dL, dR);
-        lv[0] = fma(g, dR, lv[0]);
+      const double nu = sL + sRp;
+      const DelayAt d = delay_at(A, jq, n);
+      const double r = A.lring[((size_t)nm * kStages + STAGE) * A.P + jq];
+      g = d.k == 0 ? r : nu + r;
+      value_partials<PDE, DIR>(tl, PDE == 1 ? v[0] : 0.0, pL, pR);
+      if (own) {
         for (int i = 0; i < d.qe; ++i) {
           const double ci = d.c[i];
           if (ci != 0.0 && d.k + i >= 1)
-            A.lring[((size_t)slot_of(d.k + i) * kStages + STAGE) * A.P + jL] += ci * (-nu);
+            A.lring[((size_t)slot_of(d.k + i) * kStages + STAGE) * A.P + jq] += ci * (-nu);
         }
-        // clear the entry the previous adjoint kernel read: (n, s+1), or (n+1, 0) for s = 2
         const int pst = STAGE == 2 ? 0 : STAGE + 1;
         const int psl = STAGE == 2 ? (nm + 1 == A.R ? 0 : nm + 1) : nm;
-        A.lring[((size_t)psl * kStages + pst) * A.P + jL] = 0.0;
-      }
-      if (jR >= 0) {
-        const double nu = sLp + sR;
-        const DelayAt d = delay_at(A, jR, n);
-        const double r = A.lring[((size_t)nm * kStages + STAGE) * A.P + jR];
-        const double g = d.k == 0 ? r : nu + r;
-        double tl = 0.0, tr = 0.0;
-        if (PDE == 1) {
-          tl = v[NP - 1];
-          tr = __ldg(A.v + eR);
-        }
-        double dL, dR;
-        value_partials<PDE, DIR>(tl, tr, dL, dR);
-        lv[NP - 1] = fma(g, dL, lv[NP - 1]);
+        A.lring[((size_t)psl * kStages + pst) * A.P + jq] = 0.0;
       }
     }
+    if (own && face) lv[0] = fma(g, pR, lv[0]);
+    const double gR = __shfl_down_sync(full, g, 1);
+    const double pLR = __shfl_down_sync(full, pL, 1);
+    const bool faceR = __shfl_down_sync(full, face ? 1 : 0, 1) != 0;
+    if (own && faceR) lv[NP - 1] = fma(gR, pLR, lv[NP - 1]);
   }
 
-  if (e < K) {
+  if (own) {
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
       const size_t o = (size_t)i * K + e;
@@ -276,9 +215,13 @@ template <int NP, int PDE, int STAGE, bool FACES>
 cudaError_t adj_launch(const AdjStage &A, int dir, cudaStream_t s) {
   const int bs = stage_block(A.K);
   const unsigned grid = (unsigned)((A.K + bs - 1) / bs);
-  if (PDE == 1) k_adj_stage<NP, 1, STAGE, 0, FACES><<<grid, bs, 0, s>>>(A);
-  else if (dir > 0) k_adj_stage<NP, 0, STAGE, 1, FACES><<<grid, bs, 0, s>>>(A);
-  else k_adj_stage<NP, 0, STAGE, -1, FACES><<<grid, bs, 0, s>>>(A);
+  (void)grid;
+  // 30 elements per warp (halo lanes)
+  const int64_t warps = (A.K + 29) / 30;
+  const unsigned g = (unsigned)((warps * 32 + bs - 1) / bs);
+  if (PDE == 1) k_adj_stage_halo<NP, 1, STAGE, 0, FACES><<<g, bs, 0, s>>>(A);
+  else if (dir > 0) k_adj_stage_halo<NP, 0, STAGE, 1, FACES><<<g, bs, 0, s>>>(A);
+  else k_adj_stage_halo<NP, 0, STAGE, -1, FACES><<<g, bs, 0, s>>>(A);
   return cudaGetLastError();
 }
 

@@ -373,6 +373,7 @@ struct adg_ctx {
   bool batch_fixed = false;     // ... in fixed point
   adg::BatchLite *lites_ept[3] = {};   // work records of 256, 512, 1024 elements (batch tuner)
   int nlites_ept[3] = {};
+  bool batch_even = false;             // every instance has an even K (the paired kernel)
   std::unique_ptr<adg::BatchUniform> bu;   // shared coefficients per degree, when they are
   double *partials = nullptr, *red_out = nullptr;
   double *pinned = nullptr;
@@ -470,11 +471,12 @@ void two_register_butcher(int rk, int &S, ld a[adg::kMaxStages][adg::kMaxStages]
 
 // Composed step constants (StepConsts in adg_internal.h) of upwind advection with a > 0, in
 // long double: from the SSP-RK3 stages in Shu and Osher's form, or, for the low-storage
-// schemes of at most three stages, from their Butcher form (unused channels are zero).
+// schemes (one to five stages), from their Butcher form (unused channels are zero).
 void fold_step_constants(InstHost &h) {
   const Ops &o = h.ops;
   const int Np = o.Np;
   const ld c2a = advection_c2a(h);
+  constexpr int CS = adg::kMaxCS;
   typedef std::vector<ld> Mat;
   auto mul = [&](const Mat &X, const Mat &Y) {
     Mat Z(Np * Np, 0);
@@ -490,13 +492,17 @@ void fold_step_constants(InstHost &h) {
     return z;
   };
   const int p = Np - 1;
-  // the step's constants: u'^e = G u^e + sum_t h_t P_t, channel scalars v1_p = r1 . u + k0 P0,
-  // v2_p = r2 . u + k1 P0 + k2 P1, PE-face responses R and rho
+  // the step's constants: u'^e = G u^e + sum_t h_t P_t, channel scalars
+  // Y_s p = r_s . u + sum_{t<s} k_st P_t, PE-face responses R and rho
+  int S = 3;
   Mat Gl(Np * Np, 0);
-  std::vector<ld> r1l(Np, 0), r2l(Np, 0), hl[3];
-  for (auto &v : hl) v.assign(Np, 0);
-  ld kl[3] = {0, 0, 0}, rhol[3] = {0, 0, 0};
-  ld Rl[3][4][adg::kMaxNp] = {};
+  std::vector<ld> rl[CS], hl[CS];
+  for (int s = 0; s < CS; ++s) {
+    rl[s].assign(Np, 0);
+    hl[s].assign(Np, 0);
+  }
+  ld kl[CS][CS] = {}, rhol[CS][CS] = {};
+  ld Rl[CS][CS + 1][adg::kMaxNp] = {};
 
   if (h.cfg.rk == ADG_SSPRK3) {
     const ld alpha[3] = {0.0L, 0.75L, 1.0L / 3.0L};
@@ -524,12 +530,12 @@ void fold_step_constants(InstHost &h) {
     hl[2] = cv[2];
     std::vector<ld> M1c0 = mulv(M[1], cv[0]);
     for (int i = 0; i < Np; ++i) {
-      r1l[i] = M[0][p * Np + i];
-      r2l[i] = M10[p * Np + i] + (i == p ? alpha[1] : 0.0L);
+      rl[1][i] = M[0][p * Np + i];
+      rl[2][i] = M10[p * Np + i] + (i == p ? alpha[1] : 0.0L);
     }
-    kl[0] = cv[0][p];
-    kl[1] = M1c0[p];
-    kl[2] = cv[1][p];
+    kl[1][0] = cv[0][p];
+    kl[2][0] = M1c0[p];
+    kl[2][1] = cv[1][p];
     // PE-face correction responses: inject lL_s at element e and lR_s at element e-1 after
     // stage s, then apply the remaining stages' perturbation maps
     // dx'^m = M_t dx^m + c_t dx^{m-1}_p (t = s+1 .. 2) on elements e-1 .. e+2; rho collects
@@ -542,9 +548,7 @@ void fold_step_constants(InstHost &h) {
         d[0 * Np + i] = -sc * o.Minv[i * Np + p];
       }
       for (int t = st + 1; t < 3; ++t) {
-        if (st == 0 && t == 1) rhol[0] = d[0 * Np + p];
-        if (st == 0 && t == 2) rhol[1] = d[0 * Np + p];
-        if (st == 1 && t == 2) rhol[2] = d[0 * Np + p];
+        rhol[t][st] = d[0 * Np + p];
         std::vector<ld> nd(4 * Np, 0.0L);
         for (int m = 0; m < 4; ++m)
           for (int i = 0; i < Np; ++i) {
@@ -559,11 +563,9 @@ void fold_step_constants(InstHost &h) {
         for (int i = 0; i < Np; ++i) Rl[st][m][i] = d[m * Np + i];
     }
   } else {
-    // Butcher form: Y_1 = u, k_s = dt L(Y_s) = W Y_s + w P_s (W = c2a (D + M^{-1} e_0 e_0^T),
-    // w = -c2a M^{-1} e_0, P_s the left neighbour's right trace of Y_s), Y_{s+1} =
-    // u + sum_j a_{s+1,j} k_j, u' = u + sum_j b_j k_j. Every quantity is kept as
-    // A u + sum_t H_t P_t.
-    int S = 0;
+    // Butcher form of a low-storage scheme: k_s = W Y_s + w P_s (stage s with all faces
+    // synchronous, P_s = the left neighbour's Y_s trace), Y_s = u + sum_{j<s} a_sj k_j,
+    // u' = u + sum_j b_j k_j. Every quantity is kept as A u + sum_t H_t P_t.
     ld a[adg::kMaxStages][adg::kMaxStages], b[adg::kMaxStages];
     two_register_butcher(h.cfg.rk, S, a, b);
     Mat W(Np * Np, 0);
@@ -577,11 +579,11 @@ void fold_step_constants(InstHost &h) {
     for (int i = 0; i < Np; ++i) I[i * Np + i] = 1;
     struct Rep {
       Mat A;
-      std::vector<ld> H[3];
+      std::vector<ld> H[CS];
     };
-    Rep Y[3], Kr[3];
-    for (int s = 0; s < 3; ++s)
-      for (int t = 0; t < 3; ++t) {
+    Rep Y[CS], Kr[CS];
+    for (int s = 0; s < CS; ++s)
+      for (int t = 0; t < CS; ++t) {
         Y[s].H[t].assign(Np, 0);
         Kr[s].H[t].assign(Np, 0);
       }
@@ -589,51 +591,45 @@ void fold_step_constants(InstHost &h) {
     auto combine = [&](int s, const ld *coef) {   // I u + sum_{j<s} coef_j k_j
       Rep r;
       r.A = I;
-      for (int t = 0; t < 3; ++t) r.H[t].assign(Np, 0);
+      for (int t = 0; t < CS; ++t) r.H[t].assign(Np, 0);
       for (int j = 0; j < s; ++j) {
         for (int x = 0; x < Np * Np; ++x) r.A[x] += coef[j] * Kr[j].A[x];
-        for (int t = 0; t < 3; ++t)
+        for (int t = 0; t < CS; ++t)
           for (int i = 0; i < Np; ++i) r.H[t][i] += coef[j] * Kr[j].H[t][i];
       }
       return r;
     };
     for (int s = 0; s < S; ++s) {
       Kr[s].A = mul(W, Y[s].A);
-      for (int t = 0; t < 3; ++t) Kr[s].H[t] = mulv(W, Y[s].H[t]);
+      for (int t = 0; t < CS; ++t) Kr[s].H[t] = mulv(W, Y[s].H[t]);
       for (int i = 0; i < Np; ++i) Kr[s].H[s][i] += w[i];
       if (s + 1 < S) Y[s + 1] = combine(s + 1, a[s + 1]);
     }
     Rep U = combine(S, b);
     Gl = U.A;
-    for (int t = 0; t < 3; ++t) hl[t] = U.H[t];
-    for (int i = 0; i < Np; ++i) {
-      if (S >= 2) r1l[i] = Y[1].A[p * Np + i];
-      if (S >= 3) r2l[i] = Y[2].A[p * Np + i];
-    }
-    if (S >= 2) kl[0] = Y[1].H[0][p];
-    if (S >= 3) {
-      kl[1] = Y[2].H[0][p];
-      kl[2] = Y[2].H[1][p];
+    for (int t = 0; t < S; ++t) hl[t] = U.H[t];
+    for (int s = 1; s < S; ++s) {
+      for (int i = 0; i < Np; ++i) rl[s][i] = Y[s].A[p * Np + i];
+      for (int t = 0; t < s; ++t) kl[s][t] = Y[s].H[t][p];
     }
     // PE-face responses: the stage-st correction d enters k_st as c2a M^{-1} e_0 d at element e
     // and -c2a M^{-1} e_p d at element e-1 and spreads through the later stages on elements
-    // e-1 .. e+2; rho is the right trace of element e-1's later stage inputs.
+    // e-1 .. e+S-1 (one element further per stage); rho is the right trace of element e-1's
+    // later stage inputs.
+    const int nw = S + 1;
     for (int st = 0; st < S; ++st) {
-      std::vector<ld> dK[3];
-      for (auto &v : dK) v.assign(4 * Np, 0.0L);
+      std::vector<ld> dK[CS];
+      for (auto &v : dK) v.assign((size_t)nw * Np, 0.0L);
       for (int i = 0; i < Np; ++i) {
         dK[st][1 * Np + i] = c2a * o.Minv[i * Np + 0];
         dK[st][0 * Np + i] = -c2a * o.Minv[i * Np + p];
       }
       for (int t = st + 1; t < S; ++t) {
-        std::vector<ld> dY(4 * Np, 0.0L);
+        std::vector<ld> dY((size_t)nw * Np, 0.0L);
         for (int jj = st; jj < t; ++jj)
-          for (int x = 0; x < 4 * Np; ++x) dY[x] += a[t][jj] * dK[jj][x];
-        const ld r = dY[0 * Np + p];
-        if (st == 0 && t == 1) rhol[0] = r;
-        if (st == 0 && t == 2) rhol[1] = r;
-        if (st == 1 && t == 2) rhol[2] = r;
-        for (int m = 0; m < 4; ++m)
+          for (int x = 0; x < nw * Np; ++x) dY[x] += a[t][jj] * dK[jj][x];
+        rhol[t][st] = dY[0 * Np + p];
+        for (int m = 0; m < nw; ++m)
           for (int i = 0; i < Np; ++i) {
             ld acc = 0;
             for (int k = 0; k < Np; ++k) acc += W[i * Np + k] * dY[m * Np + k];
@@ -641,7 +637,7 @@ void fold_step_constants(InstHost &h) {
             dK[t][m * Np + i] = acc;
           }
       }
-      for (int m = 0; m < 4; ++m)
+      for (int m = 0; m < nw; ++m)
         for (int i = 0; i < Np; ++i) {
           ld acc = 0;
           for (int jj = st; jj < S; ++jj) acc += b[jj] * dK[jj][m * Np + i];
@@ -649,22 +645,26 @@ void fold_step_constants(InstHost &h) {
         }
     }
   }
+  // the composed kernels keep S slots per ring level: three for schemes of up to three stages
+  // (unused channels zero), five for the five-stage scheme
+  h.I.ns = S <= 3 ? 3 : adg::kMaxCS;
 
   adg::StepConsts &Sc = h.I.st;
   std::memset(&Sc, 0, sizeof(Sc));
-  for (int i = 0; i < Np; ++i) {
+  for (int i = 0; i < Np; ++i)
     for (int j = 0; j < Np; ++j) Sc.G[i * Np + j] = (double)Gl[i * Np + j];
-    Sc.r1[i] = (double)r1l[i];
-    Sc.r2[i] = (double)r2l[i];
-    for (int t = 0; t < 3; ++t) Sc.h[t][i] = (double)hl[t][i];
+  for (int s = 0; s < CS; ++s) {
+    for (int i = 0; i < Np; ++i) {
+      Sc.r[s][i] = (double)rl[s][i];
+      Sc.h[s][i] = (double)hl[s][i];
+    }
+    for (int t = 0; t < CS; ++t) {
+      Sc.k[s][t] = (double)kl[s][t];
+      Sc.rho[s][t] = (double)rhol[s][t];
+    }
+    for (int m = 0; m <= CS; ++m)
+      for (int i = 0; i < Np; ++i) Sc.R[s][m][i] = (double)Rl[s][m][i];
   }
-  for (int t = 0; t < 3; ++t) {
-    Sc.k[t] = (double)kl[t];
-    Sc.rho[t] = (double)rhol[t];
-  }
-  for (int st = 0; st < 3; ++st)
-    for (int m = 0; m < 4; ++m)
-      for (int i = 0; i < Np; ++i) Sc.R[st][m][i] = (double)Rl[st][m][i];
 
   // Fixed-point limbs of the same coefficients (from the long double values): C =
   // round(c 2^58) in balanced limbs C = ch 2^29 + cl (adg_fixed.cuh); every |c| < 2 keeps
@@ -696,42 +696,49 @@ void fold_step_constants(InstHost &h) {
     }
     return ab < ldexpl(1.0L, 62) && bb < ldexpl(1.0L, 62) && rb < 15.9L;
   };
-  ld b1 = fabsl(kl[0]), b2 = fabsl(kl[1]);
   bool sums = true;
-  std::vector<std::pair<ld, int>> s1{{kl[0], 1}}, s2{{kl[1], 1}, {kl[2], 2}};
   for (int i = 0; i < Np; ++i) {
     std::vector<std::pair<ld, int>> row;
     for (int j = 0; j < Np; ++j) {
       F.G[i * Np + j] = limbs(Gl[i * Np + j]);
       row.push_back({Gl[i * Np + j], 1});
     }
-    F.r1[i] = limbs(r1l[i]);
-    F.r2[i] = limbs(r2l[i]);
-    for (int t = 0; t < 3; ++t) {
+    for (int t = 0; t < S; ++t) {
       F.h[t][i] = limbs(hl[t][i]);
       row.push_back({hl[t][i], t == 0 ? 1 : 2});
     }
     sums = sums && sum_ok(row);
-    s1.push_back({r1l[i], 1});
-    s2.push_back({r2l[i], 1});
-    b1 += fabsl(r1l[i]);
-    b2 += fabsl(r2l[i]);
   }
-  for (int t = 0; t < 3; ++t) F.k[t] = limbs(kl[t]);
-  sums = sums && sum_ok(s1) && sum_ok(s2);
-  b2 += fabsl(kl[2]) * b1;
-  // channel scalars v1_p, v2_p at most twice the input bound (|X| < 2^58 as multiplicands;
-  // inputs are < 2^57)
-  h.fixed_ok = ok && sums && b1 < 1.999L && b2 < 1.999L;
+  // channel scalars Y_s p below twice the input bound (|X| < 2^58 as multiplicands; inputs
+  // are < 2^57): B_s = sum |r_s| + |k_s0| + sum_{t>=1} |k_st| B_t < 2
+  ld B[CS] = {1.0L};
+  bool chan = true;
+  for (int s = 1; s < S; ++s) {
+    std::vector<std::pair<ld, int>> sm;
+    B[s] = 0;
+    for (int i = 0; i < Np; ++i) {
+      F.r[s][i] = limbs(rl[s][i]);
+      sm.push_back({rl[s][i], 1});
+      B[s] += fabsl(rl[s][i]);
+    }
+    for (int t = 0; t < s; ++t) {
+      F.k[s][t] = limbs(kl[s][t]);
+      sm.push_back({kl[s][t], t == 0 ? 1 : 2});
+      B[s] += fabsl(kl[s][t]) * (t == 0 ? 1.0L : B[t]);
+    }
+    sums = sums && sum_ok(sm);
+    chan = chan && B[s] < 1.999L;
+  }
+  h.fixed_ok = ok && sums && chan;
   // the PE-face responses likewise (from the long double values), for the integer correction
   // of differences below 2^57
   std::memset(h.I.Rf, 0, sizeof(h.I.Rf));
   ok = true;
   bool rsums = true;
-  for (int m = 0; m < 4; ++m)
+  for (int m = 0; m <= S; ++m)
     for (int i = 0; i < Np; ++i) {
       std::vector<std::pair<ld, int>> row;
-      for (int st = 0; st < 3; ++st) {
+      for (int st = 0; st < S; ++st) {
         h.I.Rf[st][m][i] = limbs(Rl[st][m][i]);
         row.push_back({Rl[st][m][i], 1});
       }
@@ -813,8 +820,8 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   Inst &I = h.I;
   const size_t nd = (size_t)I.K * I.Np;
   if (h.cfg.ept > 0) {   // forced by the caller
-    if (I.fused == 2 && h.cfg.ept > 2)
-      return fail(c, ADG_EINVAL, "the fixed-point composed step takes ept 1 or 2");
+    if (I.fused == 2 && (h.cfg.ept > 2 || (h.cfg.ept == 2 && I.K % 2)))
+      return fail(c, ADG_EINVAL, "the fixed-point composed step takes ept 1, or 2 for even K");
     I.ept = h.cfg.ept;
     return ADG_OK;
   }
@@ -837,7 +844,7 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   // Per choice one untimed launch, then two timed ones (the choices differ by about 10% on
   // large meshes, far above the event resolution; the autotuner runs inside adg_init, so it is
   // kept short).
-  for (int ept = 1; ept <= (fixed ? 2 : 4); ept *= 2) {
+  for (int ept = 1; ept <= (fixed ? (I.K % 2 ? 1 : 2) : 4); ept *= 2) {
     Inst T = I;
     T.ept = ept;
     CK(adg::launch_fused_step(T, I.v1, I.v2, rel, c->stream, false, fmt));
@@ -987,25 +994,41 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     }
   }
   {
-    // the composed step: SSP-RK3, or a low-storage scheme of at most three stages
+    // the composed step: SSP-RK3, or a low-storage scheme (five stages: fixed point only).
+    // With PE faces the correction windows of the composed step's S stages (elements e-S ..
+    // e+S-1 of face e) must not overlap: K/P >= 8, and >= 10 for five stages.
+    const int S = (I.ls && I.ns > kStages) ? adg::kMaxCS : kStages;
     const bool eligible = cfg->pde == ADG_ADVECTION && cfg->a > 0 && K >= 8 &&
-                          (!I.async || I.Kpe >= 8) && (!I.ls || I.ns <= kStages);
+                          (!I.async || I.Kpe >= (S == kStages ? 8 : 10)) &&
+                          (!I.ls || I.ns <= adg::kMaxCS) && !I.visc && !I.euler;
     const bool want_composed = cfg->variant == ADG_VARIANT_COMPOSED ||
                                cfg->variant == ADG_VARIANT_COMPOSED_FIXED;
     if (want_composed && !eligible)
-      return fail(c, ADG_EINVAL, "the composed step needs a scheme of at most three stages, "
-                                 "advection with a > 0, K >= 8 and K/P >= 8");
+      return fail(c, ADG_EINVAL, "the composed step needs advection with a > 0, K >= 8 and "
+                                 "K/P >= 8 (10 for the five-stage scheme)");
+    if (cfg->variant == ADG_VARIANT_COMPOSED && S != kStages)
+      return fail(c, ADG_EINVAL, "the FP64 composed step takes schemes of at most three "
+                                 "stages; the five-stage scheme composes in fixed point");
     I.fused = (eligible && cfg->variant != ADG_VARIANT_STAGED) ? 1 : 0;
     I.ept = 1;
+    const int ls0 = I.ls, ns0 = I.ns;
     if (I.fused) {
-      // the composed kernels keep three stage slots per ring level whatever the scheme
       I.ls = 0;
-      I.ns = kStages;
-      fold_step_constants(h);
+      fold_step_constants(h);   // sets I.ns to the composed kernels' stage slots
       if (cfg->variant == ADG_VARIANT_COMPOSED_FIXED && !h.fixed_ok)
         return fail(c, ADG_EINVAL,
                     "the fixed-point composed step needs every composed coefficient "
                     "below 2 in magnitude (a smaller Courant number)");
+      const bool fixed = h.fixed_ok && (cfg->variant == ADG_VARIANT_AUTO ||
+                                        cfg->variant == ADG_VARIANT_COMPOSED_FIXED);
+      if (!fixed && S != kStages) {
+        // five stages without the fixed-point bounds: the staged 2N kernels
+        I.fused = 0;
+        I.ls = ls0;
+        I.ns = ns0;
+      }
+    }
+    if (I.fused) {
       const bool fixed = h.fixed_ok && (cfg->variant == ADG_VARIANT_AUTO ||
                                         cfg->variant == ADG_VARIANT_COMPOSED_FIXED);
       if (fixed) {
@@ -1013,7 +1036,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
         CK(cudaMalloc(&h.fx, 3 * sizeof(adg::FxSlot)));
         I.fx = h.fx;
         if (I.async && !c->batch) {
-          CK(cudaMalloc(&h.fd, (size_t)2 * I.P * 3 * sizeof(double)));
+          CK(cudaMalloc(&h.fd, (size_t)2 * I.P * I.ns * sizeof(double)));
           I.fd = h.fd;
         }
         int r2 = reset_exponent(c, h);
@@ -1799,7 +1822,8 @@ int tune_batch(adg_ctx *c, const double *const *u0_devs) {
     if (forced >= 0 && kind != forced) continue;
     if (kind == 2 && c->bu) {
       for (int ept : {2, 1, 4})
-        if (!ept_forced || ept == ept_forced) cands.push_back({kind, ept});
+        if ((!ept_forced || ept == ept_forced) && (ept != 2 || c->batch_even))
+          cands.push_back({kind, ept});
     } else {
       cands.push_back({kind, 1});
     }
@@ -1880,7 +1904,7 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       const InstHost &h = c->inst[i];
       all_fused = all_fused && h.I.fused;
       all_fixed = all_fixed && h.I.fused == 2;
-      if (h.I.ls)
+      if (h.cfg.rk != ADG_SSPRK3)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches need rk = ADG_SSPRK3");
       else if (h.I.visc || h.I.euler)
         r = fail(c, ADG_EINVAL, "instance " + std::to_string(i) + ": batches take the inviscid scalar equations");
@@ -1956,9 +1980,14 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
         }
       }
     }
+    bool all_even = true;
+    for (int i = 0; i < n; ++i) all_even = all_even && c->inst[i].I.K % 2 == 0;
+    c->batch_even = all_even;
     if (!r && ept_forced && ept_forced != 1 && !(all_fixed && c->bu && forced != ADG_VARIANT_COMPOSED &&
                                                   forced != ADG_VARIANT_STAGED))
       r = fail(c, ADG_EINVAL, "ept > 1 in a batch needs the fixed-point step with shared coefficients");
+    if (!r && ept_forced == 2 && !all_even)
+      r = fail(c, ADG_EINVAL, "ept 2 in a batch needs an even K in every instance");
     c->nwork = (int)work.size();
     c->nfwork = (int)fwork.size();
     if (cudaMalloc(&c->insts_dev, sizeof(Inst) * n) != cudaSuccess ||
@@ -2142,7 +2171,7 @@ int adg_grad(adg_ctx *c, const double *target_dev, int64_t nsteps, int32_t ckpt_
              double *grad_u0_dev, double *J_out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
   if (c->batch) return fail(c, ADG_ESTATE, "adg_grad takes a single-instance context");
-  if (c->inst[0].I.ls) return fail(c, ADG_EINVAL, "adg_grad needs rk = ADG_SSPRK3");
+  if (c->inst[0].cfg.rk != ADG_SSPRK3) return fail(c, ADG_EINVAL, "adg_grad needs rk = ADG_SSPRK3");
   if (c->inst[0].I.visc || c->inst[0].I.euler)
     return fail(c, ADG_EINVAL, "adg_grad covers the inviscid scalar equations");
   if (nsteps < 0 || ckpt_every < 1) return fail(c, ADG_EINVAL, "need nsteps >= 0 and ckpt_every >= 1");

@@ -1,20 +1,19 @@
-// Composed SSP-RK3 step of upwind advection (a > 0) in fixed-point integer arithmetic:
-// the StepConsts stencil (adg_internal.h) evaluated with 32 x 32 -> 64-bit integer
-// multiply-adds on two-limb values (adg_fixed.cuh). Within a chunk of steps the field stays
-// int64 between steps; only the chunk's first step reads FP64 and its last writes FP64.
+// Composed step of upwind advection (a > 0; SSP-RK3, or a low-storage scheme of up to five
+// stages) in fixed-point integer arithmetic: the StepConsts stencil (adg_internal.h) evaluated
+// with 32 x 32 -> 64-bit integer multiply-adds on two-limb values (adg_fixed.cuh). The field
+// stays int64 from step to step; only a run's first step reads FP64.
 #include "adg_device.cuh"
 #include "adg_fixed.cuh"
 
 namespace adg {
 namespace {
 
-template <int EPT>
+// Per element slot (S slots before the block's tile for the elements e0-S .. e0-1): the right
+// trace p and the unrounded own parts (a, b) of its channel scalars r_s . u, s = 1 .. S-1.
+template <int EPT, int S>
 struct FixedShared {
-  // per element slot: the right trace p and the unrounded own parts (a, b) of its channel
-  // scalars r1 . u, r2 . u
-  long long p[EPT * kTile + 3];
-  long long s1a[EPT * kTile + 3], s1b[EPT * kTile + 3];
-  long long s2a[EPT * kTile + 3], s2b[EPT * kTile + 3];
+  long long p[EPT * kTile + S];
+  long long sa[S - 1][EPT * kTile + S], sb[S - 1][EPT * kTile + S];
   FxScale sc;
 };
 
@@ -26,33 +25,124 @@ __device__ __forceinline__ long long fx_in(double x, long long X, const FxScale 
   return fx_from_double(x, sc.sigma + 1079);
 }
 
-// p = the element's right trace, s1 / s2 = the own parts r1 . u, r2 . u of its channel
-// scalars (unrounded sums), and the limbs of its values for the output rows.
-template <int NP, bool FIN>
+// p = the element's right trace, own[s-1] = the own parts r_s . u of its channel scalars
+// (unrounded sums, s = 1 .. S-1), and the limbs of its values for the output rows.
+template <int NP, bool FIN, int S>
 __device__ __forceinline__ void fx_own(const StepFixed &F, const double *ud, const long long *uq,
-                                       const FxScale &sc, long long &p, FxAcc &s1, FxAcc &s2,
-                                       int *xh, int *xl) {
+                                       const FxScale &sc, long long &p, FxAcc *own, int *xh,
+                                       int *xl) {
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
     const long long X = fx_in<FIN>(FIN ? 0.0 : ud[j], FIN ? uq[j] : 0ll, sc);
     fx_split(X, xh[j], xl[j]);
-    fx_mac(s1, F.r1[j], xh[j], xl[j]);
-    fx_mac(s2, F.r2[j], xh[j], xl[j]);
+#pragma unroll
+    for (int s = 1; s < S; ++s) fx_mac(own[s - 1], F.r[s][j], xh[j], xl[j]);
     if (j == NP - 1) p = X;
+  }
+}
+
+template <int EPT, int S>
+__device__ __forceinline__ void fx_publish(FixedShared<EPT, S> &sh, int sl, long long p,
+                                           const FxAcc *own) {
+  sh.p[sl] = p;
+#pragma unroll
+  for (int s = 0; s < S - 1; ++s) {
+    sh.sa[s][sl] = own[s].a;
+    sh.sb[s][sl] = own[s].b;
+  }
+}
+
+// The channel scalars of element e-1 (P[s], split into limbs) from the published slots
+// b .. b+S-1 of elements e-S .. e-1: element e-S+w forms Y_1 .. Y_w from its own parts and the
+// scalars of the element before it, Y_s = r_s . u + sum_{t<s} k_st Y_t (each rounded once; every
+// thread that needs one of them forms it from the same values, so all agree bit for bit).
+template <int EPT, int S>
+__device__ __forceinline__ void fx_left_channels(const StepFixed &F, const FixedShared<EPT, S> &sh,
+                                                 int b, int (*P)[2]) {
+  long long Yp[S];
+  Yp[0] = sh.p[b];
+#pragma unroll
+  for (int w = 1; w < S; ++w) {
+    int ph[S], pl[S];
+#pragma unroll
+    for (int t = 0; t < w; ++t) fx_split(Yp[t], ph[t], pl[t]);
+    long long Y[S];
+    Y[0] = sh.p[b + w];
+#pragma unroll
+    for (int s = 1; s <= w; ++s) {
+      FxAcc c{sh.sa[s - 1][b + w], sh.sb[s - 1][b + w]};
+#pragma unroll
+      for (int t = 0; t < s; ++t) fx_mac(c, F.k[s][t], ph[t], pl[t]);
+      Y[s] = fx_round(c);
+    }
+#pragma unroll
+    for (int s = 0; s <= w; ++s) Yp[s] = Y[s];
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) fx_split(Yp[s], P[s][0], P[s][1]);
+}
+
+// u'^e = G u^e + sum_s h_s P_s for output row i.
+template <int NP, int S>
+__device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int *xh, const int *xl,
+                                            const int (*P)[2]) {
+  FxAcc acc;
+#pragma unroll
+  for (int j = 0; j < NP; ++j) fx_mac(acc, F.G[i * NP + j], xh[j], xl[j]);
+#pragma unroll
+  for (int s = 0; s < S; ++s) fx_mac(acc, F.h[s][i], P[s][0], P[s][1]);
+  return fx_round(acc);
+}
+
+// The block's scale read (thread 0, one barrier; every warp reading it itself measured 4%
+// slower) and the slot bookkeeping of the block holding element 0: it clears the slot of
+// u^{n+2} and, for an int64 output, sets u^{n+1}'s scale and NaN mark.
+template <bool FIN, bool FOUT, class I, class SH>
+__device__ __forceinline__ FxScale fx_block_scale(const I &inst, int e0, int rel, SH &sh) {
+  if (threadIdx.x == 0) {
+    const FxScale sc = fx_scale(inst.fx, inst.meta[0] + rel, FIN);
+    sh.sc = sc;
+    if (e0 == 0) {
+      FxSlot &c = inst.fx[fx_clear(sc.slot)];
+      c.mag = 0;
+      c.E = 0;
+      c.sigma = 0;
+      if (FOUT) {
+        inst.fx[fx_next(sc.slot)].sigma = sc.sigma;
+        if (sc.bad) inst.fx[fx_next(sc.slot)].E = 2047;
+      }
+    }
+  }
+  __syncthreads();
+  return sh.sc;
+}
+
+// The scale of u^{n+1}: OR of |y| (int64 output) or largest exponent (FP64 output), one slot
+// update per warp.
+template <bool FOUT, class I>
+__device__ __forceinline__ void fx_block_next(const I &inst, const FxScale &sc,
+                                              unsigned long long mag, int emax) {
+  FxSlot &nx = inst.fx[fx_next(sc.slot)];
+  if (FOUT) {
+    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mag);
+    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mag >> 32));
+    if ((threadIdx.x & 31) == 0) or_slot(&nx.mag, ((unsigned long long)hi << 32) | lo);
+  } else {
+    emax = __reduce_max_sync(0xffffffffu, emax);
+    if ((threadIdx.x & 31) == 0) raise_slot(&nx.E, emax);
   }
 }
 
 // One thread per element (EPT elements per thread, e = e0 + t + h kTile): the right trace and
 // the unrounded own parts of the channel scalars go to shared memory (one barrier); each
-// thread then forms its left neighbour's v1_p and v2_p from those of elements e-3 .. e-1 and
-// u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2. The first three threads publish the three elements
-// before the block with the same arithmetic (the working scale is one per field, so every
-// element converts the same way).
-// The block holding element 0 clears the scale slot of u^{n+2}.
-template <int NP, int EPT, int FMT, class I>
+// thread then forms its left neighbour's channel scalars from those of elements e-S .. e-1
+// and u'^e = G u^e + sum_s h_s P_s. The first S threads publish the S elements before the
+// block with the same arithmetic (the working scale is one per field, so every element
+// converts the same way).
+template <int NP, int EPT, int FMT, int S, class I>
 __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict__ uin_,
                                            void *__restrict__ uout_, int e0, int rel,
-                                           FixedShared<EPT> &sh) {
+                                           FixedShared<EPT, S> &sh) {
   constexpr bool FIN = (FMT & kFmtInFixed) != 0;
   constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
   const double *uin_d = static_cast<const double *>(uin_);
@@ -64,8 +154,8 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
   // loads first: they do not depend on the scale
   double hd[NP];
   long long hq[NP];
-  if (t < 3) {
-    int m = e0 - 3 + t;
+  if (t < S) {
+    int m = e0 - S + t;
     if (m < 0) m += K;   // K >= 8 on this path
     if (FIN) load_elem<NP>(uin_q, K, m, hq);
     else load_elem<NP>(uin_d, K, m, hd);
@@ -78,24 +168,7 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
     if (FIN) load_elem<NP>(uin_q, K, e < K ? e : K - 1, uq[h]);
     else load_elem<NP>(uin_d, K, e < K ? e : K - 1, ud[h]);
   }
-  // thread 0 reads the scale of u^n for the block (every warp reading it itself, without
-  // this barrier, measured 4% slower)
-  if (t == 0) {
-    const FxScale sc = fx_scale(inst.fx, inst.meta[0] + rel, FIN);
-    sh.sc = sc;
-    if (e0 == 0) {
-      FxSlot &c = inst.fx[fx_clear(sc.slot)];   // the slot of u^{n+2}
-      c.mag = 0;
-      c.E = 0;
-      c.sigma = 0;
-      if (FOUT) {
-        inst.fx[fx_next(sc.slot)].sigma = sc.sigma;
-        if (sc.bad) inst.fx[fx_next(sc.slot)].E = 2047;
-      }
-    }
-  }
-  __syncthreads();
-  const FxScale sc = sh.sc;
+  const FxScale sc = fx_block_scale<FIN, FOUT>(inst, e0, rel, sh);
   if (FIN && sc.shift != 0) {   // block-uniform: the field grew past 2^57 or shrank
 #pragma unroll
     for (int j = 0; j < NP; ++j) hq[j] = fx_rescale(hq[j], sc.shift);
@@ -105,72 +178,35 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
       for (int j = 0; j < NP; ++j) uq[h][j] = fx_rescale(uq[h][j], sc.shift);
   }
   // publish p and the unrounded own parts of every element's channel scalars (the halo's too)
-  if (t < 3) {
+  if (t < S) {
     int xh[NP], xl[NP];
     long long p;
-    FxAcc hs1, hs2;
-    fx_own<NP, FIN>(F, hd, hq, sc, p, hs1, hs2, xh, xl);
-    sh.p[t] = p;
-    sh.s1a[t] = hs1.a;
-    sh.s1b[t] = hs1.b;
-    sh.s2a[t] = hs2.a;
-    sh.s2b[t] = hs2.b;
+    FxAcc own[S - 1];
+    fx_own<NP, FIN, S>(F, hd, hq, sc, p, own, xh, xl);
+    fx_publish(sh, t, p, own);
   }
   int xh[EPT][NP], xl[EPT][NP];
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
     long long p;
-    FxAcc s1, s2;
-    fx_own<NP, FIN>(F, ud[h], uq[h], sc, p, s1, s2, xh[h], xl[h]);
-    const int sl = t + h * kTile + 3;
-    sh.p[sl] = p;
-    sh.s1a[sl] = s1.a;
-    sh.s1b[sl] = s1.b;
-    sh.s2a[sl] = s2.a;
-    sh.s2b[sl] = s2.b;
+    FxAcc own[S - 1];
+    fx_own<NP, FIN, S>(F, ud[h], uq[h], sc, p, own, xh[h], xl[h]);
+    fx_publish(sh, t + h * kTile + S, p, own);
   }
   __syncthreads();
   unsigned long long mag = 0;   // FOUT: OR of |y|
   int emax = 0;                 // FP64 output: largest biased exponent
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
-    const int b = t + h * kTile;   // slots of the elements e-3, e-2, e-1: b, b+1, b+2
+    const int b = t + h * kTile;   // slots of the elements e-S .. e-1: b .. b+S-1
     const int e = e0 + b;
-    // the left neighbour's channel scalars, each rounded once from the published parts:
-    // v1_p^{e-2} = r1 . u^{e-2} + k_0 p^{e-3}, v1_p^{e-1} = r1 . u^{e-1} + k_0 p^{e-2},
-    // v2_p^{e-1} = r2 . u^{e-1} + k_1 p^{e-2} + k_2 v1_p^{e-2} (every thread that needs one of
-    // them forms it from the same values, so all agree bit for bit)
-    int p3h, p3l, p2h, p2l;
-    fx_split(sh.p[b], p3h, p3l);
-    fx_split(sh.p[b + 1], p2h, p2l);
-    FxAcc c1m2{sh.s1a[b + 1], sh.s1b[b + 1]};
-    fx_mac(c1m2, F.k[0], p3h, p3l);
-    const long long q1m2 = fx_round(c1m2);
-    FxAcc c1m1{sh.s1a[b + 2], sh.s1b[b + 2]};
-    fx_mac(c1m1, F.k[0], p2h, p2l);
-    const long long q1m1 = fx_round(c1m1);
-    int qh, ql;
-    fx_split(q1m2, qh, ql);
-    FxAcc c2m1{sh.s2a[b + 2], sh.s2b[b + 2]};
-    fx_mac(c2m1, F.k[1], p2h, p2l);
-    fx_mac(c2m1, F.k[2], qh, ql);
-    const long long q2m1 = fx_round(c2m1);
-    int P0h, P0l, P1h, P1l, P2h, P2l;
-    fx_split(sh.p[b + 2], P0h, P0l);
-    fx_split(q1m1, P1h, P1l);
-    fx_split(q2m1, P2h, P2l);
-    const size_t base = (size_t)e;
-    double *od = static_cast<double *>(uout_) + base;
-    long long *oq = static_cast<long long *>(uout_) + base;
+    int P[S][2];
+    fx_left_channels(F, sh, b, P);
+    double *od = static_cast<double *>(uout_) + (size_t)e;
+    long long *oq = static_cast<long long *>(uout_) + (size_t)e;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      FxAcc acc;
-#pragma unroll
-      for (int j = 0; j < NP; ++j) fx_mac(acc, F.G[i * NP + j], xh[h][j], xl[h][j]);
-      fx_mac(acc, F.h[0][i], P0h, P0l);
-      fx_mac(acc, F.h[1][i], P1h, P1l);
-      fx_mac(acc, F.h[2][i], P2h, P2l);
-      const long long y = fx_round(acc);
+      const long long y = fx_row<NP, S>(F, i, xh[h], xl[h], P);
       if (FOUT) {
         if (e < K) {
           *oq = y;
@@ -188,26 +224,132 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
       oq += K;
     }
   }
-  // the scale of u^{n+1}: OR of |y| (int64 output) or largest exponent (FP64 output), one
-  // slot update per warp
-  FxSlot &nx = inst.fx[fx_next(sc.slot)];
-  if (FOUT) {
-    const unsigned lo = __reduce_or_sync(0xffffffffu, (unsigned)mag);
-    const unsigned hi = __reduce_or_sync(0xffffffffu, (unsigned)(mag >> 32));
-    if ((t & 31) == 0) or_slot(&nx.mag, ((unsigned long long)hi << 32) | lo);
-  } else {
-    emax = __reduce_max_sync(0xffffffffu, emax);
-    if ((t & 31) == 0) raise_slot(&nx.E, emax);
+  fx_block_next<FOUT>(inst, sc, mag, emax);
+}
+
+// Two consecutive elements per thread (e = e0 + 2t and e + 1, the block's 512-element tile; K
+// even): each node plane is read and written as one 128-bit access per thread (a fallback to
+// two 64-bit accesses for odd K cost 5% in this kernel, so odd meshes take one element per
+// thread), the elements e-S .. e-1 come from the published slots (one barrier),
+// and the odd element takes its left neighbour's channel scalars from the even element's
+// registers (S(S-1)/2 multiply-adds instead of the recursion over S-1 elements, half the
+// shared-memory reads). The arithmetic of every sum is that of fixed_body, so the results are
+// bit-identical to it.
+template <int NP, int FMT, int S, class I>
+__device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__restrict__ uin_,
+                                                void *__restrict__ uout_, int e0, int rel,
+                                                FixedShared<2, S> &sh) {
+  constexpr bool FIN = (FMT & kFmtInFixed) != 0;
+  constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
+  const double *uin_d = static_cast<const double *>(uin_);
+  const long long *uin_q = static_cast<const long long *>(uin_);
+  const int K = inst.K;
+  const int t = threadIdx.x;
+  const StepFixed &F = inst.sf;
+  double hd[NP];
+  long long hq[NP];
+  if (t < S) {
+    int m = e0 - S + t;
+    if (m < 0) m += K;
+    if (FIN) load_elem<NP>(uin_q, K, m, hq);
+    else load_elem<NP>(uin_d, K, m, hd);
   }
+  const int e = e0 + 2 * t;
+  // K even: both elements in range or both out, every pair 16-byte aligned in every plane
+  const int el = e < K ? e : K - 2;
+  double ud[2][NP];
+  long long uq[2][NP];
+#pragma unroll
+  for (int j = 0; j < NP; ++j) {
+    if (FIN) {
+      const longlong2 v = __ldg(reinterpret_cast<const longlong2 *>(uin_q + (size_t)j * K + el));
+      uq[0][j] = v.x;
+      uq[1][j] = v.y;
+    } else {
+      const double2 v = __ldg(reinterpret_cast<const double2 *>(uin_d + (size_t)j * K + el));
+      ud[0][j] = v.x;
+      ud[1][j] = v.y;
+    }
+  }
+  const FxScale sc = fx_block_scale<FIN, FOUT>(inst, e0, rel, sh);
+  if (FIN && sc.shift != 0) {
+#pragma unroll
+    for (int j = 0; j < NP; ++j) hq[j] = fx_rescale(hq[j], sc.shift);
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int j = 0; j < NP; ++j) uq[h][j] = fx_rescale(uq[h][j], sc.shift);
+  }
+  if (t < S) {
+    int xh[NP], xl[NP];
+    long long p;
+    FxAcc own[S - 1];
+    fx_own<NP, FIN, S>(F, hd, hq, sc, p, own, xh, xl);
+    fx_publish(sh, t, p, own);
+  }
+  int xh[2][NP], xl[2][NP];
+  long long pE;
+  FxAcc ownE[S - 1];
+  {
+    long long pO;
+    FxAcc ownO[S - 1];
+    fx_own<NP, FIN, S>(F, ud[0], uq[0], sc, pE, ownE, xh[0], xl[0]);
+    fx_own<NP, FIN, S>(F, ud[1], uq[1], sc, pO, ownO, xh[1], xl[1]);
+    fx_publish(sh, 2 * t + S, pE, ownE);
+    fx_publish(sh, 2 * t + S + 1, pO, ownO);
+  }
+  __syncthreads();
+  // the even element's left channels from slots 2t .. 2t+S-1 (elements E-S .. E-1)
+  int P[2][S][2];
+  fx_left_channels(F, sh, 2 * t, P[0]);
+  // the odd element's left neighbour is E: Y_s^E = r_s . u^E + sum_{t<s} k_st P_t(E)
+  fx_split(pE, P[1][0][0], P[1][0][1]);
+#pragma unroll
+  for (int s = 1; s < S; ++s) {
+    FxAcc c = ownE[s - 1];
+#pragma unroll
+    for (int q = 0; q < s; ++q) fx_mac(c, F.k[s][q], P[0][q][0], P[0][q][1]);
+    fx_split(fx_round(c), P[1][s][0], P[1][s][1]);
+  }
+  unsigned long long mag = 0;
+  int emax = 0;
+  const bool ok = e < K;
+  double *od = static_cast<double *>(uout_) + (size_t)el;
+  long long *oq = static_cast<long long *>(uout_) + (size_t)el;
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    long long y[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) y[h] = fx_row<NP, S>(F, i, xh[h], xl[h], P[h]);
+    if (FOUT) {
+      if (ok) {
+        *reinterpret_cast<longlong2 *>(oq) = make_longlong2(y[0], y[1]);
+        mag |= fx_mag(y[0]) | fx_mag(y[1]);
+      }
+    } else {
+      const double v0 = sc.bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(y[0], sc.sigma);
+      const double v1 = sc.bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(y[1], sc.sigma);
+      if (ok) {
+        *reinterpret_cast<double2 *>(od) = make_double2(v0, v1);
+        emax = max(emax, max(biased_exponent(v0), biased_exponent(v1)));
+      }
+    }
+    od += K;
+    oq += K;
+  }
+  fx_block_next<FOUT>(inst, sc, mag, emax);
 }
 
 // One element per thread runs at full occupancy (8 blocks of 256 threads per SM, at most 32
 // registers); two per thread keep 64 registers for the second element's values.
-template <int NP, int EPT, int FMT>
+template <int NP, int EPT, int FMT, int S>
 __global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4)
     k_step_fixed(const Inst inst, const void *__restrict__ uin, void *__restrict__ uout, int rel) {
-  __shared__ FixedShared<EPT> sh;
-  fixed_body<NP, EPT, FMT>(inst, uin, uout, blockIdx.x * (kTile * EPT), rel, sh);
+  __shared__ FixedShared<EPT, S> sh;
+  if constexpr (EPT == 2)
+    fixed_body_pair<NP, FMT, S>(inst, uin, uout, blockIdx.x * (kTile * 2), rel, sh);
+  else
+    fixed_body<NP, EPT, FMT, S>(inst, uin, uout, blockIdx.x * (kTile * EPT), rel, sh);
 }
 
 __device__ __forceinline__ void *inst_field(const Inst &I, int sel) {
@@ -222,7 +364,7 @@ __global__ void __launch_bounds__(kTile)
     k_batch_fixed(const Inst *__restrict__ insts, const int2 *__restrict__ work, int src, int dst,
                   int rel) {
   __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
-  __shared__ FixedShared<1> sh;
+  __shared__ FixedShared<1, 3> sh;
   const int2 w = work[blockIdx.x];
   {
     const int4 *from = reinterpret_cast<const int4 *>(insts + w.x);
@@ -235,10 +377,10 @@ __global__ void __launch_bounds__(kTile)
   const void *uin = inst_field(I, src);
   void *uout = inst_field(I, dst);
   switch (I.Np) {
-    case 2: fixed_body<2, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
-    case 3: fixed_body<3, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
-    case 4: fixed_body<4, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
-    default: fixed_body<5, 1, FMT>(I, uin, uout, w.y, rel, sh); break;
+    case 2: fixed_body<2, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
+    case 3: fixed_body<3, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
+    case 4: fixed_body<4, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
+    default: fixed_body<5, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
   }
 }
 
@@ -258,16 +400,25 @@ template <int FMT, int EPT>
 __global__ void __launch_bounds__(kTile, EPT == 1 ? 6 : (EPT == 2 ? 4 : 2))
     k_batch_fixed_uniform(const BatchLite *__restrict__ items, int src, int dst, int rel,
                           const UniformFixed uf) {
-  __shared__ FixedShared<EPT> sh;
+  __shared__ FixedShared<EPT, 3> sh;
   const BatchLite L = items[blockIdx.x];
   const int2 w = make_int2(0, L.e0);
   const void *uin = src == 0 ? L.f[0] : (src == 1 ? L.f[1] : L.f[2]);
   void *uout = dst == 0 ? L.f[0] : (dst == 1 ? L.f[1] : L.f[2]);
-  switch (L.Np) {
-    case 2: fixed_body<2, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
-    case 3: fixed_body<3, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
-    case 4: fixed_body<4, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
-    default: fixed_body<5, EPT, FMT>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
+  if constexpr (EPT == 2) {
+    switch (L.Np) {
+      case 2: fixed_body_pair<2, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
+      case 3: fixed_body_pair<3, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
+      case 4: fixed_body_pair<4, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
+      default: fixed_body_pair<5, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
+    }
+  } else {
+    switch (L.Np) {
+      case 2: fixed_body<2, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
+      case 3: fixed_body<3, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
+      case 4: fixed_body<4, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
+      default: fixed_body<5, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
+    }
   }
 }
 
@@ -293,12 +444,18 @@ __global__ void k_fixed_to_fp64(const long long *__restrict__ X, double *__restr
     u[i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(X[i], sigma);
 }
 
+template <int NP, int FMT, int S>
+void fixed_np_fmt_s(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s) {
+  if (I.ept == 2)
+    k_step_fixed<NP, 2, FMT, S><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, uin, uout, rel);
+  else
+    k_step_fixed<NP, 1, FMT, S><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout, rel);
+}
+
 template <int NP, int FMT>
 void fixed_np_fmt(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s) {
-  if (I.ept == 2)
-    k_step_fixed<NP, 2, FMT><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, uin, uout, rel);
-  else
-    k_step_fixed<NP, 1, FMT><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout, rel);
+  if (I.ns == kMaxCS) fixed_np_fmt_s<NP, FMT, kMaxCS>(I, uin, uout, rel, s);
+  else fixed_np_fmt_s<NP, FMT, 3>(I, uin, uout, rel, s);
 }
 
 template <int NP>

@@ -39,46 +39,48 @@ struct StageConsts {
   double alpha, beta;
 };
 
-// The three stages of one SSP-RK3 step of upwind advection (a > 0) composed into one
-// stencil. With M_s = A_s + lL_s e_0^T and c_s = -lL_s (stage s of the folded form above,
-// all faces synchronous) and x^m_p the right trace of x on element m:
-//   v1 = M_0 u^e + c_0 P0,  v2 = alpha_1 u^e + M_1 v1 + c_1 P1,  u' = alpha_2 u^e + M_2 v2 + c_2 P2,
-// where P0 = u^{e-1}_p, P1 = v1^{e-1}_p, P2 = v2^{e-1}_p are the three channel scalars of
-// the left neighbour. Hence
-//   u'^e = G u^e + h_0 P0 + h_1 P1 + h_2 P2,   G = alpha_2 I + M_2 (alpha_1 I + M_1 M_0),
-//   h_0 = M_2 M_1 c_0,  h_1 = M_2 c_1,  h_2 = c_2,
+// The S stages (S = 3 for SSP-RK3, up to kMaxCS for the low-storage schemes) of one step of
+// upwind advection (a > 0) composed into one stencil. With Y_s the stage inputs (Y_0 = u^e;
+// for SSP-RK3 Y_1 = v1, Y_2 = v2 of the Shu-Osher stages) and P_s = Y_s^{e-1}_p the right
+// traces of the left neighbour's stage inputs (the channel scalars):
+//   u'^e = G u^e + sum_{s<S} h_s P_s,
 // and every element forms its own channel scalars from its neighbour's:
-//   v1^e_p = r1 . u^e + k_0 P0,  v2^e_p = r2 . u^e + k_1 P0 + k_2 P1,
-//   r1 = M_0^T e_p, r2 = (alpha_1 I + M_1 M_0)^T e_p, k_0 = c_0[p], k_1 = (M_1 c_0)[p],
-//   k_2 = c_1[p].
-// Cost: Np^2 + 5 Np + 3 multiply-adds per element and step.
+//   Y_s^e_p = r_s . u^e + sum_{t<s} k_{s,t} P_t   (s >= 1; Y_0^e_p = u^e_p).
+// For SSP-RK3 (M_s = A_s + lL_s e_0^T, c_s = -lL_s of the folded stage form above):
+//   G = alpha_2 I + M_2 (alpha_1 I + M_1 M_0), h_0 = M_2 M_1 c_0, h_1 = M_2 c_1, h_2 = c_2,
+//   r_1 = M_0^T e_p, r_2 = (alpha_1 I + M_1 M_0)^T e_p, k_10 = c_0[p], k_20 = (M_1 c_0)[p],
+//   k_21 = c_1[p];
+// for the other schemes from their Butcher form (k_s = W Y_s + w P_s, W = c2 a (D + M^-1
+// e_0 e_0^T), w = -c2 a M^-1 e_0). Cost: Np^2 + (2S - 1) Np + S(S-1)/2 multiply-adds per
+// element and step (39 at Np = 4, S = 3; 62 at S = 5).
 //
 // PE-face correction of the composed step (upwind advection is linear): at PE face j
 // (e = j Kpe) stage s replaces the synchronous face value by the delayed / AT one, which
 // adds lL_s d_s to stage s's output on element e and lR_s d_s on element e-1, with
 // d_s = T_s - V_s (T_s the stage-s input's right trace of element e-1, V_s the delayed / AT
 // value). The step's result is the synchronous composed step plus
-//   sum_s R_s d_s  on elements e-1 .. e+2  (R[s][m + 1], m = -1 .. 2),
+//   sum_s R_s d_s  on elements e-1 .. e+S-1  (R[s][m + 1], m = -1 .. S-1),
 // R_s the response of the remaining stages to that injection, and
-//   T_1 = q1^{e-1} + rho[0] d_0,  T_2 = q2^{e-1} + rho[1] d_0 + rho[2] d_1
-// (q1, q2 the synchronous channel scalars v1_p, v2_p of element e-1).
+//   T_s = Y_s^{e-1}_p + sum_{t<s} rho_{s,t} d_t
+// (Y_s^{e-1}_p the synchronous channel scalars of element e-1).
+constexpr int kMaxCS = 5;   // stages of a composed step
 struct StepConsts {
   double G[kMaxNp * kMaxNp];
-  double r1[kMaxNp], r2[kMaxNp];
-  double h[3][kMaxNp];
-  double k[3];
-  double R[3][4][kMaxNp];
-  double rho[3];
+  double r[kMaxCS][kMaxNp];        // r[s], s >= 1
+  double h[kMaxCS][kMaxNp];
+  double k[kMaxCS][kMaxCS];        // k[s][t], t < s
+  double R[kMaxCS][kMaxCS + 1][kMaxNp];
+  double rho[kMaxCS][kMaxCS];      // rho[s][t], t < s
 };
 
 // The StepConsts in fixed point for the integer composed step: each coefficient c
-// (|c| < 2) is C = round(c 2^58), split into balanced limbs C = ch 2^29 + cl with
+// (|c| < 2) is C = round(c 2^58), split into limbs C = ch 2^29 + cl with balanced
 // -2^28 <= cl < 2^28 (int2 {ch, cl}).
 struct StepFixed {
   int2 G[kMaxNp * kMaxNp];
-  int2 r1[kMaxNp], r2[kMaxNp];
-  int2 h[3][kMaxNp];
-  int2 k[3];
+  int2 r[kMaxCS][kMaxNp];
+  int2 h[kMaxCS][kMaxNp];
+  int2 k[kMaxCS][kMaxCS];
 };
 
 // Formats of a fixed-point composed step (launch_fused_step's fmt): bit 0 the input, bit 1
@@ -110,16 +112,17 @@ struct alignas(16) Inst {
                         // 2: fixed-point integer arithmetic (StepFixed)
   int ept;              // elements per thread of the composed-step kernel (1, 2 or 4, autotuned)
   FxSlot *fx;           // fused == 2: [3] scale of u^n in slot n % 3
-  double *fd;           // fused == 2 with PE faces: [2][P][3] stage differences d_s of each
+  double *fd;           // fused == 2 with PE faces: [2][P][ns] stage differences d_s of each
                         // face, buffer n & 1 for step n
   StageConsts sc[kStages];
   StepConsts st;
   StepFixed sf;
   // fused == 2: the PE-face responses st.R in fixed point (limbs as in StepFixed), used when
   // face_fx is set (every |R| < 2)
-  int2 Rf[kStages][4][kMaxNp];
+  int2 Rf[kMaxCS][kMaxCS + 1][kMaxNp];
   int face_fx;
-  int ns;               // stages per step: the ring holds [R][ns][P] stage-input traces
+  int ns;               // stages per step: the ring holds [R][ns][P] stage-input traces; the
+                        // composed steps' S (3, or 5 for the five-stage scheme)
   int ls;               // 1: a 2N low-storage scheme (k_lsrk_stage, coefficients lsA, lsB)
   int visc;             // 1: viscous Burgers by the local DG method (k_ldg_q, then the stage)
   double lsA[kMaxStages], lsB[kMaxStages];
@@ -141,7 +144,9 @@ struct alignas(16) Inst {
 };
 
 static_assert(sizeof(Inst) % 16 == 0, "Inst is copied to shared memory as int4");
-static_assert(sizeof(Inst) <= 4000, "Inst is passed by value as a kernel parameter");
+// Kernel parameters may take up to 32764 bytes (CUDA 12.1 and later); the batched kernels also
+// stage an Inst in shared memory.
+static_assert(sizeof(Inst) <= 8192, "Inst is passed by value as a kernel parameter");
 
 // Adjoint of one stage (adg_adjoint.cu): w is the adjoint of the stage output, v the stage
 // input (Burgers), lv receives the adjoint of the stage input (stages 1, 2); lacc collects

@@ -213,6 +213,122 @@ __device__ __forceinline__ void stage_body(const I &inst, int e, int64_t n = 0,
   }
 }
 
+// One SSP-RK3 stage with halo lanes: warp w takes elements 30w .. 30w+29 in lanes 1 .. 30,
+// and lanes 0 and 31 hold the elements on either side (periodic), so every face flux is formed
+// by one full-warp instruction sequence (lane l forms the flux of its left face; lane l-1
+// reads it as its right face) instead of an extra flux on the warp's last lane. At a PE face
+// the delayed / AT value is formed once, by the lane of the element right of the face (which,
+// owned, also writes the ring), and the element left of it reads the difference from the next
+// lane. Per element the arithmetic is that of stage_body, so the results are bit-identical to
+// it (the halo lanes' 2/32 redundant work replaces the single-lane flux and the second
+// evaluation of every PE-face value, which a warp's FP64 instruction pays in full whatever its
+// active lanes).
+template <int NP, int PDE, int STAGE, int DIR, bool FACES, class I>
+__device__ __forceinline__ void stage_body_halo(const I &inst, int warp, int64_t n) {
+  const int K = inst.K;
+  const int lane = threadIdx.x & 31;
+  const int e = 30 * warp + lane - 1;
+  const bool own = lane >= 1 && lane <= 30 && e < K;
+  // the element's periodic image (halo lanes at the ends wrap; lanes past the halo reuse 0)
+  const int ec = e < 0 ? e + K : (e < K ? e : (e == K ? 0 : 0));
+  const double *vin = STAGE == 0 ? inst.u : (STAGE == 1 ? inst.v1 : inst.v2);
+  double *vout = STAGE == 0 ? inst.v1 : (STAGE == 1 ? inst.v2 : inst.unext);
+  const StageConsts &C = inst.sc[STAGE];
+
+  double v[NP];
+  {
+    const double *q = vin + ec;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      v[i] = __ldg(q);
+      q += K;
+    }
+  }
+  double u[NP];   // the alpha operand u^n (owned lanes)
+  if (STAGE > 0) {
+    const double *q = inst.u + (own ? ec : 0);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      u[i] = own ? *q : 0.0;
+      q += K;
+    }
+  }
+  const unsigned full = 0xffffffffu;
+  const double vLm = __shfl_up_sync(full, v[NP - 1], 1);   // lanes >= 1
+  const double vRp = __shfl_down_sync(full, v[0], 1);      // lanes <= 30
+  double jL = 0.0, jR = 0.0;
+  if (PDE == 0) {
+    if (DIR > 0) jL = __dsub_rn(v[0], vLm);
+    else jR = __dsub_rn(v[NP - 1], vRp);
+  } else {
+    const double FL = num_flux<1>(0.0, vLm, v[0]);
+    const double FR = __shfl_down_sync(full, FL, 1);
+    jL = __dsub_rn(phys_flux<1>(0.0, v[0]), FL);
+    jR = __dsub_rn(phys_flux<1>(0.0, v[NP - 1]), FR);
+  }
+
+  double g[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) g[i] = PDE == 0 ? v[i] : v[i] * v[i];
+
+  double out[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    double acc;
+    if (PDE == 0) {
+      acc = STAGE == 0 ? C.A[i * NP] * g[0] : fma(C.A[i * NP], g[0], C.alpha * u[i]);
+    } else {
+      acc = STAGE == 0 ? v[i] : fma(C.beta, v[i], C.alpha * u[i]);
+      acc = fma(C.A[i * NP], g[0], acc);
+    }
+#pragma unroll
+    for (int jj = 1; jj < NP; ++jj) acc = fma(C.A[i * NP + jj], g[jj], acc);
+    out[i] = acc;
+  }
+  if (PDE == 1 || DIR > 0) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], jL, out[i]);
+  }
+  if (PDE == 1 || DIR < 0) {
+#pragma unroll
+    for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], jR, out[i]);
+  }
+  if (FACES) {
+    // lane l (1 .. 31) forms the PE-face difference of its left face when its element owns
+    // one (e = j Kpe, or e = K: face 0 seen from element K-1); owned lanes write the ring
+    const int Kpe = inst.Kpe;
+    const int eo = e < K ? e : e - K;
+    const int jq = eo / Kpe;
+    const bool face = lane >= 1 && e <= K && eo - jq * Kpe == 0;
+    double d = 0.0;
+    if (face) d = pe_face_delta<PDE, DIR>(inst, jq, n, STAGE, vLm, v[0], own);
+    const double dR = __shfl_down_sync(full, d, 1);
+    const bool faceR = __shfl_down_sync(full, face ? 1 : 0, 1) != 0;
+    if (own && face && nonzero(d)) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) out[i] = fma(C.lL[i], d, out[i]);
+    }
+    if (own && faceR && nonzero(dR)) {
+#pragma unroll
+      for (int i = 0; i < NP; ++i) out[i] = fma(C.lR[i], dR, out[i]);
+    }
+  }
+  if (own) {
+    double *q = vout + e;
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      *q = out[i];
+      q += K;
+    }
+  }
+}
+
+template <int NP, int PDE, int STAGE, int DIR, bool FACES>
+__global__ void __launch_bounds__(kTile) k_stage_halo(const Inst inst, int rel) {
+  const int64_t n = FACES ? inst.meta[0] + rel : 0;
+  stage_body_halo<NP, PDE, STAGE, DIR, FACES>(inst, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, n);
+}
+
 template <int NP, int PDE, int STAGE, int DIR, bool FACES, bool VISC = false>
 __global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
   const int64_t n = FACES ? inst.meta[0] + rel : 0;
@@ -303,12 +419,12 @@ template <int NP>
 __device__ __forceinline__ void own_scalars(const StepConsts &S, const double *u, double &sp,
                                             double &s1, double &s2) {
   sp = u[NP - 1];
-  s1 = S.r1[0] * u[0];
-  s2 = S.r2[0] * u[0];
+  s1 = S.r[1][0] * u[0];
+  s2 = S.r[2][0] * u[0];
 #pragma unroll
   for (int j = 1; j < NP; ++j) {
-    s1 = fma(S.r1[j], u[j], s1);
-    s2 = fma(S.r2[j], u[j], s2);
+    s1 = fma(S.r[1][j], u[j], s1);
+    s2 = fma(S.r[2][j], u[j], s2);
   }
 }
 
@@ -351,19 +467,19 @@ __device__ __forceinline__ void fused_body(const I &inst, const double *__restri
   }
   __syncthreads();
   // v1_p = r1 . u + k_0 P0 (the halo's first element needs none)
-  if (t == 1 || t == 2) sh.q1[t] = fma(S.k[0], sh.p[t - 1], hs1);
+  if (t == 1 || t == 2) sh.q1[t] = fma(S.k[1][0], sh.p[t - 1], hs1);
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
     const int sl = t + h * kTile + 3;
-    sh.q1[sl] = fma(S.k[0], sh.p[sl - 1], s1[h]);
+    sh.q1[sl] = fma(S.k[1][0], sh.p[sl - 1], s1[h]);
   }
   __syncthreads();
   // v2_p = r2 . u + k_1 P0 + k_2 P1 (of the halo, only the element just before the block)
-  if (t == 2) sh.q2[2] = fma(S.k[2], sh.q1[1], fma(S.k[1], sh.p[1], hs2));
+  if (t == 2) sh.q2[2] = fma(S.k[2][1], sh.q1[1], fma(S.k[2][0], sh.p[1], hs2));
 #pragma unroll
   for (int h = 0; h < EPT; ++h) {
     const int sl = t + h * kTile + 3;
-    sh.q2[sl] = fma(S.k[2], sh.q1[sl - 1], fma(S.k[1], sh.p[sl - 1], s2[h]));
+    sh.q2[sl] = fma(S.k[2][1], sh.q1[sl - 1], fma(S.k[2][0], sh.p[sl - 1], s2[h]));
   }
   __syncthreads();
 #pragma unroll
@@ -395,9 +511,10 @@ __global__ void __launch_bounds__(kTile) k_step_fused(const Inst inst, const dou
 
 // What the PE-face correction of face j at step n reads besides the field: its delay k and
 // order q' (delay_at), the AT coefficients, and the upwind traces of levels n-k-i (i < q')
-// for the three stages from the ring [slot][stage][P] (zero when k = 0).
+// for the S stages from the ring [slot][stage][P] (zero when k = 0).
+template <int S>
 struct FaceLoads {
-  double Rv[kStages][kMaxQ];
+  double Rv[S][kMaxQ];
   double c[kMaxQ];
   int k, qe, nm;   // nm: the ring slot of step n
 };
@@ -407,7 +524,8 @@ __device__ __forceinline__ int mod_step(int64_t n, int m) {
   return n <= 0x7fffffff ? (int)((unsigned)n % (unsigned)m) : (int)(n % m);
 }
 
-__device__ __forceinline__ void face_loads(const Inst &I, int j, int64_t n, FaceLoads &f) {
+template <int S>
+__device__ __forceinline__ void face_loads(const Inst &I, int j, int64_t n, FaceLoads<S> &f) {
   const DelayAt dl = delay_at(I, j, n);
   const int P = I.P, R = I.R;
   const int nm = mod_step(n, R);
@@ -421,90 +539,111 @@ __device__ __forceinline__ void face_loads(const Inst &I, int j, int64_t n, Face
     if (sl < 0) sl += R;
     const bool use = dl.k > 0 && i < dl.qe;
     f.c[i] = i < dl.qe ? dl.c[i] : 0.0;
-    const double2 *lv = col + (size_t)sl * (kStages * P);
+    const double2 *lv = col + (size_t)sl * (S * P);
 #pragma unroll
-    for (int st = 0; st < kStages; ++st) f.Rv[st][i] = use ? lv[st * P].x : 0.0;
+    for (int st = 0; st < S; ++st) f.Rv[st][i] = use ? lv[st * P].x : 0.0;
   }
 }
 
 // The synchronous traces of element e-1's stage inputs at a PE face (e the face's element):
-// T0 = p^{e-1}, the right trace of u^{e-1}, and the channel scalars
-// b1 = q1^{e-1} = r1 . u^{e-1} + k0 p^{e-2}, b2 = q2^{e-1} = r2 . u^{e-1} + k1 p^{e-2} + k2 q1^{e-2}
-// with q1^{e-2} = r1 . u^{e-2} + k0 p^{e-3}, from elements e-3 .. e-1 (w = 0 .. 2).
+// T[0] = p^{e-1}, the right trace of u^{e-1}, and the channel scalars T[s] = Y_s^{e-1}_p =
+// r_s . u^{e-1} + sum_{t<s} k_st Y_t^{e-2}_p, from elements e-S .. e-1 (w = 0 .. S-1).
+template <int S>
 struct FaceTraces {
-  double T0, b1, b2;
+  double T[S];
 };
 
-// From FP64 values.
-template <int NP>
-__device__ __forceinline__ FaceTraces face_traces(const Inst &I, const double (*U)[NP]) {
-  const StepConsts &S = I.st;
-  double a1 = S.k[0] * U[0][NP - 1], b1 = S.k[0] * U[1][NP - 1], b2 = S.k[1] * U[1][NP - 1];
+// The channel scalars Y_s^m_p of elements m = e-S+1 .. e-1 in FP64, from the elements
+// e-S .. e-1 (U[w], w = 0 .. S-1): element e-S+w forms Y_1 .. Y_w from its values and the
+// scalars of the element before it.
+template <int NP, int S>
+__device__ __forceinline__ FaceTraces<S> face_traces(const Inst &I, const double (*U)[NP]) {
+  const StepConsts &C = I.st;
+  double Yp[S];   // the channel scalars of the element one to the left (Yp[0] = its trace)
+  Yp[0] = U[0][NP - 1];
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    a1 = fma(S.r1[i], U[1][i], a1);
-    b1 = fma(S.r1[i], U[2][i], b1);
-    b2 = fma(S.r2[i], U[2][i], b2);
+  for (int w = 1; w < S; ++w) {
+    const int ns = w;   // channels 1 .. w of element e-S+w
+    double Y[S];
+    Y[0] = U[w][NP - 1];
+#pragma unroll
+    for (int s = 1; s <= ns; ++s) {
+      double a = C.r[s][0] * U[w][0];
+#pragma unroll
+      for (int i = 1; i < NP; ++i) a = fma(C.r[s][i], U[w][i], a);
+#pragma unroll
+      for (int t = 0; t < s; ++t) a = fma(C.k[s][t], Yp[t], a);
+      Y[s] = a;
+    }
+#pragma unroll
+    for (int s = 0; s <= ns; ++s) Yp[s] = Y[s];
   }
-  FaceTraces t;
-  t.T0 = U[2][NP - 1];
-  t.b1 = b1;
-  t.b2 = fma(S.k[2], a1, b2);
+  FaceTraces<S> t;
+#pragma unroll
+  for (int s = 0; s < S; ++s) t.T[s] = Yp[s];
   return t;
 }
 
 // From int64 values X at scale 2^sig: the same sums in the composed step's two-limb integer
-// arithmetic (StepFixed coefficients) at a scale chosen from these three elements alone
+// arithmetic (StepFixed coefficients) at a scale chosen from these S elements alone
 // (|X'| < 2^56, so the result does not depend on any other face), then rounded to FP64. Off
-// the FP64 pipe but for four conversions.
-template <int NP>
-__device__ __forceinline__ FaceTraces face_traces_fixed(const Inst &I, const long long (*X)[NP],
-                                                        int sig) {
+// the FP64 pipe but for S conversions.
+template <int NP, int S>
+__device__ __forceinline__ FaceTraces<S> face_traces_fixed(const Inst &I, const long long (*X)[NP],
+                                                           int sig) {
   const StepFixed &F = I.sf;
   unsigned long long m = 0;
 #pragma unroll
-  for (int w = 0; w < 3; ++w)
+  for (int w = 0; w < S; ++w)
 #pragma unroll
     for (int i = 0; i < NP; ++i) m |= fx_mag(X[w][i]);
   const int L = m ? 64 - __clzll((long long)m) : 0;   // |X| < 2^(L+1)
   const int sh = L > 55 ? L - 55 : 0;
-  int xh[3][NP], xl[3][NP];
+  long long Yp[S];
+  Yp[0] = fx_rescale(X[0][NP - 1], sh);
 #pragma unroll
-  for (int w = 0; w < 3; ++w)
+  for (int w = 1; w < S; ++w) {
+    const int ns = w;   // channels 1 .. w of element e-S+w
+    int xh[NP], xl[NP];
 #pragma unroll
-    for (int i = 0; i < NP; ++i) fx_split(fx_rescale(X[w][i], sh), xh[w][i], xl[w][i]);
-  FxAcc A1, B1, B2;
-  fx_mac(A1, F.k[0], xh[0][NP - 1], xl[0][NP - 1]);
-  fx_mac(B1, F.k[0], xh[1][NP - 1], xl[1][NP - 1]);
-  fx_mac(B2, F.k[1], xh[1][NP - 1], xl[1][NP - 1]);
+    for (int i = 0; i < NP; ++i) fx_split(fx_rescale(X[w][i], sh), xh[i], xl[i]);
+    int ph[S], pl[S];
 #pragma unroll
-  for (int i = 0; i < NP; ++i) {
-    fx_mac(A1, F.r1[i], xh[1][i], xl[1][i]);
-    fx_mac(B1, F.r1[i], xh[2][i], xl[2][i]);
-    fx_mac(B2, F.r2[i], xh[2][i], xl[2][i]);
+    for (int t = 0; t < S - 1; ++t)
+      if (t < ns) fx_split(Yp[t], ph[t], pl[t]);
+    long long Y[S];
+    Y[0] = fx_rescale(X[w][NP - 1], sh);
+#pragma unroll
+    for (int s = 1; s <= ns; ++s) {
+      FxAcc acc;
+#pragma unroll
+      for (int i = 0; i < NP; ++i) fx_mac(acc, F.r[s][i], xh[i], xl[i]);
+#pragma unroll
+      for (int t = 0; t < s; ++t) fx_mac(acc, F.k[s][t], ph[t], pl[t]);
+      Y[s] = fx_round(acc);
+    }
+#pragma unroll
+    for (int s = 0; s <= ns; ++s) Yp[s] = Y[s];
   }
-  int ah, al;
-  fx_split(fx_round(A1), ah, al);
-  fx_mac(B2, F.k[2], ah, al);
-  FaceTraces t;
-  t.T0 = pow2_scale((double)X[2][NP - 1], sig);
-  t.b1 = pow2_scale((double)fx_round(B1), sig + sh);
-  t.b2 = pow2_scale((double)fx_round(B2), sig + sh);
+  FaceTraces<S> t;
+  t.T[0] = pow2_scale((double)X[S - 1][NP - 1], sig);
+#pragma unroll
+  for (int s = 1; s < S; ++s) t.T[s] = pow2_scale((double)Yp[s], sig + sh);
   return t;
 }
 
 // The stage differences d_s = T_s - V_s at PE face j, step n, from the synchronous traces and
 // the face's loads, and the ring write of T_s (the PE-face correction below).
-__device__ __forceinline__ void face_diffs(const Inst &I, int j, const FaceLoads &f,
-                                           const FaceTraces &tr, double &d0, double &d1,
-                                           double &d2) {
+template <int S>
+__device__ __forceinline__ void face_diffs(const Inst &I, int j, const FaceLoads<S> &f,
+                                           const FaceTraces<S> &tr, double *d) {
   const int P = I.P;
-  const StepConsts &S = I.st;
+  const StepConsts &C = I.st;
   double2 *col = I.ring + j;
   const int k = f.k, qe = f.qe;
-  double V[kStages];
+  double V[S];
 #pragma unroll
-  for (int st = 0; st < kStages; ++st) {
+  for (int st = 0; st < S; ++st) {
     double v = __dmul_rn(f.c[0], f.Rv[st][0]);
 #pragma unroll
     for (int i = 1; i < kMaxQ; ++i) {
@@ -517,21 +656,20 @@ __device__ __forceinline__ void face_diffs(const Inst &I, int j, const FaceLoads
   }
   // T_s: the traces plus the responses to the earlier stages' corrections; with zero delay
   // V_s = T_s (the current traces), so d_s = 0
-  const double T0 = tr.T0;
-  d0 = k > 0 ? __dsub_rn(T0, V[0]) : 0.0;
-  const double T1 = fma(S.rho[0], d0, tr.b1);
-  d1 = k > 0 ? __dsub_rn(T1, V[1]) : 0.0;
-  const double T2 = fma(S.rho[2], d1, fma(S.rho[1], d0, tr.b2));
-  d2 = k > 0 ? __dsub_rn(T2, V[2]) : 0.0;
-  double2 *lv = col + (size_t)f.nm * (kStages * P);
-  lv[0] = make_double2(T0, 0.0);
-  lv[P] = make_double2(T1, 0.0);
-  lv[2 * P] = make_double2(T2, 0.0);
+  double2 *lv = col + (size_t)f.nm * (S * P);
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    double T = tr.T[s];
+#pragma unroll
+    for (int t = 0; t < s; ++t) T = fma(C.rho[s][t], d[t], T);
+    d[s] = k > 0 ? __dsub_rn(T, V[s]) : 0.0;
+    lv[s * P] = make_double2(T, 0.0);
+  }
 }
 
-// PE-face correction of a composed step (upwind advection, a > 0; StepConsts): thread j
-// forms, for PE face j (e = j Kpe), the synchronous right traces of element e-1's stage
-// inputs (p, q1 = v1_p, q2 = v2_p, from elements e-3 .. e-1 with the composed step's
+// PE-face correction of a three-stage composed step (upwind advection, a > 0; StepConsts):
+// thread j forms, for PE face j (e = j Kpe), the synchronous right traces of element e-1's
+// stage inputs (p, q1 = v1_p, q2 = v2_p, from elements e-3 .. e-1 with the composed step's
 // coefficients), then stage by stage T_s (those traces plus the responses to the earlier
 // corrections), the delayed / AT value V_s (Eq. at-flux-gen over the upwind traces of levels
 // n-k-i in the ring; the face's delay k is one per step, so V_s does not depend on T), and
@@ -596,21 +734,22 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       }
     }
   }
-  FaceLoads fl;
-  face_loads(I, j, n, fl);
-  FaceTraces tr;
+  FaceLoads<3> fl;
+  face_loads<3>(I, j, n, fl);
+  FaceTraces<3> tr;
   if (fin) {
-    tr = face_traces_fixed<NP>(I, Xr, sig_in);
+    tr = face_traces_fixed<NP, 3>(I, Xr, sig_in);
   } else {
     double U[3][NP];
 #pragma unroll
     for (int w = 0; w < 3; ++w)
 #pragma unroll
       for (int i = 0; i < NP; ++i) U[w][i] = __longlong_as_double(Xr[w][i]);
-    tr = face_traces<NP>(I, U);
+    tr = face_traces<NP, 3>(I, U);
   }
-  double d0, d1, d2;
-  face_diffs(I, j, fl, tr, d0, d1, d2);
+  double dd[3];
+  face_diffs<3>(I, j, fl, tr, dd);
+  const double d0 = dd[0], d1 = dd[1], d2 = dd[2];
   // with a NaN or infinity in u^n the fixed-point step has already written NaN (or carries
   // the mark); nothing is added
   if (!(nonzero(d0) || nonzero(d1) || nonzero(d2)) || sc.bad) return;
@@ -677,21 +816,22 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
 }
 
 // PE-face work of the fixed-point step between two steps, on the field u that is the output
-// of step n-1 and the input of step n (n = meta[0] + rel), for PE face j (e = j Kpe). A block
-// of 128 threads takes 32 faces, warp w element e-1+w of their correction windows (so the
-// FP64 work of the differences runs in full warps):
+// of step n-1 and the input of step n (n = meta[0] + rel), for PE face j (e = j Kpe), with S
+// the composed step's stages. A block of (S+1) warps takes 32 faces, warp w element e-1+w of
+// their correction windows (so the FP64 work of the differences runs in full warps):
 //   kFaceApply: adds step n-1's correction sum_s R_s[w] d_s (its differences in I.fd, buffer
 //               (n-1) & 1) to element e-1+w of u at step n-1's working scale, with the scale
 //               bookkeeping of the values written (slot n % 3);
-//   kFaceDiff:  warp 0 then forms step n's differences d_s from elements e-3 .. e-1 of u
+//   kFaceDiff:  warp 0 then forms step n's differences d_s from elements e-S .. e-1 of u
 //               (e-1 as corrected) and the ring (face_diffs), writes the ring slot of step n
 //               and I.fd buffer n & 1.
 // fu: u is int64 (at the scale of slot n % 3), else FP64; fin_prev: step n-1 read int64. Every
-// load is issued before any value is used; the windows of different faces are disjoint when
-// Kpe >= 8.
-template <int NP>
-__global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restrict__ u, int rel,
-                                                   int fu, int fin_prev, int mode) {
+// load is issued before any value is used; the windows of different faces (e-S .. e+S-1) are
+// disjoint when Kpe >= 2S.
+template <int NP, int S>
+__global__ void __launch_bounds__(32 * (S + 1)) k_face_step(const Inst I, void *__restrict__ u,
+                                                          int rel, int fu, int fin_prev,
+                                                          int mode) {
   const int j = blockIdx.x * 32 + (threadIdx.x & 31), w = threadIdx.x >> 5;
   if (j >= I.P) return;
   const int K = I.K, P = I.P;
@@ -699,22 +839,22 @@ __global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restric
   const int64_t n = I.meta[0] + rel;
   const bool diff = (mode & kFaceDiff) && w == 0;
   long long *uq = static_cast<long long *>(u);
-  int m = e - 1 + w;   // this thread's element; warp 0 also reads e-3 and e-2
+  int m = e - 1 + w;   // this thread's element; warp 0 also reads e-S .. e-2
   if (m < 0) m += K;
   if (m >= K) m -= K;
-  long long V[3][NP];   // raw 64-bit values (int64, or the bits of FP64): e-3, e-2, own
+  long long V[S][NP];   // raw 64-bit values (int64, or the bits of FP64): e-S .. e-2, own
   {
     const long long *q = uq + m;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      V[2][i] = *q;
+      V[S - 1][i] = *q;
       q += K;
     }
   }
   if (diff) {
 #pragma unroll
-    for (int b = 0; b < 2; ++b) {
-      int mb = e - 3 + b;
+    for (int b = 0; b < S - 1; ++b) {
+      int mb = e - S + b;
       if (mb < 0) mb += K;
       const long long *q = uq + mb;
 #pragma unroll
@@ -724,43 +864,55 @@ __global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restric
       }
     }
   }
-  FaceLoads fl;
-  if (diff) face_loads(I, j, n, fl);
+  FaceLoads<S> fl;
+  if (diff) face_loads<S>(I, j, n, fl);
   if (mode & kFaceApply) {
-    const double *dd = I.fd + (size_t)((n - 1) & 1) * 3 * P + 3 * (size_t)j;
-    const double d0 = dd[0], d1 = dd[1], d2 = dd[2];
+    const double *dd = I.fd + (size_t)((n - 1) & 1) * S * P + S * (size_t)j;
+    double d[S];
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      d[s] = dd[s];
+      any = any || nonzero(d[s]);
+    }
     const FxScale sc = fx_scale(I.fx, n - 1, fin_prev != 0);
-    if ((nonzero(d0) || nonzero(d1) || nonzero(d2)) && !sc.bad) {
+    if (any && !sc.bad) {
       bool done = false;
       if (fu && I.face_fx) {
         // D_s = round(d_s 2^-sigma) and sum_s R_s D_s in the step's two-limb arithmetic
         const double sf = pow2_scale(1.0, -sc.sigma);
-        const long long D0 = llrint(d0 * sf), D1 = llrint(d1 * sf), D2 = llrint(d2 * sf);
         const long long lim = 1ll << 57;
-        if (D0 > -lim && D0 < lim && D1 > -lim && D1 < lim && D2 > -lim && D2 < lim) {
-          int h0, l0, h1, l1, h2, l2;
-          fx_split(D0, h0, l0);
-          fx_split(D1, h1, l1);
-          fx_split(D2, h2, l2);
+        long long D[S];
+        bool inr = true;
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+          D[s] = llrint(d[s] * sf);
+          inr = inr && D[s] > -lim && D[s] < lim;
+        }
+        if (inr) {
+          int hh[S], ll[S];
+#pragma unroll
+          for (int s = 0; s < S; ++s) fx_split(D[s], hh[s], ll[s]);
 #pragma unroll
           for (int i = 0; i < NP; ++i) {
             FxAcc acc;
-            fx_mac(acc, I.Rf[0][w][i], h0, l0);
-            fx_mac(acc, I.Rf[1][w][i], h1, l1);
-            fx_mac(acc, I.Rf[2][w][i], h2, l2);
-            V[2][i] += fx_round(acc);
+#pragma unroll
+            for (int s = 0; s < S; ++s) fx_mac(acc, I.Rf[s][w][i], hh[s], ll[s]);
+            V[S - 1][i] += fx_round(acc);
           }
           done = true;
         }
       }
       if (!done) {
         // FP64: an FP64 output, or a difference beyond the integer range
-        const StepConsts &S = I.st;
+        const StepConsts &C = I.st;
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-          const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
-          if (fu) V[2][i] += llrint(pow2_scale(c, -sc.sigma));
-          else V[2][i] = __double_as_longlong(__dadd_rn(__longlong_as_double(V[2][i]), c));
+          double c = C.R[0][w][i] * d[0];
+#pragma unroll
+          for (int s = 1; s < S; ++s) c = fma(C.R[s][w][i], d[s], c);
+          if (fu) V[S - 1][i] += llrint(pow2_scale(c, -sc.sigma));
+          else V[S - 1][i] = __double_as_longlong(__dadd_rn(__longlong_as_double(V[S - 1][i]), c));
         }
       }
       int emax = 0;
@@ -768,7 +920,7 @@ __global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restric
       long long *q = uq + m;
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        const long long X = V[2][i];
+        const long long X = V[S - 1][i];
         *q = X;
         q += K;
         if (fu) {
@@ -784,23 +936,22 @@ __global__ void __launch_bounds__(128) k_face_step(const Inst I, void *__restric
     }
   }
   if (diff) {
-    FaceTraces tr;
+    FaceTraces<S> tr;
     if (fu) {
-      tr = face_traces_fixed<NP>(I, V, I.fx[(int)(n % 3)].sigma);
+      tr = face_traces_fixed<NP, S>(I, V, I.fx[(int)(n % 3)].sigma);
     } else {
-      double U[3][NP];
+      double U[S][NP];
 #pragma unroll
-      for (int b = 0; b < 3; ++b)
+      for (int b = 0; b < S; ++b)
 #pragma unroll
         for (int i = 0; i < NP; ++i) U[b][i] = __longlong_as_double(V[b][i]);
-      tr = face_traces<NP>(I, U);
+      tr = face_traces<NP, S>(I, U);
     }
-    double d0, d1, d2;
-    face_diffs(I, j, fl, tr, d0, d1, d2);
-    double *o = I.fd + (size_t)(n & 1) * 3 * P + 3 * (size_t)j;
-    o[0] = d0;
-    o[1] = d1;
-    o[2] = d2;
+    double d[S];
+    face_diffs<S>(I, j, fl, tr, d);
+    double *o = I.fd + (size_t)(n & 1) * S * P + S * (size_t)j;
+#pragma unroll
+    for (int s = 0; s < S; ++s) o[s] = d[s];
   }
 }
 
@@ -1084,10 +1235,13 @@ cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
   if (PDE == 1 && I.visc) {
     if (I.async) k_stage<NP, PDE, STAGE, DIR, true, true><<<grid, bs, 0, s>>>(I, rel);
     else k_stage<NP, PDE, STAGE, DIR, false, true><<<grid, bs, 0, s>>>(I, rel);
-  } else if (I.async) {
-    k_stage<NP, PDE, STAGE, DIR, true><<<grid, bs, 0, s>>>(I, rel);
   } else {
-    k_stage<NP, PDE, STAGE, DIR, false><<<grid, bs, 0, s>>>(I, rel);
+    // 30 elements per warp (halo lanes); one-thread-per-element stage_body is kept for the
+    // 2N low-storage, viscous and batched stages
+    const int64_t warps = (I.K + 29) / 30;
+    const unsigned g = (unsigned)((warps * 32 + bs - 1) / bs);
+    if (I.async) k_stage_halo<NP, PDE, STAGE, DIR, true><<<g, bs, 0, s>>>(I, rel);
+    else k_stage_halo<NP, PDE, STAGE, DIR, false><<<g, bs, 0, s>>>(I, rel);
   }
   return cudaGetLastError();
 }
@@ -1226,13 +1380,25 @@ cudaError_t fused_np(const Inst &I, const void *uin, void *uout, int rel, cudaSt
 
 cudaError_t launch_face_step(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
                              cudaStream_t s) {
-  const unsigned g = (unsigned)((I.P + 31) / 32);   // 32 faces per block of four warps
-  switch (I.Np) {
-    case 2: k_face_step<2><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-    case 3: k_face_step<3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-    case 4: k_face_step<4><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-    case 5: k_face_step<5><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-    default: return cudaErrorInvalidValue;
+  const unsigned g = (unsigned)((I.P + 31) / 32);   // 32 faces per block of S + 1 warps
+  if (I.ns == 3) {
+    switch (I.Np) {
+      case 2: k_face_step<2, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      case 3: k_face_step<3, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      case 4: k_face_step<4, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      case 5: k_face_step<5, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else if (I.ns == kMaxCS) {
+    switch (I.Np) {
+      case 2: k_face_step<2, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      case 3: k_face_step<3, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      case 4: k_face_step<4, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      case 5: k_face_step<5, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
+      default: return cudaErrorInvalidValue;
+    }
+  } else {
+    return cudaErrorInvalidValue;
   }
   return cudaGetLastError();
 }
