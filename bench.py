@@ -36,8 +36,8 @@ STAGES = 3
 # The large advection workload; its Courant number is not fixed by the workload statement
 # and is set inside the stability bound of the delayed self-feedback (sigma (p+1)^2 k < 1
 # for k <= 7 with the AT extrapolation); the work per step does not depend on it.
-from workloads import (ADJOINT_64K as _WADJ, ADVECTION_16M as _W16M, BURGERS_1M,  # noqa: E402
-                       batched_instances)
+from workloads import (ADJOINT_64K as _WADJ, ADVECTION_16M as _W16M, ADVECTION_SMALL,  # noqa: E402
+                       BURGERS_1M, batched_instances)
 
 WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P, L=_W16M.L,
                 q=_W16M.q, cfl=_W16M.cfl, seed=_W16M.seed,
@@ -53,10 +53,10 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
 #  - staged FP64 kernels: 2 (Np + 2) flop per DOF-stage.
 NP = WORKLOAD["p"] + 1
 MACS_PER_ELEMENT_STEP = NP * NP + 5 * NP + 3
-# fixed point: each multiply-add of the kernel is one 32 x 32 -> 64-bit multiply-add and two
-# high-word multiply-adds (adg_fixed.cuh); the kernel forms Np^2 + 5 Np + 4 of them per element
-# (one more for the left neighbour's v1_p^{e-2})
-FIXED_MACS_PER_ELEMENT_STEP = MACS_PER_ELEMENT_STEP + 1
+# fixed point: each multiply-add of the kernel is three 32 x 32 -> 64-bit products
+# (adg_fixed.cuh); with two elements per thread the kernel forms Np^2 + 5 Np + 3.5 of them per
+# element (the neighbour's channel scalars: 7 per pair instead of 8)
+FIXED_MACS_PER_ELEMENT_STEP = MACS_PER_ELEMENT_STEP + 0.5
 FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # A 2N low-storage stage: dt L(U) + A_s dU (one multiply and NP + 1 FMA per DOF) and
@@ -68,9 +68,11 @@ LOW_STORAGE_STAGES = {"rk1": 1, "rk2": 2, "lsrk3": 3, "lsrk4": 5}
 VISC_NP = 3
 FLOP_PER_DOF_STAGE_VISC = 6 * VISC_NP + 17
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
-# dominates the step, keyed by variant; a kernel changed since its counters were taken has no
-# entry (null in the line).
-TRAFFIC_BYTES_PER_LAUNCH = {}
+# dominates the step, keyed by variant and elements per thread; a kernel changed since its
+# counters were taken has no entry (null in the line). k_step_fixed, two per thread, int64 ->
+# int64, K = 2^24: 537,010,176 B read + 488,685,824 B written (the algorithmic 536,870,912 B
+# each way; part of the written field is still in L2 when the launch ends).
+TRAFFIC_BYTES_PER_LAUNCH = {"fixed/2": 537010176 + 488685824}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 # The staged SSP-RK3 step reads and writes 16 / 24 / 24 B per DOF in its three stages (the
@@ -81,12 +83,6 @@ BYTES_PER_DOF_STEP_STAGED = 64
 # two lifts and the alpha / beta combination: 2 (Np + 4) + 1 flop per DOF-stage.
 FLOP_PER_DOF_STAGE_BURGERS = 2 * (5 + 4) + 1
 GRAPH_STEPS = 32
-
-
-# Issue rates of the heavy integer pipe measured on this part (lanes per clock per SM, all
-# SMs, independent chains): 32 x 32 -> 64-bit multiply-add 33.9, mad.hi.s32 42.3.
-WIDE_PER_CLK_SM = 33.9
-HI_PER_CLK_SM = 42.3
 
 
 def sm_count() -> int:
@@ -459,7 +455,7 @@ def batched_timed(steps: int, warmup: int):
     ev1.synchronize()
     ms = ev0.elapsed_time(ev1)
     b.check_finite()
-    variant = b.variant(0)[0]
+    variant = "%s, %d element(s) per thread" % b.variant(0)
     b.close()
     return ndof * STAGES * steps / (ms * 1e-3), ms / steps, ndof, len(ws), variant
 
@@ -541,6 +537,116 @@ def oracle_timed(window: int, steps: int, warmup: int = 1, threads: int = 0):
     return rate, el / steps * 1e3, used, sample
 
 
+def small_timed(mode: str) -> dict:
+    """The small advection workload (K = 64, p = 2, 16 PEs, delays uniform in {0..3}, sigma =
+    0.1, t_end = 2 pi: 640 steps) on the GPU: CUDA-event time of the whole run after one
+    untimed run. Latency-bound (192 DOF): a measure of per-step overhead, not of throughput."""
+    import torch
+    import paper_2404_03399_gb300 as adg
+    w = ADVECTION_SMALL
+    cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode=mode, L=w.L,
+                     q=w.q if mode == "at" else 0, seed=w.seed)
+    m = w.modes
+    u0 = adg.eval_modes(cfg, m.amp, m.kappa, m.phase, m.offset)
+    stream = torch.cuda.current_stream()
+    for rep in range(2):
+        s = adg.Solver(cfg, u0)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        s.run(w.t_end)
+        ev1.record(stream)
+        ev1.synchronize()
+        ms = ev0.elapsed_time(ev1)
+        s.state()
+        n = s.n
+        variant = s.variant[0]
+        s.close()
+    ndof = w.K * (w.p + 1)
+    return {"value": ndof * STAGES * n / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / n,
+            "steps": n, "variant": variant}
+
+
+def oracle_configs() -> dict:
+    """The oracle on samples of every workload, with all of torch's CPU threads and with one:
+    the small advection workload (all 640 steps, ADG-AT3), the Burgers workload (2 steps on a
+    2^18-element window), the batched workload (2 steps of its first 8 instances), and the
+    adjoint workload's gradient / forward cost (10 steps of the oracle's automatic-
+    differentiation adjoint on the full K = 65536 mesh)."""
+    import numpy as np
+    import torch
+    from oracle import dg, delays
+    out = {}
+
+    def rate_of(fn, units):
+        t0 = time.perf_counter()
+        fn()
+        return units / (time.perf_counter() - t0)
+
+    def both(fn, units):
+        old = torch.get_num_threads()
+        r_all = rate_of(fn, units)
+        torch.set_num_threads(1)
+        try:
+            r_one = rate_of(fn, units)
+        finally:
+            torch.set_num_threads(old)
+        return {"all_threads": r_all, "one_thread": r_one, "threads": old}
+
+    w = ADVECTION_SMALL
+    dx = 2 * math.pi / w.K
+    nsmall = math.ceil(w.t_end / (w.cfl * dx))
+    tbl = delays.delay_table(w.seed, w.P, nsmall, w.L)
+    prob = dg.Problem(pde="advection", K=w.K, p=w.p, P=w.P, dt=w.t_end / nsmall, mode="adg",
+                      q=w.q, delays=tbl)
+    u0 = dg.modes_initial(w.modes, w.K, w.p)
+    out["advection_small"] = both(lambda: dg.run(prob, u0, nsmall),
+                                  w.K * (w.p + 1) * STAGES * nsmall)
+    out["advection_small"]["sample"] = f"all {nsmall} steps"
+
+    b = BURGERS_1M
+    win = 1 << 18
+    dxb = 2 * math.pi / b.K
+    x = dg.node_coordinates(win, b.p, 0.0, 2 * math.pi, 0, b.K)
+    ub = b.modes.offset + np.sin(x)
+    tblb = delays.delay_table(b.seed, b.P, 4, b.L)
+    probb = dg.Problem(pde="burgers", K=win, p=b.p, P=b.P, dt=0.005 * dxb / 1.5, mode="adg",
+                       q=b.q, delays=tblb, window_lo=0, K_global=b.K)
+    out["burgers_1m"] = both(lambda: dg.run(probb, ub, 2), win * (b.p + 1) * STAGES * 2)
+    out["burgers_1m"]["sample"] = "2 steps on a 2^18-element window"
+
+    ws = batched_instances()[:8]
+    runs = []
+    for wi in ws:
+        dxi = 2 * math.pi / wi.K
+        tb = delays.delay_table(wi.seed, wi.P, 4, wi.L)
+        pr = dg.Problem(pde="advection", K=wi.K, p=wi.p, P=wi.P, a=wi.a, dt=wi.cfl * dxi / wi.a,
+                        mode="adg", q=wi.q, delays=tb)
+        runs.append((pr, dg.modes_initial(wi.modes, wi.K, wi.p)))
+    units = sum(wi.K * (wi.p + 1) * STAGES * 2 for wi in ws)
+    out["batched"] = both(lambda: [dg.run(pr, uu, 2) for pr, uu in runs], units)
+    out["batched"]["sample"] = "2 steps of the first 8 instances"
+
+    a = _WADJ
+    dxa = 2 * math.pi / a.K
+    xa = dg.node_coordinates(a.K, a.p, 0.0, 2 * math.pi)
+    ua = a.modes.offset + np.sin(xa)
+    ga = 0.5 + np.sin(xa - 0.003)
+    tba = delays.delay_table(a.seed, a.P, 10, a.L)
+    pra = dg.Problem(pde="burgers", K=a.K, p=a.p, P=a.P, dt=a.cfl * dxa / 1.5, mode="adg",
+                     q=a.q, delays=tba)
+    t0 = time.perf_counter()
+    dg.run(pra, ua, 10)
+    tf = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    dg.gradient(pra, ua, ga, 10)
+    tg = time.perf_counter() - t0
+    out["adjoint"] = {"forward_s": tf, "grad_s": tg, "grad_over_forward": tg / tf,
+                      "threads": torch.get_num_threads(),
+                      "sample": "10 steps on the full K = 65536 mesh (store-all autograd)"}
+    return out
+
+
 def cpu_baseline(window: int = 1 << 22, steps: int = 3) -> dict:
     """The oracle on all of torch's CPU threads and on one thread (a 2^20-element window)."""
     rate, _, used, sample = oracle_timed(window, steps)
@@ -548,6 +654,38 @@ def cpu_baseline(window: int = 1 << 22, steps: int = 3) -> dict:
     out = {"value": rate, "unit": UNIT, "cores": used, "kind": "oracle", "sample": sample,
            "one_thread": {"value": one, "sample": one_sample}}
     out.update(host_info())
+    return out
+
+
+def profile_case(name: str) -> dict:
+    """A few steps of a smaller case in two calls (4 + 8 steps, or 3 + 3 for Burgers), for
+    ncu captures that stay within a few GB and a few seconds."""
+    import torch
+    import paper_2404_03399_gb300 as adg
+    w = WORKLOAD
+    if name == "burgers_1m":
+        b = BURGERS_1M
+        cfg = adg.Config(pde="burgers", K=b.K, p=b.p, P=b.P, cfl=0.005, mode="at", L=b.L, q=b.q,
+                         seed=b.seed)
+        m = b.modes
+        u0 = adg.eval_modes(cfg, m.amp, m.kappa, m.phase, m.offset)
+        calls = (3, 3)
+    else:
+        K = w["K"] if name == "fixed_16m" else 1 << 22
+        # two elements per thread, the choice the autotuner makes outside the profiler (its
+        # timing launches run differently under it)
+        cfg = adg.Config(pde="advection", K=K, p=w["p"], P=K // (w["K"] // w["P"]), cfl=w["cfl"],
+                         mode="at", L=w["L"], q=w["q"], seed=w["seed"], ept=2,
+                         rk="lsrk4" if name == "lsrk4_4m" else "ssprk3")
+        amp, kap, ph, off = w["modes"]
+        u0 = adg.eval_modes(cfg, amp, kap, ph, off)
+        calls = (4, 8)
+    s = adg.Solver(cfg, u0)
+    for k in calls:
+        s.step(k)
+    torch.cuda.synchronize()
+    out = {"case": name, "K": cfg.K, "variant": list(s.variant), "steps": sum(calls)}
+    s.close()
     return out
 
 
@@ -620,6 +758,13 @@ def main():
     ap.add_argument("--extra-only", choices=["lsrk4", "viscous", "euler"], default=None,
                     help="only time that extra workload (the LSRK4 scheme on the large mesh, "
                          "viscous Burgers, Euler) and print its dict (for profiling runs)")
+    ap.add_argument("--profile", choices=["fixed_4m", "fixed_16m", "lsrk4_4m", "burgers_1m"],
+                    default=None,
+                    help="run a few steps of a case for ncu captures and print its dict: "
+                         "advection K = 2^22 (the large workload's PE size, delays and AT order) "
+                         "with the fixed-point step, the same at the full K = 2^24, the K = 2^22 "
+                         "case with LSRK4, or the Burgers workload (K = 2^20) at Courant number "
+                         "0.005")
     ap.add_argument("--batched-only", type=int, default=0, metavar="STEPS",
                     help="only time the batched workload for STEPS steps and print that dict "
                          "(for profiling runs)")
@@ -651,6 +796,9 @@ def main():
             out = {"euler_ms_per_step": ms / 4, "dof": dof, "finite": fin}
         print(json.dumps(out), flush=True)
         return
+    if args.profile:
+        print(json.dumps(profile_case(args.profile)), flush=True)
+        return
     if args.batched_only:
         rate, ms, ndof, n, variant = batched_timed(args.batched_only, 3)
         print(json.dumps({"batched": rate, "ms_per_step": ms, "dof": ndof, "instances": n,
@@ -676,28 +824,30 @@ def main():
     # the larger one).
     hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / step_s / 1e9
     roofline = {"bound": "hbm", "achieved": hbm_algo_gbs, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": hbm_algo_gbs / hbm_gbs, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(variant),
+                "frac": hbm_algo_gbs / hbm_gbs, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(f"{variant}/{ept}"),
                 "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)",
                 "bytes_per_dof_step": BYTES_PER_DOF_STEP}
     if variant == "fixed":
-        wide, hi = FIXED_MACS_PER_ELEMENT_STEP, 2 * FIXED_MACS_PER_ELEMENT_STEP
-        pipe_s = K * (wide / WIDE_PER_CLK_SM + hi / HI_PER_CLK_SM) / (sms * sm_mhz * 1e6)
+        wide = FIXED_MACS_PER_ELEMENT_STEP
+        # 3 products per multiply-add, 2 passes each, 16 lanes per clock per sub-partition
+        pipe_s = K * 3 * wide * 2 / (16 * 4 * sms * sm_mhz * 1e6)
         roofline["kernel"] = (f"k_step_fixed (composed SSP-RK3 step in 58-bit block fixed point, "
                               f"{ept} element(s) per thread) + k_face_step")
         roofline["alu"] = {
-            "what": f"heavy integer pipe: {wide} 32x32->64-bit multiply-adds and {hi} high-word "
-                    f"products per element at the measured issue rates ({WIDE_PER_CLK_SM} and "
-                    f"{HI_PER_CLK_SM} per clock per SM, {sms} SMs, {sm_mhz:.0f} MHz)",
+            "what": f"heavy FMA pipe: {wide} multiply-adds of 58-bit precision per element, three "
+                    f"32x32->64-bit products each, every product two passes of the pipe's 16 "
+                    f"lanes per clock per SM sub-partition ({sms} SMs x 4, {sm_mhz:.0f} MHz)",
             "pipe_bound_ms": pipe_s * 1e3, "frac": pipe_s / step_s}
     else:
         roofline["kernel"] = f"k_step_fused / k_stage ({variant}, FP64)"
         roofline["fp64"] = {"achieved_tflops": ndof * FLOP_PER_DOF_STEP / step_s / 1e12,
                             "peak_tflops": fp64_tflops,
                             "frac": ndof * FLOP_PER_DOF_STEP / step_s / 1e12 / fp64_tflops}
-    arithmetic = ("58-bit block fixed point (one scale per field per step, 2^-57 of the field's "
-                  "largest value per unit; a few units of error per sum), int64 state inside each "
-                  "adg_step call; FP64 at its first input, its last output and in the PE-face "
-                  "stage differences") if variant == "fixed" else "FP64"
+    arithmetic = ("58-bit block fixed point: int64 values at one scale per field and step "
+                  "(unit 2^-57 of the field's largest value; a sum of n products is off by less "
+                  "than n/2 + 1/2 units), the state kept in int64 from step to step; FP64 in the "
+                  "PE-face stage differences and where the state is read") \
+        if variant == "fixed" else "FP64"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -748,6 +898,9 @@ def main():
                     "bytes_frac": BURGERS_1M.ndof * BYTES_PER_DOF_STEP_STAGED / bstep / 1e9 / hbm_gbs,
                     "error_vs_characteristics": bacc}
         line["burgers_1m"] = bline
+        line["advection_small"] = {mode: small_timed(mode) for mode in ("sync", "async", "at")}
+        line["advection_small"]["workload"] = ("K = 64, p = 2, 16 PEs, delays uniform in {0..3}, "
+                                               "sigma = 0.1, t_end = 2 pi (640 steps), AT order 3")
         # the same ADG-AT steps in FP64 (the composed step on the FP64 pipe)
         f_ms, _, ffin, (fvar, _) = device_timed("at", args.steps, args.warmup, barrier, False,
                                                local, variant="composed")
@@ -762,6 +915,8 @@ def main():
         brate, bms, bdof, bn, bvariant = batched_timed(100, 3)
         line["batched"] = {"value": brate, "unit": UNIT, "ms_per_step": bms, "instances": bn,
                            "dof": bdof, "steps": 100, "variant": bvariant,
+                           "hbm_frac": bdof * BYTES_PER_DOF_STEP / (bms * 1e-3) / 1e9 / hbm_gbs,
+                           "chosen_by": "the batch autotuner at adg_batch_init",
                            "workload": "512 advection instances, K log-uniform in [1024, 262144], "
                                        "p in 1..4, L in 2..8, AT order min(p+1, 3)"}
         line["adjoint"] = adjoint_cost()
@@ -808,6 +963,8 @@ def main():
                                "peak_source": "FP64 unit counts x max SM clock"}
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
+        if not args.no_extras:
+            line["cpu_baseline"]["other_workloads"] = oracle_configs()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

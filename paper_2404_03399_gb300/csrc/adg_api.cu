@@ -369,6 +369,8 @@ struct adg_ctx {
   int nwork = 0;
   int2 *fwork_dev = nullptr;   // (instance, first PE face) items of the batched face pass
   int nfwork = 0;
+  int2 *fflat_dev = nullptr;   // (instance, PE face) of every PE face: the composed steps' fix-up
+  int nflat = 0;
   bool batch_fused = false;     // every instance runs composed steps
   bool batch_fixed = false;     // ... in fixed point
   adg::BatchLite *lites_ept[3] = {};   // work records of 256, 512, 1024 elements (batch tuner)
@@ -1123,7 +1125,7 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkFP64) {
     for (int rel = 0; rel < nsteps; ++rel) {
       const int out = in == 1 ? 2 : 1;
       const int fmt = (in != 0 ? adg::kFmtInFixed : 0) | adg::kFmtOutFixed;
-      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
+      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fflat_dev, c->nflat,
                                       in, out, fmt, true, rel, c->stream, c->bu.get()));
       in = out;
     }
@@ -1132,7 +1134,7 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkFP64) {
   }
   if (c->batch && c->batch_fused) {
     for (int rel = 0; rel < nsteps; ++rel)
-      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fwork_dev, c->nfwork,
+      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fflat_dev, c->nflat,
                                       rel % 2, 1 - rel % 2, 0, c->batch_fixed, rel, c->stream,
                                       c->batch_fixed ? c->bu.get() : nullptr));
     if (nsteps % 2) CK(adg::launch_batch_copy_back(c->insts_dev, c->work_dev, c->nwork, c->stream));
@@ -1717,6 +1719,7 @@ void adg_destroy(adg_ctx *c) {
   for (auto *l : c->lites_ept) cudaFree(l);
   cudaFree(c->work_dev);
   cudaFree(c->fwork_dev);
+  cudaFree(c->fflat_dev);
   cudaFree(c->partials);
   cudaFree(c->red_out);
   if (c->pinned) cudaFreeHost(c->pinned);
@@ -1894,7 +1897,7 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
   }
   if (!r) {
     std::vector<Inst> hi(n);
-    std::vector<int2> work, fwork;
+    std::vector<int2> work, fwork, fflat;
     // the kinds of step every instance admits (a batch runs one kind for all instances):
     // fixed point, the FP64 composed step, the staged kernels; a variant forced by the
     // instances' configs leaves only that kind
@@ -1932,6 +1935,8 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       for (int e0 = 0; e0 < hi[i].K; e0 += adg::kTile) work.push_back(make_int2(i, e0));
       if (hi[i].async)
         for (int j0 = 0; j0 < hi[i].P; j0 += 256) fwork.push_back(make_int2(i, j0));
+      if (hi[i].async)
+        for (int j = 0; j < hi[i].P; ++j) fflat.push_back(make_int2(i, j));
     }
     // every instance of a degree with the same fixed-point coefficients: pass them per degree,
     // with one record per work item of ept tiles (ept elements per thread)
@@ -1990,6 +1995,11 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       r = fail(c, ADG_EINVAL, "ept 2 in a batch needs an even K in every instance");
     c->nwork = (int)work.size();
     c->nfwork = (int)fwork.size();
+    c->nflat = (int)fflat.size();
+    if (!r && (cudaMalloc(&c->fflat_dev, sizeof(int2) * std::max<size_t>(1, fflat.size())) != cudaSuccess ||
+               (!fflat.empty() && cudaMemcpy(c->fflat_dev, fflat.data(), sizeof(int2) * fflat.size(),
+                                             cudaMemcpyHostToDevice) != cudaSuccess)))
+      r = fail(c, ADG_ENOMEM, "cudaMalloc(batch face list)");
     if (cudaMalloc(&c->insts_dev, sizeof(Inst) * n) != cudaSuccess ||
         cudaMalloc(&c->work_dev, sizeof(int2) * work.size()) != cudaSuccess ||
         cudaMalloc(&c->fwork_dev, sizeof(int2) * std::max<size_t>(1, fwork.size())) != cudaSuccess)

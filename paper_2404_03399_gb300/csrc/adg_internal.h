@@ -252,7 +252,8 @@ struct BatchUniform {
 // Batched composed steps over all instances: src / dst select u (0), v1 (1) or v2 (2) of
 // every instance. FP64 (fixed false): u -> v1 or v1 -> u. Fixed point (fixed true): fmt as in
 // launch_fused_step, with the shared coefficients of bu when bu is not null. Then the PE-face
-// correction of every instance.
+// correction of every instance: fwork_dev lists (instance, face) for every PE face of every
+// instance (nfwork entries).
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
                                     bool fixed, int rel, cudaStream_t s,

@@ -988,13 +988,17 @@ __global__ void __launch_bounds__(kTile) k_batch_fused(const Inst *__restrict__ 
   }
 }
 
+// The PE-face corrections of a batched composed step, one thread per PE face of any instance:
+// fflat lists (instance, face) for every PE face of every instance, so the threads of a block
+// are all busy however few faces an instance has.
 __global__ void __launch_bounds__(64) k_batch_fixup(const Inst *__restrict__ insts,
-                                                    const int2 *__restrict__ fwork, int src,
-                                                    int dst, int fmt, int rel) {
-  const int2 w = fwork[blockIdx.y];
+                                                    const int2 *__restrict__ fflat, int nflat,
+                                                    int src, int dst, int fmt, int rel) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= nflat) return;
+  const int2 w = fflat[t];
   const Inst &I = insts[w.x];
-  const int j = w.y + blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= I.P || blockIdx.x * blockDim.x + threadIdx.x >= 256) return;
+  const int j = w.y;
   const void *uin = src == 0 ? (const void *)I.u : (src == 1 ? (const void *)I.v1 : (const void *)I.v2);
   void *uout = dst == 0 ? (void *)I.u : (dst == 1 ? (void *)I.v1 : (void *)I.v2);
   switch (I.Np) {
@@ -1468,7 +1472,8 @@ cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev,
     k_batch_fused<<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src == 1 ? 1 : 0);
   }
   if (nfwork > 0)
-    k_batch_fixup<<<dim3(4, nfwork), 64, 0, s>>>(insts_dev, fwork_dev, src, dst, fmt, rel);
+    k_batch_fixup<<<(unsigned)((nfwork + 63) / 64), 64, 0, s>>>(insts_dev, fwork_dev, nfwork, src,
+                                                              dst, fmt, rel);
   return cudaGetLastError();
 }
 
