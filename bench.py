@@ -55,8 +55,11 @@ NP = WORKLOAD["p"] + 1
 MACS_PER_ELEMENT_STEP = NP * NP + 5 * NP + 3
 # fixed point: each multiply-add of the kernel is three 32 x 32 -> 64-bit products
 # (adg_fixed.cuh); with two elements per thread the kernel forms Np^2 + 5 Np + 3.5 of them per
-# element (the neighbour's channel scalars: 7 per pair instead of 8)
+# element (the neighbour's channel scalars: 7 per pair instead of 8), and in the block basis
+# of the element operator (2 x 2 blocks of G whose first rows are shifts and adds)
+# 2 floor(Np / 2) + (Np odd) + 5 Np + 3.5 (27.5 at p = 3)
 FIXED_MACS_PER_ELEMENT_STEP = MACS_PER_ELEMENT_STEP + 0.5
+FIXED_MACS_PER_ELEMENT_STEP_BASIS = 2 * (NP // 2) + (NP % 2) + 5 * NP + 3.5
 FLOP_PER_DOF_STEP = 2 * MACS_PER_ELEMENT_STEP / NP
 FLOP_PER_DOF_STAGE_STAGED = 2 * (NP + 2)
 # A 2N low-storage stage: dt L(U) + A_s dU (one multiply and NP + 1 FMA per DOF) and
@@ -68,11 +71,12 @@ LOW_STORAGE_STAGES = {"rk1": 1, "rk2": 2, "lsrk3": 3, "lsrk4": 5}
 VISC_NP = 3
 FLOP_PER_DOF_STAGE_VISC = 6 * VISC_NP + 17
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
-# dominates the step, keyed by variant and elements per thread; a kernel changed since its
-# counters were taken has no entry (null in the line). k_step_fixed, two per thread, int64 ->
-# int64, K = 2^24: 537,010,176 B read + 488,685,824 B written (the algorithmic 536,870,912 B
-# each way; part of the written field is still in L2 when the launch ends).
-TRAFFIC_BYTES_PER_LAUNCH = {"fixed/2": 537010176 + 488685824}
+# dominates the step, keyed by variant, elements per thread and coordinates; a kernel changed
+# since its counters were taken has no entry (null in the line). k_step_fixed, two per thread,
+# nodal values, int64 -> int64, K = 2^24: 537,010,176 B read + 488,685,824 B written (the
+# algorithmic 536,870,912 B each way; part of the written field is still in L2 when the
+# launch ends).
+TRAFFIC_BYTES_PER_LAUNCH = {"fixed/2/nodal": 537010176 + 488685824}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 # The staged SSP-RK3 step reads and writes 16 / 24 / 24 B per DOF in its three stages (the
@@ -242,7 +246,7 @@ def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks
     except adg.AdgError:
         s.check_finite_ok = False
     finite = s.check_finite_ok
-    variant = s.variant
+    variant = s.variant + (s.fixed_basis,)
     if exact_error is not None:
         exact_error.update(linf_vs_translation(s, cfg, warmup + steps))
     s.close()
@@ -786,7 +790,7 @@ def main():
         return
     if args.extra_only:
         if args.extra_only == "lsrk4":
-            ms, _, fin, (var, _) = device_timed("at", 4, 2, lambda: None, False, local, "lsrk4")
+            ms, _, fin, (var, _, _) = device_timed("at", 4, 2, lambda: None, False, local, "lsrk4")
             out = {"lsrk4_ms_per_step": ms / 4, "finite": fin, "variant": var}
         elif args.extra_only == "viscous":
             ms, dof, fin = viscous_timed(4, 2)
@@ -809,7 +813,7 @@ def main():
     K, p = WORKLOAD["K"], WORKLOAD["p"]
     ndof = K * (p + 1)
     acc_at = {}
-    ms, clocks, finite, (variant, ept) = device_timed("at", args.steps, args.warmup, barrier,
+    ms, clocks, finite, (variant, ept, basis) = device_timed("at", args.steps, args.warmup, barrier,
                                                       rank == 0, local, exact_error=acc_at)
     units = ndof * STAGES * args.steps
     ms_max, units_all = aggregate(dist, ms, units)
@@ -824,14 +828,16 @@ def main():
     # the larger one).
     hbm_algo_gbs = ndof * BYTES_PER_DOF_STEP / step_s / 1e9
     roofline = {"bound": "hbm", "achieved": hbm_algo_gbs, "peak": hbm_gbs, "unit": "GB/s",
-                "frac": hbm_algo_gbs / hbm_gbs, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(f"{variant}/{ept}"),
+                "frac": hbm_algo_gbs / hbm_gbs, "traffic": TRAFFIC_BYTES_PER_LAUNCH.get(
+                    f"{variant}/{ept}/{'basis' if basis else 'nodal'}"),
                 "peak_source": f"{hbm_src} copy bandwidth (MEASURED_PEAKS.json)",
                 "bytes_per_dof_step": BYTES_PER_DOF_STEP}
     if variant == "fixed":
-        wide = FIXED_MACS_PER_ELEMENT_STEP
+        wide = FIXED_MACS_PER_ELEMENT_STEP_BASIS if basis else FIXED_MACS_PER_ELEMENT_STEP
         # 3 products per multiply-add, 2 passes each, 16 lanes per clock per sub-partition
         pipe_s = K * 3 * wide * 2 / (16 * 4 * sms * sm_mhz * 1e6)
         roofline["kernel"] = (f"k_step_fixed (composed SSP-RK3 step in 58-bit block fixed point, "
+                              f"{'block-basis coordinates' if basis else 'nodal values'}, "
                               f"{ept} element(s) per thread) + k_face_step")
         roofline["alu"] = {
             "what": f"heavy FMA pipe: {wide} multiply-adds of 58-bit precision per element, three "
@@ -845,8 +851,10 @@ def main():
                             "frac": ndof * FLOP_PER_DOF_STEP / step_s / 1e12 / fp64_tflops}
     arithmetic = ("58-bit block fixed point: int64 values at one scale per field and step "
                   "(unit 2^-57 of the field's largest value; a sum of n products is off by less "
-                  "than n/2 + 1/2 units), the state kept in int64 from step to step; FP64 in the "
-                  "PE-face stage differences and where the state is read") \
+                  "than n/2 + 1/2 units), the state kept in int64 from step to step"
+                  + (" as coordinates in the block basis of the element operator (one bit of "
+                     "headroom; cond_inf of the basis 10.6 at p = 3)" if basis else "")
+                  + "; FP64 in the PE-face stage differences and where the state is read") \
         if variant == "fixed" else "FP64"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
@@ -868,7 +876,7 @@ def main():
                        "what": "pinned host u0 -> device, adg_init, all steps, state -> pinned host"}
         # synchronous DG on the same mesh, the same number of steps in one adg_step call
         acc_sync = {}
-        sync_ms, _, _, (svar, _) = device_timed("sync", args.steps, args.warmup, barrier, False,
+        sync_ms, _, _, (svar, _, _) = device_timed("sync", args.steps, args.warmup, barrier, False,
                                                local, exact_error=acc_sync)
         line["sync_dg"] = {"value": ndof * STAGES * args.steps / (sync_ms * 1e-3), "unit": UNIT,
                            "ms_per_step": sync_ms / args.steps, "steps": args.steps,
@@ -902,7 +910,7 @@ def main():
         line["advection_small"]["workload"] = ("K = 64, p = 2, 16 PEs, delays uniform in {0..3}, "
                                                "sigma = 0.1, t_end = 2 pi (640 steps), AT order 3")
         # the same ADG-AT steps in FP64 (the composed step on the FP64 pipe)
-        f_ms, _, ffin, (fvar, _) = device_timed("at", args.steps, args.warmup, barrier, False,
+        f_ms, _, ffin, (fvar, _, _) = device_timed("at", args.steps, args.warmup, barrier, False,
                                                local, variant="composed")
         f_s = f_ms / args.steps * 1e-3
         line["fp64_composed"] = {
@@ -923,7 +931,7 @@ def main():
         # the 2N low-storage schemes (staged kernels) on the same mesh, ADG-AT3
         ls = {}
         for rk, S in LOW_STORAGE_STAGES.items():
-            lms, _, lfin, (lvar, _) = device_timed("at", 10, 3, barrier, False, local, rk)
+            lms, _, lfin, (lvar, _, _) = device_timed("at", 10, 3, barrier, False, local, rk)
             step_s = lms / 10 * 1e-3
             staged = lvar == "staged"   # schemes of <= 3 stages run the composed fixed-point step
             ls[rk] = {"value": ndof * S / step_s, "unit": UNIT, "ms_per_step": lms / 10,

@@ -214,6 +214,15 @@ int adg_get_dt(adg_ctx *c, int32_t index, double *dt_out);
  * composed-step kernel chosen at init (1 for the staged kernels). Either pointer may be NULL. */
 int adg_get_variant(adg_ctx *c, int32_t index, int32_t *variant_out, int32_t *ept_out);
 
+/* The coordinates of instance `index`'s fixed-point state (not a paper quantity): *basis_out =
+ * 1 when the int64 state holds each element's coordinates w = T^-1 u in a basis of invariant
+ * subspaces of the element operator, in which the step matrix G is block diagonal (2 x 2
+ * blocks: each output row takes two of G's multiply-adds instead of Np). A single instance on
+ * COMPOSED_FIXED uses it where the basis is well conditioned (cond_inf(T) <= 64: p = 1, 2,
+ * 3); 0 for nodal values, a batch, or another variant. The FP64 state read through the API is
+ * nodal either way. basis_out must not be NULL. */
+int adg_get_fixed_basis(adg_ctx *c, int32_t index, int32_t *basis_out);
+
 /*
  * Discrete gradient of the final-time L2 misfit
  *     J = 1/2 sum_e (dx/2) (u_N^e - g^e)^T M (u_N^e - g^e)

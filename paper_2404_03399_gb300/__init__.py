@@ -184,6 +184,13 @@ class Solver:
         check(load().adg_get_variant(self.ctx, 0, C.byref(v), C.byref(e)), self.ctx)
         return {1: "staged", 2: "composed", 3: "fixed"}[v.value], e.value
 
+    @property
+    def fixed_basis(self) -> bool:
+        """True when the fixed-point state holds block-basis coordinates (adg_get_fixed_basis)."""
+        b = C.c_int32()
+        check(load().adg_get_fixed_basis(self.ctx, 0, C.byref(b)), self.ctx)
+        return bool(b.value)
+
     def comm_stats(self) -> dict:
         """PE-face exchanges a distributed run of the steps so far would make, against
         synchronous DG (adg_comm_stats)."""

@@ -22,7 +22,7 @@ EXPORTS = [
     "adg_config_default", "adg_init", "adg_batch_init", "adg_step", "adg_run",
     "adg_get_state", "adg_get_dt", "adg_get_variant", "adg_grad", "adg_integral", "adg_check_finite",
     "adg_delay_table", "adg_eval_modes", "adg_lgl_nodes", "adg_last_error", "adg_destroy",
-    "adg_integral_noalloc", "adg_misfit", "adg_comm_stats",
+    "adg_integral_noalloc", "adg_misfit", "adg_comm_stats", "adg_get_fixed_basis",
 ]
 
 
@@ -73,6 +73,7 @@ def load(require: bool = True):
         "adg_get_state": (C.c_int, [vp, i32, vp, C.POINTER(i64)]),
         "adg_get_dt": (C.c_int, [vp, i32, dp]),
         "adg_get_variant": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
+        "adg_get_fixed_basis": (C.c_int, [vp, i32, C.POINTER(i32)]),
         "adg_grad": (C.c_int, [vp, vp, i64, i32, vp, dp]),
         "adg_integral": (C.c_int, [vp, i32, dp]),
         "adg_check_finite": (C.c_int, [vp]),

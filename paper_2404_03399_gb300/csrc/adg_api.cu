@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <complex>
 #include <cstdio>
 #include <cstring>
 #include <memory>
@@ -471,10 +472,247 @@ void two_register_butcher(int rk, int &S, ld a[adg::kMaxStages][adg::kMaxStages]
   }
 }
 
+// Block basis of the element operator for the fixed-point composed step. Every matrix of the
+// composed step of upwind advection (G, and the stage maps behind h, r and R) is a polynomial
+// in the element operator A = D + M^-1 e_0 e_0^T. In a basis of A-invariant subspaces of
+// dimension two (a complex-conjugate pair of eigenvalues, or two real ones) and, for odd Np,
+// one last eigenvector, G is block diagonal with 2 x 2 blocks, so each of its rows takes two
+// multiply-adds instead of Np. Each pair's first vector has right trace 1 and its second
+// trace 0 (a single vector: trace 1), so the right trace of u = T w is the sum of the even
+// coordinates of w. Built in long double: eigenvalues as the roots of the characteristic
+// polynomial (Faddeev-LeVerrier coefficients, Weierstrass iteration, Newton polishing),
+// eigenvectors as null vectors of A - lambda I (elimination with complete pivoting). The
+// basis is rejected (nodal values are kept) unless T^-1 A T is block diagonal to 1e-13 of
+// its largest entry and cond_inf(T) <= 64: the fixed-point error of a step, relative to the
+// field, grows with that condition number.
+using cld = std::complex<ld>;
+
+std::vector<ld> char_poly(const std::vector<ld> &A, int n) {
+  // c[n] = 1; M_1 = I, c_{n-k} = -tr(A M_k) / k, M_{k+1} = A M_k + c_{n-k} I
+  std::vector<ld> c(n + 1, 0.0L), M(n * n, 0.0L), AM(n * n);
+  c[n] = 1;
+  for (int i = 0; i < n; ++i) M[i * n + i] = 1;
+  for (int k = 1; k <= n; ++k) {
+    ld tr = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) {
+        ld a = 0;
+        for (int l = 0; l < n; ++l) a += A[i * n + l] * M[l * n + j];
+        AM[i * n + j] = a;
+      }
+    for (int i = 0; i < n; ++i) tr += AM[i * n + i];
+    c[n - k] = -tr / k;
+    M = AM;
+    for (int i = 0; i < n; ++i) M[i * n + i] += c[n - k];
+  }
+  return c;
+}
+
+cld poly_at(const std::vector<ld> &c, cld z) {
+  cld v = 0;
+  for (int k = (int)c.size() - 1; k >= 0; --k) v = v * z + c[k];
+  return v;
+}
+
+std::vector<cld> poly_roots(const std::vector<ld> &c) {
+  const int n = (int)c.size() - 1;
+  ld R = 1;
+  for (int k = 0; k < n; ++k) R = std::max(R, 1 + fabsl(c[k]));
+  std::vector<cld> z(n);
+  cld zz = 1;
+  for (int i = 0; i < n; ++i) {
+    zz *= cld(0.4L, 0.9L);
+    z[i] = zz * R;
+  }
+  for (int it = 0; it < 4000; ++it) {
+    ld change = 0;
+    for (int i = 0; i < n; ++i) {
+      cld den = 1;
+      for (int j = 0; j < n; ++j)
+        if (j != i) den *= z[i] - z[j];
+      if (std::abs(den) == 0) den = 1e-30L;
+      const cld dz = poly_at(c, z[i]) / den;
+      z[i] -= dz;
+      change = std::max(change, std::abs(dz) / (1 + std::abs(z[i])));
+    }
+    if (change < 1e-30L) break;
+  }
+  std::vector<ld> dc(n);
+  for (int k = 1; k <= n; ++k) dc[k - 1] = k * c[k];
+  for (int i = 0; i < n; ++i)
+    for (int it = 0; it < 3; ++it) {
+      const cld d = poly_at(dc, z[i]);
+      if (std::abs(d) > 0) z[i] -= poly_at(c, z[i]) / d;
+    }
+  return z;
+}
+
+// A null vector of A - lam I (unit 2-norm), or false.
+bool null_vector(const std::vector<ld> &A, int n, cld lam, std::vector<cld> &v) {
+  std::vector<cld> B(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) B[i * n + j] = A[i * n + j] - (i == j ? lam : cld(0));
+  std::vector<int> col(n);
+  for (int j = 0; j < n; ++j) col[j] = j;
+  for (int k = 0; k < n - 1; ++k) {
+    int pi = k, pj = k;
+    ld best = -1;
+    for (int i = k; i < n; ++i)
+      for (int j = k; j < n; ++j)
+        if (std::abs(B[i * n + j]) > best) {
+          best = std::abs(B[i * n + j]);
+          pi = i;
+          pj = j;
+        }
+    if (!(best > 0)) return false;
+    for (int j = 0; j < n; ++j) std::swap(B[k * n + j], B[pi * n + j]);
+    for (int i = 0; i < n; ++i) std::swap(B[i * n + k], B[i * n + pj]);
+    std::swap(col[k], col[pj]);
+    for (int i = k + 1; i < n; ++i) {
+      const cld f = B[i * n + k] / B[k * n + k];
+      for (int j = k; j < n; ++j) B[i * n + j] -= f * B[k * n + j];
+    }
+  }
+  std::vector<cld> y(n);
+  y[n - 1] = 1;
+  for (int k = n - 2; k >= 0; --k) {
+    cld acc = 0;
+    for (int j = k + 1; j < n; ++j) acc += B[k * n + j] * y[j];
+    y[k] = -acc / B[k * n + k];
+  }
+  v.assign(n, 0);
+  ld nrm = 0;
+  for (int k = 0; k < n; ++k) {
+    v[col[k]] = y[k];
+    nrm += std::norm(y[k]);
+  }
+  nrm = sqrtl(nrm);
+  if (!(nrm > 0)) return false;
+  for (auto &x : v) x /= nrm;
+  return true;
+}
+
+// Two indices share a block: (2m, 2m+1), and the last index alone for odd n.
+bool same_block(int i, int j) { return (i >> 1) == (j >> 1); }
+
+// The block-diagonality of X in the block basis: largest off-block entry against the
+// largest entry.
+bool block_diagonal(const std::vector<ld> &X, int n, ld tol) {
+  ld mx = 0, off = 0;
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) {
+      mx = std::max(mx, fabsl(X[i * n + j]));
+      if (!same_block(i, j)) off = std::max(off, fabsl(X[i * n + j]));
+    }
+  return off <= tol * mx;
+}
+
+std::vector<ld> similar(const std::vector<ld> &Ti, const std::vector<ld> &X,
+                        const std::vector<ld> &T, int n) {
+  std::vector<ld> Y(n * n, 0.0L), Z(n * n, 0.0L);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) Y[i * n + j] += X[i * n + k] * T[k * n + j];
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j)
+      for (int k = 0; k < n; ++k) Z[i * n + j] += Ti[i * n + k] * Y[k * n + j];
+  return Z;
+}
+
+ld cond_inf(const std::vector<ld> &T, const std::vector<ld> &Ti, int n) {
+  ld nt = 0, nti = 0;
+  for (int i = 0; i < n; ++i) {
+    ld a = 0, b = 0;
+    for (int j = 0; j < n; ++j) {
+      a += fabsl(T[i * n + j]);
+      b += fabsl(Ti[i * n + j]);
+    }
+    nt = std::max(nt, a);
+    nti = std::max(nti, b);
+  }
+  return nt * nti;
+}
+
+bool block_basis(const Ops &o, std::vector<ld> &T, std::vector<ld> &Ti) {
+  const int n = o.Np, p = n - 1;
+  std::vector<ld> A(n * n);
+  for (int i = 0; i < n; ++i)
+    for (int j = 0; j < n; ++j) A[i * n + j] = o.D[i * n + j] + (j == 0 ? o.Minv[i * n + 0] : 0.0L);
+  const std::vector<cld> lam = poly_roots(char_poly(A, n));
+  ld anorm = 0;
+  for (ld x : A) anorm = std::max(anorm, fabsl(x));
+  // vectors spanning the invariant subspaces: complex pairs (Re v, Im v) first, then the real
+  // eigenvectors two at a time, the last one alone for odd n
+  std::vector<std::vector<ld>> span;
+  std::vector<std::vector<ld>> reals;
+  for (int i = 0; i < n; ++i) {
+    const ld tol = 1e-9L * (1 + std::abs(lam[i]));
+    std::vector<cld> v;
+    if (!null_vector(A, n, lam[i], v)) return false;
+    for (int r = 0; r < n; ++r) {   // residual
+      cld acc = -lam[i] * v[r];
+      for (int k = 0; k < n; ++k) acc += A[r * n + k] * v[k];
+      if (std::abs(acc) > 1e-12L * (1 + anorm)) return false;
+    }
+    if (lam[i].imag() > tol) {
+      std::vector<ld> re(n), im(n);
+      for (int k = 0; k < n; ++k) {
+        re[k] = v[k].real();
+        im[k] = v[k].imag();
+      }
+      span.push_back(re);
+      span.push_back(im);
+    } else if (fabsl(lam[i].imag()) <= tol) {
+      // a real eigenvalue: v is real up to a unit factor
+      int km = 0;
+      for (int k = 1; k < n; ++k)
+        if (std::abs(v[k]) > std::abs(v[km])) km = k;
+      const cld ph = v[km] / std::abs(v[km]);
+      std::vector<ld> re(n);
+      for (int k = 0; k < n; ++k) re[k] = (v[k] / ph).real();
+      reals.push_back(re);
+    }
+  }
+  for (auto &r : reals) span.push_back(r);
+  if ((int)span.size() != n) return false;
+  T.assign(n * n, 0.0L);
+  auto dot = [&](const std::vector<ld> &a, const std::vector<ld> &b) {
+    ld s = 0;
+    for (int k = 0; k < n; ++k) s += a[k] * b[k];
+    return s;
+  };
+  for (int m = 0; m + 1 < n; m += 2) {
+    std::vector<ld> q1 = span[m], q2 = span[m + 1];
+    const ld n1 = sqrtl(dot(q1, q1));
+    if (!(n1 > 0)) return false;
+    for (auto &x : q1) x /= n1;
+    const ld pr = dot(q1, q2);
+    for (int k = 0; k < n; ++k) q2[k] -= pr * q1[k];
+    const ld n2 = sqrtl(dot(q2, q2));
+    if (!(n2 > 1e-9L * sqrtl(dot(span[m + 1], span[m + 1])))) return false;
+    for (auto &x : q2) x /= n2;
+    const ld t1 = q1[p], t2 = q2[p], tt = t1 * t1 + t2 * t2;
+    if (!(tt > 1e-12L)) return false;
+    for (int k = 0; k < n; ++k) {
+      T[k * n + m] = (t1 * q1[k] + t2 * q2[k]) / tt;
+      T[k * n + m + 1] = (t2 * q1[k] - t1 * q2[k]) / tt;
+    }
+  }
+  if (n % 2) {
+    const std::vector<ld> &v = span[n - 1];
+    if (!(fabsl(v[p]) > 1e-6L * sqrtl(dot(v, v)))) return false;
+    for (int k = 0; k < n; ++k) T[k * n + n - 1] = v[k] / v[p];
+  }
+  for (int j = 0; j < n; ++j) T[p * n + j] = (j % 2 == 0) ? 1.0L : 0.0L;
+  if (!invert(T, n, Ti)) return false;
+  if (!block_diagonal(similar(Ti, A, T, n), n, 1e-13L)) return false;
+  return cond_inf(T, Ti, n) <= 64.0L;
+}
+
 // Composed step constants (StepConsts in adg_internal.h) of upwind advection with a > 0, in
 // long double: from the SSP-RK3 stages in Shu and Osher's form, or, for the low-storage
 // schemes (one to five stages), from their Butcher form (unused channels are zero).
-void fold_step_constants(InstHost &h) {
+void fold_step_constants(InstHost &h, bool allow_basis) {
   const Ops &o = h.ops;
   const int Np = o.Np;
   const ld c2a = advection_c2a(h);
@@ -668,6 +906,99 @@ void fold_step_constants(InstHost &h) {
       for (int i = 0; i < Np; ++i) Sc.R[s][m][i] = (double)Rl[s][m][i];
   }
 
+  // The fixed-point step's coordinates: the block basis of the element operator for a single
+  // instance where it is well conditioned (G block diagonal, h, R times T^-1, r times T), else
+  // nodal values.
+  h.I.basis = 0;
+  h.I.fxh = 0;
+  h.I.fxe = 0;
+  std::memset(h.I.Tb, 0, sizeof(h.I.Tb));
+  std::memset(h.I.Tbi, 0, sizeof(h.I.Tbi));
+  std::vector<ld> Tm, Tim;
+  bool basis = allow_basis && block_basis(o, Tm, Tim);
+  Mat Gc = Gl;
+  std::vector<ld> hc[CS], rc[CS];
+  ld Rc[CS][CS + 1][adg::kMaxNp] = {};
+  for (int s = 0; s < CS; ++s) {
+    hc[s] = hl[s];
+    rc[s] = rl[s];
+    for (int m = 0; m <= CS; ++m)
+      for (int i = 0; i < Np; ++i) Rc[s][m][i] = Rl[s][m][i];
+  }
+  int gshift[adg::kMaxNp / 2] = {};
+  if (basis) {
+    Gc = similar(Tim, Gl, Tm, Np);
+    if (!block_diagonal(Gc, Np, 1e-13L)) basis = false;
+  }
+  if (basis) {
+    // Within a 2 x 2 block two parameters of the basis are free: the trace-1 vector f may take
+    // any multiple of its trace-0 partner g, and g any scale. f' = f + alpha g, g' = beta g
+    // with alpha = -(G - I)_11 / (G - I)_12 and beta = 2^-k / (G - I)_12 make the block's first
+    // row of G exactly (1, 2^-k) (k the nearest power of two, so beta is near 1): a row of
+    // shifts and adds in the kernel.
+    std::vector<ld> Ts = Tm, Tis;
+    for (int m = 0; m + 1 < Np && basis; m += 2) {
+      const ld n11 = Gc[m * Np + m] - 1.0L, n12 = Gc[m * Np + m + 1];
+      const int k = fabsl(n12) > 0 ? (int)lroundl(-log2l(fabsl(n12))) : -1;
+      if (k < 1 || k > 27) {
+        basis = false;
+        break;
+      }
+      const ld al = -n11 / n12, be = ldexpl(1.0L, -k) / n12;
+      for (int r = 0; r < Np; ++r) {
+        const ld f = Ts[r * Np + m], g = Ts[r * Np + m + 1];
+        Ts[r * Np + m] = f + al * g;
+        Ts[r * Np + m + 1] = be * g;
+      }
+      gshift[m / 2] = 29 - k;
+    }
+    if (basis && invert(Ts, Np, Tis) && cond_inf(Ts, Tis, Np) <= 64.0L) {
+      const Mat Gs = similar(Tis, Gl, Ts, Np);
+      bool rows = block_diagonal(Gs, Np, 1e-13L);
+      for (int m = 0; m + 1 < Np; m += 2)
+        rows = rows && fabsl(Gs[m * Np + m] - 1.0L) < 1e-15L &&
+               fabsl(Gs[m * Np + m + 1] - ldexpl(1.0L, gshift[m / 2] - 29)) <
+                   1e-15L * ldexpl(1.0L, gshift[m / 2] - 29);
+      if (rows) {
+        Tm = Ts;
+        Tim = Tis;
+        Gc = Gs;
+        for (int m = 0; m + 1 < Np; m += 2) {
+          Gc[m * Np + m] = 1.0L;
+          Gc[m * Np + m + 1] = ldexpl(1.0L, gshift[m / 2] - 29);
+        }
+      } else {
+        basis = false;
+      }
+    } else {
+      basis = false;
+    }
+  }
+  if (basis) {
+    for (int i = 0; i < Np; ++i)
+      for (int j = 0; j < Np; ++j)
+        if (!same_block(i, j)) Gc[i * Np + j] = 0;
+    auto times_ti = [&](const std::vector<ld> &v) {
+      std::vector<ld> z(Np, 0.0L);
+      for (int i = 0; i < Np; ++i)
+        for (int k = 0; k < Np; ++k) z[i] += Tim[i * Np + k] * v[k];
+      return z;
+    };
+    for (int s = 0; s < CS; ++s) {
+      hc[s] = times_ti(hl[s]);
+      for (int j = 0; j < Np; ++j) {
+        ld a = 0;
+        for (int i = 0; i < Np; ++i) a += rl[s][i] * Tm[i * Np + j];
+        rc[s][j] = a;
+      }
+      for (int m = 0; m <= CS; ++m) {
+        std::vector<ld> v(Rl[s][m], Rl[s][m] + Np);
+        const std::vector<ld> z = times_ti(v);
+        for (int i = 0; i < Np; ++i) Rc[s][m][i] = z[i];
+      }
+    }
+  }
+
   // Fixed-point limbs of the same coefficients (from the long double values): C =
   // round(c 2^58) in balanced limbs C = ch 2^29 + cl (adg_fixed.cuh); every |c| < 2 keeps
   // both within 32 bits.
@@ -683,14 +1014,13 @@ void fold_step_constants(InstHost &h) {
     r.y = (int)cl;
     return r;
   };
-  // Bounds of one fixed-point sum of terms c_m x_m whose multiplicands are below g_m 2^57
-  // (g = 1: input values and traces; g = 2: channel scalars), so |xh| <= g 2^28 and
-  // 0 <= xl < 2^29: a = sum ch xh and b = 2^28 + sum (ch xl + cl xh) below 2^62, and the
-  // result, below sum |c| g 2^57 + n, below 2^61.
-  auto sum_ok = [&](const std::vector<std::pair<ld, int>> &terms) {
+  // Bounds of one fixed-point sum of terms c_m x_m whose multiplicands are below g_m 2^57,
+  // so |xh| <= g 2^28 and 0 <= xl < 2^29: a = sum ch xh and b = 2^28 + sum (ch xl + cl xh)
+  // below 2^62, and the result, below sum |c| g 2^57 + n, below 2^61.
+  auto sum_ok = [&](const std::vector<std::pair<ld, ld>> &terms) {
     ld ab = 0, bb = ldexpl(1.0L, 28), rb = 0;
     for (auto &cg : terms) {
-      const ld c = fabsl(cg.first), g = (ld)cg.second;
+      const ld c = fabsl(cg.first), g = cg.second;
       const ld ch = c * ldexpl(1.0L, 29) + 1.0L, xh = g * ldexpl(1.0L, 28) + 1.0L;
       ab += ch * xh;
       bb += ch * ldexpl(1.0L, 29) + ldexpl(1.0L, 28) * xh;
@@ -698,40 +1028,71 @@ void fold_step_constants(InstHost &h) {
     }
     return ab < ldexpl(1.0L, 62) && bb < ldexpl(1.0L, 62) && rb < 15.9L;
   };
-  bool sums = true;
-  for (int i = 0; i < Np; ++i) {
-    std::vector<std::pair<ld, int>> row;
-    for (int j = 0; j < Np; ++j) {
-      F.G[i * Np + j] = limbs(Gl[i * Np + j]);
-      row.push_back({Gl[i * Np + j], 1});
+  // Inputs below 2^(57 - hb) (g = 2^-hb); the right trace, a sum of nb of them (nb = 1 for
+  // nodal values, the number of blocks in the block basis); channel scalars Y_s below B_s 2^57
+  // with B_s = sum |r_s| 2^-hb + |k_s0| g_0 + sum_{t>=1} |k_st| B_t. Nodal values keep the
+  // bound B_s < 2 (multiplicands below 2^58); block-basis coordinates, whose channel scalars
+  // are sums of about nb coordinates, take B_s < 7.9 (below 2^60, so the high limb
+  // X >> 29 fits 32 bits), every sum then checked with its terms' own bounds. The smallest
+  // headroom hb that passes every check (0 for nodal values).
+  const int nb = basis ? (Np + 1) / 2 : 1;
+  auto checks = [&](int hb) {
+    const ld gin = ldexpl(1.0L, -hb), g0 = nb * gin, blim = basis ? 7.9L : 1.999L;
+    bool good = true;
+    ld B[CS] = {g0};
+    auto gch = [&](int t) { return basis ? B[t] : (t == 0 ? g0 : 2.0L); };
+    for (int s = 1; s < S; ++s) {
+      std::vector<std::pair<ld, ld>> sm;
+      B[s] = 0;
+      for (int i = 0; i < Np; ++i) {
+        sm.push_back({rc[s][i], gin});
+        B[s] += fabsl(rc[s][i]) * gin;
+      }
+      for (int t = 0; t < s; ++t) {
+        sm.push_back({kl[s][t], gch(t)});
+        B[s] += fabsl(kl[s][t]) * B[t];
+      }
+      good = good && sum_ok(sm) && B[s] < blim;
     }
-    for (int t = 0; t < S; ++t) {
-      F.h[t][i] = limbs(hl[t][i]);
-      row.push_back({hl[t][i], t == 0 ? 1 : 2});
-    }
-    sums = sums && sum_ok(row);
-  }
-  // channel scalars Y_s p below twice the input bound (|X| < 2^58 as multiplicands; inputs
-  // are < 2^57): B_s = sum |r_s| + |k_s0| + sum_{t>=1} |k_st| B_t < 2
-  ld B[CS] = {1.0L};
-  bool chan = true;
-  for (int s = 1; s < S; ++s) {
-    std::vector<std::pair<ld, int>> sm;
-    B[s] = 0;
     for (int i = 0; i < Np; ++i) {
-      F.r[s][i] = limbs(rl[s][i]);
-      sm.push_back({rl[s][i], 1});
-      B[s] += fabsl(rl[s][i]);
+      std::vector<std::pair<ld, ld>> row;
+      for (int j = 0; j < Np; ++j)
+        if (Gc[i * Np + j] != 0 || !basis) row.push_back({Gc[i * Np + j], gin});
+      for (int t = 0; t < S; ++t) row.push_back({hc[t][i], gch(t)});
+      good = good && sum_ok(row);
     }
-    for (int t = 0; t < s; ++t) {
-      F.k[s][t] = limbs(kl[s][t]);
-      sm.push_back({kl[s][t], t == 0 ? 1 : 2});
-      B[s] += fabsl(kl[s][t]) * (t == 0 ? 1.0L : B[t]);
-    }
-    sums = sums && sum_ok(sm);
-    chan = chan && B[s] < 1.999L;
+    return good;
+  };
+  int hb = 0;
+  while (hb < (basis ? 4 : 1) && !checks(hb)) ++hb;
+  const bool sums = hb < (basis ? 4 : 1);
+  for (int i = 0; i < Np; ++i) {
+    for (int j = 0; j < Np; ++j) F.G[i * Np + j] = limbs(Gc[i * Np + j]);
+    for (int t = 0; t < S; ++t) F.h[t][i] = limbs(hc[t][i]);
   }
-  h.fixed_ok = ok && sums && chan;
+  for (int s = 1; s < S; ++s) {
+    for (int i = 0; i < Np; ++i) F.r[s][i] = limbs(rc[s][i]);
+    for (int t = 0; t < s; ++t) F.k[s][t] = limbs(kl[s][t]);
+  }
+  h.fixed_ok = ok && sums;
+  if (basis)
+    for (int m = 0; m < Np / 2; ++m) F.gs[m] = gshift[m];
+  if (basis && h.fixed_ok) {
+    // FP64 inputs: w = T^-1 u in FP64 is below ||T^-1||_inf 2^(E - 1022) (1 + 2^-40)
+    ld nti = 0;
+    for (int i = 0; i < Np; ++i) {
+      ld a = 0;
+      for (int j = 0; j < Np; ++j) a += fabsl(Tim[i * Np + j]);
+      nti = std::max(nti, a);
+    }
+    h.I.basis = 1;
+    h.I.fxh = hb;
+    h.I.fxe = hb + (int)ceill(log2l(nti * (1.0L + ldexpl(1.0L, -40))));
+    for (int i = 0; i < Np * Np; ++i) {
+      h.I.Tb[i] = (double)Tm[i];
+      h.I.Tbi[i] = (double)Tim[i];
+    }
+  }
   // the PE-face responses likewise (from the long double values), for the integer correction
   // of differences below 2^57
   std::memset(h.I.Rf, 0, sizeof(h.I.Rf));
@@ -739,10 +1100,10 @@ void fold_step_constants(InstHost &h) {
   bool rsums = true;
   for (int m = 0; m <= S; ++m)
     for (int i = 0; i < Np; ++i) {
-      std::vector<std::pair<ld, int>> row;
+      std::vector<std::pair<ld, ld>> row;
       for (int st = 0; st < S; ++st) {
-        h.I.Rf[st][m][i] = limbs(Rl[st][m][i]);
-        row.push_back({Rl[st][m][i], 1});
+        h.I.Rf[st][m][i] = limbs(Rc[st][m][i]);
+        row.push_back({Rc[st][m][i], 1.0L});
       }
       rsums = rsums && sum_ok(row);
     }
@@ -1016,7 +1377,8 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     const int ls0 = I.ls, ns0 = I.ns;
     if (I.fused) {
       I.ls = 0;
-      fold_step_constants(h);   // sets I.ns to the composed kernels' stage slots
+      // sets I.ns to the composed kernels' stage slots; the block basis for a single instance
+      fold_step_constants(h, !c->batch);
       if (cfg->variant == ADG_VARIANT_COMPOSED_FIXED && !h.fixed_ok)
         return fail(c, ADG_EINVAL,
                     "the fixed-point composed step needs every composed coefficient "
@@ -1108,7 +1470,7 @@ int sync_state(adg_ctx *c) {
   for (auto &h : c->inst) {
     const Inst &I = h.I;
     const long long *X = reinterpret_cast<const long long *>(c->fx_live == 1 ? I.v1 : I.v2);
-    CK(adg::launch_fixed_to_fp64(X, I.u, (size_t)I.K * I.Np, I.fx, c->n, c->stream));
+    CK(adg::launch_fixed_to_fp64(I, X, c->n, c->stream));
   }
   c->u_fresh = true;
   return ADG_OK;
@@ -1222,20 +1584,22 @@ int launch_fused_steps(adg_ctx *c, int nsteps, int kind) {
       void *out = nxt == 1 ? static_cast<void *>(I.v1) : static_cast<void *>(I.v2);
       const bool fin = cur != 0;
       const int fmt = (fin ? adg::kFmtInFixed : 0) | adg::kFmtOutFixed;
+      // Within the chunk every kernel after the first is a programmatic dependent of the one
+      // before it (launch_maybe_pdl): its blocks start while that one drains.
       if (faces) {
         if (rel == 0)
           CK(adg::launch_face_step(I, in, 0, fin ? 1 : 0, 0, adg::kFaceDiff, c->stream));
         else
           CK(adg::launch_face_step(I, in, rel, 1, fin_prev, adg::kFaceApply | adg::kFaceDiff,
-                                   c->stream));
+                                   c->stream, true));
       }
-      CK(adg::launch_fixed_step(I, in, out, rel, fmt, c->stream));
+      CK(adg::launch_fixed_step(I, in, out, rel, fmt, c->stream, faces || rel > 0));
       fin_prev = fin ? 1 : 0;
       in = out;
       cur = nxt;
     }
     if (faces && nsteps > 0)
-      CK(adg::launch_face_step(I, in, nsteps, 1, fin_prev, adg::kFaceApply, c->stream));
+      CK(adg::launch_face_step(I, in, nsteps, 1, fin_prev, adg::kFaceApply, c->stream, true));
   } else {
     for (int rel = 0; rel < nsteps; ++rel) {
       const double *uin = (rel % 2 == 0) ? I.u : I.v1;
@@ -2093,6 +2457,15 @@ int adg_get_variant(adg_ctx *c, int32_t index, int32_t *variant_out, int32_t *ep
     *variant_out = I.fused == 2 ? ADG_VARIANT_COMPOSED_FIXED
                                 : (I.fused == 1 ? ADG_VARIANT_COMPOSED : ADG_VARIANT_STAGED);
   if (ept_out) *ept_out = I.fused ? I.ept : 1;
+  return ADG_OK;
+}
+
+int adg_get_fixed_basis(adg_ctx *c, int32_t index, int32_t *basis_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size() || !basis_out)
+    return fail(c, ADG_EINVAL, "bad argument");
+  const Inst &I = c->inst[index].I;
+  *basis_out = (I.fused == 2 && I.basis) ? 1 : 0;
   return ADG_OK;
 }
 

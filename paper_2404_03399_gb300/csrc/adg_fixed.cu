@@ -1,7 +1,10 @@
 // Composed step of upwind advection (a > 0; SSP-RK3, or a low-storage scheme of up to five
 // stages) in fixed-point integer arithmetic: the StepConsts stencil (adg_internal.h) evaluated
 // with 32 x 32 -> 64-bit integer multiply-adds on two-limb values (adg_fixed.cuh). The field
-// stays int64 from step to step; only a run's first step reads FP64.
+// stays int64 from step to step; only a run's first step reads FP64. A single instance keeps
+// the coordinates of each element in the block basis of the element operator (Inst.basis,
+// FMT bit kFmtBasis): G is then block diagonal with 2 x 2 blocks whose first rows are shifts
+// and adds, and the right trace is the sum of the even coordinates.
 #include "adg_device.cuh"
 #include "adg_fixed.cuh"
 
@@ -26,18 +29,33 @@ __device__ __forceinline__ long long fx_in(double x, long long X, const FxScale 
 }
 
 // p = the element's right trace, own[s-1] = the own parts r_s . u of its channel scalars
-// (unrounded sums, s = 1 .. S-1), and the limbs of its values for the output rows.
-template <int NP, bool FIN, int S>
-__device__ __forceinline__ void fx_own(const StepFixed &F, const double *ud, const long long *uq,
-                                       const FxScale &sc, long long &p, FxAcc *own, int *xh,
-                                       int *xl) {
+// (unrounded sums, s = 1 .. S-1), and the limbs of its values for the output rows. BLK: the
+// values are block-basis coordinates w (an FP64 input is transformed, w = Tbi u, in FP64
+// before its conversion) and the right trace is the exact sum of the even coordinates.
+template <int NP, bool FIN, int S, bool BLK>
+__device__ __forceinline__ void fx_own(const StepFixed &F, const double *Tbi, const double *ud,
+                                       const long long *uq, const FxScale &sc, long long &p,
+                                       FxAcc *own, int *xh, int *xl) {
+  double wd[NP];
+#pragma unroll
+  for (int i = 0; i < NP; ++i) {
+    if (BLK && !FIN) {
+      double a = Tbi[i * NP] * ud[0];
+#pragma unroll
+      for (int k = 1; k < NP; ++k) a = fma(Tbi[i * NP + k], ud[k], a);
+      wd[i] = a;
+    } else {
+      wd[i] = FIN ? 0.0 : ud[i];
+    }
+  }
+  p = 0;
 #pragma unroll
   for (int j = 0; j < NP; ++j) {
-    const long long X = fx_in<FIN>(FIN ? 0.0 : ud[j], FIN ? uq[j] : 0ll, sc);
+    const long long X = fx_in<FIN>(wd[j], FIN ? uq[j] : 0ll, sc);
     fx_split(X, xh[j], xl[j]);
 #pragma unroll
     for (int s = 1; s < S; ++s) fx_mac(own[s - 1], F.r[s][j], xh[j], xl[j]);
-    if (j == NP - 1) p = X;
+    if (BLK ? (j % 2 == 0) : (j == NP - 1)) p += X;
   }
 }
 
@@ -82,13 +100,29 @@ __device__ __forceinline__ void fx_left_channels(const StepFixed &F, const Fixed
   for (int s = 0; s < S; ++s) fx_split(Yp[s], P[s][0], P[s][1]);
 }
 
-// u'^e = G u^e + sum_s h_s P_s for output row i.
-template <int NP, int S>
+// u'^e = G u^e + sum_s h_s P_s for output row i. BLK: G's entries of row i's block only; the
+// first row of a 2 x 2 block is (1, 2^-k), whose products, X_i and
+// xh_{i+1} 2^(29-k) + xl_{i+1} 2^(29-k) 2^-29, are shifts (the same sums as the multiply-adds
+// with the limbs {2^29, 0} and {2^(29-k), 0}).
+template <int NP, int S, bool BLK>
 __device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int *xh, const int *xl,
                                             const int (*P)[2]) {
   FxAcc acc;
+  if (BLK) {
+    const int j0 = i & ~1;
+    if (i == j0 && j0 + 1 < NP) {
+      const int sh = F.gs[i >> 1];
+      acc.a += (long long)((unsigned long long)(long long)xh[i] << 29) + xl[i];
+      acc.a += (long long)((unsigned long long)(long long)xh[i + 1] << sh);
+      acc.b += (long long)xl[i + 1] << sh;
+    } else {
+      fx_mac(acc, F.G[i * NP + j0], xh[j0], xl[j0]);
+      if (j0 + 1 < NP) fx_mac(acc, F.G[i * NP + j0 + 1], xh[j0 + 1], xl[j0 + 1]);
+    }
+  } else {
 #pragma unroll
-  for (int j = 0; j < NP; ++j) fx_mac(acc, F.G[i * NP + j], xh[j], xl[j]);
+    for (int j = 0; j < NP; ++j) fx_mac(acc, F.G[i * NP + j], xh[j], xl[j]);
+  }
 #pragma unroll
   for (int s = 0; s < S; ++s) fx_mac(acc, F.h[s][i], P[s][0], P[s][1]);
   return fx_round(acc);
@@ -97,10 +131,15 @@ __device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int
 // The block's scale read (thread 0, one barrier; every warp reading it itself measured 4%
 // slower) and the slot bookkeeping of the block holding element 0: it clears the slot of
 // u^{n+2} and, for an int64 output, sets u^{n+1}'s scale and NaN mark.
-template <bool FIN, bool FOUT, class I, class SH>
+template <bool FIN, bool FOUT, bool BLK, class I, class SH>
 __device__ __forceinline__ FxScale fx_block_scale(const I &inst, int e0, int rel, SH &sh) {
   if (threadIdx.x == 0) {
-    const FxScale sc = fx_scale(inst.fx, inst.meta[0] + rel, FIN);
+    int hb = 0, he = 0;
+    if constexpr (BLK) {
+      hb = inst.fxh;
+      he = inst.fxe;
+    }
+    const FxScale sc = fx_scale(inst.fx, inst.meta[0] + rel, FIN, hb, he);
     sh.sc = sc;
     if (e0 == 0) {
       FxSlot &c = inst.fx[fx_clear(sc.slot)];
@@ -145,11 +184,15 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
                                            FixedShared<EPT, S> &sh) {
   constexpr bool FIN = (FMT & kFmtInFixed) != 0;
   constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
+  constexpr bool BLK = (FMT & kFmtBasis) != 0;
+  static_assert(FOUT || !BLK, "a block-basis state is written as int64");
   const double *uin_d = static_cast<const double *>(uin_);
   const long long *uin_q = static_cast<const long long *>(uin_);
   const int K = inst.K;
   const int t = threadIdx.x;
   const StepFixed &F = inst.sf;
+  const double *Tbi = nullptr;
+  if constexpr (BLK) Tbi = inst.Tbi;
 
   // loads first: they do not depend on the scale
   double hd[NP];
@@ -168,7 +211,7 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
     if (FIN) load_elem<NP>(uin_q, K, e < K ? e : K - 1, uq[h]);
     else load_elem<NP>(uin_d, K, e < K ? e : K - 1, ud[h]);
   }
-  const FxScale sc = fx_block_scale<FIN, FOUT>(inst, e0, rel, sh);
+  const FxScale sc = fx_block_scale<FIN, FOUT, BLK>(inst, e0, rel, sh);
   if (FIN && sc.shift != 0) {   // block-uniform: the field grew past 2^57 or shrank
 #pragma unroll
     for (int j = 0; j < NP; ++j) hq[j] = fx_rescale(hq[j], sc.shift);
@@ -182,7 +225,7 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
     int xh[NP], xl[NP];
     long long p;
     FxAcc own[S - 1];
-    fx_own<NP, FIN, S>(F, hd, hq, sc, p, own, xh, xl);
+    fx_own<NP, FIN, S, BLK>(F, Tbi, hd, hq, sc, p, own, xh, xl);
     fx_publish(sh, t, p, own);
   }
   int xh[EPT][NP], xl[EPT][NP];
@@ -190,7 +233,7 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
   for (int h = 0; h < EPT; ++h) {
     long long p;
     FxAcc own[S - 1];
-    fx_own<NP, FIN, S>(F, ud[h], uq[h], sc, p, own, xh[h], xl[h]);
+    fx_own<NP, FIN, S, BLK>(F, Tbi, ud[h], uq[h], sc, p, own, xh[h], xl[h]);
     fx_publish(sh, t + h * kTile + S, p, own);
   }
   __syncthreads();
@@ -206,7 +249,7 @@ __device__ __forceinline__ void fixed_body(const I &inst, const void *__restrict
     long long *oq = static_cast<long long *>(uout_) + (size_t)e;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-      const long long y = fx_row<NP, S>(F, i, xh[h], xl[h], P);
+      const long long y = fx_row<NP, S, BLK>(F, i, xh[h], xl[h], P);
       if (FOUT) {
         if (e < K) {
           *oq = y;
@@ -241,11 +284,15 @@ __device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__res
                                                 FixedShared<2, S> &sh) {
   constexpr bool FIN = (FMT & kFmtInFixed) != 0;
   constexpr bool FOUT = (FMT & kFmtOutFixed) != 0;
+  constexpr bool BLK = (FMT & kFmtBasis) != 0;
+  static_assert(FOUT || !BLK, "a block-basis state is written as int64");
   const double *uin_d = static_cast<const double *>(uin_);
   const long long *uin_q = static_cast<const long long *>(uin_);
   const int K = inst.K;
   const int t = threadIdx.x;
   const StepFixed &F = inst.sf;
+  const double *Tbi = nullptr;
+  if constexpr (BLK) Tbi = inst.Tbi;
   double hd[NP];
   long long hq[NP];
   if (t < S) {
@@ -271,7 +318,7 @@ __device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__res
       ud[1][j] = v.y;
     }
   }
-  const FxScale sc = fx_block_scale<FIN, FOUT>(inst, e0, rel, sh);
+  const FxScale sc = fx_block_scale<FIN, FOUT, BLK>(inst, e0, rel, sh);
   if (FIN && sc.shift != 0) {
 #pragma unroll
     for (int j = 0; j < NP; ++j) hq[j] = fx_rescale(hq[j], sc.shift);
@@ -284,7 +331,7 @@ __device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__res
     int xh[NP], xl[NP];
     long long p;
     FxAcc own[S - 1];
-    fx_own<NP, FIN, S>(F, hd, hq, sc, p, own, xh, xl);
+    fx_own<NP, FIN, S, BLK>(F, Tbi, hd, hq, sc, p, own, xh, xl);
     fx_publish(sh, t, p, own);
   }
   int xh[2][NP], xl[2][NP];
@@ -293,8 +340,8 @@ __device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__res
   {
     long long pO;
     FxAcc ownO[S - 1];
-    fx_own<NP, FIN, S>(F, ud[0], uq[0], sc, pE, ownE, xh[0], xl[0]);
-    fx_own<NP, FIN, S>(F, ud[1], uq[1], sc, pO, ownO, xh[1], xl[1]);
+    fx_own<NP, FIN, S, BLK>(F, Tbi, ud[0], uq[0], sc, pE, ownE, xh[0], xl[0]);
+    fx_own<NP, FIN, S, BLK>(F, Tbi, ud[1], uq[1], sc, pO, ownO, xh[1], xl[1]);
     fx_publish(sh, 2 * t + S, pE, ownE);
     fx_publish(sh, 2 * t + S + 1, pO, ownO);
   }
@@ -320,7 +367,7 @@ __device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__res
   for (int i = 0; i < NP; ++i) {
     long long y[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) y[h] = fx_row<NP, S>(F, i, xh[h], xl[h], P[h]);
+    for (int h = 0; h < 2; ++h) y[h] = fx_row<NP, S, BLK>(F, i, xh[h], xl[h], P[h]);
     if (FOUT) {
       if (ok) {
         *reinterpret_cast<longlong2 *>(oq) = make_longlong2(y[0], y[1]);
@@ -341,11 +388,15 @@ __device__ __forceinline__ void fixed_body_pair(const I &inst, const void *__res
 }
 
 // One element per thread runs at full occupancy (8 blocks of 256 threads per SM, at most 32
-// registers); two per thread keep 64 registers for the second element's values.
+// registers); two per thread keep 48 registers for the second element's values (five
+// blocks per SM: 2% faster than four with 64 registers on the large mesh). The five-stage
+// step keeps more channel scalars live and takes one block fewer per SM.
 template <int NP, int EPT, int FMT, int S>
-__global__ void __launch_bounds__(kTile, EPT == 1 ? 8 : 4)
+__global__ void __launch_bounds__(kTile, EPT == 1 ? (S == 3 ? 8 : 6) : (S == 3 ? 5 : 4))
     k_step_fixed(const Inst inst, const void *__restrict__ uin, void *__restrict__ uout, int rel) {
   __shared__ FixedShared<EPT, S> sh;
+  pdl_wait();   // the face kernel before it corrects u^n near the PE faces
+  pdl_trigger();
   if constexpr (EPT == 2)
     fixed_body_pair<NP, FMT, S>(inst, uin, uout, blockIdx.x * (kTile * 2), rel, sh);
   else
@@ -444,42 +495,74 @@ __global__ void k_fixed_to_fp64(const long long *__restrict__ X, double *__restr
     u[i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : fx_to_double(X[i], sigma);
 }
 
+// The same for a block-basis state, element by element: u = Tb w with the coordinates w_j =
+// X_j 2^sigma rounded to FP64 first.
+template <int NP>
+__global__ void __launch_bounds__(256) k_fixed_to_fp64_basis(const Inst I, const long long *__restrict__ X,
+                                                             int slot) {
+  const int sigma = I.fx[slot].sigma;
+  const bool bad = I.fx[slot].E >= 2047;
+  const int K = I.K;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < K; e += gridDim.x * blockDim.x) {
+    double w[NP];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) w[j] = fx_to_double(X[(size_t)j * K + e], sigma);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+      double a = I.Tb[i * NP] * w[0];
+#pragma unroll
+      for (int j = 1; j < NP; ++j) a = fma(I.Tb[i * NP + j], w[j], a);
+      I.u[(size_t)i * K + e] = bad ? __longlong_as_double(0x7ff8000000000000ll) : a;
+    }
+  }
+}
+
 template <int NP, int FMT, int S>
-void fixed_np_fmt_s(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s) {
+cudaError_t fixed_np_fmt_s(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s,
+                           bool pdl) {
   if (I.ept == 2)
-    k_step_fixed<NP, 2, FMT, S><<<(unsigned)((I.K + 2 * kTile - 1) / (2 * kTile)), kTile, 0, s>>>(I, uin, uout, rel);
-  else
-    k_step_fixed<NP, 1, FMT, S><<<(unsigned)((I.K + kTile - 1) / kTile), kTile, 0, s>>>(I, uin, uout, rel);
+    return launch_maybe_pdl(k_step_fixed<NP, 2, FMT, S>,
+                            dim3((unsigned)((I.K + 2 * kTile - 1) / (2 * kTile))), dim3(kTile), s,
+                            pdl, I, uin, uout, rel);
+  return launch_maybe_pdl(k_step_fixed<NP, 1, FMT, S>, dim3((unsigned)((I.K + kTile - 1) / kTile)),
+                          dim3(kTile), s, pdl, I, uin, uout, rel);
 }
 
 template <int NP, int FMT>
-void fixed_np_fmt(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s) {
-  if (I.ns == kMaxCS) fixed_np_fmt_s<NP, FMT, kMaxCS>(I, uin, uout, rel, s);
-  else fixed_np_fmt_s<NP, FMT, 3>(I, uin, uout, rel, s);
+cudaError_t fixed_np_fmt(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s,
+                         bool pdl) {
+  if (I.ns == kMaxCS) return fixed_np_fmt_s<NP, FMT, kMaxCS>(I, uin, uout, rel, s, pdl);
+  return fixed_np_fmt_s<NP, FMT, 3>(I, uin, uout, rel, s, pdl);
 }
 
+// Single-instance steps write int64 (the state stays in fixed point until it is read).
 template <int NP>
-void fixed_np(const Inst &I, const void *uin, void *uout, int rel, int fmt, cudaStream_t s) {
-  switch (fmt & 3) {
-    case 0: fixed_np_fmt<NP, 0>(I, uin, uout, rel, s); break;
-    case 1: fixed_np_fmt<NP, 1>(I, uin, uout, rel, s); break;
-    case 2: fixed_np_fmt<NP, 2>(I, uin, uout, rel, s); break;
-    default: fixed_np_fmt<NP, 3>(I, uin, uout, rel, s); break;
+cudaError_t fixed_np(const Inst &I, const void *uin, void *uout, int rel, int fmt,
+                     cudaStream_t s, bool pdl) {
+  switch (fmt) {
+    case kFmtOutFixed: return fixed_np_fmt<NP, kFmtOutFixed>(I, uin, uout, rel, s, pdl);
+    case kFmtInFixed | kFmtOutFixed:
+      return fixed_np_fmt<NP, kFmtInFixed | kFmtOutFixed>(I, uin, uout, rel, s, pdl);
+    case kFmtBasis | kFmtOutFixed:
+      return fixed_np_fmt<NP, kFmtBasis | kFmtOutFixed>(I, uin, uout, rel, s, pdl);
+    default:
+      return fixed_np_fmt<NP, kFmtBasis | kFmtInFixed | kFmtOutFixed>(I, uin, uout, rel, s, pdl);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int rel, int fmt,
-                              cudaStream_t s) {
+                              cudaStream_t s, bool pdl) {
+  if (!(fmt & kFmtOutFixed)) return cudaErrorInvalidValue;
+  fmt = (fmt & (kFmtInFixed | kFmtOutFixed)) | (I.basis ? kFmtBasis : 0);
   switch (I.Np) {
-    case 2: fixed_np<2>(I, uin, uout, rel, fmt, s); break;
-    case 3: fixed_np<3>(I, uin, uout, rel, fmt, s); break;
-    case 4: fixed_np<4>(I, uin, uout, rel, fmt, s); break;
-    case 5: fixed_np<5>(I, uin, uout, rel, fmt, s); break;
+    case 2: return fixed_np<2>(I, uin, uout, rel, fmt, s, pdl);
+    case 3: return fixed_np<3>(I, uin, uout, rel, fmt, s, pdl);
+    case 4: return fixed_np<4>(I, uin, uout, rel, fmt, s, pdl);
+    case 5: return fixed_np<5>(I, uin, uout, rel, fmt, s, pdl);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
@@ -526,12 +609,24 @@ cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_
   return cudaGetLastError();
 }
 
-cudaError_t launch_fixed_to_fp64(const long long *X, double *u, size_t n, const FxSlot *fx,
-                                int64_t step, cudaStream_t s) {
+cudaError_t launch_fixed_to_fp64(const Inst &I, const long long *X, int64_t step,
+                                 cudaStream_t s) {
+  const int slot = (int)(step % 3);
+  const size_t n = I.basis ? (size_t)I.K : (size_t)I.K * I.Np;
   const size_t want = (n + 255) / 256;
   const size_t cap = 8 * (size_t)sm_count();
   const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
-  k_fixed_to_fp64<<<grid, 256, 0, s>>>(X, u, n, fx, (int)(step % 3));
+  if (!I.basis) {
+    k_fixed_to_fp64<<<grid, 256, 0, s>>>(X, I.u, n, I.fx, slot);
+  } else {
+    switch (I.Np) {
+      case 2: k_fixed_to_fp64_basis<2><<<grid, 256, 0, s>>>(I, X, slot); break;
+      case 3: k_fixed_to_fp64_basis<3><<<grid, 256, 0, s>>>(I, X, slot); break;
+      case 4: k_fixed_to_fp64_basis<4><<<grid, 256, 0, s>>>(I, X, slot); break;
+      case 5: k_fixed_to_fp64_basis<5><<<grid, 256, 0, s>>>(I, X, slot); break;
+      default: return cudaErrorInvalidValue;
+    }
+  }
   return cudaGetLastError();
 }
 

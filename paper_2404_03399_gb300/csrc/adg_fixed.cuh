@@ -8,7 +8,9 @@
 // n/2 + 1/2 units of its last place, 2^-57 of the field's largest value per unit).
 //
 // Representation: a field at step n is either FP64 or int64 values X with one scale for the
-// whole field, value = X 2^sigma. A step first brings its input to the working scale sigma'
+// whole field, value = X 2^sigma (for a single instance the int64 values are the coordinates
+// of each element in the block basis of Inst.Tb, with the headroom of Inst.fxh / fxe; the
+// bounds below are those of nodal values, hb = he = 0). A step first brings its input to the working scale sigma'
 // at which |X| < 2^57:
 //   FP64 input: sigma' = En - 1079, En the largest biased FP64 exponent over u^n
 //               (|x| < 2^(En - 1022)), X = round(x 2^-sigma');
@@ -150,20 +152,33 @@ struct FxScale {
   bool bad;    // u^n holds a NaN or an infinity
 };
 
-__device__ __forceinline__ FxScale fx_scale(const FxSlot *fx, int64_t n, bool fin) {
+// hb, he: the headroom of a block-basis state (Inst.fxh, Inst.fxe; 0 for nodal values):
+// int64 inputs are brought below 2^(57 - hb), FP64 inputs converted at 2^(E - 1079 + he).
+__device__ __forceinline__ FxScale fx_scale(const FxSlot *fx, int64_t n, bool fin, int hb = 0,
+                                            int he = 0) {
   FxScale s;
   s.slot = (int)(n % 3);
   const FxSlot &cur = fx[s.slot];
   s.bad = cur.E >= 2047;
   if (!fin) {
-    s.sigma = cur.E - 1079;
+    s.sigma = cur.E - 1079 + he;
     s.shift = 0;
   } else {
     const unsigned long long M = cur.mag;   // bit length of max |X| is at most b + 1
-    s.shift = M ? (64 - __clzll((long long)M)) - 56 : 0;
+    s.shift = M ? (64 - __clzll((long long)M)) - 56 + hb : 0;
     s.sigma = cur.sigma + s.shift;
   }
   return s;
+}
+
+// Waits until the kernel this one was launched as a programmatic dependent of (launch_maybe_pdl)
+// has completed and its writes are visible; returns at once for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the chain (launched with the attribute) start launching its blocks
+// once every block of this one has passed this point. Called after pdl_wait, so the kernel
+// before this one has completed when the next one starts.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 }
 
 __device__ __forceinline__ int fx_next(int slot) { return slot == 2 ? 0 : slot + 1; }

@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace adg {
@@ -76,17 +77,22 @@ struct StepConsts {
 // The StepConsts in fixed point for the integer composed step: each coefficient c
 // (|c| < 2) is C = round(c 2^58), split into limbs C = ch 2^29 + cl with balanced
 // -2^28 <= cl < 2^28 (int2 {ch, cl}).
+// In the block basis (Inst.basis) the first row of each 2 x 2 block of G is (1, 2^-k_m),
+// exactly: gs[m] = 29 - k_m, and that row is formed by shifts and adds (no multiplies).
 struct StepFixed {
   int2 G[kMaxNp * kMaxNp];
   int2 r[kMaxCS][kMaxNp];
   int2 h[kMaxCS][kMaxNp];
   int2 k[kMaxCS][kMaxCS];
+  int gs[kMaxNp / 2];
 };
 
 // Formats of a fixed-point composed step (launch_fused_step's fmt): bit 0 the input, bit 1
-// the output is int64 fixed point; FP64 otherwise.
+// the output is int64 fixed point; FP64 otherwise. Bit 2 (set by launch_fixed_step from
+// Inst.basis): the int64 state holds block-basis coordinates (below).
 constexpr int kFmtInFixed = 1;
 constexpr int kFmtOutFixed = 2;
+constexpr int kFmtBasis = 4;
 
 // Scale of a field at one step for the fixed-point composed step (adg_fixed.cuh): E is the
 // largest biased FP64 exponent (2047: a NaN or infinity is present), sigma and mag the scale
@@ -121,6 +127,16 @@ struct alignas(16) Inst {
   // face_fx is set (every |R| < 2)
   int2 Rf[kMaxCS][kMaxCS + 1][kMaxNp];
   int face_fx;
+  // fused == 2, single instance: the int64 state holds w = Tbi u, the coordinates of u in a
+  // basis (columns of Tb) in which every composed-step matrix G is block diagonal (2 x 2
+  // blocks (2m, 2m+1), a 1 x 1 block last for odd Np) with block rows 2m equal to
+  // (1, 2^-k_m), and whose even columns have right trace 1, odd columns 0 (so u_p = sum of
+  // the even w_j); sf and Rf then hold the coefficients in these coordinates (G Tb-similar,
+  // h and R multiplied by Tbi, r by Tb). int64 inputs are
+  // kept below 2^(57 - fxh); an FP64 input at step n is converted at scale
+  // 2^(E - 1079 + fxe) (fxe >= fxh + log2 of the row sums of Tbi).
+  int basis, fxh, fxe, pad0_;
+  double Tb[kMaxNp * kMaxNp], Tbi[kMaxNp * kMaxNp];
   int ns;               // stages per step: the ring holds [R][ns][P] stage-input traces; the
                         // composed steps' S (3, or 5 for the five-stage scheme)
   int ls;               // 1: a 2N low-storage scheme (k_lsrk_stage, coefficients lsA, lsB)
@@ -215,8 +231,12 @@ cudaError_t launch_advance(int64_t *meta, int nmeta_stride, int ninst, int64_t b
 // to u, bit 1 then forms step rel's differences from u and the ring (ring write, I.fd). fu: u
 // is int64, else FP64; fin_prev: step rel-1 read int64.
 constexpr int kFaceApply = 1, kFaceDiff = 2;
+// pdl (this and launch_fixed_step): launched as a programmatic dependent of the kernel before
+// it in the stream (that kernel must be a k_step_fixed or k_face_step of the same chunk): its
+// blocks may start while that kernel drains, and wait (griddepcontrol.wait) for its completion
+// before they touch anything it writes.
 cudaError_t launch_face_step(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
-                             cudaStream_t s);
+                             cudaStream_t s, bool pdl = false);
 // Composed step uin -> uout (rel: step offset from meta[0]) and, with PE faces, the fix-up
 // of the elements next to each PE face with the delayed / AT flux. fmt (fixed-point step,
 // fused == 2, only): bit 0 the input, bit 1 the output is int64 fixed point (adg_fixed.cuh);
@@ -225,7 +245,23 @@ cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int re
                               cudaStream_t s, bool with_fixup = true, int fmt = 0);
 // The fixed-point composed step alone (adg_fixed.cu).
 cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int rel, int fmt,
-                              cudaStream_t s);
+                              cudaStream_t s, bool pdl = false);
+// A launch with the programmatic-stream-serialization attribute when pdl is set.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_maybe_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                             bool pdl, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 // What the batched fixed-point step reads of an instance when the coefficients are shared
 // (below): its fields u, v1, v2, step counter, scale slots, K and Np.
 struct BatchLite {
@@ -280,10 +316,11 @@ cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const De
 // index `step`: all three slots cleared, then E of slot step % 3 = largest biased exponent.
 cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,
                                cudaStream_t s);
-// The FP64 field u (n values) of the int64 fixed-point field X of step `step`, from the scale
-// slot step % 3 of fx (NaN everywhere when it marks a NaN or infinity).
-cudaError_t launch_fixed_to_fp64(const long long *X, double *u, size_t n, const FxSlot *fx,
-                                 int64_t step, cudaStream_t s);
+// The FP64 field I.u of the int64 fixed-point field X of step `step`, from the scale slot
+// step % 3 of I.fx (NaN everywhere when it marks a NaN or infinity); u = Tb w element by
+// element when I.basis is set.
+cudaError_t launch_fixed_to_fp64(const Inst &I, const long long *X, int64_t step,
+                                 cudaStream_t s);
 // Copies v1 into u for every instance (after an odd number of FP64 batched composed steps, or
 // a single fixed-point step).
 cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,

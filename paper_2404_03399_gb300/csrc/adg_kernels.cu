@@ -584,10 +584,21 @@ __device__ __forceinline__ FaceTraces<S> face_traces(const Inst &I, const double
   return t;
 }
 
+// The right trace of an int64 element: its last value, or for block-basis coordinates the
+// sum of the even ones (exact).
+template <int NP>
+__device__ __forceinline__ long long fx_trace(const Inst &I, const long long *X) {
+  if (!I.basis) return X[NP - 1];
+  long long p = 0;
+#pragma unroll
+  for (int j = 0; j < NP; j += 2) p += X[j];
+  return p;
+}
+
 // From int64 values X at scale 2^sig: the same sums in the composed step's two-limb integer
 // arithmetic (StepFixed coefficients) at a scale chosen from these S elements alone
-// (|X'| < 2^56, so the result does not depend on any other face), then rounded to FP64. Off
-// the FP64 pipe but for S conversions.
+// (|X'| < 2^(56 - fxh), so the result does not depend on any other face), then rounded to
+// FP64. Off the FP64 pipe but for S conversions.
 template <int NP, int S>
 __device__ __forceinline__ FaceTraces<S> face_traces_fixed(const Inst &I, const long long (*X)[NP],
                                                            int sig) {
@@ -598,9 +609,15 @@ __device__ __forceinline__ FaceTraces<S> face_traces_fixed(const Inst &I, const 
 #pragma unroll
     for (int i = 0; i < NP; ++i) m |= fx_mag(X[w][i]);
   const int L = m ? 64 - __clzll((long long)m) : 0;   // |X| < 2^(L+1)
-  const int sh = L > 55 ? L - 55 : 0;
+  const int top = 55 - I.fxh;
+  const int sh = L > top ? L - top : 0;
   long long Yp[S];
-  Yp[0] = fx_rescale(X[0][NP - 1], sh);
+  {
+    long long Xs[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) Xs[i] = fx_rescale(X[0][i], sh);
+    Yp[0] = fx_trace<NP>(I, Xs);
+  }
 #pragma unroll
   for (int w = 1; w < S; ++w) {
     const int ns = w;   // channels 1 .. w of element e-S+w
@@ -612,7 +629,12 @@ __device__ __forceinline__ FaceTraces<S> face_traces_fixed(const Inst &I, const 
     for (int t = 0; t < S - 1; ++t)
       if (t < ns) fx_split(Yp[t], ph[t], pl[t]);
     long long Y[S];
-    Y[0] = fx_rescale(X[w][NP - 1], sh);
+    {
+      long long Xs[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i) Xs[i] = fx_rescale(X[w][i], sh);
+      Y[0] = fx_trace<NP>(I, Xs);
+    }
 #pragma unroll
     for (int s = 1; s <= ns; ++s) {
       FxAcc acc;
@@ -626,7 +648,7 @@ __device__ __forceinline__ FaceTraces<S> face_traces_fixed(const Inst &I, const 
     for (int s = 0; s <= ns; ++s) Yp[s] = Y[s];
   }
   FaceTraces<S> t;
-  t.T[0] = pow2_scale((double)X[S - 1][NP - 1], sig);
+  t.T[0] = pow2_scale((double)fx_trace<NP>(I, X[S - 1]), sig);
 #pragma unroll
   for (int s = 1; s < S; ++s) t.T[s] = pow2_scale((double)Yp[s], sig + sh);
   return t;
@@ -842,6 +864,12 @@ __global__ void __launch_bounds__(32 * (S + 1)) k_face_step(const Inst I, void *
   int m = e - 1 + w;   // this thread's element; warp 0 also reads e-S .. e-2
   if (m < 0) m += K;
   if (m >= K) m -= K;
+  // The delay, AT coefficients and ring levels of steps before n do not depend on the step
+  // kernel before this one: loaded before waiting for it (programmatic launch).
+  FaceLoads<S> fl;
+  if (diff) face_loads<S>(I, j, n, fl);
+  pdl_wait();
+  pdl_trigger();
   long long V[S][NP];   // raw 64-bit values (int64, or the bits of FP64): e-S .. e-2, own
   {
     const long long *q = uq + m;
@@ -864,8 +892,6 @@ __global__ void __launch_bounds__(32 * (S + 1)) k_face_step(const Inst I, void *
       }
     }
   }
-  FaceLoads<S> fl;
-  if (diff) face_loads<S>(I, j, n, fl);
   if (mode & kFaceApply) {
     const double *dd = I.fd + (size_t)((n - 1) & 1) * S * P + S * (size_t)j;
     double d[S];
@@ -875,7 +901,7 @@ __global__ void __launch_bounds__(32 * (S + 1)) k_face_step(const Inst I, void *
       d[s] = dd[s];
       any = any || nonzero(d[s]);
     }
-    const FxScale sc = fx_scale(I.fx, n - 1, fin_prev != 0);
+    const FxScale sc = fx_scale(I.fx, n - 1, fin_prev != 0, I.fxh, I.fxe);
     if (any && !sc.bad) {
       bool done = false;
       if (fu && I.face_fx) {
@@ -904,15 +930,31 @@ __global__ void __launch_bounds__(32 * (S + 1)) k_face_step(const Inst I, void *
         }
       }
       if (!done) {
-        // FP64: an FP64 output, or a difference beyond the integer range
+        // FP64: an FP64 output, or a difference beyond the integer range (block-basis
+        // coordinates: the nodal correction times Tbi)
         const StepConsts &C = I.st;
+        double c[NP];
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-          double c = C.R[0][w][i] * d[0];
+          c[i] = C.R[0][w][i] * d[0];
 #pragma unroll
-          for (int s = 1; s < S; ++s) c = fma(C.R[s][w][i], d[s], c);
-          if (fu) V[S - 1][i] += llrint(pow2_scale(c, -sc.sigma));
-          else V[S - 1][i] = __double_as_longlong(__dadd_rn(__longlong_as_double(V[S - 1][i]), c));
+          for (int s = 1; s < S; ++s) c[i] = fma(C.R[s][w][i], d[s], c[i]);
+        }
+        if (fu && I.basis) {
+          double cb[NP];
+#pragma unroll
+          for (int i = 0; i < NP; ++i) {
+            cb[i] = I.Tbi[i * NP] * c[0];
+#pragma unroll
+            for (int k = 1; k < NP; ++k) cb[i] = fma(I.Tbi[i * NP + k], c[k], cb[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < NP; ++i) c[i] = cb[i];
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          if (fu) V[S - 1][i] += llrint(pow2_scale(c[i], -sc.sigma));
+          else V[S - 1][i] = __double_as_longlong(__dadd_rn(__longlong_as_double(V[S - 1][i]), c[i]));
         }
       }
       int emax = 0;
@@ -1382,29 +1424,24 @@ cudaError_t fused_np(const Inst &I, const void *uin, void *uout, int rel, cudaSt
 }
 }  // namespace
 
-cudaError_t launch_face_step(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
-                             cudaStream_t s) {
-  const unsigned g = (unsigned)((I.P + 31) / 32);   // 32 faces per block of S + 1 warps
-  if (I.ns == 3) {
-    switch (I.Np) {
-      case 2: k_face_step<2, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      case 3: k_face_step<3, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      case 4: k_face_step<4, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      case 5: k_face_step<5, 3><<<g, 128, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      default: return cudaErrorInvalidValue;
-    }
-  } else if (I.ns == kMaxCS) {
-    switch (I.Np) {
-      case 2: k_face_step<2, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      case 3: k_face_step<3, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      case 4: k_face_step<4, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      case 5: k_face_step<5, kMaxCS><<<g, 192, 0, s>>>(I, u, rel, fu, fin_prev, mode); break;
-      default: return cudaErrorInvalidValue;
-    }
-  } else {
-    return cudaErrorInvalidValue;
+template <int S>
+cudaError_t face_step_s(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
+                        cudaStream_t s, bool pdl) {
+  const dim3 g((unsigned)((I.P + 31) / 32)), b(32 * (S + 1));   // 32 faces per block
+  switch (I.Np) {
+    case 2: return launch_maybe_pdl(k_face_step<2, S>, g, b, s, pdl, I, u, rel, fu, fin_prev, mode);
+    case 3: return launch_maybe_pdl(k_face_step<3, S>, g, b, s, pdl, I, u, rel, fu, fin_prev, mode);
+    case 4: return launch_maybe_pdl(k_face_step<4, S>, g, b, s, pdl, I, u, rel, fu, fin_prev, mode);
+    case 5: return launch_maybe_pdl(k_face_step<5, S>, g, b, s, pdl, I, u, rel, fu, fin_prev, mode);
+    default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
+}
+
+cudaError_t launch_face_step(const Inst &I, void *u, int rel, int fu, int fin_prev, int mode,
+                             cudaStream_t s, bool pdl) {
+  if (I.ns == 3) return face_step_s<3>(I, u, rel, fu, fin_prev, mode, s, pdl);
+  if (I.ns == kMaxCS) return face_step_s<kMaxCS>(I, u, rel, fu, fin_prev, mode, s, pdl);
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_fused_step(const Inst &I, const void *uin, void *uout, int rel,
