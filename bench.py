@@ -44,11 +44,10 @@ WORKLOAD = dict(name=_W16M.name, pde=_W16M.pde, K=_W16M.K, p=_W16M.p, P=_W16M.P,
                 modes=(list(_W16M.modes.amp), list(_W16M.modes.kappa), list(_W16M.modes.phase),
                        _W16M.modes.offset))
 # Algorithmic work of the kernels that can run the bench step (the composed SSP-RK3 step of
-# upwind advection, Np^2 + 5 Np + 3 multiply-adds per element and step):
+# upwind advection, Np^2 + 5 Np + 3 multiply-adds per element and step in nodal values):
 #  - fixed-point integer step (picked where the coefficients fit, as here): each
-#    multiply-add is three 32 x 32 -> 64-bit integer products, 3 (Np^2 + 5 Np + 3) per element
-#    (117 at p = 3), plus 3 for forming the left neighbour's v1_p^{e-2}; the bound is the
-#    integer multiply pipe;
+#    multiply-add is three 32 x 32 -> 64-bit integer products; the bound is the integer
+#    multiply pipe (counts below);
 #  - FP64 composed step: 2 (Np^2 + 5 Np + 3) / Np flop per DOF-step (19.5 at p = 3);
 #  - staged FP64 kernels: 2 (Np + 2) flop per DOF-stage.
 NP = WORKLOAD["p"] + 1
@@ -667,6 +666,22 @@ def profile_case(name: str) -> dict:
     import torch
     import paper_2404_03399_gb300 as adg
     w = WORKLOAD
+    if name == "batched":
+        # the 512-instance batched workload, two elements per thread (the tuner's choice
+        # outside the profiler), 2 + 4 steps
+        ws = batched_instances()
+        cfgs = [adg.Config(pde="advection", K=v.K, p=v.p, P=v.P, a=v.a, cfl=v.cfl, mode=v.mode,
+                           L=v.L, q=v.q, seed=v.seed, ept=2) for v in ws]
+        u0s = [adg.eval_modes(c, v.modes.amp, v.modes.kappa, v.modes.phase)
+               for c, v in zip(cfgs, ws)]
+        b = adg.BatchSolver(cfgs, u0s)
+        del u0s
+        for k in (2, 4):
+            b.step(k)
+        torch.cuda.synchronize()
+        out = {"case": name, "instances": len(ws), "variant": list(b.variant(0)), "steps": 6}
+        b.close()
+        return out
     if name == "burgers_1m":
         b = BURGERS_1M
         cfg = adg.Config(pde="burgers", K=b.K, p=b.p, P=b.P, cfl=0.005, mode="at", L=b.L, q=b.q,
@@ -762,7 +777,8 @@ def main():
     ap.add_argument("--extra-only", choices=["lsrk4", "viscous", "euler"], default=None,
                     help="only time that extra workload (the LSRK4 scheme on the large mesh, "
                          "viscous Burgers, Euler) and print its dict (for profiling runs)")
-    ap.add_argument("--profile", choices=["fixed_4m", "fixed_16m", "lsrk4_4m", "burgers_1m"],
+    ap.add_argument("--profile", choices=["fixed_4m", "fixed_16m", "lsrk4_4m", "burgers_1m",
+                                          "batched"],
                     default=None,
                     help="run a few steps of a case for ncu captures and print its dict: "
                          "advection K = 2^22 (the large workload's PE size, delays and AT order) "
@@ -852,8 +868,8 @@ def main():
     arithmetic = ("58-bit block fixed point: int64 values at one scale per field and step "
                   "(unit 2^-57 of the field's largest value; a sum of n products is off by less "
                   "than n/2 + 1/2 units), the state kept in int64 from step to step"
-                  + (" as coordinates in the block basis of the element operator (one bit of "
-                     "headroom; cond_inf of the basis 10.6 at p = 3)" if basis else "")
+                  + (" as coordinates in the block basis of the element operator (cond_inf "
+                     "15.1 at p = 3, which scales the rounding bound)" if basis else "")
                   + "; FP64 in the PE-face stage differences and where the state is read") \
         if variant == "fixed" else "FP64"
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,

@@ -217,10 +217,10 @@ int adg_get_variant(adg_ctx *c, int32_t index, int32_t *variant_out, int32_t *ep
 /* The coordinates of instance `index`'s fixed-point state (not a paper quantity): *basis_out =
  * 1 when the int64 state holds each element's coordinates w = T^-1 u in a basis of invariant
  * subspaces of the element operator, in which the step matrix G is block diagonal (2 x 2
- * blocks: each output row takes two of G's multiply-adds instead of Np). A single instance on
- * COMPOSED_FIXED uses it where the basis is well conditioned (cond_inf(T) <= 64: p = 1, 2,
- * 3); 0 for nodal values, a batch, or another variant. The FP64 state read through the API is
- * nodal either way. basis_out must not be NULL. */
+ * blocks, the first row of each an exact shift-add). COMPOSED_FIXED uses it, for single
+ * instances and batched ones, where the basis is well conditioned (cond_inf(T) <= 64: p = 1,
+ * 2, 3); 0 for nodal values or another variant. The FP64 state read through the API is nodal
+ * either way. basis_out must not be NULL. */
 int adg_get_fixed_basis(adg_ctx *c, int32_t index, int32_t *basis_out);
 
 /*

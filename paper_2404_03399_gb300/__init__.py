@@ -274,6 +274,12 @@ class BatchSolver:
         check(load().adg_get_variant(self._ctx, int(i), C.byref(v), C.byref(e)), self._ctx)
         return {1: "staged", 2: "composed", 3: "fixed"}[v.value], e.value
 
+    def fixed_basis(self, i: int) -> bool:
+        """True when instance i's fixed-point state holds block-basis coordinates."""
+        b = C.c_int32()
+        check(load().adg_get_fixed_basis(self._ctx, int(i), C.byref(b)), self._ctx)
+        return bool(b.value)
+
     def integral(self, i: int) -> float:
         """Discrete integral (dx/2) sum_e w^T u^e of instance i's current state."""
         v = C.c_double()

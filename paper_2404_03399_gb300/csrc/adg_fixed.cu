@@ -5,6 +5,8 @@
 // the coordinates of each element in the block basis of the element operator (Inst.basis,
 // FMT bit kFmtBasis): G is then block diagonal with 2 x 2 blocks whose first rows are shifts
 // and adds, and the right trace is the sum of the even coordinates.
+#include <type_traits>
+
 #include "adg_device.cuh"
 #include "adg_fixed.cuh"
 
@@ -111,10 +113,17 @@ __device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int
   if (BLK) {
     const int j0 = i & ~1;
     if (i == j0 && j0 + 1 < NP) {
-      const int sh = F.gs[i >> 1];
-      acc.a += (long long)((unsigned long long)(long long)xh[i] << 29) + xl[i];
-      acc.a += (long long)((unsigned long long)(long long)xh[i + 1] << sh);
-      acc.b += (long long)xl[i + 1] << sh;
+      // 64-bit values from 32-bit funnel shifts of the limbs (sign words s0, s1)
+      const unsigned sh = (unsigned)F.gs[i >> 1];
+      const unsigned h0 = (unsigned)xh[i], s0 = (unsigned)(xh[i] >> 31);
+      const unsigned h1 = (unsigned)xh[i + 1], s1 = (unsigned)(xh[i + 1] >> 31);
+      const unsigned l1 = (unsigned)xl[i + 1];
+      const long long x0 = fx_join(__funnelshift_l(0u, h0, 29) | (unsigned)xl[i],
+                                   __funnelshift_l(h0, s0, 29));   // X_i
+      const long long t1 = fx_join(__funnelshift_l(0u, h1, sh), __funnelshift_l(h1, s1, sh));
+      const long long b1 = fx_join(__funnelshift_l(0u, l1, sh), __funnelshift_l(l1, 0u, sh));
+      acc.a += x0 + t1;
+      acc.b += b1;
     } else {
       fx_mac(acc, F.G[i * NP + j0], xh[j0], xl[j0]);
       if (j0 + 1 < NP) fx_mac(acc, F.G[i * NP + j0 + 1], xh[j0 + 1], xl[j0 + 1]);
@@ -409,13 +418,16 @@ __device__ __forceinline__ void *inst_field(const Inst &I, int sel) {
 
 // Batched fixed-point steps: block b takes work item (instance, first element); the
 // instance's descriptor is staged in shared memory; src / dst select u (0), v1 (1) or v2 (2)
-// of every instance, FMT their formats.
+// of every instance, FMT their formats (int64 output), the instance's own flag the block
+// basis.
 template <int FMT>
 __global__ void __launch_bounds__(kTile)
     k_batch_fixed(const Inst *__restrict__ insts, const int2 *__restrict__ work, int src, int dst,
                   int rel) {
   __shared__ __align__(16) unsigned char smem[sizeof(Inst)];
   __shared__ FixedShared<1, 3> sh;
+  pdl_wait();   // the fix-up before it corrects u^n near the PE faces
+  pdl_trigger();
   const int2 w = work[blockIdx.x];
   {
     const int4 *from = reinterpret_cast<const int4 *>(insts + w.x);
@@ -427,20 +439,36 @@ __global__ void __launch_bounds__(kTile)
   const Inst &I = *reinterpret_cast<const Inst *>(smem);
   const void *uin = inst_field(I, src);
   void *uout = inst_field(I, dst);
+  constexpr int FB = FMT | kFmtBasis;
   switch (I.Np) {
-    case 2: fixed_body<2, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
-    case 3: fixed_body<3, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
-    case 4: fixed_body<4, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
-    default: fixed_body<5, 1, FMT, 3>(I, uin, uout, w.y, rel, sh); break;
+    case 2:
+      if (I.basis) fixed_body<2, 1, FB, 3>(I, uin, uout, w.y, rel, sh);
+      else fixed_body<2, 1, FMT, 3>(I, uin, uout, w.y, rel, sh);
+      break;
+    case 3:
+      if (I.basis) fixed_body<3, 1, FB, 3>(I, uin, uout, w.y, rel, sh);
+      else fixed_body<3, 1, FMT, 3>(I, uin, uout, w.y, rel, sh);
+      break;
+    case 4:
+      if (I.basis) fixed_body<4, 1, FB, 3>(I, uin, uout, w.y, rel, sh);
+      else fixed_body<4, 1, FMT, 3>(I, uin, uout, w.y, rel, sh);
+      break;
+    default:
+      if (I.basis) fixed_body<5, 1, FB, 3>(I, uin, uout, w.y, rel, sh);
+      else fixed_body<5, 1, FMT, 3>(I, uin, uout, w.y, rel, sh);
+      break;
   }
 }
 
-// The fields fixed_body reads, with the coefficients taken from a kernel parameter.
+// The fields fixed_body reads, with the coefficients (and the block basis of the degree)
+// taken from a kernel parameter.
 struct LiteView {
   int K;
   const int64_t *meta;
   FxSlot *fx;
   const StepFixed &sf;
+  int fxh, fxe;
+  const double *Tbi;
 };
 
 // Batched fixed-point steps with the coefficients shared per degree (BatchUniform): block b
@@ -448,28 +476,34 @@ struct LiteView {
 // ahead of the data instead of a work-list entry and then the instance) and takes EPT kTile
 // elements.
 template <int FMT, int EPT>
-__global__ void __launch_bounds__(kTile, EPT == 1 ? 6 : (EPT == 2 ? 4 : 2))
+__global__ void __launch_bounds__(kTile, EPT == 1 ? 6 : (EPT == 2 ? 5 : 2))
     k_batch_fixed_uniform(const BatchLite *__restrict__ items, int src, int dst, int rel,
                           const UniformFixed uf) {
   __shared__ FixedShared<EPT, 3> sh;
   const BatchLite L = items[blockIdx.x];
+  pdl_wait();   // the fix-up before it corrects u^n near the PE faces
+  pdl_trigger();
   const int2 w = make_int2(0, L.e0);
   const void *uin = src == 0 ? L.f[0] : (src == 1 ? L.f[1] : L.f[2]);
   void *uout = dst == 0 ? L.f[0] : (dst == 1 ? L.f[1] : L.f[2]);
-  if constexpr (EPT == 2) {
-    switch (L.Np) {
-      case 2: fixed_body_pair<2, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
-      case 3: fixed_body_pair<3, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
-      case 4: fixed_body_pair<4, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
-      default: fixed_body_pair<5, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
+  // one body per degree, in the block basis where the degree has one
+  auto body = [&](auto np) {
+    constexpr int NP = decltype(np)::value;
+    const int d = NP - 2;
+    const LiteView V{L.K, L.meta, L.fx, uf.sf[d], uf.fxh[d], uf.fxe[d], uf.Tbi[d]};
+    if constexpr (EPT == 2) {
+      if (uf.basis[d]) fixed_body_pair<NP, FMT | kFmtBasis, 3>(V, uin, uout, w.y, rel, sh);
+      else fixed_body_pair<NP, FMT, 3>(V, uin, uout, w.y, rel, sh);
+    } else {
+      if (uf.basis[d]) fixed_body<NP, EPT, FMT | kFmtBasis, 3>(V, uin, uout, w.y, rel, sh);
+      else fixed_body<NP, EPT, FMT, 3>(V, uin, uout, w.y, rel, sh);
     }
-  } else {
-    switch (L.Np) {
-      case 2: fixed_body<2, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[0]}, uin, uout, w.y, rel, sh); break;
-      case 3: fixed_body<3, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[1]}, uin, uout, w.y, rel, sh); break;
-      case 4: fixed_body<4, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[2]}, uin, uout, w.y, rel, sh); break;
-      default: fixed_body<5, EPT, FMT, 3>(LiteView{L.K, L.meta, L.fx, uf.sf[3]}, uin, uout, w.y, rel, sh); break;
-    }
+  };
+  switch (L.Np) {
+    case 2: body(std::integral_constant<int, 2>()); break;
+    case 3: body(std::integral_constant<int, 3>()); break;
+    case 4: body(std::integral_constant<int, 4>()); break;
+    default: body(std::integral_constant<int, 5>()); break;
   }
 }
 
@@ -565,48 +599,41 @@ cudaError_t launch_fixed_step(const Inst &I, const void *uin, void *uout, int re
   }
 }
 
+// Batched steps write int64 (fmt has kFmtOutFixed; the state stays in fixed point).
 cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
-                                    int src, int dst, int fmt, int rel, cudaStream_t s) {
+                                    int src, int dst, int fmt, int rel, cudaStream_t s, bool pdl) {
   if (nwork <= 0) return cudaSuccess;
-  switch (fmt & 3) {
-    case 0: k_batch_fixed<0><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
-    case 1: k_batch_fixed<1><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
-    case 2: k_batch_fixed<2><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
-    default: k_batch_fixed<3><<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src, dst, rel); break;
-  }
-  return cudaGetLastError();
+  if (!(fmt & kFmtOutFixed)) return cudaErrorInvalidValue;
+  if (fmt & kFmtInFixed)
+    return launch_maybe_pdl(k_batch_fixed<kFmtInFixed | kFmtOutFixed>, dim3(nwork), dim3(kTile), s,
+                            pdl, insts_dev, work_dev, src, dst, rel);
+  return launch_maybe_pdl(k_batch_fixed<kFmtOutFixed>, dim3(nwork), dim3(kTile), s, pdl, insts_dev,
+                          work_dev, src, dst, rel);
 }
 
+namespace {
+template <int EPT>
+cudaError_t batch_uniform_ept(const BatchUniform &bu, int src, int dst, int fmt, int rel,
+                              cudaStream_t s, bool pdl) {
+  const dim3 g(bu.nitems), b(kTile);
+  if (fmt & kFmtInFixed)
+    return launch_maybe_pdl(k_batch_fixed_uniform<kFmtInFixed | kFmtOutFixed, EPT>, g, b, s, pdl,
+                            bu.items_dev, src, dst, rel, bu.uf);
+  return launch_maybe_pdl(k_batch_fixed_uniform<kFmtOutFixed, EPT>, g, b, s, pdl, bu.items_dev, src,
+                          dst, rel, bu.uf);
+}
+}  // namespace
+
 cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_dev, int nwork,
-                                       int src, int dst, int fmt, int rel, cudaStream_t s) {
+                                       int src, int dst, int fmt, int rel, cudaStream_t s,
+                                       bool pdl) {
   (void)work_dev;
   (void)nwork;
-  const int n = bu.nitems;
-  if (n <= 0) return cudaSuccess;
-  const BatchLite *l = bu.items_dev;
-  if (bu.ept == 4) {
-    switch (fmt & 3) {
-      case 0: k_batch_fixed_uniform<0, 4><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      case 1: k_batch_fixed_uniform<1, 4><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      case 2: k_batch_fixed_uniform<2, 4><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      default: k_batch_fixed_uniform<3, 4><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-    }
-  } else if (bu.ept == 2) {
-    switch (fmt & 3) {
-      case 0: k_batch_fixed_uniform<0, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      case 1: k_batch_fixed_uniform<1, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      case 2: k_batch_fixed_uniform<2, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      default: k_batch_fixed_uniform<3, 2><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-    }
-  } else {
-    switch (fmt & 3) {
-      case 0: k_batch_fixed_uniform<0, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      case 1: k_batch_fixed_uniform<1, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      case 2: k_batch_fixed_uniform<2, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-      default: k_batch_fixed_uniform<3, 1><<<n, kTile, 0, s>>>(l, src, dst, rel, bu.uf); break;
-    }
-  }
-  return cudaGetLastError();
+  if (bu.nitems <= 0) return cudaSuccess;
+  if (!(fmt & kFmtOutFixed)) return cudaErrorInvalidValue;
+  if (bu.ept == 4) return batch_uniform_ept<4>(bu, src, dst, fmt, rel, s, pdl);
+  if (bu.ept == 2) return batch_uniform_ept<2>(bu, src, dst, fmt, rel, s, pdl);
+  return batch_uniform_ept<1>(bu, src, dst, fmt, rel, s, pdl);
 }
 
 cudaError_t launch_fixed_to_fp64(const Inst &I, const long long *X, int64_t step,

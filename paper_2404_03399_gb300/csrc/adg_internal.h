@@ -127,7 +127,7 @@ struct alignas(16) Inst {
   // face_fx is set (every |R| < 2)
   int2 Rf[kMaxCS][kMaxCS + 1][kMaxNp];
   int face_fx;
-  // fused == 2, single instance: the int64 state holds w = Tbi u, the coordinates of u in a
+  // fused == 2 (where the basis is accepted): the int64 state holds w = Tbi u, the coordinates of u in a
   // basis (columns of Tb) in which every composed-step matrix G is block diagonal (2 x 2
   // blocks (2m, 2m+1), a 1 x 1 block last for odd Np) with block rows 2m equal to
   // (1, 2^-k_m), and whose even columns have right trace 1, odd columns 0 (so u_p = sum of
@@ -278,6 +278,9 @@ struct BatchLite {
 // step instead of shared-memory loads.
 struct UniformFixed {
   StepFixed sf[kMaxNp - 1];
+  // per degree: the block basis as in Inst (basis, fxh, fxe, Tbi)
+  int basis[kMaxNp - 1], fxh[kMaxNp - 1], fxe[kMaxNp - 1], pad_[kMaxNp - 1];
+  double Tbi[kMaxNp - 1][kMaxNp * kMaxNp];
 };
 struct BatchUniform {
   const BatchLite *items_dev;   // one record per work item (the instance's fields and e0) of
@@ -293,12 +296,14 @@ struct BatchUniform {
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
                                     bool fixed, int rel, cudaStream_t s,
-                                    const BatchUniform *bu = nullptr);
+                                    const BatchUniform *bu = nullptr, bool pdl = false);
 cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_dev, int nwork,
-                                       int src, int dst, int fmt, int rel, cudaStream_t s);
+                                       int src, int dst, int fmt, int rel, cudaStream_t s,
+                                       bool pdl = false);
 // The batched fixed-point step alone (adg_fixed.cu).
 cudaError_t launch_batch_fixed_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
-                                    int src, int dst, int fmt, int rel, cudaStream_t s);
+                                    int src, int dst, int fmt, int rel, cudaStream_t s,
+                                    bool pdl = false);
 // Seeded delay-table rows on the device, identical to the host generator: entry (row r,
 // face j) is the bin of output (first + r) P + j of SplitMix64(seed), u = (z >> 11) 2^-53,
 // bin = the first b with u < edges[b] (else L - 1), compared in integers as

@@ -704,31 +704,17 @@ __device__ __forceinline__ void face_diffs(const Inst &I, int j, const FaceLoads
 // AT sums and the stage-by-stage traces are FP64; with an int64 input the synchronous traces,
 // and with an int64 output the correction itself, are formed in the step's integer limbs (as in
 // k_face_step, so batched and single runs agree bit for bit).
-template <int NP>
+template <int NP, bool FOUT>
 __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__restrict__ uin,
-                                           void *__restrict__ uout, int rel, int fmt) {
+                                           void *__restrict__ uout, int rel, bool fin) {
   const int K = I.K;
   const int e = j * I.Kpe;
   const int64_t n = I.meta[0] + rel;
-  const bool fin = (fmt & kFmtInFixed) != 0, fout = (fmt & kFmtOutFixed) != 0;
+  const bool fout = FOUT;
   const StepConsts &S = I.st;
-  FxScale sc{0, 0, 0, false};
-  int sig_in = 0;
-  if (I.fused == 2) {
-    sc = fx_scale(I.fx, n, fin);
-    sig_in = I.fx[sc.slot].sigma;
-  }
-  // elements e-3 .. e-1 of u^n (w = 0 .. 2) and the composed result of e-1 .. e+2 (w = 0 .. 3)
-  int mw[4];
-  for (int w = 0; w < 4; ++w) {
-    int m = e - 1 + w;
-    if (m < 0) m += K;
-    if (m >= K) m -= K;
-    mw[w] = m;
-  }
+  // Loads that do not depend on the step kernel before this one (its input u^n, the delay, AT
+  // coefficients and earlier ring levels) come before waiting for it (programmatic launch).
   long long Xr[3][NP];   // raw 64-bit values of e-3 .. e-1: int64, or the bits of FP64
-  long long Xq[4][NP];
-  double Yd[4][NP];
   for (int w = 0; w < 3; ++w) {
     int m = e - 3 + w;
     if (m < 0) m += K;
@@ -739,6 +725,26 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       q += K;
     }
   }
+  FaceLoads<3> fl;
+  face_loads<3>(I, j, n, fl);
+  pdl_wait();
+  pdl_trigger();
+  FxScale sc{0, 0, 0, false};
+  int sig_in = 0;
+  if (I.fused == 2) {
+    sc = fx_scale(I.fx, n, fin, I.fxh, I.fxe);
+    sig_in = I.fx[sc.slot].sigma;
+  }
+  // the composed result of e-1 .. e+2 (w = 0 .. 3)
+  int mw[4];
+  for (int w = 0; w < 4; ++w) {
+    int m = e - 1 + w;
+    if (m < 0) m += K;
+    if (m >= K) m -= K;
+    mw[w] = m;
+  }
+  long long Xq[4][NP];
+  double Yd[4][NP];
   for (int w = 0; w < 4; ++w) {
     if (fout) {
       const long long *q = static_cast<const long long *>(uout) + mw[w];
@@ -756,8 +762,6 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
       }
     }
   }
-  FaceLoads<3> fl;
-  face_loads<3>(I, j, n, fl);
   FaceTraces<3> tr;
   if (fin) {
     tr = face_traces_fixed<NP, 3>(I, Xr, sig_in);
@@ -807,11 +811,26 @@ __device__ __forceinline__ void fixup_body(const Inst &I, int j, const void *__r
   }
   for (int w = 0; w < 4; ++w) {   // elements e-1 .. e+2
     if (fout) {
+      // FP64 sum (block-basis coordinates: the nodal correction times Tbi)
+      double c[NP];
+#pragma unroll
+      for (int i = 0; i < NP; ++i)
+        c[i] = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
+      if (I.basis) {
+        double cb[NP];
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          cb[i] = I.Tbi[i * NP] * c[0];
+#pragma unroll
+          for (int k = 1; k < NP; ++k) cb[i] = fma(I.Tbi[i * NP + k], c[k], cb[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < NP; ++i) c[i] = cb[i];
+      }
       long long *q = static_cast<long long *>(uout) + mw[w];
 #pragma unroll
       for (int i = 0; i < NP; ++i) {
-        const double c = fma(S.R[2][w][i], d2, fma(S.R[1][w][i], d1, S.R[0][w][i] * d0));
-        const long long X = Xq[w][i] + llrint(pow2_scale(c, -sc.sigma));
+        const long long X = Xq[w][i] + llrint(pow2_scale(c[i], -sc.sigma));
         *q = X;
         q += K;
         mag |= fx_mag(X);
@@ -1002,7 +1021,8 @@ __global__ void __launch_bounds__(64) k_step_fixup(const Inst I, const void *__r
                                                    void *__restrict__ uout, int rel, int fmt) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= I.P) return;
-  fixup_body<NP>(I, j, uin, uout, rel, fmt);
+  if (fmt & kFmtOutFixed) fixup_body<NP, true>(I, j, uin, uout, rel, (fmt & kFmtInFixed) != 0);
+  else fixup_body<NP, false>(I, j, uin, uout, rel, (fmt & kFmtInFixed) != 0);
 }
 
 // Batched composed steps: block b takes work item (instance, first element); `parity`
@@ -1033,9 +1053,11 @@ __global__ void __launch_bounds__(kTile) k_batch_fused(const Inst *__restrict__ 
 // The PE-face corrections of a batched composed step, one thread per PE face of any instance:
 // fflat lists (instance, face) for every PE face of every instance, so the threads of a block
 // are all busy however few faces an instance has.
+// FOUT: the step wrote int64 (fixed point), else FP64 (the FP64 composed step).
+template <bool FOUT>
 __global__ void __launch_bounds__(64) k_batch_fixup(const Inst *__restrict__ insts,
                                                     const int2 *__restrict__ fflat, int nflat,
-                                                    int src, int dst, int fmt, int rel) {
+                                                    int src, int dst, bool fin, int rel) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= nflat) return;
   const int2 w = fflat[t];
@@ -1044,10 +1066,10 @@ __global__ void __launch_bounds__(64) k_batch_fixup(const Inst *__restrict__ ins
   const void *uin = src == 0 ? (const void *)I.u : (src == 1 ? (const void *)I.v1 : (const void *)I.v2);
   void *uout = dst == 0 ? (void *)I.u : (dst == 1 ? (void *)I.v1 : (void *)I.v2);
   switch (I.Np) {
-    case 2: fixup_body<2>(I, j, uin, uout, rel, fmt); break;
-    case 3: fixup_body<3>(I, j, uin, uout, rel, fmt); break;
-    case 4: fixup_body<4>(I, j, uin, uout, rel, fmt); break;
-    default: fixup_body<5>(I, j, uin, uout, rel, fmt); break;
+    case 2: fixup_body<2, FOUT>(I, j, uin, uout, rel, fin); break;
+    case 3: fixup_body<3, FOUT>(I, j, uin, uout, rel, fin); break;
+    case 4: fixup_body<4, FOUT>(I, j, uin, uout, rel, fin); break;
+    default: fixup_body<5, FOUT>(I, j, uin, uout, rel, fin); break;
   }
 }
 
@@ -1499,18 +1521,30 @@ cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const De
 
 cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                     const int2 *fwork_dev, int nfwork, int src, int dst, int fmt,
-                                    bool fixed, int rel, cudaStream_t s, const BatchUniform *bu) {
+                                    bool fixed, int rel, cudaStream_t s, const BatchUniform *bu,
+                                    bool pdl) {
+  cudaError_t e;
   if (fixed) {
-    cudaError_t e = bu ? launch_batch_fixed_uniform(*bu, work_dev, nwork, src, dst, fmt, rel, s)
-                       : launch_batch_fixed_step(insts_dev, work_dev, nwork, src, dst, fmt, rel, s);
+    e = bu ? launch_batch_fixed_uniform(*bu, work_dev, nwork, src, dst, fmt, rel, s, pdl)
+           : launch_batch_fixed_step(insts_dev, work_dev, nwork, src, dst, fmt, rel, s, pdl);
     if (e != cudaSuccess) return e;
   } else {
     fmt = 0;
     k_batch_fused<<<nwork, kTile, 0, s>>>(insts_dev, work_dev, src == 1 ? 1 : 0);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  if (nfwork > 0)
-    k_batch_fixup<<<(unsigned)((nfwork + 63) / 64), 64, 0, s>>>(insts_dev, fwork_dev, nfwork, src,
-                                                              dst, fmt, rel);
+  if (nfwork > 0) {
+    // a programmatic dependent of the step kernel: its input, delay and ring loads overlap it
+    const dim3 g((unsigned)((nfwork + 63) / 64)), b(64);
+    const bool fin = (fmt & kFmtInFixed) != 0;
+    if (fmt & kFmtOutFixed)
+      e = launch_maybe_pdl(k_batch_fixup<true>, g, b, s, true, insts_dev, fwork_dev, nfwork, src,
+                           dst, fin, rel);
+    else
+      e = launch_maybe_pdl(k_batch_fixup<false>, g, b, s, true, insts_dev, fwork_dev, nfwork, src,
+                           dst, fin, rel);
+    if (e != cudaSuccess) return e;
+  }
   return cudaGetLastError();
 }
 
