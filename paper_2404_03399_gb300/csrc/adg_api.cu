@@ -592,11 +592,10 @@ bool null_vector(const std::vector<ld> &A, int n, cld lam, std::vector<cld> &v) 
   return true;
 }
 
-// Two indices share a block: (2m, 2m+1), and the last index alone for odd n.
-bool same_block(int i, int j) { return (i >> 1) == (j >> 1); }
+// The blocks of the block basis: A = {0, 1} and B = {2, .., n-1} (a pair for n = 4, one
+// vector for n = 3, a triple for n = 5); the first vector of each block has right trace 1.
+bool same_block(int i, int j) { return (i < 2) == (j < 2); }
 
-// The block-diagonality of X in the block basis: largest off-block entry against the
-// largest entry.
 bool block_diagonal(const std::vector<ld> &X, int n, ld tol) {
   ld mx = 0, off = 0;
   for (int i = 0; i < n; ++i)
@@ -673,40 +672,118 @@ bool block_basis(const Ops &o, std::vector<ld> &T, std::vector<ld> &Ti) {
       reals.push_back(re);
     }
   }
+  std::vector<std::vector<ld>> pairs_re, pairs_im;   // the complex pairs
+  for (size_t k = 0; k + 1 < span.size(); k += 2) {
+    pairs_re.push_back(span[k]);
+    pairs_im.push_back(span[k + 1]);
+  }
   for (auto &r : reals) span.push_back(r);
-  if ((int)span.size() != n) return false;
-  T.assign(n * n, 0.0L);
   auto dot = [&](const std::vector<ld> &a, const std::vector<ld> &b) {
     ld s = 0;
     for (int k = 0; k < n; ++k) s += a[k] * b[k];
     return s;
   };
-  for (int m = 0; m + 1 < n; m += 2) {
-    std::vector<ld> q1 = span[m], q2 = span[m + 1];
-    const ld n1 = sqrtl(dot(q1, q1));
-    if (!(n1 > 0)) return false;
-    for (auto &x : q1) x /= n1;
-    const ld pr = dot(q1, q2);
-    for (int k = 0; k < n; ++k) q2[k] -= pr * q1[k];
-    const ld n2 = sqrtl(dot(q2, q2));
-    if (!(n2 > 1e-9L * sqrtl(dot(span[m + 1], span[m + 1])))) return false;
-    for (auto &x : q2) x /= n2;
-    const ld t1 = q1[p], t2 = q2[p], tt = t1 * t1 + t2 * t2;
+  // One block from the vectors spanning an invariant subspace (columns c0 .. of T): an
+  // orthonormal basis Q of it (Gram-Schmidt), traces t = Q^T e_p; the first column Q t / |t|^2
+  // (trace 1), the others Q c / |t| for an orthonormal basis c of the complement of t (trace 0).
+  auto put_block = [&](std::vector<std::vector<ld>> vs, int c0) {
+    const int d = (int)vs.size();
+    for (int a = 0; a < d; ++a) {
+      const ld n0 = sqrtl(dot(vs[a], vs[a]));
+      for (int b = 0; b < a; ++b) {
+        const ld pr = dot(vs[b], vs[a]);
+        for (int k = 0; k < n; ++k) vs[a][k] -= pr * vs[b][k];
+      }
+      const ld na = sqrtl(dot(vs[a], vs[a]));
+      if (!(na > 1e-9L * n0)) return false;
+      for (auto &x : vs[a]) x /= na;
+    }
+    std::vector<ld> t(d);
+    ld tt = 0;
+    for (int a = 0; a < d; ++a) {
+      t[a] = vs[a][p];
+      tt += t[a] * t[a];
+    }
     if (!(tt > 1e-12L)) return false;
+    const ld tn = sqrtl(tt);
+    // orthonormal complement of t in R^d (Gram-Schmidt of the unit vectors against t / |t|)
+    std::vector<std::vector<ld>> cs;
+    std::vector<ld> th(d);
+    for (int a = 0; a < d; ++a) th[a] = t[a] / tn;
+    for (int e = 0; e < d && (int)cs.size() < d - 1; ++e) {
+      std::vector<ld> c(d, 0.0L);
+      c[e] = 1;
+      ld pr = th[e];
+      for (int a = 0; a < d; ++a) c[a] -= pr * th[a];
+      for (auto &o2 : cs) {
+        ld q = 0;
+        for (int a = 0; a < d; ++a) q += o2[a] * c[a];
+        for (int a = 0; a < d; ++a) c[a] -= q * o2[a];
+      }
+      ld cn = 0;
+      for (int a = 0; a < d; ++a) cn += c[a] * c[a];
+      cn = sqrtl(cn);
+      if (cn < 0.5L) continue;
+      for (auto &x : c) x /= cn;
+      cs.push_back(c);
+    }
+    if ((int)cs.size() != d - 1) return false;
     for (int k = 0; k < n; ++k) {
-      T[k * n + m] = (t1 * q1[k] + t2 * q2[k]) / tt;
-      T[k * n + m + 1] = (t2 * q1[k] - t1 * q2[k]) / tt;
+      ld f = 0;
+      for (int a = 0; a < d; ++a) f += t[a] * vs[a][k];
+      T[k * n + c0] = f / tt;
+      for (int b = 0; b + 1 < d; ++b) {
+        ld g = 0;
+        for (int a = 0; a < d; ++a) g += cs[b][a] * vs[a][k];
+        T[k * n + c0 + 1 + b] = g / tn;
+      }
+    }
+    return true;
+  };
+  // the layouts: n = 2: one pair; n = 3: a pair (a complex pair, else two real vectors) and
+  // the remaining real vector; n = 4: two pairs; n = 5: a complex pair and a triple (the other
+  // complex pair with the real vector), whichever pair goes first gives the smaller cond_inf
+  std::vector<std::vector<std::vector<ld>>> layouts;   // candidate: block A vectors, block B
+  if ((int)span.size() != n) return false;
+  if (n == 5) {
+    if (pairs_re.size() != 2 || reals.size() != 1) return false;
+    for (int f = 0; f < 2; ++f)
+      layouts.push_back({pairs_re[f], pairs_im[f], pairs_re[1 - f], pairs_im[1 - f], reals[0]});
+  } else {
+    layouts.push_back(span);
+  }
+  std::vector<ld> bestT, bestTi;
+  ld bestc = -1;
+  for (auto &vs : layouts) {
+    T.assign(n * n, 0.0L);
+    bool ok = put_block({vs[0], vs[1]}, 0);
+    if (ok && n > 2) {
+      std::vector<std::vector<ld>> rest(vs.begin() + 2, vs.end());
+      if (rest.size() == 1) {
+        const std::vector<ld> &v = rest[0];
+        ok = fabsl(v[p]) > 1e-6L * sqrtl(dot(v, v));
+        if (ok)
+          for (int k = 0; k < n; ++k) T[k * n + 2] = v[k] / v[p];
+      } else {
+        ok = put_block(rest, 2);
+      }
+    }
+    if (!ok) continue;
+    for (int j = 0; j < n; ++j) T[p * n + j] = (j == 0 || j == 2) ? 1.0L : 0.0L;
+    std::vector<ld> Tinv;
+    if (!invert(T, n, Tinv)) continue;
+    if (!block_diagonal(similar(Tinv, A, T, n), n, 1e-13L)) continue;
+    const ld cnd = cond_inf(T, Tinv, n);
+    if (bestc < 0 || cnd < bestc) {
+      bestc = cnd;
+      bestT = T;
+      bestTi = Tinv;
     }
   }
-  if (n % 2) {
-    const std::vector<ld> &v = span[n - 1];
-    if (!(fabsl(v[p]) > 1e-6L * sqrtl(dot(v, v)))) return false;
-    for (int k = 0; k < n; ++k) T[k * n + n - 1] = v[k] / v[p];
-  }
-  for (int j = 0; j < n; ++j) T[p * n + j] = (j % 2 == 0) ? 1.0L : 0.0L;
-  if (!invert(T, n, Ti)) return false;
-  if (!block_diagonal(similar(Ti, A, T, n), n, 1e-13L)) return false;
-  return cond_inf(T, Ti, n) <= 64.0L;
+  if (bestc < 0) return false;
+  T = bestT;
+  Ti = bestTi;
+  return bestc <= 64.0L;
 }
 
 // Composed step constants (StepConsts in adg_internal.h) of upwind advection with a > 0, in
@@ -937,7 +1014,7 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
     // row of G exactly (1, 2^-k) (k the nearest power of two, so beta is near 1): a row of
     // shifts and adds in the kernel.
     std::vector<ld> Ts = Tm, Tis;
-    for (int m = 0; m + 1 < Np && basis; m += 2) {
+    for (int m = 0; m <= (Np == 4 ? 2 : 0) && basis; m += 2) {   // the 2 x 2 blocks
       const ld n11 = Gc[m * Np + m] - 1.0L, n12 = Gc[m * Np + m + 1];
       const int k = fabsl(n12) > 0 ? (int)lroundl(-log2l(fabsl(n12))) : -1;
       if (k < 1 || k > 27) {
@@ -955,7 +1032,7 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
     if (basis && invert(Ts, Np, Tis) && cond_inf(Ts, Tis, Np) <= 64.0L) {
       const Mat Gs = similar(Tis, Gl, Ts, Np);
       bool rows = block_diagonal(Gs, Np, 1e-13L);
-      for (int m = 0; m + 1 < Np; m += 2)
+      for (int m = 0; m <= (Np == 4 ? 2 : 0); m += 2)
         rows = rows && fabsl(Gs[m * Np + m] - 1.0L) < 1e-15L &&
                fabsl(Gs[m * Np + m + 1] - ldexpl(1.0L, gshift[m / 2] - 29)) <
                    1e-15L * ldexpl(1.0L, gshift[m / 2] - 29);
@@ -963,7 +1040,7 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
         Tm = Ts;
         Tim = Tis;
         Gc = Gs;
-        for (int m = 0; m + 1 < Np; m += 2) {
+        for (int m = 0; m <= (Np == 4 ? 2 : 0); m += 2) {
           Gc[m * Np + m] = 1.0L;
           Gc[m * Np + m + 1] = ldexpl(1.0L, gshift[m / 2] - 29);
         }
@@ -1035,7 +1112,7 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
   // are sums of about nb coordinates, take B_s < 7.9 (below 2^60, so the high limb
   // X >> 29 fits 32 bits), every sum then checked with its terms' own bounds. The smallest
   // headroom hb that passes every check (0 for nodal values).
-  const int nb = basis ? (Np + 1) / 2 : 1;
+  const int nb = basis ? (Np > 2 ? 2 : 1) : 1;
   auto checks = [&](int hb) {
     const ld gin = ldexpl(1.0L, -hb), g0 = nb * gin, blim = basis ? 7.9L : 1.999L;
     bool good = true;
@@ -1076,7 +1153,7 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
   }
   h.fixed_ok = ok && sums;
   if (basis)
-    for (int m = 0; m < Np / 2; ++m) F.gs[m] = gshift[m];
+    for (int m = 0; m < (Np == 4 ? 2 : 1); ++m) F.gs[m] = gshift[m];
   if (basis && h.fixed_ok) {
     // FP64 inputs: w = T^-1 u in FP64 is below ||T^-1||_inf 2^(E - 1022) (1 + 2^-40)
     ld nti = 0;

@@ -33,7 +33,8 @@ __device__ __forceinline__ long long fx_in(double x, long long X, const FxScale 
 // p = the element's right trace, own[s-1] = the own parts r_s . u of its channel scalars
 // (unrounded sums, s = 1 .. S-1), and the limbs of its values for the output rows. BLK: the
 // values are block-basis coordinates w (an FP64 input is transformed, w = Tbi u, in FP64
-// before its conversion) and the right trace is the exact sum of the even coordinates.
+// before its conversion) and the right trace is the exact sum w_0 + w_2 (the first
+// coordinate of each block).
 template <int NP, bool FIN, int S, bool BLK>
 __device__ __forceinline__ void fx_own(const StepFixed &F, const double *Tbi, const double *ud,
                                        const long long *uq, const FxScale &sc, long long &p,
@@ -57,7 +58,7 @@ __device__ __forceinline__ void fx_own(const StepFixed &F, const double *Tbi, co
     fx_split(X, xh[j], xl[j]);
 #pragma unroll
     for (int s = 1; s < S; ++s) fx_mac(own[s - 1], F.r[s][j], xh[j], xl[j]);
-    if (BLK ? (j % 2 == 0) : (j == NP - 1)) p += X;
+    if (BLK ? (j == 0 || j == 2) : (j == NP - 1)) p += X;
   }
 }
 
@@ -102,17 +103,17 @@ __device__ __forceinline__ void fx_left_channels(const StepFixed &F, const Fixed
   for (int s = 0; s < S; ++s) fx_split(Yp[s], P[s][0], P[s][1]);
 }
 
-// u'^e = G u^e + sum_s h_s P_s for output row i. BLK: G's entries of row i's block only; the
-// first row of a 2 x 2 block is (1, 2^-k), whose products, X_i and
-// xh_{i+1} 2^(29-k) + xl_{i+1} 2^(29-k) 2^-29, are shifts (the same sums as the multiply-adds
-// with the limbs {2^29, 0} and {2^(29-k), 0}).
+// u'^e = G u^e + sum_s h_s P_s for output row i. BLK: G's entries of row i's block only
+// (blocks {0, 1} and {2, .., NP-1}); the first row of a 2 x 2 block is (1, 2^-k), whose
+// products, X_i and xh_{i+1} 2^(29-k) + xl_{i+1} 2^(29-k) 2^-29, are shifts (the same sums
+// as the multiply-adds with the limbs {2^29, 0} and {2^(29-k), 0}).
 template <int NP, int S, bool BLK>
 __device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int *xh, const int *xl,
                                             const int (*P)[2]) {
   FxAcc acc;
   if (BLK) {
-    const int j0 = i & ~1;
-    if (i == j0 && j0 + 1 < NP) {
+    const int j0 = i < 2 ? 0 : 2, j1 = i < 2 ? 2 : NP;   // the block [j0, j1)
+    if (i == j0 && j1 - j0 == 2) {
       // 64-bit values from 32-bit funnel shifts of the limbs (sign words s0, s1)
       const unsigned sh = (unsigned)F.gs[i >> 1];
       const unsigned h0 = (unsigned)xh[i], s0 = (unsigned)(xh[i] >> 31);
@@ -125,8 +126,8 @@ __device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int
       acc.a += x0 + t1;
       acc.b += b1;
     } else {
-      fx_mac(acc, F.G[i * NP + j0], xh[j0], xl[j0]);
-      if (j0 + 1 < NP) fx_mac(acc, F.G[i * NP + j0 + 1], xh[j0 + 1], xl[j0 + 1]);
+#pragma unroll
+      for (int j = j0; j < j1; ++j) fx_mac(acc, F.G[i * NP + j], xh[j], xl[j]);
     }
   } else {
 #pragma unroll

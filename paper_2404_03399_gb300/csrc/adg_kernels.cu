@@ -585,14 +585,11 @@ __device__ __forceinline__ FaceTraces<S> face_traces(const Inst &I, const double
 }
 
 // The right trace of an int64 element: its last value, or for block-basis coordinates the
-// sum of the even ones (exact).
+// sum of the first coordinate of each block, w_0 + w_2 (exact).
 template <int NP>
 __device__ __forceinline__ long long fx_trace(const Inst &I, const long long *X) {
   if (!I.basis) return X[NP - 1];
-  long long p = 0;
-#pragma unroll
-  for (int j = 0; j < NP; j += 2) p += X[j];
-  return p;
+  return NP > 2 ? X[0] + X[2] : X[0];
 }
 
 // From int64 values X at scale 2^sig: the same sums in the composed step's two-limb integer

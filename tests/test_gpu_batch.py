@@ -57,19 +57,10 @@ def _eligible_batch():
     return ws
 
 
-def _check_single(got, single, basis, steps, i, batch_basis=None):
-    """A batched instance against its single-instance run: bit-identical when both keep the
-    same coordinates (block basis at p <= 3 for fixed point, else nodal values). Where only the
-    single run keeps block-basis coordinates (a batch that runs another kind of step is not
-    compared this way) the two are the same scheme rounded differently: each step's sums are
-    off by less than (n/2 + 1/2) units of 2^-56 of the field (n <= 10 terms), times cond_inf of
-    the basis (<= 16 here) for the block-basis run, so below 4e-15 of the field's maximum per
-    step."""
-    if batch_basis is None or batch_basis == basis:
-        assert np.array_equal(got, single), f"instance {i} differs from its single run"
-    else:
-        d = np.max(np.abs(got - single)) / np.max(np.abs(single))
-        assert d < 4e-15 * steps, (i, d)
+def _check_single(got, single, i):
+    """A batched instance against its single-instance run: bit-identical (both keep the same
+    coordinates, the block basis of the element operator for fixed point)."""
+    assert np.array_equal(got, single), f"instance {i} differs from its single run"
 
 
 @pytest.mark.parametrize("kind,variant,single_variant", [
@@ -92,9 +83,8 @@ def test_small_batch_matches_oracle_and_single_runs(kind, variant, single_varian
         s.step(steps)
         single = s.state().cpu().numpy()
         dt = s.dt
-        basis = single_variant == "fixed" and s.fixed_basis
         s.close()
-        _check_single(got, single, basis, steps, i)
+        _check_single(got, single, i)
         q = w.q if w.mode == "at" else 1
         tbl = odelays.delay_table(w.seed, w.P, steps, w.L) if (w.mode != "sync" and w.P > 1) else None
         prob = dg.Problem(pde="advection", K=w.K, p=w.p, P=w.P, dt=dt, a=w.a,
@@ -158,8 +148,7 @@ def test_batch_of_fixed_point_steps_in_calls_of_one_and_two():
 def test_fixed_point_batch_with_different_coefficients_per_degree():
     # Two Courant numbers among instances of the same degree: the coefficients differ, so the
     # batch reads each instance's own coefficients (the general batched kernel) instead of one
-    # set per degree; every instance still equals its single-instance fixed-point run (up to
-    # the rounding of the single run's block basis).
+    # set per degree; every instance still equals its single-instance fixed-point run.
     ws = _eligible_batch()
     cfgs = [adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, a=w.a, cfl=0.002 + 0.001 * (i % 2),
                        mode=w.mode, L=w.L, q=w.q, seed=w.seed) for i, w in enumerate(ws)]
@@ -170,7 +159,7 @@ def test_fixed_point_batch_with_different_coefficients_per_degree():
     for i, c in enumerate(cfgs):
         s = adg.Solver(adg.Config(**{**c.__dict__, "variant": "fixed"}), u0s[i])
         s.step(40)
-        _check_single(b.state(i).cpu().numpy(), s.state().cpu().numpy(), s.fixed_basis, 40, i)
+        _check_single(b.state(i).cpu().numpy(), s.state().cpu().numpy(), i)
         s.close()
     b.close()
 
@@ -185,8 +174,7 @@ def test_batch_autotuner_choice_and_forced_choices_agree():
     # AUTO: the tuner times fixed point (256-, 512- and 1024-element work items), the FP64
     # composed step and the staged kernels and keeps the fastest; every forced choice runs the
     # same scheme. The fixed-point choices are bit-identical to each other and to the
-    # single-instance fixed-point run in nodal values (up to rounding where it keeps block-basis
-    # coordinates); every choice stays on the oracle.
+    # single-instance fixed-point run; every choice stays on the oracle.
     ws = _tuned_batch_workloads()
     assert sum(w.K for w in ws) >= 1 << 20
     steps = 12
@@ -220,9 +208,8 @@ def test_batch_autotuner_choice_and_forced_choices_agree():
         s.step(steps)
         single = s.state().cpu().numpy()
         dt = s.dt
-        basis = s.fixed_basis
         s.close()
-        _check_single(base[k], single, basis, steps, i)
+        _check_single(base[k], single, i)
         tbl = odelays.delay_table(w.seed, w.P, steps, w.L)
         prob = dg.Problem(pde="advection", K=w.K, p=w.p, P=w.P, dt=dt, a=w.a, mode="adg", q=w.q,
                           delays=tbl)
