@@ -72,10 +72,11 @@ FLOP_PER_DOF_STAGE_VISC = 6 * VISC_NP + 17
 # DRAM bytes per launch measured by ncu on this workload (read + write) for the kernel that
 # dominates the step, keyed by variant, elements per thread and coordinates; a kernel changed
 # since its counters were taken has no entry (null in the line). k_step_fixed, two per thread,
-# nodal values, int64 -> int64, K = 2^24: 537,010,176 B read + 488,685,824 B written (the
-# algorithmic 536,870,912 B each way; part of the written field is still in L2 when the
-# launch ends).
-TRAFFIC_BYTES_PER_LAUNCH = {"fixed/2/nodal": 537010176 + 488685824}
+# int64 -> int64, K = 2^24 (the algorithmic 536,870,912 B each way; part of the written field
+# is still in L2 when the launch ends): nodal values 537,010,176 B read + 488,685,824 B
+# written; block-basis coordinates 536,897,536 + 487,339,520 B.
+TRAFFIC_BYTES_PER_LAUNCH = {"fixed/2/nodal": 537010176 + 488685824,
+                            "fixed/2/basis": 536897536 + 487339520}
 # Algorithmic HBM bytes: read u^n, write u^{n+1} once per step: 16 B per DOF-step.
 BYTES_PER_DOF_STEP = 16
 # The staged SSP-RK3 step reads and writes 16 / 24 / 24 B per DOF in its three stages (the
