@@ -1557,6 +1557,15 @@ int sync_state(adg_ctx *c) {
 
 int launch_fused_steps(adg_ctx *c, int nsteps, int kind);
 
+// Steps are launched directly (not through CUDA graphs) from 2^20 DOF in all: a step there
+// takes hundreds of microseconds, and programmatic launches overlapped better outside a graph
+// (0.2315 -> 0.2276 ms per fixed-point step on the 2^26-DOF mesh).
+bool direct_launches(const adg_ctx *c) {
+  int64_t dof = 0;
+  for (const auto &h : c->inst) dof += (int64_t)h.I.K * h.I.Np;
+  return dof >= (int64_t(1) << 20);
+}
+
 int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkFP64) {
   if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps, kind);
   if (c->batch && c->batch_fixed) {
@@ -1634,7 +1643,12 @@ int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkFP64) {
       } else {
         const Inst &I = c->inst[0].I;
         if (I.visc) CK(adg::launch_ldg_q(I, s == 0 ? I.u : (s == 1 ? I.v1 : I.v2), s, rel, c->stream));
-        CK(adg::launch_stage(I, s, rel, c->stream));
+        // a programmatic dependent of the stage before it on runs launched without graphs
+        // (the first of the chunk follows other work; the viscous stage follows its q pass).
+        // Inside the graphs of small runs programmatic launches measured slower (the adjoint
+        // workload's forward 78 -> 95 ms), on the 2^20-element Burgers mesh 1.6% faster.
+        CK(adg::launch_stage(I, s, rel, c->stream,
+                             direct_launches(c) && !I.visc && (rel > 0 || s > 0)));
       }
     }
   }
@@ -2479,13 +2493,9 @@ int adg_step(adg_ctx *c, int64_t nsteps) {
   if (nsteps < 0) return fail(c, ADG_EINVAL, "nsteps must be >= 0");
   // the fixed-point step carries its int64 state from chunk to chunk and call to call
   const bool carry = fixed_state(c);
-  // CUDA graphs of G steps where launches dominate (below 2^20 DOF in all); larger runs
-  // launch chunks of up to kDirectChunk steps directly: a step there takes hundreds of
-  // microseconds, and the programmatic launches of the fixed-point chunk overlapped better
-  // outside a graph (0.2315 -> 0.2276 ms per step on the 2^26-DOF mesh).
-  int64_t dof = 0;
-  for (const auto &h : c->inst) dof += (int64_t)h.I.K * h.I.Np;
-  const bool graphs = dof < (int64_t(1) << 20);
+  // CUDA graphs of G steps where launches dominate; larger runs launch chunks of up to
+  // kDirectChunk steps directly (direct_launches)
+  const bool graphs = !direct_launches(c);
   int64_t left = nsteps;
   while (left > 0) {
     const int chunk = (int)std::min<int64_t>(left, graphs ? c->G : kDirectChunk);

@@ -6,6 +6,16 @@
 namespace adg {
 namespace {
 
+// Waits until the kernel this one was launched as a programmatic dependent of (launch_maybe_pdl)
+// has completed and its writes are visible; returns at once for an ordinary launch.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// Lets the next kernel of the chain (launched with the attribute) start launching its blocks
+// once every block of this one has passed this point. Called after pdl_wait, so the kernel
+// before this one has completed when the next one starts.
+__device__ __forceinline__ void pdl_trigger() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // Physical flux f(u): a u (advection) or u^2/2 (Burgers). Explicit round-to-nearest
 // intrinsics keep every evaluation of a face flux bit-identical wherever it is computed.
 template <int PDE>

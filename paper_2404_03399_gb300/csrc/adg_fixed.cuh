@@ -178,16 +178,6 @@ __device__ __forceinline__ FxScale fx_scale(const FxSlot *fx, int64_t n, bool fi
   return s;
 }
 
-// Waits until the kernel this one was launched as a programmatic dependent of (launch_maybe_pdl)
-// has completed and its writes are visible; returns at once for an ordinary launch.
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
-// Lets the next kernel of the chain (launched with the attribute) start launching its blocks
-// once every block of this one has passed this point. Called after pdl_wait, so the kernel
-// before this one has completed when the next one starts.
-__device__ __forceinline__ void pdl_trigger() {
-  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
-}
-
 __device__ __forceinline__ int fx_next(int slot) { return slot == 2 ? 0 : slot + 1; }
 __device__ __forceinline__ int fx_clear(int slot) { return slot == 0 ? 2 : slot - 1; }
 

@@ -203,7 +203,7 @@ struct AdjFace {
 // Launchers (adg_kernels.cu). All return cudaGetLastError() after the launch.
 // One stage over all elements; for an asynchronous instance the same kernel applies the
 // PE-face correction (delayed / AT flux) and writes the ring (step meta[0] + rel).
-cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s);
+cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s, bool pdl = false);
 // Stage s of a 2N low-storage step (I.ls): dU_s = A_s dU_{s-1} + dt L(U_{s-1}) in place in
 // I.v1 (A_1 = 0: dU_0 is not read) and U_s = U_{s-1} + B_s dU_s from uin (U_{s-1}) into uout,
 // with the delayed / AT flux and the ring write of the stage-input traces at PE faces.

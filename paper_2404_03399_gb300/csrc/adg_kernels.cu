@@ -325,12 +325,16 @@ __device__ __forceinline__ void stage_body_halo(const I &inst, int warp, int64_t
 
 template <int NP, int PDE, int STAGE, int DIR, bool FACES>
 __global__ void __launch_bounds__(kTile) k_stage_halo(const Inst inst, int rel) {
+  pdl_wait();   // the stage before (programmatic launch) has written this one's input
+  pdl_trigger();
   const int64_t n = FACES ? inst.meta[0] + rel : 0;
   stage_body_halo<NP, PDE, STAGE, DIR, FACES>(inst, (blockIdx.x * blockDim.x + threadIdx.x) >> 5, n);
 }
 
 template <int NP, int PDE, int STAGE, int DIR, bool FACES, bool VISC = false>
 __global__ void __launch_bounds__(kTile) k_stage(const Inst inst, int rel) {
+  pdl_wait();
+  pdl_trigger();
   const int64_t n = FACES ? inst.meta[0] + rel : 0;
   stage_body<NP, PDE, STAGE, DIR, FACES, false, VISC>(inst, blockIdx.x * blockDim.x + threadIdx.x,
                                                       n);
@@ -1294,46 +1298,49 @@ __global__ void __launch_bounds__(kRedThreads)
 }
 
 template <int NP, int PDE, int STAGE, int DIR>
-cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s) {
+cudaError_t launch_np_pde_stage(const Inst &I, int rel, cudaStream_t s, bool pdl) {
   const int bs = stage_block(I.K);
   const unsigned grid = (unsigned)((I.K + bs - 1) / bs);
   if (PDE == 1 && I.visc) {
-    if (I.async) k_stage<NP, PDE, STAGE, DIR, true, true><<<grid, bs, 0, s>>>(I, rel);
-    else k_stage<NP, PDE, STAGE, DIR, false, true><<<grid, bs, 0, s>>>(I, rel);
-  } else {
-    // 30 elements per warp (halo lanes); one-thread-per-element stage_body is kept for the
-    // 2N low-storage, viscous and batched stages
-    const int64_t warps = (I.K + 29) / 30;
-    const unsigned g = (unsigned)((warps * 32 + bs - 1) / bs);
-    if (I.async) k_stage_halo<NP, PDE, STAGE, DIR, true><<<g, bs, 0, s>>>(I, rel);
-    else k_stage_halo<NP, PDE, STAGE, DIR, false><<<g, bs, 0, s>>>(I, rel);
+    if (I.async)
+      return launch_maybe_pdl(k_stage<NP, PDE, STAGE, DIR, true, true>, dim3(grid), dim3(bs), s,
+                              pdl, I, rel);
+    return launch_maybe_pdl(k_stage<NP, PDE, STAGE, DIR, false, true>, dim3(grid), dim3(bs), s,
+                            pdl, I, rel);
   }
-  return cudaGetLastError();
+  // 30 elements per warp (halo lanes); one-thread-per-element stage_body is kept for the 2N
+  // low-storage, viscous and batched stages
+  const int64_t warps = (I.K + 29) / 30;
+  const dim3 g((unsigned)((warps * 32 + bs - 1) / bs));
+  if (I.async)
+    return launch_maybe_pdl(k_stage_halo<NP, PDE, STAGE, DIR, true>, g, dim3(bs), s, pdl, I, rel);
+  return launch_maybe_pdl(k_stage_halo<NP, PDE, STAGE, DIR, false>, g, dim3(bs), s, pdl, I, rel);
 }
 
 template <int NP, int PDE, int DIR>
-cudaError_t launch_np_pde(const Inst &I, int stage, int rel, cudaStream_t s) {
+cudaError_t launch_np_pde(const Inst &I, int stage, int rel, cudaStream_t s, bool pdl) {
   switch (stage) {
-    case 0: return launch_np_pde_stage<NP, PDE, 0, DIR>(I, rel, s);
-    case 1: return launch_np_pde_stage<NP, PDE, 1, DIR>(I, rel, s);
-    default: return launch_np_pde_stage<NP, PDE, 2, DIR>(I, rel, s);
+    case 0: return launch_np_pde_stage<NP, PDE, 0, DIR>(I, rel, s, pdl);
+    case 1: return launch_np_pde_stage<NP, PDE, 1, DIR>(I, rel, s, pdl);
+    default: return launch_np_pde_stage<NP, PDE, 2, DIR>(I, rel, s, pdl);
   }
 }
 
 template <int NP>
-cudaError_t launch_np(const Inst &I, int stage, int rel, cudaStream_t s) {
-  if (I.pde == 1) return launch_np_pde<NP, 1, 0>(I, stage, rel, s);
-  return I.a >= 0.0 ? launch_np_pde<NP, 0, 1>(I, stage, rel, s) : launch_np_pde<NP, 0, -1>(I, stage, rel, s);
+cudaError_t launch_np(const Inst &I, int stage, int rel, cudaStream_t s, bool pdl) {
+  if (I.pde == 1) return launch_np_pde<NP, 1, 0>(I, stage, rel, s, pdl);
+  return I.a >= 0.0 ? launch_np_pde<NP, 0, 1>(I, stage, rel, s, pdl)
+                    : launch_np_pde<NP, 0, -1>(I, stage, rel, s, pdl);
 }
 
 }  // namespace
 
-cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s) {
+cudaError_t launch_stage(const Inst &I, int stage, int rel, cudaStream_t s, bool pdl) {
   switch (I.Np) {
-    case 2: return launch_np<2>(I, stage, rel, s);
-    case 3: return launch_np<3>(I, stage, rel, s);
-    case 4: return launch_np<4>(I, stage, rel, s);
-    case 5: return launch_np<5>(I, stage, rel, s);
+    case 2: return launch_np<2>(I, stage, rel, s, pdl);
+    case 3: return launch_np<3>(I, stage, rel, s, pdl);
+    case 4: return launch_np<4>(I, stage, rel, s, pdl);
+    case 5: return launch_np<5>(I, stage, rel, s, pdl);
     default: return cudaErrorInvalidValue;
   }
 }
