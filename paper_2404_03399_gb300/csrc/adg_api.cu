@@ -357,6 +357,10 @@ struct InstHost {
   std::vector<uint8_t> host_rows;
 };
 
+// Parts of a uniform fixed-point batch advanced on separate streams (instances split by DOF;
+// two, three and four parts measured 0.3404, 0.3368 and 0.3428 ms per batched step).
+constexpr int kBatchParts = 3;
+
 struct adg_ctx {
   std::string err;
   cudaStream_t stream = nullptr;
@@ -376,17 +380,17 @@ struct adg_ctx {
   bool batch_fixed = false;     // ... in fixed point
   adg::BatchLite *lites_ept[3] = {};   // work records of 256, 512, 1024 elements (batch tuner)
   int nlites_ept[3] = {};
-  // the same records and the PE-face list in two halves of the instances (balanced by DOF;
-  // pointers into lites_ept and fflat_dev, which hold the first half's entries first),
-  // advanced on two streams so that the fix-up of one half overlaps the step of the other
-  // (uniform fixed-point batches launched directly)
-  adg::BatchLite *lites_half[3][2] = {};
-  int nlites_half[3][2] = {};
-  int2 *fflat_half[2] = {};
-  int nflat_half[2] = {};
-  std::unique_ptr<adg::BatchUniform> bu2;   // the second half's records (bu holds the first's)
-  cudaStream_t side = nullptr;
-  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
+  // the same records and the PE-face list in kBatchParts parts of the instances (balanced by
+  // DOF; pointers into lites_ept and fflat_dev, which hold the parts' entries in order),
+  // advanced on separate streams so that the fix-up of one part overlaps the steps of the
+  // others (uniform fixed-point batches launched directly)
+  adg::BatchLite *lites_half[3][kBatchParts] = {};
+  int nlites_half[3][kBatchParts] = {};
+  int2 *fflat_half[kBatchParts] = {};
+  int nflat_half[kBatchParts] = {};
+  bool split = false;                          // the parts have their streams and events
+  cudaStream_t side[kBatchParts] = {};         // side[0] unused: part 0 runs on `stream`
+  cudaEvent_t fork_ev = nullptr, join_ev[kBatchParts] = {};
   bool batch_even = false;             // every instance has an even K (the paired kernel)
   std::unique_ptr<adg::BatchUniform> bu;   // shared coefficients per degree, when they are
   double *partials = nullptr, *red_out = nullptr;
@@ -1579,28 +1583,30 @@ bool direct_launches(const adg_ctx *c) {
 
 int launch_steps(adg_ctx *c, int nsteps, int kind = kChunkFP64) {
   if (!c->batch && c->inst[0].I.fused) return launch_fused_steps(c, nsteps, kind);
-  if (c->batch && c->batch_fixed && c->bu2 && direct_launches(c)) {
-    // the two halves of the instances on the context's stream and the side stream (forked
-    // and joined around the chunk); each half's chain as below
+  if (c->batch && c->batch_fixed && c->bu && c->split && direct_launches(c)) {
+    // the parts of the instances on the context's stream and the side streams (forked and
+    // joined around the chunk); each part's chain as below
+    const int k = c->bu->ept == 4 ? 2 : c->bu->ept - 1;
     CK(cudaEventRecord(c->fork_ev, c->stream));
-    CK(cudaStreamWaitEvent(c->side, c->fork_ev, 0));
+    for (int q = 1; q < kBatchParts; ++q) CK(cudaStreamWaitEvent(c->side[q], c->fork_ev, 0));
+    adg::BatchUniform part = *c->bu;
     int in = kind == kChunkFP64 ? 0 : kind;
     for (int rel = 0; rel < nsteps; ++rel) {
       const int out = in == 1 ? 2 : 1;
       const int fmt = (in != 0 ? adg::kFmtInFixed : 0) | adg::kFmtOutFixed;
-      adg::BatchUniform first = *c->bu;
-      first.items_dev = c->bu->items_dev;
-      first.nitems = c->bu->nitems - c->bu2->nitems;
-      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fflat_half[0],
-                                      c->nflat_half[0], in, out, fmt, true, rel, c->stream, &first,
-                                      rel > 0));
-      CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fflat_half[1],
-                                      c->nflat_half[1], in, out, fmt, true, rel, c->side,
-                                      c->bu2.get(), rel > 0));
+      for (int q = 0; q < kBatchParts; ++q) {
+        part.items_dev = c->lites_half[k][q];
+        part.nitems = c->nlites_half[k][q];
+        CK(adg::launch_batch_fused_step(c->insts_dev, c->work_dev, c->nwork, c->fflat_half[q],
+                                        c->nflat_half[q], in, out, fmt, true, rel,
+                                        q ? c->side[q] : c->stream, &part, rel > 0));
+      }
       in = out;
     }
-    CK(cudaEventRecord(c->join_ev, c->side));
-    CK(cudaStreamWaitEvent(c->stream, c->join_ev, 0));
+    for (int q = 1; q < kBatchParts; ++q) {
+      CK(cudaEventRecord(c->join_ev[q], c->side[q]));
+      CK(cudaStreamWaitEvent(c->stream, c->join_ev[q], 0));
+    }
     CK(adg::launch_advance(c->meta, 2, (int)c->inst.size(), nsteps, c->stream));
     return ADG_OK;
   }
@@ -2212,8 +2218,10 @@ void adg_destroy(adg_ctx *c) {
   cudaFree(c->insts_dev);
   for (auto *l : c->lites_ept) cudaFree(l);
   if (c->fork_ev) cudaEventDestroy(c->fork_ev);
-  if (c->join_ev) cudaEventDestroy(c->join_ev);
-  if (c->side) cudaStreamDestroy(c->side);
+  for (auto e : c->join_ev)
+    if (e) cudaEventDestroy(e);
+  for (auto st : c->side)
+    if (st) cudaStreamDestroy(st);
   cudaFree(c->work_dev);
   cudaFree(c->fwork_dev);
   cudaFree(c->fflat_dev);
@@ -2292,11 +2300,7 @@ int apply_batch_kind(adg_ctx *c, int kind, int ept) {
     c->bu->items_dev = c->lites_ept[k];
     c->bu->nitems = c->nlites_ept[k];
     c->bu->ept = ept;
-    if (c->bu2) {
-      c->bu2->items_dev = c->lites_half[k][1];
-      c->bu2->nitems = c->nlites_half[k][1];
-      c->bu2->ept = ept;
-    }
+
   }
   CK(cudaMemcpy(c->insts_dev, hi.data(), sizeof(Inst) * hi.size(), cudaMemcpyHostToDevice));
   return ADG_OK;
@@ -2429,16 +2433,19 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       r = fail(c, ADG_EINVAL, "the fixed-point composed step needs every instance of the batch to admit it");
     if (!r && forced == ADG_VARIANT_COMPOSED && !all_fused)
       r = fail(c, ADG_EINVAL, "the composed step needs every instance of the batch to admit it");
-    // the two halves of the instances: largest first, each to the half with fewer DOF
+    // the parts of the instances: largest first, each to the part with the fewest DOF
     std::vector<int> half(n, 0), order(n);
     {
       for (int i = 0; i < n; ++i) order[i] = i;
       auto dof = [&](int i) { return (int64_t)c->inst[i].I.K * c->inst[i].I.Np; };
       std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return dof(a) > dof(b); });
-      int64_t load[2] = {0, 0};
+      int64_t load[kBatchParts] = {};
       for (int i : order) {
-        half[i] = load[1] < load[0] ? 1 : 0;
-        load[half[i]] += dof(i);
+        int best = 0;
+        for (int q = 1; q < kBatchParts; ++q)
+          if (load[q] < load[best]) best = q;
+        half[i] = best;
+        load[best] += dof(i);
       }
     }
     // the FP64 composed step of instances that admit fixed point (their I.fused is 2)
@@ -2450,12 +2457,12 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
       if (hi[i].async)
         for (int j0 = 0; j0 < hi[i].P; j0 += 256) fwork.push_back(make_int2(i, j0));
     }
-    int nflat0 = 0;
-    for (int hh = 0; hh < 2; ++hh)
+    int nflat_part[kBatchParts] = {};
+    for (int hh = 0; hh < kBatchParts; ++hh)
       for (int i = 0; i < n; ++i)
         if (half[i] == hh && hi[i].async) {
           for (int j = 0; j < hi[i].P; ++j) fflat.push_back(make_int2(i, j));
-          if (hh == 0) nflat0 += hi[i].P;
+          nflat_part[hh] += hi[i].P;
         }
     // every instance of a degree with the same fixed-point coefficients: pass them per degree,
     // with one record per work item of ept tiles (ept elements per thread)
@@ -2478,12 +2485,12 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
           const int ept = 1 << k;
           if (ept_forced && ept != ept_forced) continue;
           std::vector<adg::BatchLite> lites;
-          int nlite0 = 0;
-          for (int hh = 0; hh < 2; ++hh)
+          int nlite_part[kBatchParts] = {};
+          for (int hh = 0; hh < kBatchParts; ++hh)
           for (int i = 0; i < n; ++i) {
             if (half[i] != hh) continue;
             const Inst &I = c->inst[i].I;
-            if (hh == 0) nlite0 += (I.K + ept * adg::kTile - 1) / (ept * adg::kTile);
+            nlite_part[hh] += (I.K + ept * adg::kTile - 1) / (ept * adg::kTile);
             for (int e0 = 0; e0 < I.K; e0 += ept * adg::kTile) {
               adg::BatchLite L;
               L.f[0] = I.u;
@@ -2503,18 +2510,21 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
                          cudaMemcpyHostToDevice) != cudaSuccess)
             r = fail(c, ADG_ENOMEM, "cudaMalloc(batch records)");
           c->nlites_ept[k] = (int)lites.size();
-          c->lites_half[k][0] = c->lites_ept[k];
-          c->nlites_half[k][0] = nlite0;
-          c->lites_half[k][1] = c->lites_ept[k] + nlite0;
-          c->nlites_half[k][1] = (int)lites.size() - nlite0;
+          int off = 0;
+          for (int q = 0; q < kBatchParts; ++q) {
+            c->lites_half[k][q] = c->lites_ept[k] + off;
+            c->nlites_half[k][q] = nlite_part[q];
+            off += nlite_part[q];
+          }
         }
-        // the second half's stream and its fork / join events (batches of two or more)
-        if (!r && n >= 2) {
-          c->bu2.reset(new (std::nothrow) adg::BatchUniform());
-          if (!c->bu2 || cudaStreamCreateWithFlags(&c->side, cudaStreamNonBlocking) != cudaSuccess ||
-              cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-              cudaEventCreateWithFlags(&c->join_ev, cudaEventDisableTiming) != cudaSuccess)
-            r = fail(c, ADG_ENOMEM, "batch side stream");
+        // the parts' streams and fork / join events (batches of at least kBatchParts)
+        if (!r && n >= kBatchParts) {
+          bool ok = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming) == cudaSuccess;
+          for (int q = 1; q < kBatchParts && ok; ++q)
+            ok = cudaStreamCreateWithFlags(&c->side[q], cudaStreamNonBlocking) == cudaSuccess &&
+                 cudaEventCreateWithFlags(&c->join_ev[q], cudaEventDisableTiming) == cudaSuccess;
+          if (!ok) r = fail(c, ADG_ENOMEM, "batch side streams");
+          c->split = ok;
         }
         if (!r) {
           std::memset(&c->bu->uf, 0, sizeof(c->bu->uf));
@@ -2527,7 +2537,6 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
               uf.fxe[d] = ref[d]->fxe;
               std::memcpy(uf.Tbi[d], ref[d]->Tbi, sizeof(uf.Tbi[d]));
             }
-          if (c->bu2) c->bu2->uf = c->bu->uf;
         }
       }
     }
@@ -2546,10 +2555,14 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
                (!fflat.empty() && cudaMemcpy(c->fflat_dev, fflat.data(), sizeof(int2) * fflat.size(),
                                              cudaMemcpyHostToDevice) != cudaSuccess)))
       r = fail(c, ADG_ENOMEM, "cudaMalloc(batch face list)");
-    c->fflat_half[0] = c->fflat_dev;
-    c->nflat_half[0] = nflat0;
-    c->fflat_half[1] = c->fflat_dev + nflat0;
-    c->nflat_half[1] = c->nflat - nflat0;
+    {
+      int off = 0;
+      for (int q = 0; q < kBatchParts; ++q) {
+        c->fflat_half[q] = c->fflat_dev + off;
+        c->nflat_half[q] = nflat_part[q];
+        off += nflat_part[q];
+      }
+    }
     if (cudaMalloc(&c->insts_dev, sizeof(Inst) * n) != cudaSuccess ||
         cudaMalloc(&c->work_dev, sizeof(int2) * work.size()) != cudaSuccess ||
         cudaMalloc(&c->fwork_dev, sizeof(int2) * std::max<size_t>(1, fwork.size())) != cudaSuccess)
