@@ -144,11 +144,12 @@ enum {
  *               point, FP64 composed, staged) at init and keeps the fastest (adg_get_variant
  *               reports it). All give the same scheme up to rounding.
  *   ept       : elements per thread of the composed-step kernels (not a paper quantity):
- *               0 (default) lets init time the choices and keep the fastest (1, or 2
- *               consecutive elements for even K, for the fixed-point step; 1, 2 or 4 for the
- *               FP64 step; a batch's fixed-point step also 4, i.e. work items of 256, 512 or
- *               1024 elements); 1, 2 or 4 forces one (ADG_EINVAL where that kernel has no such
- *               form). Results do not depend on it.
+ *               0 (default) lets init choose: the FP64 step times 1, 2 and 4 and keeps the
+ *               fastest; a single instance's fixed-point step takes 2 consecutive elements for
+ *               even K (measured faster throughout) and 1 for odd K or K < 2048; a batch's
+ *               fixed-point step times 1, 2 and 4 (work items of 256, 512 or 1024 elements);
+ *               1, 2 or 4 forces one (ADG_EINVAL where that kernel has no such form). Results
+ *               do not depend on it.
  */
 typedef struct {
   int32_t pde;

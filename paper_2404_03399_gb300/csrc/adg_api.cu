@@ -1267,10 +1267,12 @@ int reset_exponent(adg_ctx *c, InstHost &h) {
   return ADG_OK;
 }
 
-// Autotuner of the composed-step kernel: times one, two and four elements per thread on a
-// copy of u0 held in the instance's v1/v2 fields (free at this point) and keeps the fastest.
-// Every choice computes every element with the same arithmetic, so results do not depend on
-// it.
+// Elements per thread of the composed-step kernel. The FP64 composed step times one, two and
+// four on a copy of u0 held in the instance's v1/v2 fields (free at this point) and keeps the
+// fastest; the fixed-point step takes two for even K, which measured faster in every timing
+// of both (223.6 against 255.3 us per step on 2^24 elements), without timing them at init
+// (a run's end-to-end cost includes adg_init). Every choice computes every element with the
+// same arithmetic, so results do not depend on it.
 int autotune_fused(adg_ctx *c, InstHost &h) {
   Inst &I = h.I;
   const size_t nd = (size_t)I.K * I.Np;
@@ -1281,16 +1283,11 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
     return ADG_OK;
   }
   if (I.K < 4 * 2 * adg::kTile) return ADG_OK;   // tiny meshes: one element per thread
-  // The fixed-point step is timed in its int64 -> int64 form (the bulk of a chunk): one
-  // FP64 -> int64 step fills v1, then v1 and v2 alternate. The FP64 step alternates copies
-  // of u0 in v1 and v2.
-  const bool fixed = I.fused == 2;
-  if (fixed)
-    CK(adg::launch_fused_step(I, I.u, I.v1, 0, c->stream, false, adg::kFmtOutFixed));
-  else
-    CK(cudaMemcpyAsync(I.v1, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
-  const int fmt = fixed ? adg::kFmtInFixed | adg::kFmtOutFixed : 0;
-  const int rel = fixed ? 1 : 0;   // the slot the first step wrote
+  if (I.fused == 2) {
+    I.ept = I.K % 2 ? 1 : 2;
+    return ADG_OK;
+  }
+  CK(cudaMemcpyAsync(I.v1, I.u, nd * sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
   cudaEvent_t a = nullptr, b = nullptr;
   CK(cudaEventCreate(&a));
   CK(cudaEventCreate(&b));
@@ -1299,13 +1296,13 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   // Per choice one untimed launch, then two timed ones (the choices differ by about 10% on
   // large meshes, far above the event resolution; the autotuner runs inside adg_init, so it is
   // kept short).
-  for (int ept = 1; ept <= (fixed ? (I.K % 2 ? 1 : 2) : 4); ept *= 2) {
+  for (int ept = 1; ept <= 4; ept *= 2) {
     Inst T = I;
     T.ept = ept;
-    CK(adg::launch_fused_step(T, I.v1, I.v2, rel, c->stream, false, fmt));
+    CK(adg::launch_fused_step(T, I.v1, I.v2, 0, c->stream, false, 0));
     cudaEventRecord(a, c->stream);
     for (int k = 0; k < 2; ++k)
-      CK(adg::launch_fused_step(T, k ? I.v1 : I.v2, k ? I.v2 : I.v1, rel, c->stream, false, fmt));
+      CK(adg::launch_fused_step(T, k ? I.v1 : I.v2, k ? I.v2 : I.v1, 0, c->stream, false, 0));
     cudaEventRecord(b, c->stream);
     CK(cudaEventSynchronize(b));
     float ms = 0.0f;
@@ -1500,10 +1497,6 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
       }
       if (!c->batch) {
         int r2 = autotune_fused(c, h);
-        if (r2) return r2;
-      }
-      if (fixed) {   // the autotuner's launches moved the exponent slots
-        int r2 = reset_exponent(c, h);
         if (r2) return r2;
       }
     }
