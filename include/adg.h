@@ -133,7 +133,11 @@ enum {
  *               of n terms is off by less than n/2 + 1/2 units of 2^-57 max|u^n|, so the error is
  *               bounded relative to the field's maximum (as FP64's is relative to a sum's
  *               largest term), not per value: values below about 2^-55 max|u^n| keep no
- *               digits. The state stays in int64 from step to step and across adg_step calls;
+ *               digits. The int64 state holds each element's coordinates in the block basis
+ *               of the element operator where that basis is well conditioned (p = 1 .. 4; see
+ *               adg_get_fixed_basis), which multiplies that bound by the basis's condition
+ *               number (at most 64; 15.1 at p = 3). The state stays in int64 from step to step
+ *               and across adg_step calls;
  *               the FP64 state is formed (rounded once) when it is read (adg_get_state,
  *               adg_integral, adg_misfit, adg_check_finite, adg_grad), so every splitting of a
  *               run into calls gives the same result. It needs every composed coefficient below
