@@ -86,7 +86,8 @@ BYTES_PER_DOF_STEP_STAGED = 64
 # Burgers LLF stage at p = 4 (Np = 5): per node v^2 (one multiply), Np FMA of the volume row,
 # two lifts and the alpha / beta combination: 2 (Np + 4) + 1 flop per DOF-stage.
 FLOP_PER_DOF_STAGE_BURGERS = 2 * (5 + 4) + 1
-GRAPH_STEPS = 32
+# steps per directly launched chunk on the large mesh (adg_step)
+CHUNK_STEPS = 256
 
 
 def sm_count() -> int:
@@ -184,7 +185,8 @@ def bench_config(ws: int) -> dict:
     return {"workload": w["name"], "K": w["K"], "p": w["p"], "P": w["P"], "L": w["L"],
             "at_order": w["q"], "cfl": w["cfl"], "dof": w["K"] * (w["p"] + 1),
             "parallelism": f"replicas x{ws}",
-            "l2": "inputs larger than L2 (537 MB per nodal field)", "graph_steps": GRAPH_STEPS}
+            "l2": "inputs larger than L2 (537 MB per nodal field)",
+            "launches": "direct chunks of up to 256 steps, programmatic dependent launches"}
 
 
 def host_info() -> dict:
@@ -880,9 +882,9 @@ def main():
             "config": bench_config(ws), "variant": variant, "arithmetic": arithmetic,
             "roofline": roofline,
             # per step: the composed-step kernel and one PE-face kernel (correction of the step
-            # before, differences of the next); per chunk of GRAPH_STEPS steps one step-counter
-            # kernel, and per call one more PE-face kernel
-            "gpu_launches": 2 * args.steps + 1 + math.ceil(args.steps / GRAPH_STEPS),
+            # before, differences of the next); per chunk of CHUNK_STEPS steps one step-counter
+            # kernel and one more PE-face kernel
+            "gpu_launches": 2 * args.steps + 2 * math.ceil(args.steps / CHUNK_STEPS),
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:

@@ -282,9 +282,10 @@ def _window_oracle(cfg, u0_full_fn, e, steps, dt, table_rows, both_sides):
 @pytest.mark.parametrize("which", ["advection_16m", "advection_16m_staged", "advection_16m_composed",
                                    "advection_16m_lsrk4", "burgers_1m"])
 def test_full_size_sampled(which):
-    # Full-size meshes in the launch configuration the benchmark times (graph replay of
-    # 32-step chunks plus a direct remainder), checked at sampled elements against the
-    # oracle run on a window wide enough to contain each sample's dependence cone.
+    # Full-size meshes in the launch configuration the benchmark times (at these sizes steps
+    # are launched directly, kernels of a chunk as programmatic dependents of the one before),
+    # checked at sampled elements against the oracle run on a window wide enough to contain
+    # each sample's dependence cone.
     if which.startswith("advection_16m"):
         w = ADVECTION_16M
         suffix = which[len("advection_16m_"):]
