@@ -185,8 +185,7 @@ def bench_config(ws: int) -> dict:
     return {"workload": w["name"], "K": w["K"], "p": w["p"], "P": w["P"], "L": w["L"],
             "at_order": w["q"], "cfl": w["cfl"], "dof": w["K"] * (w["p"] + 1),
             "parallelism": f"replicas x{ws}",
-            "l2": "inputs larger than L2 (537 MB per nodal field)",
-            "launches": "direct chunks of up to 256 steps, programmatic dependent launches"}
+            "l2": "inputs larger than L2 (537 MB per nodal field)"}
 
 
 def host_info() -> dict:
@@ -885,6 +884,8 @@ def main():
             # before, differences of the next); per chunk of CHUNK_STEPS steps one step-counter
             # kernel and one more PE-face kernel
             "gpu_launches": 2 * args.steps + 2 * math.ceil(args.steps / CHUNK_STEPS),
+            "launches": "direct chunks of up to 256 steps, kernels launched as programmatic "
+                        "dependents of the one before",
             "finite": finite, "clocks": clocks}
 
     if not args.no_extras:

@@ -1028,39 +1028,68 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
     // with alpha = -(G - I)_11 / (G - I)_12 and beta = 2^-k / (G - I)_12 make the block's first
     // row of G exactly (1, 2^-k) (k the nearest power of two, so beta is near 1): a row of
     // shifts and adds in the kernel.
-    std::vector<ld> Ts = Tm, Tis;
-    for (int m = 0; m <= (Np == 4 ? 2 : 0) && basis; m += 2) {   // the 2 x 2 blocks
-      const ld n11 = Gc[m * Np + m] - 1.0L, n12 = Gc[m * Np + m + 1];
-      const int k = fabsl(n12) > 0 ? (int)lroundl(-log2l(fabsl(n12))) : -1;
-      if (k < 1 || k > 27) {
-        basis = false;
-        break;
-      }
-      const ld al = -n11 / n12, be = ldexpl(1.0L, -k) / n12;
-      for (int r = 0; r < Np; ++r) {
-        const ld f = Ts[r * Np + m], g = Ts[r * Np + m + 1];
-        Ts[r * Np + m] = f + al * g;
-        Ts[r * Np + m + 1] = be * g;
-      }
-      gshift[m / 2] = 29 - k;
-    }
-    if (basis && invert(Ts, Np, Tis) && cond_inf(Ts, Tis, Np) <= 64.0L) {
-      const Mat Gs = similar(Tis, Gl, Ts, Np);
-      bool rows = block_diagonal(Gs, Np, 1e-13L);
-      for (int m = 0; m <= (Np == 4 ? 2 : 0); m += 2)
-        rows = rows && fabsl(Gs[m * Np + m] - 1.0L) < 1e-15L &&
-               fabsl(Gs[m * Np + m + 1] - ldexpl(1.0L, gshift[m / 2] - 29)) <
-                   1e-15L * ldexpl(1.0L, gshift[m / 2] - 29);
-      if (rows) {
-        Tm = Ts;
-        Tim = Tis;
-        Gc = Gs;
-        for (int m = 0; m <= (Np == 4 ? 2 : 0); m += 2) {
-          Gc[m * Np + m] = 1.0L;
-          Gc[m * Np + m + 1] = ldexpl(1.0L, gshift[m / 2] - 29);
+    // The 3 x 3 block at p = 4 likewise: f' = f + a1 g1 + a2 g2 with (a1, a2) the smallest
+    // solution of (G - I)_11 + (G - I)_12 a1 + (G - I)_13 a2 = 0, g1' = (n12 g1 + n13 g2)
+    // 2^-k / |n|^2 and g2' = (n13 g1 - n12 g2) / |n|, n = ((G - I)_12, (G - I)_13): its first
+    // row becomes (1, 2^-k, 0); where that basis is worse conditioned than allowed the triple
+    // keeps its dense rows.
+    auto shear = [&](bool triple, std::vector<ld> &Ts, std::vector<ld> &Tis, Mat &Gs, int *gsh) {
+      Ts = Tm;
+      gsh[0] = gsh[1] = 0;
+      auto k_of = [](ld x) { return fabsl(x) > 0 ? (int)lroundl(-log2l(fabsl(x))) : -1; };
+      for (int m = 0; m <= (Np == 4 ? 2 : 0); m += 2) {   // the 2 x 2 blocks
+        const ld n11 = Gc[m * Np + m] - 1.0L, n12 = Gc[m * Np + m + 1];
+        const int k = k_of(n12);
+        if (k < 1 || k > 27) return false;
+        const ld al = -n11 / n12, be = ldexpl(1.0L, -k) / n12;
+        for (int r = 0; r < Np; ++r) {
+          const ld f = Ts[r * Np + m], g = Ts[r * Np + m + 1];
+          Ts[r * Np + m] = f + al * g;
+          Ts[r * Np + m + 1] = be * g;
         }
-      } else {
-        basis = false;
+        gsh[m / 2] = 29 - k;
+      }
+      if (triple) {
+        const ld n11 = Gc[2 * Np + 2] - 1.0L, n12 = Gc[2 * Np + 3], n13 = Gc[2 * Np + 4];
+        const ld nn2 = n12 * n12 + n13 * n13, nn = sqrtl(nn2);
+        const int k = k_of(nn);
+        if (k < 1 || k > 27) return false;
+        const ld a1 = -n11 * n12 / nn2, a2 = -n11 * n13 / nn2, sc = ldexpl(1.0L, -k) / nn2;
+        for (int r = 0; r < Np; ++r) {
+          const ld f = Ts[r * Np + 2], g1 = Ts[r * Np + 3], g2 = Ts[r * Np + 4];
+          Ts[r * Np + 2] = f + a1 * g1 + a2 * g2;
+          Ts[r * Np + 3] = (n12 * g1 + n13 * g2) * sc;
+          Ts[r * Np + 4] = (n13 * g1 - n12 * g2) / nn;
+        }
+        gsh[1] = 29 - k;
+      }
+      if (!invert(Ts, Np, Tis) || cond_inf(Ts, Tis, Np) > 64.0L) return false;
+      Gs = similar(Tis, Gl, Ts, Np);
+      bool rows = block_diagonal(Gs, Np, 1e-13L);
+      for (int m = 0; m <= (Np >= 4 ? 2 : 0); m += 2) {
+        if (m == 2 && Np == 5 && !triple) break;
+        const ld t = ldexpl(1.0L, gsh[m / 2] - 29);
+        rows = rows && fabsl(Gs[m * Np + m] - 1.0L) < 1e-15L &&
+               fabsl(Gs[m * Np + m + 1] - t) < 1e-15L * t;
+        if (m == 2 && Np == 5) rows = rows && fabsl(Gs[2 * Np + 4]) < 1e-15L * t;
+      }
+      return rows;
+    };
+    std::vector<ld> Ts, Tis;
+    Mat Gs;
+    int gsh[2] = {0, 0};
+    const bool ok = (Np == 5 && shear(true, Ts, Tis, Gs, gsh)) || shear(false, Ts, Tis, Gs, gsh);
+    if (ok) {
+      Tm = Ts;
+      Tim = Tis;
+      Gc = Gs;
+      gshift[0] = gsh[0];
+      gshift[1] = gsh[1];
+      for (int m = 0; m <= (Np >= 4 ? 2 : 0); m += 2) {
+        if (gshift[m / 2] == 0) continue;   // the triple without its shear
+        Gc[m * Np + m] = 1.0L;
+        Gc[m * Np + m + 1] = ldexpl(1.0L, gshift[m / 2] - 29);
+        if (m == 2 && Np == 5) Gc[2 * Np + 4] = 0.0L;
       }
     } else {
       basis = false;
@@ -1168,7 +1197,7 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
   }
   h.fixed_ok = ok && sums;
   if (basis)
-    for (int m = 0; m < (Np == 4 ? 2 : 1); ++m) F.gs[m] = gshift[m];
+    for (int m = 0; m < 2; ++m) F.gs[m] = gshift[m];
   if (basis && h.fixed_ok) {
     // FP64 inputs: w = T^-1 u in FP64 is below ||T^-1||_inf 2^(E - 1022) (1 + 2^-40)
     ld nti = 0;

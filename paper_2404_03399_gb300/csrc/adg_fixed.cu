@@ -104,7 +104,8 @@ __device__ __forceinline__ void fx_left_channels(const StepFixed &F, const Fixed
 }
 
 // u'^e = G u^e + sum_s h_s P_s for output row i. BLK: G's entries of row i's block only
-// (blocks {0, 1} and {2, .., NP-1}); the first row of a 2 x 2 block is (1, 2^-k), whose
+// (blocks {0, 1} and {2, .., NP-1}); the first row of a 2 x 2 block (and of the 3 x 3 block
+// where it was sheared) is (1, 2^-k), whose
 // products, X_i and xh_{i+1} 2^(29-k) + xl_{i+1} 2^(29-k) 2^-29, are shifts (the same sums
 // as the multiply-adds with the limbs {2^29, 0} and {2^(29-k), 0}).
 template <int NP, int S, bool BLK>
@@ -113,7 +114,9 @@ __device__ __forceinline__ long long fx_row(const StepFixed &F, int i, const int
   FxAcc acc;
   if (BLK) {
     const int j0 = i < 2 ? 0 : 2, j1 = i < 2 ? 2 : NP;   // the block [j0, j1)
-    if (i == j0 && j1 - j0 == 2) {
+    // a pair's first row, or the triple's (NP = 5) when its basis was sheared (gs[1] != 0):
+    // (1, 2^-k) or (1, 2^-k, 0)
+    if (i == j0 && (j1 - j0 == 2 || (j1 - j0 == 3 && F.gs[1] != 0))) {
       // 64-bit values from 32-bit funnel shifts of the limbs (sign words s0, s1)
       const unsigned sh = (unsigned)F.gs[i >> 1];
       const unsigned h0 = (unsigned)xh[i], s0 = (unsigned)(xh[i] >> 31);

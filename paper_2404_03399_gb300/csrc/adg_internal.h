@@ -78,7 +78,8 @@ struct StepConsts {
 // (|c| < 2) is C = round(c 2^58), split into limbs C = ch 2^29 + cl with balanced
 // -2^28 <= cl < 2^28 (int2 {ch, cl}).
 // In the block basis (Inst.basis) the first row of each 2 x 2 block of G is (1, 2^-k_m),
-// exactly: gs[m] = 29 - k_m, and that row is formed by shifts and adds (no multiplies).
+// exactly: gs[m] = 29 - k_m, and that row is formed by shifts and adds (no multiplies); at
+// Np = 5 gs[1] != 0 marks the 3 x 3 block's first row as (1, 2^-k, 0) likewise.
 struct StepFixed {
   int2 G[kMaxNp * kMaxNp];
   int2 r[kMaxCS][kMaxNp];

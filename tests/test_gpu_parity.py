@@ -30,7 +30,7 @@ def _built():
 
 # Rounding of one fixed-point step relative to the field's maximum: a sum of n <= 10 products
 # is off by less than (n/2 + 1/2) units of 2^-56 max|w|, and the state is kept as block-basis
-# coordinates w = T^-1 u, which scales that by cond_inf(T) (1.7, 11.5, 15.1 and 34.8 at
+# coordinates w = T^-1 u, which scales that by cond_inf(T) (1.7, 11.5, 15.1 and 43.3 at
 # p = 1 .. 4; the cases held to these bounds are at p = 1 and 3, so 16 covers them). An FP64
 # step (composed or staged) rounds each value to within a few units in the last place of the
 # field: 1e-15 of its maximum per step, generously.
