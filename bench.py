@@ -411,9 +411,10 @@ def euler_timed(steps: int, warmup: int):
 
 
 def e2e_timed(steps: int):
-    """Public-API run from host buffers: pinned u0 -> device, adg_init, `steps` steps,
-    state -> pinned host; all inside one timed region (wall clock around synchronised
-    work, bracketed by CUDA events on the same stream)."""
+    """Public-API run from host buffers: `adg_init_host` on pinned u0 (the layout kernel reads
+    it over the host link), `steps` steps, `adg_get_state_host` into pinned memory (written by
+    the layout kernel over the link); all inside one timed region (wall clock around
+    synchronised work, bracketed by CUDA events on the same stream)."""
     import torch
     import paper_2404_03399_gb300 as adg
     cfg = make_cfg("at")
@@ -425,11 +426,9 @@ def e2e_timed(steps: int):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     t0 = time.perf_counter()
     ev0.record(stream)
-    dev_u0 = host_u0.to("cuda", non_blocking=True)
-    s = adg.Solver(cfg, dev_u0)
+    s = adg.Solver(cfg, host_u0)
     s.step(steps)
-    out = s.state()
-    host_out.copy_(out, non_blocking=True)
+    s.state(out=host_out)
     ev1.record(stream)
     ev1.synchronize()
     wall = time.perf_counter() - t0
@@ -893,7 +892,8 @@ def main():
         ems, nbytes = e2e_timed(args.steps)
         line["e2e"] = {"value": ndof * STAGES * args.steps / (ems * 1e-3), "unit": UNIT,
                        "h2d_bytes_per_step": nbytes / args.steps, "d2h_bytes_per_step": nbytes / args.steps,
-                       "what": "pinned host u0 -> device, adg_init, all steps, state -> pinned host"}
+                       "what": "adg_init_host from pinned u0 (read in place over the host link), all "
+                               "steps, adg_get_state_host into pinned memory"}
         # synchronous DG on the same mesh, the same number of steps in one adg_step call
         acc_sync = {}
         sync_ms, _, _, (svar, _, _) = device_timed("sync", args.steps, args.warmup, barrier, False,

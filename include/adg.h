@@ -192,6 +192,16 @@ void adg_config_default(adg_config *cfg);
 int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx **out);
 
 /*
+ * adg_init with the initial field in host memory (the same (K, p+1) row-major FP64 layout,
+ * three fields for ADG_EULER). Pinned memory (cudaHostAlloc, cudaMallocHost, cudaHostRegister)
+ * and managed memory are read in place by the kernel that lays the field out in node planes,
+ * so the transfer over the host link and the layout are one pass; pageable memory is first
+ * copied into the instance's scratch field. The call synchronises, so u0_host may be reused or
+ * freed when it returns. Errors as adg_init, and ADG_EINVAL when u0_host is device memory.
+ */
+int adg_init_host(const adg_config *cfg, const double *u0_host, void *stream, adg_ctx **out);
+
+/*
  * Create one context that advances n independent instances together (batched runs):
  * every stage launch covers all instances; chunks of steps replay one CUDA graph.
  * cfgs[i], u0_devs[i] as in adg_init. Only ADG_ADVECTION / ADG_UPWIND instances.
@@ -210,6 +220,12 @@ int adg_run(adg_ctx *c, double t_end);
 /* Copy instance `index` (0 for a single-instance context) to u_dev, device (K, p+1)
  * row-major FP64, and its step counter to *step_out (may be NULL). Synchronises. */
 int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out);
+
+/* adg_get_state into host memory u_host ((K, p+1) row-major FP64, three fields for
+ * ADG_EULER): pinned or managed memory is written in place by the layout kernel over the host
+ * link; pageable memory through a device field that holds no state and one copy. Synchronises.
+ * ADG_EINVAL when u_host is device memory. */
+int adg_get_state_host(adg_ctx *c, int32_t index, double *u_host, int64_t *step_out);
 
 /* The fixed time step of instance `index`. */
 int adg_get_dt(adg_ctx *c, int32_t index, double *dt_out);

@@ -100,9 +100,9 @@ def _shape(cfg) -> tuple:
     return (3, cfg.K, cfg.p + 1) if cfg.pde == "euler" else (cfg.K, cfg.p + 1)
 
 
-def _as_field(x: torch.Tensor, K: int, Np: int, ncomp: int = 1) -> torch.Tensor:
-    if not (isinstance(x, torch.Tensor) and x.is_cuda):
-        raise ValueError("expected a CUDA tensor")
+def _as_field(x: torch.Tensor, K: int, Np: int, ncomp: int = 1, host: bool = False) -> torch.Tensor:
+    if not (isinstance(x, torch.Tensor) and (x.device.type == "cpu" if host else x.is_cuda)):
+        raise ValueError("expected a CPU tensor" if host else "expected a CUDA tensor")
     x = x.to(torch.float64).contiguous()
     want = (K, Np) if ncomp == 1 else (ncomp, K, Np)
     if tuple(x.shape) != want:
@@ -139,16 +139,20 @@ def lgl_nodes(p: int):
 
 
 class Solver:
-    """One ADG instance on the current CUDA device (``adg_init`` / ``adg_step`` / ...)."""
+    """One ADG instance on the current CUDA device (``adg_init`` / ``adg_step`` / ...). u0 is
+    a CUDA tensor (``adg_init``) or a CPU tensor (``adg_init_host``: read in place over the
+    host link when pinned, staged through device memory otherwise)."""
 
     def __init__(self, cfg: Config, u0: torch.Tensor, stream: Optional[torch.cuda.Stream] = None):
         self.cfg = cfg
         self.Np = cfg.p + 1
-        u0 = _as_field(u0, cfg.K, self.Np, 3 if cfg.pde == "euler" else 1)
+        host = isinstance(u0, torch.Tensor) and u0.device.type == "cpu"
+        u0 = _as_field(u0, cfg.K, self.Np, 3 if cfg.pde == "euler" else 1, host=host)
         c, keep = cfg.to_c()
         self._stream = stream
         ctx = C.c_void_p()
-        check(load().adg_init(C.byref(c), u0.data_ptr(), _stream_ptr(stream), C.byref(ctx)))
+        init = load().adg_init_host if host else load().adg_init
+        check(init(C.byref(c), u0.data_ptr(), _stream_ptr(stream), C.byref(ctx)))
         self._ctx = ctx
 
     @property
@@ -164,10 +168,15 @@ class Solver:
         check(load().adg_run(self.ctx, float(t_end)), self.ctx)
 
     def state(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """The FP64 state: into a new CUDA tensor, or into `out` (a contiguous FP64 tensor of
+        the field's shape on the GPU, or on the host: ``adg_get_state_host``)."""
         if out is None:
             out = torch.empty(_shape(self.cfg), dtype=torch.float64, device="cuda")
+        if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != _shape(self.cfg):
+            raise ValueError(f"out must be a contiguous float64 tensor of shape {_shape(self.cfg)}")
         n = C.c_int64()
-        check(load().adg_get_state(self.ctx, 0, out.data_ptr(), C.byref(n)), self.ctx)
+        get = load().adg_get_state_host if out.device.type == "cpu" else load().adg_get_state
+        check(get(self.ctx, 0, out.data_ptr(), C.byref(n)), self.ctx)
         self.n = n.value
         return out
 
@@ -257,10 +266,16 @@ class BatchSolver:
     def step(self, nsteps: int) -> None:
         check(load().adg_step(self._ctx, int(nsteps)), self._ctx)
 
-    def state(self, i: int) -> torch.Tensor:
+    def state(self, i: int, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        """Instance i's FP64 state, into a new CUDA tensor or into `out` (GPU or host)."""
         cf = self.cfgs[i]
-        out = torch.empty((cf.K, cf.p + 1), dtype=torch.float64, device="cuda")
-        check(load().adg_get_state(self._ctx, int(i), out.data_ptr(), None), self._ctx)
+        shape = (cf.K, cf.p + 1)
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float64, device="cuda")
+        if out.dtype != torch.float64 or not out.is_contiguous() or tuple(out.shape) != shape:
+            raise ValueError(f"out must be a contiguous float64 tensor of shape {shape}")
+        get = load().adg_get_state_host if out.device.type == "cpu" else load().adg_get_state
+        check(get(self._ctx, int(i), out.data_ptr(), None), self._ctx)
         return out
 
     def dt(self, i: int) -> float:

@@ -23,6 +23,7 @@ EXPORTS = [
     "adg_get_state", "adg_get_dt", "adg_get_variant", "adg_grad", "adg_integral", "adg_check_finite",
     "adg_delay_table", "adg_eval_modes", "adg_lgl_nodes", "adg_last_error", "adg_destroy",
     "adg_integral_noalloc", "adg_misfit", "adg_comm_stats", "adg_get_fixed_basis",
+    "adg_init_host", "adg_get_state_host",
 ]
 
 
@@ -67,10 +68,12 @@ def load(require: bool = True):
     sig = {
         "adg_config_default": (None, [cfgp]),
         "adg_init": (C.c_int, [cfgp, vp, vp, C.POINTER(vp)]),
+        "adg_init_host": (C.c_int, [cfgp, vp, vp, C.POINTER(vp)]),
         "adg_batch_init": (C.c_int, [cfgp, C.POINTER(vp), i32, vp, C.POINTER(vp)]),
         "adg_step": (C.c_int, [vp, i64]),
         "adg_run": (C.c_int, [vp, C.c_double]),
         "adg_get_state": (C.c_int, [vp, i32, vp, C.POINTER(i64)]),
+        "adg_get_state_host": (C.c_int, [vp, i32, vp, C.POINTER(i64)]),
         "adg_get_dt": (C.c_int, [vp, i32, dp]),
         "adg_get_variant": (C.c_int, [vp, i32, C.POINTER(i32), C.POINTER(i32)]),
         "adg_get_fixed_basis": (C.c_int, [vp, i32, C.POINTER(i32)]),

@@ -418,6 +418,23 @@ int fail(adg_ctx *c, int code, const std::string &msg) {
                   std::string(#call) + ": " + cudaGetErrorString(e_));                    \
   } while (0)
 
+// The device address of a caller's host buffer where kernels can use it in place: pinned
+// (page-locked, mapped) and managed memory give one, pageable memory gives null (the caller
+// stages it through device memory). Device memory is refused: the _host entry points take host
+// buffers, the others device buffers.
+int host_view(adg_ctx *c, const void *p, const void **view) {
+  *view = nullptr;
+  cudaPointerAttributes a{};
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    (void)cudaGetLastError();
+    return ADG_OK;   // not known to the runtime: pageable
+  }
+  if (a.type == cudaMemoryTypeDevice)
+    return fail(c, ADG_EINVAL, "a host buffer was expected, not device memory");
+  if (a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeManaged) *view = a.devicePointer;
+  return ADG_OK;
+}
+
 // c2 a = -2 dt a / dx of upwind advection. With the step from the Courant number,
 // dt = sigma dx / |a|, it is -2 sigma sign(a) exactly: folded from sigma, every instance with
 // the same degree, sigma and sign of a gets the same constants (the rounded dt differs from
@@ -1234,6 +1251,13 @@ void fold_step_constants(InstHost &h, bool allow_basis) {
 
 int reduce(adg_ctx *c, InstHost &h, int kind, const double *g, double scale, double *host_out,
            const double *field = nullptr) {
+  if (!c->partials) {
+    // allocated at the first reduction (in adg_init that is the check of u0, after the
+    // layout kernel has started reading it): 1024 partial sums and the result
+    CK(cudaMalloc(&c->partials, 1025 * sizeof(double)));
+    c->red_out = c->partials + 1024;
+  }
+  if (!c->pinned) CK(cudaMallocHost(&c->pinned, 8 * sizeof(double)));
   const int nb = adg::reduce_blocks(h.I.K);
   const double *wm = kind == 3 ? h.M : h.w;
   CK(adg::launch_reduce(kind, field ? field : h.I.u, g, h.I.K, h.I.Np, wm, scale, c->partials, nb,
@@ -1347,8 +1371,8 @@ int autotune_fused(adg_ctx *c, InstHost &h) {
   return ADG_OK;
 }
 
-int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double *u0_dev,
-                   int64_t *meta_slot) {
+int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double *u0,
+                   int64_t *meta_slot, bool u0_host = false) {
   h.cfg = *cfg;
   if (cfg->probs) {
     h.probs.assign(cfg->probs, cfg->probs + cfg->L);
@@ -1431,26 +1455,54 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
   I.v1 = h.fields + fnd;
   I.v2 = h.fields + 2 * fnd;
   I.w = nfields == 4 ? h.fields + 3 * fnd : nullptr;
+  // the initial field into node planes: from device memory, from pinned host memory over the
+  // host link (the layout kernel reads it in place), or from pageable host memory through v1
+  const double *src = u0;
+  if (u0_host) {
+    const void *view = nullptr;
+    int r0 = host_view(c, u0, &view);
+    if (r0) return r0;
+    if (view) {
+      src = static_cast<const double *>(view);
+    } else {
+      CK(cudaMemcpyAsync(I.v1, u0, fnd * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+      src = I.v1;
+    }
+  }
   for (int comp = 0; comp < ncomp; ++comp)
-    CK(adg::launch_to_internal(u0_dev + comp * nd, I.u + comp * nd, K, Np, c->stream));
+    CK(adg::launch_to_internal(src + comp * nd, I.u + comp * nd, K, Np, c->stream));
   CK(cudaMemsetAsync(I.v1, 0, (nfields - 1) * fnd * sizeof(double), c->stream));
 
-  // weights and mass matrix for reductions
-  std::vector<double> wd(Np), Md(Np * Np);
+  // weights and mass matrix for reductions, the ring's AT coefficients; uploaded (pageable
+  // sources, which may wait for the stream) and u0 checked for NaN and Inf (a reduction read
+  // on the host) where the setup first needs u0's values on the host: for the time step of
+  // Burgers from max|u0|, else at the end, so that the host work in between overlaps the
+  // layout kernel (which reads a host u0 over the host link)
+  std::vector<double> wd(Np), Md(Np * Np), coef;
   for (int i = 0; i < Np; ++i) wd[i] = (double)h.ops.w[i];
   for (int i = 0; i < Np * Np; ++i) Md[i] = (double)h.ops.M[i];
   CK(cudaMalloc(&h.w, Np * sizeof(double)));
   CK(cudaMalloc(&h.M, Np * Np * sizeof(double)));
-  CK(cudaMemcpyAsync(h.w, wd.data(), Np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaMemcpyAsync(h.M, Md.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
-
+  auto upload_and_check = [&]() -> int {
+    CK(cudaMemcpyAsync(h.w, wd.data(), Np * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    CK(cudaMemcpyAsync(h.M, Md.data(), Np * Np * sizeof(double), cudaMemcpyHostToDevice,
+                       c->stream));
+    if (!coef.empty())
+      CK(cudaMemcpyAsync(h.coef, coef.data(), coef.size() * sizeof(double),
+                         cudaMemcpyHostToDevice, c->stream));
+    for (int comp = 0; comp < ncomp; ++comp) {
+      double nonfinite = 0;
+      const int r1 = reduce(c, h, 2, nullptr, 1.0, &nonfinite, I.u + comp * nd);
+      if (r1) return r1;
+      if (nonfinite != 0) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
+    }
+    return ADG_OK;
+  };
+  const bool dt_from_data = !(cfg->dt > 0) && cfg->pde == ADG_BURGERS;
   int r = ADG_OK;
-  for (int comp = 0; comp < ncomp; ++comp) {
-    double nonfinite = 0;
-    r = reduce(c, h, 2, nullptr, 1.0, &nonfinite, I.u + comp * nd);
+  if (dt_from_data) {
+    r = upload_and_check();
     if (r) return r;
-    if (nonfinite != 0) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
   }
 
   if (cfg->dt > 0) {
@@ -1533,13 +1585,17 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
 
   if (I.async) {
     const int q = h.q_eff, L = cfg->L;
-    std::vector<double> coef((size_t)L * q * q, 0.0);
+    std::vector<double> cf((size_t)L * q * q, 0.0);
     for (int k = 0; k < L; ++k)
       for (int qe = 1; qe <= q; ++qe)
-        for (int i = 0; i < qe; ++i) coef[((size_t)k * q + (qe - 1)) * q + i] = at_coef(k, qe, i);
-    CK(cudaMalloc(&h.coef, coef.size() * sizeof(double)));
-    CK(cudaMemcpy(h.coef, coef.data(), coef.size() * sizeof(double), cudaMemcpyHostToDevice));
+        for (int i = 0; i < qe; ++i) cf[((size_t)k * q + (qe - 1)) * q + i] = at_coef(k, qe, i);
+    CK(cudaMalloc(&h.coef, cf.size() * sizeof(double)));
     I.coef = h.coef;
+    if (dt_from_data)
+      CK(cudaMemcpyAsync(h.coef, cf.data(), cf.size() * sizeof(double), cudaMemcpyHostToDevice,
+                         c->stream));
+    else
+      coef = std::move(cf);   // uploaded with the weights below
     const size_t ring_n = (size_t)I.R * I.ns * I.P * (I.euler ? 3 : 1);
     CK(cudaMalloc(&h.ring, ring_n * sizeof(double2)));
     CK(cudaMemsetAsync(h.ring, 0, ring_n * sizeof(double2), c->stream));
@@ -1555,6 +1611,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     I.table_rows = h.TR;
     h.tbase = -(int64_t)1 << 40;   // force a fill
   }
+  if (!dt_from_data) return upload_and_check();
   return ADG_OK;
 }
 
@@ -1589,6 +1646,22 @@ int sync_state(adg_ctx *c) {
     CK(adg::launch_fixed_to_fp64(I, X, c->n, c->stream));
   }
   c->u_fresh = true;
+  return ADG_OK;
+}
+
+// Instance h's state as element-major FP64 rows in dst (device, pinned or managed memory):
+// converted straight from the int64 state while that is newer than u (after fixed-point
+// steps; the values sync_state would give, without writing u), else copied from u.
+int state_rows(adg_ctx *c, InstHost &h, double *dst) {
+  const Inst &I = h.I;
+  if (fixed_state(c) && c->fx_live != 0 && !c->u_fresh) {
+    const void *X = c->fx_live == 1 ? I.v1 : I.v2;
+    CK(adg::launch_state_rows(I, X, true, c->n, dst, c->stream));
+    return ADG_OK;
+  }
+  const size_t nd = (size_t)I.K * I.Np;
+  for (int comp = 0; comp < (I.euler ? 3 : 1); ++comp)
+    CK(adg::launch_state_rows(I, I.u + comp * nd, false, 0, dst + comp * nd, c->stream));
   return ADG_OK;
 }
 
@@ -1798,13 +1871,6 @@ int build_graph(adg_ctx *c, int kind) {
   return ADG_OK;
 }
 
-int finish_init(adg_ctx *c) {
-  CK(cudaMalloc(&c->partials, 1024 * sizeof(double)));
-  CK(cudaMalloc(&c->red_out, sizeof(double)));
-  CK(cudaMallocHost(&c->pinned, 8 * sizeof(double)));
-  return ADG_OK;
-}
-
 int begin_ctx(adg_ctx *c, void *stream) {
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -1813,7 +1879,7 @@ int begin_ctx(adg_ctx *c, void *stream) {
   CK(cudaGetDevice(&c->device));
   c->stream = (cudaStream_t)stream;
   CK(cudaStreamCreateWithFlags(&c->cap, cudaStreamNonBlocking));
-  return finish_init(c);
+  return ADG_OK;
 }
 
 // Device memory owned for the duration of one adg_grad call.
@@ -2247,19 +2313,19 @@ void adg_destroy(adg_ctx *c) {
   cudaFree(c->work_dev);
   cudaFree(c->fwork_dev);
   cudaFree(c->fflat_dev);
-  cudaFree(c->partials);
-  cudaFree(c->red_out);
+  cudaFree(c->partials);   // red_out lies inside it
   if (c->pinned) cudaFreeHost(c->pinned);
   if (c->cap) cudaStreamDestroy(c->cap);
   delete c;
 }
 
-int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx **out) {
+static int init_one(const adg_config *cfg, const double *u0, bool u0_host, void *stream,
+                    adg_ctx **out) {
   if (!out) return fail(nullptr, ADG_EINVAL, "out is NULL");
   *out = nullptr;
   std::string bad = check_config(cfg);
   if (!bad.empty()) return fail(nullptr, ADG_EINVAL, bad);
-  if (!u0_dev) return fail(nullptr, ADG_EINVAL, "u0_dev is NULL");
+  if (!u0) return fail(nullptr, ADG_EINVAL, u0_host ? "u0_host is NULL" : "u0_dev is NULL");
   adg_ctx *c = new (std::nothrow) adg_ctx();
   if (!c) return fail(nullptr, ADG_ENOMEM, "host allocation failed");
   int r = begin_ctx(c, stream);
@@ -2271,7 +2337,7 @@ int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx 
   }
   if (!r) {
     c->inst.resize(1);
-    r = setup_instance(c, c->inst[0], cfg, u0_dev, c->meta);
+    r = setup_instance(c, c->inst[0], cfg, u0, c->meta, u0_host);
   }
   if (!r) {
     cudaError_t e = cudaStreamSynchronize(c->stream);
@@ -2284,6 +2350,14 @@ int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx 
   }
   *out = c;
   return ADG_OK;
+}
+
+int adg_init(const adg_config *cfg, const double *u0_dev, void *stream, adg_ctx **out) {
+  return init_one(cfg, u0_dev, false, stream, out);
+}
+
+int adg_init_host(const adg_config *cfg, const double *u0_host, void *stream, adg_ctx **out) {
+  return init_one(cfg, u0_host, true, stream, out);
 }
 
 // Batch state at step 0 from the callers' initial fields (after the tuner's timing steps): u
@@ -2651,16 +2725,39 @@ int adg_run(adg_ctx *c, double t_end) {
 
 int adg_get_state(adg_ctx *c, int32_t index, double *u_dev, int64_t *step_out) {
   if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
-  {
-    int r0 = sync_state(c);
-    if (r0) return r0;
-  }
   if (index < 0 || index >= (int)c->inst.size()) return fail(c, ADG_EINVAL, "bad instance index");
   if (!u_dev) return fail(c, ADG_EINVAL, "u_dev is NULL");
+  {
+    int r0 = state_rows(c, c->inst[index], u_dev);
+    if (r0) return r0;
+  }
+  CK(cudaStreamSynchronize(c->stream));
+  if (step_out) *step_out = c->n;
+  return ADG_OK;
+}
+
+int adg_get_state_host(adg_ctx *c, int32_t index, double *u_host, int64_t *step_out) {
+  if (!c) return fail(nullptr, ADG_EINVAL, "ctx is NULL");
+  if (index < 0 || index >= (int)c->inst.size()) return fail(c, ADG_EINVAL, "bad instance index");
+  if (!u_host) return fail(c, ADG_EINVAL, "u_host is NULL");
+  const void *view = nullptr;
+  {
+    int r0 = host_view(c, u_host, &view);
+    if (r0) return r0;
+  }
   InstHost &h = c->inst[index];
-  const size_t nd = (size_t)h.I.K * h.I.Np;
-  for (int comp = 0; comp < (h.I.euler ? 3 : 1); ++comp)
-    CK(adg::launch_to_external(h.I.u + comp * nd, u_dev + comp * nd, h.I.K, h.I.Np, c->stream));
+  const size_t n = (size_t)(h.I.euler ? 3 : 1) * h.I.K * h.I.Np;
+  // pinned memory: the rows kernel writes it over the host link; pageable memory: through
+  // the field that holds no state (v2 while the fixed-point state is in v1, else v1) and one
+  // copy
+  double *dst = view ? static_cast<double *>(const_cast<void *>(view))
+                     : (c->fx_live == 1 ? h.I.v2 : h.I.v1);
+  {
+    int r0 = state_rows(c, h, dst);
+    if (r0) return r0;
+  }
+  if (!view)
+    CK(cudaMemcpyAsync(u_host, dst, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   if (step_out) *step_out = c->n;
   return ADG_OK;

@@ -555,6 +555,66 @@ __global__ void __launch_bounds__(256) k_fixed_to_fp64_basis(const Inst I, const
   }
 }
 
+// The state as element-major FP64 rows (K, NP), for adg_get_state(_host): a block forms the
+// values of 256 consecutive elements, stages them in shared memory and writes them as one
+// contiguous run of 16-byte stores, so that into pinned host memory every warp store fills
+// whole lines of the host link. MODE 0 copies FP64 node planes; 1 and 2 convert an int64
+// state (nodal values, block-basis coordinates) as k_fixed_to_fp64 and k_fixed_to_fp64_basis
+// do, giving the values of the FP64 field the state reads as.
+template <int NP, int MODE>
+__global__ void __launch_bounds__(256) k_state_rows(const Inst I, const void *__restrict__ src,
+                                                    int slot, double *__restrict__ dst) {
+  __shared__ __align__(16) double buf[256 * NP];
+  const int K = I.K;
+  int sigma = 0;
+  bool bad = false;
+  if (MODE != 0) {
+    sigma = I.fx[slot].sigma;
+    bad = I.fx[slot].E >= 2047;
+  }
+  const bool vec = (reinterpret_cast<uintptr_t>(dst) & 15) == 0;
+  for (int e0 = blockIdx.x * 256; e0 < K; e0 += gridDim.x * 256) {
+    const int e = e0 + threadIdx.x;
+    if (e < K) {
+      double v[NP];
+      if (MODE == 0) {
+        const double *u = static_cast<const double *>(src);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) v[j] = u[(size_t)j * K + e];
+      } else {
+        const long long *X = static_cast<const long long *>(src);
+        double w[NP];
+#pragma unroll
+        for (int j = 0; j < NP; ++j) w[j] = fx_to_double(X[(size_t)j * K + e], sigma);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+          double a = w[i];
+          if (MODE == 2) {
+            a = I.Tb[i * NP] * w[0];
+#pragma unroll
+            for (int j = 1; j < NP; ++j) a = fma(I.Tb[i * NP + j], w[j], a);
+          }
+          v[i] = bad ? __longlong_as_double(0x7ff8000000000000ll) : a;
+        }
+      }
+#pragma unroll
+      for (int i = 0; i < NP; ++i) buf[threadIdx.x * NP + i] = v[i];
+    }
+    __syncthreads();
+    const int cnt = min(256, K - e0) * NP;
+    double *out = dst + (size_t)e0 * NP;
+    if (vec) {   // e0 NP doubles from a 16-byte aligned dst: 16-byte aligned
+      const double2 *b2 = reinterpret_cast<const double2 *>(buf);
+      double2 *o2 = reinterpret_cast<double2 *>(out);
+      for (int k = threadIdx.x; k < cnt / 2; k += 256) o2[k] = b2[k];
+      if ((cnt & 1) && threadIdx.x == 0) out[cnt - 1] = buf[cnt - 1];
+    } else {
+      for (int k = threadIdx.x; k < cnt; k += 256) out[k] = buf[k];
+    }
+    __syncthreads();
+  }
+}
+
 template <int NP, int FMT, int S>
 cudaError_t fixed_np_fmt_s(const Inst &I, const void *uin, void *uout, int rel, cudaStream_t s,
                            bool pdl) {
@@ -638,6 +698,29 @@ cudaError_t launch_batch_fixed_uniform(const BatchUniform &bu, const int2 *work_
   if (bu.ept == 4) return batch_uniform_ept<4>(bu, src, dst, fmt, rel, s, pdl);
   if (bu.ept == 2) return batch_uniform_ept<2>(bu, src, dst, fmt, rel, s, pdl);
   return batch_uniform_ept<1>(bu, src, dst, fmt, rel, s, pdl);
+}
+
+cudaError_t launch_state_rows(const Inst &I, const void *src, bool fixed, int64_t step,
+                              double *dst, cudaStream_t s) {
+  const int slot = (int)(step % 3);
+  const size_t want = ((size_t)I.K + 255) / 256;
+  const size_t cap = 8 * (size_t)sm_count();
+  const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+  const int mode = fixed ? (I.basis ? 2 : 1) : 0;
+  auto go = [&](auto np) -> cudaError_t {
+    constexpr int NP = decltype(np)::value;
+    if (mode == 0) k_state_rows<NP, 0><<<grid, 256, 0, s>>>(I, src, slot, dst);
+    else if (mode == 1) k_state_rows<NP, 1><<<grid, 256, 0, s>>>(I, src, slot, dst);
+    else k_state_rows<NP, 2><<<grid, 256, 0, s>>>(I, src, slot, dst);
+    return cudaGetLastError();
+  };
+  switch (I.Np) {
+    case 2: return go(std::integral_constant<int, 2>());
+    case 3: return go(std::integral_constant<int, 3>());
+    case 4: return go(std::integral_constant<int, 4>());
+    case 5: return go(std::integral_constant<int, 5>());
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_fixed_to_fp64(const Inst &I, const long long *X, int64_t step,

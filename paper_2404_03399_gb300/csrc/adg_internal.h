@@ -322,6 +322,11 @@ cudaError_t launch_fill_delays(uint8_t *table, int64_t first, int rows, const De
 // index `step`: all three slots cleared, then E of slot step % 3 = largest biased exponent.
 cudaError_t launch_fixed_reset(const double *f, size_t n, FxSlot *fx, int64_t step,
                                cudaStream_t s);
+// Instance I's field as element-major FP64 rows (K, Np) in dst (device, pinned or managed
+// memory): src is FP64 node planes (fixed false) or the int64 state of step `step` (fixed
+// true, converted as launch_fixed_to_fp64 converts it).
+cudaError_t launch_state_rows(const Inst &I, const void *src, bool fixed, int64_t step,
+                              double *dst, cudaStream_t s);
 // The FP64 field I.u of the int64 fixed-point field X of step `step`, from the scale slot
 // step % 3 of I.fx (NaN everywhere when it marks a NaN or infinity); u = Tb w element by
 // element when I.basis is set.
