@@ -280,15 +280,17 @@ def _window_oracle(cfg, u0_full_fn, e, steps, dt, table_rows, both_sides):
 
 
 @pytest.mark.parametrize("which", ["advection_16m", "advection_16m_staged", "advection_16m_composed",
-                                   "advection_16m_lsrk4", "burgers_1m"])
+                                   "advection_16m_lsrk4", "advection_16m_host", "burgers_1m"])
 def test_full_size_sampled(which):
     # Full-size meshes in the launch configuration the benchmark times (at these sizes steps
     # are launched directly, kernels of a chunk as programmatic dependents of the one before),
     # checked at sampled elements against the oracle run on a window wide enough to contain
-    # each sample's dependence cone.
+    # each sample's dependence cone. "host": the end-to-end path, u0 read from pinned host
+    # memory by adg_init_host and the state written to pinned host memory.
+    host = which.endswith("_host")
     if which.startswith("advection_16m"):
         w = ADVECTION_16M
-        suffix = which[len("advection_16m_"):]
+        suffix = "" if host else which[len("advection_16m_"):]
         kw = {"rk": suffix} if suffix == "lsrk4" else {"variant": suffix or "auto"}
         cfg = adg.Config(pde="advection", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode="at", L=w.L, q=w.q,
                          seed=w.seed, **kw)
@@ -298,10 +300,18 @@ def test_full_size_sampled(which):
         cfg = adg.Config(pde="burgers", K=w.K, p=w.p, P=w.P, cfl=w.cfl, mode="at", L=w.L, q=w.q, seed=w.seed)
         modes, steps, both = HALF_PLUS_SIN, 36, True
     u0 = adg.eval_modes(cfg, modes.amp, modes.kappa, modes.phase, modes.offset)
-    s = adg.Solver(cfg, u0)
-    dt = s.dt
-    s.step(steps)
-    got = s.state().cpu().numpy()
+    if host:
+        u0p = u0.cpu().pin_memory()
+        s = adg.Solver(cfg, u0p)
+        dt = s.dt
+        s.step(steps)
+        out = torch.empty(tuple(u0p.shape), dtype=torch.float64).pin_memory()
+        got = s.state(out=out).numpy()
+    else:
+        s = adg.Solver(cfg, u0)
+        dt = s.dt
+        s.step(steps)
+        got = s.state().cpu().numpy()
     s.close()
     u0h = u0.cpu().numpy()
     del u0
