@@ -683,6 +683,11 @@ def profile_case(name: str) -> dict:
         out = {"case": name, "instances": len(ws), "variant": list(b.variant(0)), "steps": 6}
         b.close()
         return out
+    if name == "e2e_16m":
+        # the end-to-end path twice (host u0 in, 4 steps, state out to host): the layout and
+        # state-rows kernels over the host link
+        ms = [e2e_timed(4)[0] for _ in range(2)]
+        return {"case": name, "K": w["K"], "steps": 4, "ms": ms}
     if name == "burgers_1m":
         b = BURGERS_1M
         cfg = adg.Config(pde="burgers", K=b.K, p=b.p, P=b.P, cfl=0.005, mode="at", L=b.L, q=b.q,
@@ -779,13 +784,14 @@ def main():
                     help="only time that extra workload (the LSRK4 scheme on the large mesh, "
                          "viscous Burgers, Euler) and print its dict (for profiling runs)")
     ap.add_argument("--profile", choices=["fixed_4m", "fixed_16m", "lsrk4_4m", "burgers_1m",
-                                          "batched"],
+                                          "batched", "e2e_16m"],
                     default=None,
                     help="run a few steps of a case for ncu captures and print its dict: "
                          "advection K = 2^22 (the large workload's PE size, delays and AT order) "
                          "with the fixed-point step, the same at the full K = 2^24, the K = 2^22 "
-                         "case with LSRK4, or the Burgers workload (K = 2^20) at Courant number "
-                         "0.005")
+                         "case with LSRK4, the Burgers workload (K = 2^20) at Courant number "
+                         "0.005, the 512-instance batch, or the end-to-end path from host "
+                         "buffers on the large mesh (4 steps, twice)")
     ap.add_argument("--batched-only", type=int, default=0, metavar="STEPS",
                     help="only time the batched workload for STEPS steps and print that dict "
                          "(for profiling runs)")

@@ -368,7 +368,8 @@ struct adg_ctx {
   int device = 0;
   std::vector<InstHost> inst;
   bool batch = false;
-  int64_t *meta = nullptr;      // [ninst][2]
+  int64_t *meta = nullptr;      // [ninst][2], then one int64 holding `scan`
+  int *scan = nullptr;          // the largest biased exponent of the field being loaded
   Inst *insts_dev = nullptr;
   int2 *work_dev = nullptr;
   int nwork = 0;
@@ -1314,8 +1315,16 @@ int ensure_table_back(adg_ctx *c, InstHost &h, int64_t n) {
 
 // Scale slots of the fixed-point composed step for the current state: slot (n mod 3) gets
 // the largest biased exponent of u^n (FP64), the other two are cleared.
-int reset_exponent(adg_ctx *c, InstHost &h) {
+// from_scan: u was just loaded, and the layout kernel's exponent in scan is taken instead
+// of a pass over u.
+int reset_exponent(adg_ctx *c, InstHost &h, bool from_scan = false) {
   if (h.I.fused != 2) return ADG_OK;
+  if (from_scan) {
+    CK(cudaMemsetAsync(h.fx, 0, 3 * sizeof(adg::FxSlot), c->stream));
+    CK(cudaMemcpyAsync(&h.fx[(int)(c->n % 3)].E, c->scan, sizeof(int), cudaMemcpyDeviceToDevice,
+                       c->stream));
+    return ADG_OK;
+  }
   CK(adg::launch_fixed_reset(h.I.u, (size_t)h.I.K * h.I.Np, h.fx, c->n, c->stream));
   return ADG_OK;
 }
@@ -1469,8 +1478,11 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
       src = I.v1;
     }
   }
+  // the layout kernel also raises scan to u0's largest biased exponent (its finiteness and
+  // the fixed-point step's first scale, without another pass over u0)
+  CK(cudaMemsetAsync(c->scan, 0, sizeof(int), c->stream));
   for (int comp = 0; comp < ncomp; ++comp)
-    CK(adg::launch_to_internal(src + comp * nd, I.u + comp * nd, K, Np, c->stream));
+    CK(adg::launch_to_internal(src + comp * nd, I.u + comp * nd, K, Np, c->stream, c->scan));
   CK(cudaMemsetAsync(I.v1, 0, (nfields - 1) * fnd * sizeof(double), c->stream));
 
   // weights and mass matrix for reductions, the ring's AT coefficients; uploaded (pageable
@@ -1490,12 +1502,11 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
     if (!coef.empty())
       CK(cudaMemcpyAsync(h.coef, coef.data(), coef.size() * sizeof(double),
                          cudaMemcpyHostToDevice, c->stream));
-    for (int comp = 0; comp < ncomp; ++comp) {
-      double nonfinite = 0;
-      const int r1 = reduce(c, h, 2, nullptr, 1.0, &nonfinite, I.u + comp * nd);
-      if (r1) return r1;
-      if (nonfinite != 0) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
-    }
+    if (!c->pinned) CK(cudaMallocHost(&c->pinned, 8 * sizeof(double)));
+    int *emax = reinterpret_cast<int *>(c->pinned);
+    CK(cudaMemcpyAsync(emax, c->scan, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+    if (*emax >= 2047) return fail(c, ADG_EINVAL, "u0 holds NaN or Inf");
     return ADG_OK;
   };
   const bool dt_from_data = !(cfg->dt > 0) && cfg->pde == ADG_BURGERS;
@@ -1573,7 +1584,7 @@ int setup_instance(adg_ctx *c, InstHost &h, const adg_config *cfg, const double 
           CK(cudaMalloc(&h.fd, (size_t)2 * I.P * I.ns * sizeof(double)));
           I.fd = h.fd;
         }
-        int r2 = reset_exponent(c, h);
+        int r2 = reset_exponent(c, h, true);
         if (r2) return r2;
       }
       if (!c->batch) {
@@ -2330,10 +2341,12 @@ static int init_one(const adg_config *cfg, const double *u0, bool u0_host, void 
   if (!c) return fail(nullptr, ADG_ENOMEM, "host allocation failed");
   int r = begin_ctx(c, stream);
   if (!r) {
-    if (cudaMalloc(&c->meta, 2 * sizeof(int64_t)) != cudaSuccess)
+    if (cudaMalloc(&c->meta, 3 * sizeof(int64_t)) != cudaSuccess)
       r = fail(c, ADG_ENOMEM, "cudaMalloc(meta)");
-    else if (cudaMemsetAsync(c->meta, 0, 2 * sizeof(int64_t), c->stream) != cudaSuccess)
+    else if (cudaMemsetAsync(c->meta, 0, 3 * sizeof(int64_t), c->stream) != cudaSuccess)
       r = fail(c, ADG_ECUDA, "cudaMemsetAsync(meta)");
+    else
+      c->scan = reinterpret_cast<int *>(c->meta + 2);
   }
   if (!r) {
     c->inst.resize(1);
@@ -2488,10 +2501,12 @@ int adg_batch_init(const adg_config *cfgs, const double *const *u0_devs, int32_t
   c->batch = true;
   int r = begin_ctx(c, stream);
   if (!r) {
-    cudaError_t e = cudaMalloc(&c->meta, 2 * sizeof(int64_t) * n);
+    cudaError_t e = cudaMalloc(&c->meta, sizeof(int64_t) * (2 * n + 1));
     if (e != cudaSuccess) r = fail(c, ADG_ENOMEM, "cudaMalloc(meta)");
-    else if (cudaMemsetAsync(c->meta, 0, 2 * sizeof(int64_t) * n, c->stream) != cudaSuccess)
+    else if (cudaMemsetAsync(c->meta, 0, sizeof(int64_t) * (2 * n + 1), c->stream) != cudaSuccess)
       r = fail(c, ADG_ECUDA, "cudaMemsetAsync(meta)");
+    else
+      c->scan = reinterpret_cast<int *>(c->meta + 2 * n);
   }
   if (!r) {
     c->inst.resize(n);

@@ -336,8 +336,10 @@ cudaError_t launch_fixed_to_fp64(const Inst &I, const long long *X, int64_t step
 // a single fixed-point step).
 cudaError_t launch_batch_copy_back(const Inst *insts_dev, const int2 *work_dev, int nwork,
                                    cudaStream_t s);
+// Row-major (K, Np) values into node planes; src may be pinned host memory (read over the
+// host link). emax, when given, is raised to the largest biased FP64 exponent of the values.
 cudaError_t launch_to_internal(const double *src_rowmajor, double *dst_nodemajor, int K,
-                               int Np, cudaStream_t s);
+                               int Np, cudaStream_t s, int *emax = nullptr);
 cudaError_t launch_to_external(const double *src_nodemajor, double *dst_rowmajor, int K,
                                int Np, cudaStream_t s);
 cudaError_t launch_eval_modes(double *u_rowmajor, int K, int Np, double x0, double dx,

@@ -1205,12 +1205,32 @@ __global__ void k_advance(int64_t *meta, int stride, int ninst, int64_t by) {
   if (i < ninst) meta[(size_t)i * stride] += by;
 }
 
-__global__ void k_to_internal(const double *__restrict__ src, double *__restrict__ dst, int K,
-                              int Np) {
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (size_t)K * Np) return;
-  const size_t e = idx / Np, i = idx % Np;
-  dst[i * K + e] = src[idx];
+// Element-major rows into node planes (dst[i K + e] = src[e Np + i]); with emax, the
+// largest biased FP64 exponent of the values is raised into *emax (one atomic per block;
+// 2047 marks a NaN or an infinity among them), so that loading a field also yields its
+// finiteness and the exponent the fixed-point step scales it by.
+__global__ void __launch_bounds__(256) k_to_internal(const double *__restrict__ src,
+                                                     double *__restrict__ dst, int K, int Np,
+                                                     int *__restrict__ emax) {
+  const size_t n = (size_t)K * Np;
+  int m = 0;
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const double x = src[idx];
+    const size_t e = idx / Np, i = idx % Np;
+    dst[i * K + e] = x;
+    const int be = biased_exponent(x);
+    m = be > m ? be : m;
+  }
+  if (!emax) return;
+  __shared__ int wm[8];
+  m = __reduce_max_sync(0xffffffffu, m);
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < (int)(blockDim.x >> 5); ++w) m = wm[w] > m ? wm[w] : m;
+    raise_slot(emax, m);
+  }
 }
 
 __global__ void k_to_external(const double *__restrict__ src, double *__restrict__ dst, int K,
@@ -1563,9 +1583,13 @@ cudaError_t launch_advance(int64_t *meta, int stride, int ninst, int64_t by, cud
   return cudaGetLastError();
 }
 
-cudaError_t launch_to_internal(const double *src, double *dst, int K, int Np, cudaStream_t s) {
+cudaError_t launch_to_internal(const double *src, double *dst, int K, int Np, cudaStream_t s,
+                               int *emax) {
   const size_t n = (size_t)K * Np;
-  k_to_internal<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(src, dst, K, Np);
+  const size_t want = (n + 255) / 256;
+  const size_t cap = 16 * (size_t)sm_count();
+  const unsigned grid = (unsigned)(want < cap ? (want ? want : 1) : cap);
+  k_to_internal<<<grid, 256, 0, s>>>(src, dst, K, Np, emax);
   return cudaGetLastError();
 }
 
