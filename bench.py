@@ -224,14 +224,16 @@ def device_timed(mode: str, steps: int, warmup: int, dist_barrier, sample_clocks
     s = adg.Solver(cfg, u0)
     del u0
     stream = torch.cuda.current_stream()
+    # the sampler starts before the warm-up steps (and runs until after the timed ones), so
+    # that its start-up and the pause for its first sample fall outside the timed region
+    clocks = ClockSampler(dev) if sample_clocks else None
+    if clocks:
+        clocks.__enter__()
     s.step(warmup)
     torch.cuda.synchronize()
     dist_barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    clocks = ClockSampler(dev) if sample_clocks else None
-    if clocks:
-        clocks.__enter__()
     ev0.record(stream)
     s.step(steps)
     ev1.record(stream)
