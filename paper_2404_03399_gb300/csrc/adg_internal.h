@@ -263,6 +263,26 @@ cudaError_t launch_maybe_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cu
   cfg.numAttrs = pdl ? 1 : 0;
   return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
 }
+// The same with a scheduling priority for the launch's blocks (lower numbers first, within
+// cudaDeviceGetStreamPriorityRange): blocks of a short kernel on the critical path get SM
+// resources ahead of queued blocks of kernels on other streams.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl_priority(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t s,
+                                bool pdl, int priority, Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = s;
+  cudaLaunchAttribute at[2];
+  at[0].id = cudaLaunchAttributePriority;
+  at[0].val.priority = priority;
+  at[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[1].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 2 : 1;
+  return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 // What the batched fixed-point step reads of an instance when the coefficients are shared
 // (below): its fields u, v1, v2, step counter, scale slots, K and Np.
 struct BatchLite {

@@ -1561,12 +1561,22 @@ cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev,
     // a programmatic dependent of the step kernel: its input, delay and ring loads overlap it
     const dim3 g((unsigned)((nfwork + 63) / 64)), b(64);
     const bool fin = (fmt & kFmtInFixed) != 0;
+    // the fix-up is the short, latency-bound link between a part's steps: its blocks take
+    // SM resources ahead of the other parts' queued step blocks
+    static int prio = [] {
+      int least = 0, greatest = 0;
+      if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
+        (void)cudaGetLastError();
+        return 0;
+      }
+      return greatest;
+    }();
     if (fmt & kFmtOutFixed)
-      e = launch_maybe_pdl(k_batch_fixup<true>, g, b, s, true, insts_dev, fwork_dev, nfwork, src,
-                           dst, fin, rel);
+      e = launch_pdl_priority(k_batch_fixup<true>, g, b, s, true, prio, insts_dev, fwork_dev,
+                              nfwork, src, dst, fin, rel);
     else
-      e = launch_maybe_pdl(k_batch_fixup<false>, g, b, s, true, insts_dev, fwork_dev, nfwork, src,
-                           dst, fin, rel);
+      e = launch_pdl_priority(k_batch_fixup<false>, g, b, s, true, prio, insts_dev, fwork_dev,
+                              nfwork, src, dst, fin, rel);
     if (e != cudaSuccess) return e;
   }
   return cudaGetLastError();
