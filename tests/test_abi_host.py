@@ -50,13 +50,21 @@ def test_invalid_configs_rejected(lib, bad):
     ctx = C.c_void_p()
     code = lib.adg_init(C.byref(c), C.c_void_p(8), None, C.byref(ctx))
     assert code == _abi.ADG_EINVAL and not ctx.value
+    host = np.zeros((cfg.K, cfg.p + 1))
+    code = lib.adg_init_host(C.byref(c), host.ctypes.data, None, C.byref(ctx))
+    assert code == _abi.ADG_EINVAL and not ctx.value
 
 
 def test_null_arguments(lib):
     ctx = C.c_void_p()
     assert lib.adg_init(None, None, None, C.byref(ctx)) == _abi.ADG_EINVAL
+    assert lib.adg_init_host(None, None, None, C.byref(ctx)) == _abi.ADG_EINVAL
+    c, keep = adg.Config(K=16, p=2, P=4).to_c()
+    assert lib.adg_init_host(C.byref(c), None, None, C.byref(ctx)) == _abi.ADG_EINVAL
+    assert b"u0_host" in lib.adg_last_error(None)
     assert lib.adg_step(None, 1) == _abi.ADG_EINVAL
     assert lib.adg_get_state(None, 0, None, None) == _abi.ADG_EINVAL
+    assert lib.adg_get_state_host(None, 0, None, None) == _abi.ADG_EINVAL
     assert lib.adg_get_variant(None, 0, None, None) == _abi.ADG_EINVAL
     assert lib.adg_comm_stats(None, 0, None, None, None) == _abi.ADG_EINVAL
     lib.adg_destroy(None)
@@ -129,3 +137,7 @@ def test_init_without_gpu_reports_cuda_error(lib):
     ctx = C.c_void_p()
     assert lib.adg_init(C.byref(c), C.c_void_p(8), None, C.byref(ctx)) == _abi.ADG_ECUDA
     assert b"CUDA" in lib.adg_last_error(None) or b"device" in lib.adg_last_error(None)
+    # from host buffers too: no CPU fallback
+    host = np.zeros((16, 3))
+    assert lib.adg_init_host(C.byref(c), host.ctypes.data, None, C.byref(ctx)) == _abi.ADG_ECUDA
+    assert not ctx.value
