@@ -18,10 +18,12 @@ constexpr int kTile = 256;      // elements (threads) per block
 // per device and cached; 1 if the query fails).
 int sm_count();
 
-// Block size of the one-thread-per-element stage kernels: 256, or 128 when the mesh gives
-// fewer than two 256-blocks per SM (small meshes are latency-bound, and smaller blocks spread
-// them over every SM).
-inline int stage_block(int K) { return K < 2 * sm_count() * 256 ? 128 : 256; }
+// Block size of the stage kernels: 256, or one warp when the mesh gives fewer than two
+// 256-blocks per SM. Small meshes are latency-bound and make a single wave, whose length is
+// set by the SMs holding the most warps: one-warp blocks spread them evenly (K = 65536, 2185
+// warps of the halo-lane kernels: forward 78.1 -> 77.2 ms and gradient 209 -> 205 ms over
+// 2000 steps, against 128-thread blocks; 64-thread blocks gave no gain).
+inline int stage_block(int K) { return K < 2 * sm_count() * 256 ? 32 : 256; }
 
 // Folded constants of one SSP-RK3 stage in Shu-Osher form, v_out = alpha u + beta (v + dt L(v)),
 // with the strong form of Eq. DGscheme
