@@ -1681,7 +1681,9 @@ int launch_fused_steps(adg_ctx *c, int nsteps, int kind);
 
 // Steps are launched directly (not through CUDA graphs) from 2^20 DOF in all: a step there
 // takes hundreds of microseconds, and programmatic launches overlapped better outside a graph
-// (0.2315 -> 0.2276 ms per fixed-point step on the 2^26-DOF mesh).
+// (0.2315 -> 0.2276 ms per fixed-point step on the 2^26-DOF mesh). Below, the host's launch
+// rate is the bound: 2000 staged Burgers steps on 262144 DOF took 99.6 ms launched directly
+// and 77.1 ms as graphs.
 bool direct_launches(const adg_ctx *c) {
   int64_t dof = 0;
   for (const auto &h : c->inst) dof += (int64_t)h.I.K * h.I.Np;
