@@ -400,7 +400,8 @@ struct adg_ctx {
   cudaGraphExec_t gexec[4] = {};   // one graph of G steps per chunk kind (kChunk*)
   int fx_live = 0;                 // fixed-point state: 0 in u (FP64), 1 in v1, 2 in v2 (int64)
   bool u_fresh = true;             // u holds the state of step n (FP64)
-  int G = 32;
+  int G = 32;                      // steps per graph (128 measured slower: 78.5 against
+                                   // 77.2 ms for 2000 steps of the adjoint workload)
   int64_t n = 0;
 };
 
