@@ -1562,7 +1562,8 @@ cudaError_t launch_batch_fused_step(const Inst *insts_dev, const int2 *work_dev,
     const dim3 g((unsigned)((nfwork + 63) / 64)), b(64);
     const bool fin = (fmt & kFmtInFixed) != 0;
     // the fix-up is the short, latency-bound link between a part's steps: its blocks take
-    // SM resources ahead of the other parts' queued step blocks
+    // SM resources ahead of the other parts' queued step blocks (64 threads a block: 32
+    // measured 0.3329 against 0.3324 ms per batched step)
     static int prio = [] {
       int least = 0, greatest = 0;
       if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) {
